@@ -1,0 +1,200 @@
+"""Seeded synthetic models and scenes shaped like the paper's workloads.
+
+This module holds input generation only: it draws point positions, frame
+indices and descriptors and implants jittered model copies into clutter. It
+contains none of the matching arithmetic, so both the CPU oracle (tests) and
+the CUDA path (library, benchmark) draw their inputs from here.
+
+Shapes follow the paper's setting (Sec. 4): space-time interest points with
+162-d HoG/HoF-like descriptors, models of roughly one second (t in [0, 30)),
+scenes with many points per frame. The real KTH features are not available,
+so every input is synthetic: cluster-structured Gaussian descriptors, uniform
+positions, Poisson or fixed point counts per frame, and implanted model
+instances (xy jitter, frame jitter, descriptor noise).
+"""
+from __future__ import annotations
+
+import dataclasses
+from typing import List, Optional, Sequence, Tuple
+
+import numpy as np
+
+
+@dataclasses.dataclass
+class PointSet:
+    """A model or scene: positions (n,2) f32, frame index (n,) i32, descriptors (n,F) f32."""
+
+    xy: np.ndarray
+    t: np.ndarray
+    f: np.ndarray
+    centres: Optional[np.ndarray] = None  # descriptor cluster centres (models only)
+
+    @property
+    def n(self) -> int:
+        return int(self.t.shape[0])
+
+    @property
+    def F(self) -> int:
+        return int(self.f.shape[1])
+
+
+@dataclasses.dataclass
+class Implant:
+    model: int      # index of the implanted model
+    offset: int     # scene frame offset o of the implant
+    idx: np.ndarray  # scene indices (caller order) of the implanted points, model order
+
+
+@dataclasses.dataclass
+class Scene(PointSet):
+    n_frames: int = 0
+    implants: List[Implant] = dataclasses.field(default_factory=list)
+
+
+def make_model(rng: np.random.Generator, M: int, F: int = 162, frame: Tuple[float, float] = (160.0, 120.0),
+               t_span: int = 30, T: int = 10, n_clusters: int = 8, noise: float = 0.3) -> PointSet:
+    """One model: M points sorted by frame, descriptors from n_clusters N(0,1) centres + N(0,noise).
+
+    Frames are resampled until every t_i - t_{i-2} < T, so that a noise-free
+    implant of the model is feasible under the temporal closeness rule.
+    """
+    centres = rng.standard_normal((n_clusters, F))
+    while True:
+        t = np.sort(rng.integers(0, t_span, size=M))
+        if M < 3 or np.all(t[2:] - t[:-2] < T):
+            break
+    xy = rng.uniform((0.0, 0.0), frame, size=(M, 2))
+    lab = rng.integers(0, n_clusters, size=M)
+    f = centres[lab] + noise * rng.standard_normal((M, F))
+    return PointSet(xy.astype(np.float32), t.astype(np.int32), f.astype(np.float32), centres)
+
+
+def make_scene(rng: np.random.Generator, n_frames: int, frame: Tuple[float, float],
+               per_frame, centre_pool: np.ndarray, models: Sequence[PointSet],
+               implants: Sequence[Tuple[int, int]], translate: bool = True, noise: float = 0.3,
+               xy_jitter: float = 2.0, t_jitter: float = 1.0, f_noise: float = 0.1,
+               F_pad: Optional[int] = None) -> Scene:
+    """A scene of n_frames frames: uniform clutter plus jittered copies of models.
+
+    per_frame: an int (fixed count) or ("poisson", lam).
+    centre_pool: (C,F) descriptor centres; clutter picks one at random + N(0,noise).
+    implants: (model index, offset o) pairs; a copy of model m is placed at
+        frames t + o + rint(N(0,t_jitter)) clipped to the scene, positions
+        xy + N(0,xy_jitter) (+ a random in-frame translation if translate),
+        descriptors f + N(0,f_noise).
+    Points are emitted clutter first (frame order), implants appended after, so
+    the scene is NOT time sorted: the library's stable sort is exercised.
+    F_pad: zero-pad descriptors to this width (zeros leave distances unchanged).
+    """
+    F = centre_pool.shape[1]
+    if isinstance(per_frame, tuple):
+        counts = rng.poisson(per_frame[1], size=n_frames)
+    else:
+        counts = np.full(n_frames, int(per_frame))
+    n_clutter = int(counts.sum())
+    t = np.repeat(np.arange(n_frames, dtype=np.int64), counts)
+    xy = rng.uniform((0.0, 0.0), frame, size=(n_clutter, 2))
+    ci = rng.integers(0, centre_pool.shape[0], size=n_clutter)
+    f = centre_pool[ci] + noise * rng.standard_normal((n_clutter, F))
+    xs, ts, fs = [xy], [t], [f]
+    recs = []
+    base = n_clutter
+    for (m, o) in implants:
+        mod = models[m]
+        mxy = mod.xy.astype(np.float64) + xy_jitter * rng.standard_normal((mod.n, 2))
+        if translate:
+            lo = -mxy.min(axis=0)
+            hi = np.asarray(frame) - mxy.max(axis=0)
+            shift = rng.uniform(np.minimum(lo, hi), np.maximum(lo, hi))
+            mxy = mxy + shift
+        mt = mod.t.astype(np.int64) + o + np.rint(t_jitter * rng.standard_normal(mod.n)).astype(np.int64)
+        mt = np.clip(mt, 0, n_frames - 1)
+        mf = mod.f.astype(np.float64) + f_noise * rng.standard_normal((mod.n, F))
+        xs.append(mxy); ts.append(mt); fs.append(mf)
+        recs.append(Implant(m, int(o), np.arange(base, base + mod.n)))
+        base += mod.n
+    xy = np.concatenate(xs).astype(np.float32)
+    t = np.concatenate(ts).astype(np.int32)
+    f = np.concatenate(fs).astype(np.float32)
+    if F_pad is not None and F_pad > F:
+        f = np.concatenate([f, np.zeros((f.shape[0], F_pad - F), np.float32)], axis=1)
+    return Scene(xy, t, f, None, n_frames, recs)
+
+
+def pad_model(m: PointSet, F_pad: int) -> PointSet:
+    if F_pad <= m.F:
+        return m
+    f = np.concatenate([m.f, np.zeros((m.n, F_pad - m.F), np.float32)], axis=1)
+    return PointSet(m.xy, m.t, f, m.centres)
+
+
+@dataclasses.dataclass
+class Workload:
+    name: str
+    models: List[PointSet]
+    scenes: List[Scene]
+    K: int
+    window: int
+    lambda1: float = 0.6
+    lambda2: float = 0.2
+    lambda3: float = 5.0
+    T: int = 10
+
+    @property
+    def total_frames(self) -> int:
+        return int(sum(s.n_frames for s in self.scenes))
+
+    def n_offsets(self, m: int, s: int) -> int:
+        mod, sc = self.models[m], self.scenes[s]
+        return max(0, sc.n_frames - int(mod.t.max() - mod.t.min()))
+
+
+def single_match(seed: int = 0) -> Workload:
+    """One M=16 model vs a 60-frame, 10 points/frame scene with one implant at o=20; K=32, w=2."""
+    rng = np.random.default_rng(seed)
+    mod = make_model(rng, 16)
+    sc = make_scene(rng, 60, (160.0, 120.0), 10, mod.centres, [mod], [(0, 20)], translate=False)
+    return Workload("single_match_M16_F60_K32", [mod], [sc], K=32, window=2)
+
+
+def batched_exact(seed: int = 1, n_models: int = 10, n_scenes: int = 8, M_range=(16, 64),
+                  frames_range=(300, 1500), lam: float = 30.0, implants_per_scene: int = 3) -> Workload:
+    """10 models (M in 16..64) vs 8 scenes of 300-1500 frames, Poisson(30)/frame at 320x240; K=64, w=3."""
+    rng = np.random.default_rng(seed)
+    models = [make_model(rng, int(rng.integers(M_range[0], M_range[1] + 1))) for _ in range(n_models)]
+    pool = np.concatenate([m.centres for m in models])
+    scenes = []
+    for _ in range(n_scenes):
+        nf = int(rng.integers(frames_range[0], frames_range[1] + 1))
+        imp = []
+        for _ in range(implants_per_scene):
+            m = int(rng.integers(0, n_models))
+            span = int(models[m].t.max())
+            imp.append((m, int(rng.integers(0, max(1, nf - span)))))
+        scenes.append(make_scene(rng, nf, (320.0, 240.0), ("poisson", lam), pool, models, imp))
+    return Workload(f"batched_exact_{n_models}x{n_scenes}_K64", models, scenes, K=64, window=3)
+
+
+def precision_long(seed: int = 2, n_models: int = 50, n_frames: int = 30000, M_range=(32, 128),
+                   lam: float = 60.0, F_pad: int = 176, n_implants: int = 50) -> Workload:
+    """50 models (M in 32..128) vs one 30,000-frame 640x480 Poisson(60)/frame scene, F padded to 176; K=64, w=3."""
+    rng = np.random.default_rng(seed)
+    models = [make_model(rng, int(rng.integers(M_range[0], M_range[1] + 1))) for _ in range(n_models)]
+    pool = np.concatenate([m.centres for m in models])
+    imp = []
+    for k in range(n_implants):
+        m = k % n_models
+        imp.append((m, int(rng.integers(0, n_frames - 30))))
+    sc = make_scene(rng, n_frames, (640.0, 480.0), ("poisson", lam), pool, models, imp, F_pad=F_pad)
+    models = [pad_model(m, F_pad) for m in models]
+    return Workload(f"precision_long_{n_models}x1x{n_frames}_K64", models, [sc], K=64, window=3)
+
+
+def tiny_case(seed: int, M: int = 5, n_frames: int = 12, per_frame: int = 3, K: int = 5, window: int = 1,
+              F: int = 8, T: int = 10, frame=(20.0, 20.0)) -> Workload:
+    """Very small random instance for brute-force enumeration."""
+    rng = np.random.default_rng(seed)
+    mod = make_model(rng, M, F=F, frame=frame, t_span=min(8, n_frames), T=T, n_clusters=3)
+    sc = make_scene(rng, n_frames, frame, per_frame, mod.centres, [mod],
+                    [(0, int(rng.integers(0, max(1, n_frames - int(mod.t.max())))))], translate=False)
+    return Workload(f"tiny_{seed}", [mod], [sc], K=K, window=window, T=T)
