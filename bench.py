@@ -1,0 +1,324 @@
+"""Benchmark: scene frames per second matched (every model x every scene x every offset).
+
+One step = hgm_match_batch over the whole workload (unary table, candidate
+selection, recursion, backtrack) with models and scenes resident in HBM and
+device outputs. Default workload: 10 models (M 16..64) x 8 scenes of
+300..1500 frames, Poisson(30) points/frame, K = 64, w = 3 (seeded synthetic).
+
+Prints ONE JSON line (rank 0). See the design doc for the roofline definitions.
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Under torchrun each rank matches its own copy of the workload (seed + rank,
+weak scaling, no collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "scene frames/sec matched (all models × offsets), plain exact vs pruned+BF16"
+OPS_PER_TRIPLE = 12          # FP32 lane ops per feasible triple after hoisting
+SM_COUNT_FALLBACK = 152
+FP32_LANES_PER_SM = 128
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def workload(name: str, seed_shift: int):
+    from paper_1505_00581_gb300 import synth
+    if name == "batched_exact":
+        return synth.batched_exact(seed=1 + 1000 * seed_shift)
+    if name == "single_match":
+        return synth.single_match(seed=0 + 1000 * seed_shift)
+    raise SystemExit(f"unknown workload {name}")
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    def __init__(self, gpu_index: int):
+        self.path = tempfile.mktemp(suffix=".csv", prefix="clocks_")
+        self.proc = None
+        self.gpu = gpu_index
+
+    def __enter__(self):
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu),
+                 "--query-gpu=index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
+                 "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.fh, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        try:
+            for line in open(self.path):
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    mx.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, parts[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(nm)
+        except OSError:
+            pass
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def oracle_sample(wl, n_units: int, seed: int, threads: int):
+    """Times the FP64 oracle on a seeded sample of units; returns (seconds, units)."""
+    from concurrent.futures import ThreadPoolExecutor
+
+    from oracle import Oracle
+    rng = np.random.default_rng(seed)
+    pairs = [(m, s) for m in range(len(wl.models)) for s in range(len(wl.scenes))]
+    weights = np.array([wl.n_offsets(m, s) for m, s in pairs], dtype=np.float64)
+    picks = rng.choice(len(pairs), size=n_units, p=weights / weights.sum())
+    orcs, jobs = {}, []
+    for q in picks:
+        m, s = pairs[q]
+        if (m, s) not in orcs:
+            orcs[(m, s)] = Oracle.from_workload(wl, m, s)
+        orc = orcs[(m, s)]
+        jobs.append((orc, orc.first_offset + int(rng.integers(orc.n_offsets))))
+    t0 = time.perf_counter()
+    with ThreadPoolExecutor(max_workers=threads) as ex:
+        list(ex.map(lambda j: j[0].match(j[1]), jobs))
+    return time.perf_counter() - t0, n_units
+
+
+def total_units(wl):
+    return sum(wl.n_offsets(m, s) for m in range(len(wl.models)) for s in range(len(wl.scenes)))
+
+
+def run_reference(args):
+    """--impl reference: the FP64 oracle (as it stands) on the host cores, bounded samples."""
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return
+    wl = workload(args.workload, 0)
+    threads = os.cpu_count() or 1
+    units_total = total_units(wl)
+    per_step = max(threads, args.ref_units)
+    for w in range(args.warmup):
+        oracle_sample(wl, threads, 7 + w, threads)
+    times = []
+    for k in range(args.steps):
+        t, n = oracle_sample(wl, per_step, 100 + k, threads)
+        times.append(t / n * units_total)   # projected seconds for the whole workload
+    sec = float(np.mean(times))
+    value = wl.total_frames / sec
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "frames/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": wl.name, "models": len(wl.models), "scenes": len(wl.scenes), "K": wl.K,
+                       "window": wl.window, "frames": wl.total_frames, "units": units_total},
+            "cpu_baseline": {"value": value, "unit": "frames/s", "cores": threads, "kind": "oracle",
+                             "sample": f"{per_step} seeded units per step of {units_total}, projected to all"},
+            "e2e": {"value": value, "unit": "frames/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="batched_exact")
+    ap.add_argument("--ref-units", type=int, default=48)
+    ap.add_argument("--cpu-units", type=int, default=48)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    world, rank, local = dist_env()
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU (no CPU fallback)")
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    from paper_1505_00581_gb300 import build as hgm_build
+    if rank == 0:
+        hgm_build.build()
+    if dist:
+        dist.barrier()
+    from paper_1505_00581_gb300 import hgm
+    hgm.load()
+
+    wl = workload(args.workload, rank)
+    dev = torch.device("cuda", local)
+    p = hgm.default_params(K=wl.K, window=wl.window, T=wl.T, lambda1=wl.lambda1, lambda2=wl.lambda2,
+                           lambda3=wl.lambda3)
+    models = [hgm.Model(*(torch.from_numpy(a).to(dev) for a in (m.xy, m.t, m.f))) for m in wl.models]
+    scenes = [hgm.Scene(*(torch.from_numpy(a).to(dev) for a in (s.xy, s.t, s.f)), s.n_frames) for s in wl.scenes]
+    first, es, as_ = hgm.batch_layout(models, scenes, p)
+    n_out, n_assign = int(es[-1]), int(as_[-1])
+    energy = torch.empty(n_out, dtype=torch.float32, device=dev)
+    assign = torch.empty(n_assign, dtype=torch.int32, device=dev)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)   # > L2 (129 MB): evicts between steps
+
+    # algorithmic work: feasible triples of the whole workload (outside the timed region)
+    triples = 0
+    for mi, m in enumerate(models):
+        for si, s in enumerate(scenes):
+            q = mi * len(scenes) + si
+            n = int(es[q + 1] - es[q])
+            if n:
+                buf = torch.empty(n, dtype=torch.int64, device=dev)
+                hgm.count_triples(m, s, p, int(first[q]), n, buf)
+                triples += int(buf.sum().item())
+
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        hgm.match_batch(models, scenes, p, energy, assign)
+    torch.cuda.synchronize()
+    hgm.profile_reset()
+    hgm.profile_enable(True)
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with Clocks(local) as clk:
+        for k in range(args.steps):
+            flush.zero_()
+            starts[k].record(stream)
+            hgm.match_batch(models, scenes, p, energy, assign)
+            ends[k].record(stream)
+        torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    hgm.profile_enable(False)
+    ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends))
+    prof = hgm.profile_read()
+    t_local = torch.tensor([ms], dtype=torch.float64, device=dev)
+    if dist:
+        dist.all_reduce(t_local, op=dist.ReduceOp.MAX)
+    ms_max = float(t_local.item())
+    ms_step = ms_max / args.steps
+    frames_all = wl.total_frames * world
+    value = frames_all / (ms_step / 1e3)
+    fin = torch.isfinite(energy).sum().item()
+
+    # end to end: host arrays -> handles -> batch -> host outputs, copies inside the timed region
+    e2e = None
+    if True:
+        host_e = np.zeros(n_out, np.float32)
+        host_a = np.zeros(n_assign, np.int32)
+        h2d = sum(a.nbytes for m in wl.models for a in (m.xy, m.t, m.f)) + \
+            sum(a.nbytes for s in wl.scenes for a in (s.xy, s.t, s.f))
+        d2h = host_e.nbytes + host_a.nbytes
+        e2e_times = []
+        for k in range(max(1, min(args.steps, 3)) + 1):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            ms_ = [hgm.Model(m.xy, m.t, m.f) for m in wl.models]
+            ss_ = [hgm.Scene(s.xy, s.t, s.f, s.n_frames) for s in wl.scenes]
+            hgm.match_batch(ms_, ss_, p, host_e, host_a)
+            t1 = time.perf_counter()
+            for h in ms_ + ss_:
+                h.close()
+            if k > 0:
+                e2e_times.append(t1 - t0)
+        e2e_sec = float(np.mean(e2e_times))
+        e2e = {"value": frames_all / e2e_sec if world == 1 else wl.total_frames * world / e2e_sec,
+               "unit": "frames/s", "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
+
+    pk, pk_kind = peaks()
+    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count or SM_COUNT_FALLBACK
+    clk_sum = clk.summary()
+    rec_ms, rec_n = prof["recurse"]
+    rec_avg_ms = rec_ms / max(rec_n, 1)
+    # per launch the recursion handles the whole workload (one chunk) -> triples per launch
+    chunks_per_step = max(1, rec_n // args.steps)
+    triples_per_launch = triples / chunks_per_step
+    achieved = triples_per_launch * OPS_PER_TRIPLE / (rec_avg_ms / 1e3) / 1e12
+    peak_ops = sm_count * FP32_LANES_PER_SM * float(pk.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
+    roofline = {"bound": "alu", "kernel": "recurse_kernel", "achieved": achieved, "peak": peak_ops,
+                "unit": "Tops/s (FP32 lane ops)", "frac": achieved / peak_ops, "traffic": None,
+                "peak_source": f"{sm_count} SMs x {FP32_LANES_PER_SM} FP32 lanes x sm_max_mhz of "
+                               f"MEASURED_PEAKS.json ({pk_kind})",
+                "triples_per_launch": triples_per_launch, "ops_per_triple": OPS_PER_TRIPLE,
+                "avg_launch_ms": rec_avg_ms,
+                "kernel_ms_per_step": {k: v[0] / args.steps for k, v in prof.items()}}
+    launches = sum(v[1] for v in prof.values())
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        threads = os.cpu_count() or 1
+        n_s = max(threads, args.cpu_units)
+        t, n = oracle_sample(wl, n_s, 11, threads)
+        sec_all = t / n * total_units(wl)
+        cpu = {"value": wl.total_frames / sec_all, "unit": "frames/s", "cores": threads, "kind": "oracle",
+               "sample": f"{n} seeded units of {total_units(wl)} ({t:.1f} s on {threads} threads), "
+                         f"projected to the whole workload"}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "frames/s", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": wl.name, "models": len(wl.models), "scenes": len(wl.scenes), "K": wl.K,
+                           "window": wl.window, "T": wl.T, "frames_per_rank": wl.total_frames,
+                           "units_per_rank": total_units(wl), "feasible_triples_per_rank": triples,
+                           "form": "plain exact FP32", "l2": "flushed (512 MiB write) before every step",
+                           "parallelism": f"replicas x{world}"},
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+                "clocks": clk_sum, "finite_offsets": int(fin)}
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

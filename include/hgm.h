@@ -1,0 +1,191 @@
+/*
+ * hgm.h -- C ABI of libhgm: exact chain hypergraph matching of space-time
+ * interest points on one GB300 GPU (sm_103a).
+ *
+ * The library solves, for every scene time offset, the matching problem of
+ * Lombardi, Wolf, Celiktutan and Sankur, "Activity recognition from videos
+ * with parallel hypergraph matching on GPUs" (arXiv 1505.00581): the model
+ * points, ordered by frame, form a second-order chain hypergraph (Sec. 2.1);
+ * each is assigned a scene point so as to minimise
+ *     E(z) = sum_i U(z_i) + sum_{i>=3} D(z_i, z_{i-1}, z_{i-2})          (Eq. 9)
+ * with U the weighted descriptor distance (Eq. 2, lambda1 absorbed) and D the
+ * weighted temporal + angle distortion of the triangle (Eqs. 3-6, lambda2 and
+ * lambda3 absorbed), under causality and temporal closeness (Eqs. 7-8). The
+ * minimum is exact: the backward min-sum recursion of Eq. 10 with its
+ * initialisation (Eq. 11), argmin tables and backtracking (Eq. 12) and the
+ * initial pair search (Eq. 13).
+ *
+ * Problem statement per call (Sec. 2): matching is done one (model, scene)
+ * pair at a time; hgm_match_batch runs many pairs in one pass. For a pair,
+ * the offsets are o = -t_1 .. F_s-1-t_M (the shifted model lies inside the
+ * scene; t_1/t_M are the model's first/last frames, F_s the scene's frame
+ * count). At offset o, model point i may only take one of its candidates
+ * C_i(o): the scene points whose frame lies in [t_i+o-w, t_i+o+w]; when more
+ * than K qualify, the K with the smallest U (ties: lower scene index in the
+ * stably time-sorted scene), listed by ascending scene index.
+ *
+ * Conventions shared by every entry point
+ *  - Every function returns an hgm_status; nothing aborts. On failure
+ *    hgm_last_error() returns a message (thread-local, valid until the next
+ *    call on the same thread).
+ *  - "stream" is a cudaStream_t passed as void*; NULL is the legacy default
+ *    stream. Device work is ordered on that stream.
+ *  - A pointer documented "host or device" may be either; the library asks
+ *    the CUDA driver which. Host outputs make the call synchronous on the
+ *    stream; device outputs leave it asynchronous.
+ *  - Point arrays are row-major: xy is n x 2 float (x, y), t is n int32 frame
+ *    indices, desc is n x F float. The library copies them; the caller keeps
+ *    ownership of its buffers. Handles own device memory until hgm_destroy.
+ *  - Indices returned to the caller are the caller's own point indices
+ *    (positions in the arrays given to hgm_create_*), not sorted ones,
+ *    except where an entry point says "sorted".
+ *  - An offset at which some C_i(o) is empty or no chain is feasible is not
+ *    an error: its energy is +inf and its assignment row is all -1.
+ */
+#ifndef HGM_H
+#define HGM_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define HGM_API __attribute__((visibility("default")))
+#else
+#define HGM_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct hgm_model hgm_model;
+typedef struct hgm_scene hgm_scene;
+
+typedef enum {
+    HGM_OK = 0,
+    HGM_EINVAL = 1,         /* invalid argument (shape, range, NULL, non-finite data) */
+    HGM_ENOMEM = 2,         /* device or host allocation failed */
+    HGM_ECUDA = 3,          /* a CUDA runtime call failed (message has the CUDA error) */
+    HGM_ETIMEOUT = 4,       /* a bounded device-side wait gave up */
+    HGM_EUNSUPPORTED = 5    /* valid request outside what this build implements (e.g. K > 64) */
+} hgm_status;
+
+/* Matching parameters. Defaults (hgm_default_params) are the paper's weights
+ * lambda1 = 0.6, lambda2 = 0.2, lambda3 = 5 and T = 10 frames (Sec. 4), with
+ * window w = 3 and cap K = 64. */
+typedef struct {
+    float lambda1;      /* weight of U (Eq. 1) */
+    float lambda2;      /* weight of D (Eq. 1) */
+    float lambda3;      /* weight of D^g inside D (Eq. 3) */
+    int32_t T;          /* temporal closeness limit in frames (Eq. 8): a triple (a,b,c) needs
+                           t'(a) - t'(c) < T; T <= 0 means no limit */
+    int32_t window;     /* candidate window half-width w in frames, >= 0 */
+    int32_t K;          /* candidate cap, 1..64 (1..255 is valid; > 64 is HGM_EUNSUPPORTED) */
+    int32_t precision;  /* 0 = FP32 exact path (the only one in this build) */
+    int32_t offset_lo;  /* restrict offsets to [offset_lo, offset_hi] (inclusive); */
+    int32_t offset_hi;  /* INT32_MIN / INT32_MAX (the defaults) mean all offsets */
+} hgm_params;
+
+/* Fills *p with the defaults above. */
+HGM_API void hgm_default_params(hgm_params *p);
+
+/* Creates a model from M points (host or device pointers; copied). The chain
+ * order is the points' stable order by frame (Sec. 2.1: the hypergraph links
+ * each point to its two frame-wise predecessors). M >= 3 (Eq. 9 needs one
+ * triangle), 1 <= F <= 4096, frames >= 0, all values finite; else
+ * HGM_EINVAL. */
+HGM_API hgm_status hgm_create_model(const float *xy, const int32_t *t, const float *desc, int32_t M, int32_t F,
+                            void *stream, hgm_model **out);
+
+/* Creates a scene from S points (host or device pointers; copied). The scene
+ * is stored stably sorted by frame with its minnode table (Sec. 3.4: first
+ * point of every frame). n_frames is the scene length F_s (frames are
+ * 0..F_s-1); n_frames <= 0 means max(t)+1. S >= 0 (an empty scene has no
+ * feasible offset), frames in [0, F_s), values finite; else HGM_EINVAL. */
+HGM_API hgm_status hgm_create_scene(const float *xy, const int32_t *t, const float *desc, int32_t S, int32_t F,
+                            int32_t n_frames, void *stream, hgm_scene **out);
+
+/* Releases a model or scene handle and its device memory. NULL is a no-op.
+ * Work on the handle must be complete (or ordered before on the stream the
+ * handle was used on) -- the call synchronises the device first. */
+HGM_API void hgm_destroy(void *handle);
+
+/* Message for the last failed call on this thread ("" if none). */
+HGM_API const char *hgm_last_error(void);
+
+/* Number of offsets and the first one for a (model, scene, params) triple,
+ * host only, no device work. */
+HGM_API hgm_status hgm_offsets(const hgm_model *model, const hgm_scene *scene, const hgm_params *params,
+                       int32_t *n_offsets, int32_t *first_offset);
+
+/* Solves every offset of one (model, scene) pair (Eqs. 10-13).
+ *  energy [n_offsets] float (host or device, or NULL): minimal E per offset,
+ *         +inf where infeasible.
+ *  assign [n_offsets x M] int32 (host or device, or NULL): row k is the
+ *         optimal assignment at offset first_offset + k; column i is the
+ *         caller's model point i, the value the caller's scene index (or -1).
+ *  n_offsets / first_offset (host, may be NULL) receive the offset range.
+ * With both outputs NULL only the offset range is computed. */
+HGM_API hgm_status hgm_match(const hgm_model *model, const hgm_scene *scene, const hgm_params *params, void *stream,
+                     int32_t *n_offsets, int32_t *first_offset, float *energy, int32_t *assign);
+
+/* Output layout of a batch of n_models x n_scenes pairs; pair p = m*n_scenes + s.
+ * All arrays host, caller-allocated:
+ *  first_offset [n_pairs]        first offset of pair p
+ *  energy_start [n_pairs + 1]    pair p's energies occupy energy[energy_start[p] .. energy_start[p+1])
+ *  assign_start [n_pairs + 1]    pair p's assignment rows (M_m int32 each) start at assign[assign_start[p]]
+ * Any of them may be NULL. */
+HGM_API hgm_status hgm_batch_layout(const hgm_model *const *models, int32_t n_models, const hgm_scene *const *scenes,
+                            int32_t n_scenes, const hgm_params *params, int32_t *first_offset,
+                            int64_t *energy_start, int64_t *assign_start);
+
+/* Solves every offset of every (model, scene) pair in one pass: the unit
+ * list (model, scene, offset) is ordered by decreasing model size and run by
+ * persistent kernels, in chunks bounded by the workspace budget.
+ * energy (host or device, or NULL) and assign (host or device, or NULL) use
+ * the layout of hgm_batch_layout. */
+HGM_API hgm_status hgm_match_batch(const hgm_model *const *models, int32_t n_models, const hgm_scene *const *scenes,
+                           int32_t n_scenes, const hgm_params *params, void *stream, float *energy,
+                           int32_t *assign);
+
+/* ---- kernel-level entry points (used by the parity tests) -------------- */
+
+/* Stable frame order of a handle's points: perm[k] = caller index of the
+ * k-th point in sorted order (host, n entries). */
+HGM_API hgm_status hgm_model_order(const hgm_model *model, int32_t *perm);
+HGM_API hgm_status hgm_scene_order(const hgm_scene *scene, int32_t *perm);
+
+/* The unary table of Sec. 3.3: U[i*S + j] = lambda1 * ||f_i - f'_j|| for
+ * sorted model point i and sorted scene point j, FP32, components summed in
+ * order with fused multiply-add and an IEEE square root (the same value as
+ * the candidate ranking key). U: device, M x S floats. */
+HGM_API hgm_status hgm_unary(const hgm_model *model, const hgm_scene *scene, float lambda1, void *stream, float *U);
+
+/* Candidate lists for offsets first..first+n-1 (all must be valid offsets):
+ *  idx [n x M x K] int32 (device): sorted scene indices of C_i(o) in
+ *      ascending order, -1 after the last one; i is the sorted model index.
+ *  cnt [n x M] int32 (device): |C_i(o)|. */
+HGM_API hgm_status hgm_candidates(const hgm_model *model, const hgm_scene *scene, const hgm_params *params,
+                          int32_t first, int32_t n, void *stream, int32_t *idx, int32_t *cnt);
+
+/* Feasible (z_i, z_{i-1}, z_{i-2}) triples of the recursion at each offset
+ * (the work Sec. 2.2 counts as O(S M T^2) after pruning):
+ * triples [n] int64 (device). Used to state algorithmic work. */
+HGM_API hgm_status hgm_count_triples(const hgm_model *model, const hgm_scene *scene, const hgm_params *params,
+                             int32_t first, int32_t n, void *stream, int64_t *triples);
+
+/* ---- profiling ----------------------------------------------------------- */
+
+/* When on, every launch of the four kernels below is bracketed by CUDA
+ * events on its stream and its duration accumulated:
+ *   0 = unary distance, 1 = candidate selection, 2 = recursion, 3 = backtrack.
+ * hgm_profile_read synchronises on the recorded events and returns, per
+ * kernel, total milliseconds and launch count since the last reset. */
+HGM_API hgm_status hgm_profile_enable(int32_t on);
+HGM_API hgm_status hgm_profile_read(double *ms, int64_t *launches, int32_t n_kernels);
+HGM_API hgm_status hgm_profile_reset(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HGM_H */

@@ -1,0 +1,843 @@
+// api.cu -- libhgm host runtime behind the C ABI of include/hgm.h.
+//
+// Handles keep models and scenes resident in device memory (Sec. 3.6: data
+// stays on the GPU across launches), stably sorted by frame with the minnode
+// table of Sec. 3.4. A match call plans units (model, scene, offset), orders
+// them by decreasing model size (longest-processing-time first, so that the
+// persistent recursion kernel ends with short units), and runs
+//   (a) unary table -> candidate selection -> (b) recursion -> (c) backtrack
+// per chunk of units whose argmin tables fit the workspace budget. Nothing
+// crosses the host/device boundary between the kernels; the paper's host
+// loop over i (Alg. 2) is inside kernel (b).
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <numeric>
+#include <vector>
+
+#include "hgm_internal.cuh"
+
+namespace hgm {
+namespace {
+
+constexpr uint32_t kModelMagic = 0x4d4f444cu;   // "MODL"
+constexpr uint32_t kSceneMagic = 0x53434e45u;   // "SCNE"
+constexpr uint32_t kDeadMagic = 0xdeadbeefu;
+
+thread_local std::string g_err;
+std::mutex g_mu;
+
+hgm_status fail(hgm_status s, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return s;
+}
+
+hgm_status cuda_fail(cudaError_t e, const char *what)
+{
+    if (e == cudaErrorMemoryAllocation) return fail(HGM_ENOMEM, "%s: %s", what, cudaGetErrorString(e));
+    return fail(HGM_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define CK(call, what)                                   \
+    do {                                                 \
+        cudaError_t e_ = (call);                         \
+        if (e_ != cudaSuccess) return cuda_fail(e_, what); \
+    } while (0)
+
+bool is_device_ptr(const void *p)
+{
+    if (!p) return false;
+    cudaPointerAttributes a;
+    cudaError_t e = cudaPointerGetAttributes(&a, p);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// Copies n elements from a host-or-device pointer into a host vector.
+template <typename T>
+hgm_status fetch(const T *src, size_t n, std::vector<T> &dst, cudaStream_t st)
+{
+    dst.resize(n);
+    if (n == 0) return HGM_OK;
+    if (is_device_ptr(src)) {
+        CK(cudaMemcpyAsync(dst.data(), src, n * sizeof(T), cudaMemcpyDeviceToHost, st), "copy input to host");
+        CK(cudaStreamSynchronize(st), "synchronise input copy");
+    } else {
+        std::memcpy(dst.data(), src, n * sizeof(T));
+    }
+    return HGM_OK;
+}
+
+template <typename T>
+hgm_status upload(T **dptr, const std::vector<T> &h, cudaStream_t st)
+{
+    size_t bytes = std::max<size_t>(h.size(), 1) * sizeof(T);
+    CK(cudaMalloc((void **)dptr, bytes), "cudaMalloc");
+    if (!h.empty()) CK(cudaMemcpyAsync(*dptr, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice, st), "upload");
+    return HGM_OK;
+}
+
+int round_up4(int v) { return (v + 3) & ~3; }
+
+// ---- profiling --------------------------------------------------------------
+struct ProfRec {
+    int kernel;
+    cudaEvent_t a, b;
+};
+bool g_prof_on = false;
+std::vector<ProfRec> g_prof_pending;
+std::vector<cudaEvent_t> g_prof_free;
+double g_prof_ms[kProfCount];
+int64_t g_prof_n[kProfCount];
+std::mutex g_prof_mu;
+ProfRec g_prof_open[kProfCount];
+bool g_prof_is_open[kProfCount];
+
+cudaEvent_t prof_event()
+{
+    if (!g_prof_free.empty()) {
+        cudaEvent_t e = g_prof_free.back();
+        g_prof_free.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    return e;
+}
+
+// ---- workspace ------------------------------------------------------------------
+struct Buffer {
+    void *p = nullptr;
+    size_t bytes = 0;
+    cudaError_t ensure(size_t need)
+    {
+        if (need <= bytes) return cudaSuccess;
+        if (p) cudaFree(p);
+        p = nullptr;
+        bytes = 0;
+        size_t sz = std::max<size_t>(need, 256);
+        cudaError_t e = cudaMalloc(&p, sz);
+        if (e == cudaSuccess) bytes = sz;
+        return e;
+    }
+    template <typename T>
+    T *as() const { return static_cast<T *>(p); }
+};
+
+struct Workspace {
+    Buffer modelcat, U, cand_idx, cand_u, cand_cnt, beta, units, res, mrec, srec, counter, out_e, out_a;
+};
+Workspace g_ws;
+
+}  // namespace
+
+// Profiling hooks used by the kernel launchers.
+void prof_begin(int kernel, cudaStream_t st)
+{
+    if (!g_prof_on) return;
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    ProfRec r{kernel, prof_event(), prof_event()};
+    if (!r.a || !r.b) return;
+    cudaEventRecord(r.a, st);
+    g_prof_open[kernel] = r;
+    g_prof_is_open[kernel] = true;
+}
+
+void prof_end(int kernel, cudaStream_t st)
+{
+    if (!g_prof_on) return;
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    if (!g_prof_is_open[kernel]) return;
+    ProfRec r = g_prof_open[kernel];
+    g_prof_is_open[kernel] = false;
+    cudaEventRecord(r.b, st);
+    g_prof_pending.push_back(r);
+}
+
+}  // namespace hgm
+
+using namespace hgm;
+
+struct hgm_model {
+    uint32_t magic;
+    ModelDev d;
+    int32_t F_user;
+    std::vector<int32_t> t_sorted;   // host copy of sorted frames
+    std::vector<int32_t> perm;       // host copy of the order
+};
+
+struct hgm_scene {
+    uint32_t magic;
+    SceneDev d;
+    int32_t F_user;
+    std::vector<int32_t> perm;
+};
+
+namespace {
+
+bool valid_model(const hgm_model *m) { return m && m->magic == kModelMagic; }
+bool valid_scene(const hgm_scene *s) { return s && s->magic == kSceneMagic; }
+
+hgm_status check_params(const hgm_params *p)
+{
+    if (!p) return fail(HGM_EINVAL, "params is NULL");
+    if (!(std::isfinite(p->lambda1) && std::isfinite(p->lambda2) && std::isfinite(p->lambda3)) ||
+        p->lambda1 < 0 || p->lambda2 < 0 || p->lambda3 < 0)
+        return fail(HGM_EINVAL, "lambdas must be finite and >= 0");
+    if (p->window < 0) return fail(HGM_EINVAL, "window must be >= 0");
+    if (p->K < 1 || p->K > 255) return fail(HGM_EINVAL, "K must be in 1..255 (got %d)", p->K);
+    if (p->K > kMaxK) return fail(HGM_EUNSUPPORTED, "K > %d is not supported by this build", kMaxK);
+    if (p->precision != 0) return fail(HGM_EUNSUPPORTED, "precision %d not available", p->precision);
+    if (p->offset_lo > p->offset_hi) return fail(HGM_EINVAL, "offset_lo > offset_hi");
+    return HGM_OK;
+}
+
+Params to_params(const hgm_params *p)
+{
+    Params q;
+    q.lambda1 = p->lambda1;
+    q.lambda2 = p->lambda2;
+    q.lambda3 = p->lambda3;
+    q.T = p->T;
+    q.window = p->window;
+    q.K = p->K;
+    return q;
+}
+
+// Offset range of a pair: o in [-t_1, F_s-1-t_M] intersected with [offset_lo, offset_hi].
+void pair_offsets(const hgm_model *m, const hgm_scene *s, const hgm_params *p, int32_t *n, int32_t *first)
+{
+    int64_t t1 = m->t_sorted.front(), tM = m->t_sorted.back();
+    int64_t lo = -t1, hi = (int64_t)s->d.n_frames - 1 - tM;
+    lo = std::max<int64_t>(lo, p->offset_lo);
+    hi = std::min<int64_t>(hi, p->offset_hi);
+    *first = (int32_t)lo;
+    *n = hi >= lo ? (int32_t)(hi - lo + 1) : 0;
+}
+
+hgm_status sort_points(const std::vector<int32_t> &t, std::vector<int32_t> &perm)
+{
+    perm.resize(t.size());
+    std::iota(perm.begin(), perm.end(), 0);
+    std::stable_sort(perm.begin(), perm.end(), [&](int32_t a, int32_t b) { return t[a] < t[b]; });
+    return HGM_OK;
+}
+
+void free_model(hgm_model *m)
+{
+    cudaFree(m->d.xy);
+    cudaFree(m->d.t);
+    cudaFree(m->d.f);
+    cudaFree(m->d.perm);
+}
+
+void free_scene(hgm_scene *s)
+{
+    cudaFree(s->d.xy);
+    cudaFree(s->d.t);
+    cudaFree(s->d.f);
+    cudaFree(s->d.frame_start);
+    cudaFree(s->d.perm);
+}
+
+// Staged inputs of one batch call.
+struct Plan {
+    std::vector<ModelRec> mrec;
+    std::vector<SceneRec> srec;
+    std::vector<int32_t> first;       // per pair
+    std::vector<int64_t> e_start;     // per pair + 1
+    std::vector<int64_t> a_start;     // per pair + 1
+    int R = 0;                        // model rows in the unary table
+    int max_M = 0;
+};
+
+hgm_status build_plan(const hgm_model *const *models, int nm, const hgm_scene *const *scenes, int ns,
+                      const hgm_params *p, Plan &pl)
+{
+    pl.first.assign((size_t)nm * ns, 0);
+    pl.e_start.assign((size_t)nm * ns + 1, 0);
+    pl.a_start.assign((size_t)nm * ns + 1, 0);
+    int F = -1;
+    for (int m = 0; m < nm; ++m) {
+        if (!valid_model(models[m])) return fail(HGM_EINVAL, "models[%d] is not a model handle", m);
+        if (F < 0) F = models[m]->F_user;
+        if (models[m]->F_user != F) return fail(HGM_EINVAL, "descriptor widths differ across models");
+    }
+    for (int s = 0; s < ns; ++s) {
+        if (!valid_scene(scenes[s])) return fail(HGM_EINVAL, "scenes[%d] is not a scene handle", s);
+        if (F >= 0 && scenes[s]->F_user != F) return fail(HGM_EINVAL, "descriptor width differs between model and scene");
+    }
+    for (int m = 0; m < nm; ++m)
+        for (int s = 0; s < ns; ++s) {
+            size_t q = (size_t)m * ns + s;
+            int32_t n, first;
+            pair_offsets(models[m], scenes[s], p, &n, &first);
+            pl.first[q] = first;
+            pl.e_start[q + 1] = pl.e_start[q] + n;
+            pl.a_start[q + 1] = pl.a_start[q] + (int64_t)n * models[m]->d.M;
+        }
+    return HGM_OK;
+}
+
+hgm_status run_batch(const hgm_model *const *models, int nm, const hgm_scene *const *scenes, int ns,
+                     const hgm_params *hp, cudaStream_t st, float *energy, int32_t *assign)
+{
+    hgm_status rc = check_params(hp);
+    if (rc) return rc;
+    Plan pl;
+    rc = build_plan(models, nm, scenes, ns, hp, pl);
+    if (rc) return rc;
+    const Params p = to_params(hp);
+    const int64_t n_out = pl.e_start.back();
+    const int64_t n_assign = pl.a_start.back();
+    if (n_out == 0 || nm == 0 || ns == 0) return HGM_OK;
+    const int K = p.K;
+    const int F = models[0]->d.F;
+
+    // unary table: all model rows x every scene (row pitch padded to 4)
+    int R = 0, max_M = 0;
+    std::vector<int> urow(nm);
+    for (int m = 0; m < nm; ++m) {
+        urow[m] = R;
+        R += models[m]->d.M;
+        max_M = std::max(max_M, models[m]->d.M);
+    }
+    std::vector<int64_t> ubase(ns);
+    int64_t utot = 0;
+    for (int s = 0; s < ns; ++s) {
+        ubase[s] = utot;
+        utot += (int64_t)R * round_up4(std::max(scenes[s]->d.S, 1));
+    }
+    CK(g_ws.modelcat.ensure((size_t)R * F * sizeof(float)), "workspace (models)");
+    CK(g_ws.U.ensure((size_t)utot * sizeof(float)), "workspace (unary table)");
+    for (int m = 0; m < nm; ++m)
+        CK(cudaMemcpyAsync(g_ws.modelcat.as<float>() + (size_t)urow[m] * F, models[m]->d.f,
+                           (size_t)models[m]->d.M * F * sizeof(float), cudaMemcpyDeviceToDevice, st),
+           "gather model descriptors");
+    std::vector<ModelRec> mrec(nm);
+    for (int m = 0; m < nm; ++m)
+        mrec[m] = ModelRec{models[m]->d.xy, models[m]->d.t, models[m]->d.perm, models[m]->d.M, urow[m]};
+    std::vector<SceneRec> srec(ns);
+    for (int s = 0; s < ns; ++s) {
+        const SceneDev &d = scenes[s]->d;
+        srec[s] = SceneRec{d.xy, d.t, d.frame_start, d.perm, g_ws.U.as<float>() + ubase[s],
+                           (int64_t)round_up4(std::max(d.S, 1)), d.S, d.n_frames};
+    }
+    CK(g_ws.mrec.ensure(nm * sizeof(ModelRec)), "workspace");
+    CK(g_ws.srec.ensure(ns * sizeof(SceneRec)), "workspace");
+    CK(cudaMemcpyAsync(g_ws.mrec.p, mrec.data(), nm * sizeof(ModelRec), cudaMemcpyHostToDevice, st), "upload");
+    CK(cudaMemcpyAsync(g_ws.srec.p, srec.data(), ns * sizeof(SceneRec), cudaMemcpyHostToDevice, st), "upload");
+    for (int s = 0; s < ns; ++s) {
+        const SceneDev &d = scenes[s]->d;
+        CK(launch_unary(g_ws.modelcat.as<float>(), R, d.f, d.S, F, p.lambda1, g_ws.U.as<float>() + ubase[s],
+                        (int)srec[s].upitch, st),
+           "unary kernel");
+    }
+
+    // outputs: device pointers are written in place, host ones through staging
+    const bool e_dev = energy && is_device_ptr(energy);
+    const bool a_dev = assign && is_device_ptr(assign);
+    float *d_energy = nullptr;
+    int32_t *d_assign = nullptr;
+    if (energy) {
+        if (e_dev) d_energy = energy;
+        else {
+            CK(g_ws.out_e.ensure((size_t)n_out * sizeof(float)), "workspace (energy)");
+            d_energy = g_ws.out_e.as<float>();
+        }
+    }
+    if (assign) {
+        if (a_dev) d_assign = assign;
+        else {
+            CK(g_ws.out_a.ensure((size_t)n_assign * sizeof(int32_t)), "workspace (assign)");
+            d_assign = g_ws.out_a.as<int32_t>();
+        }
+    }
+
+    // units, longest first (counting sort by model size, stable)
+    std::vector<Unit> all;
+    all.reserve((size_t)n_out);
+    std::vector<int64_t> bucket((size_t)max_M + 2, 0);
+    for (int m = 0; m < nm; ++m)
+        for (int s = 0; s < ns; ++s) {
+            size_t q = (size_t)m * ns + s;
+            bucket[(size_t)(max_M - models[m]->d.M)] += pl.e_start[q + 1] - pl.e_start[q];
+        }
+    std::vector<int64_t> pos(bucket.size() + 1, 0);
+    for (size_t k = 0; k < bucket.size(); ++k) pos[k + 1] = pos[k] + bucket[k];
+    all.resize((size_t)n_out);
+    for (int m = 0; m < nm; ++m)
+        for (int s = 0; s < ns; ++s) {
+            size_t q = (size_t)m * ns + s;
+            int64_t n = pl.e_start[q + 1] - pl.e_start[q];
+            const int M = models[m]->d.M;
+            int64_t &w = pos[(size_t)(max_M - M)];
+            for (int64_t k = 0; k < n; ++k) {
+                Unit u{};
+                u.model = m;
+                u.scene = s;
+                u.offset = pl.first[q] + (int32_t)k;
+                u.out_e = pl.e_start[q] + k;
+                u.out_a = pl.a_start[q] + k * M;
+                all[(size_t)w++] = u;
+            }
+        }
+
+    // chunks bounded by the workspace budget for candidate lists and argmin tables
+    size_t free_b = 0, total_b = 0;
+    CK(cudaMemGetInfo(&free_b, &total_b), "cudaMemGetInfo");
+    const size_t budget = std::max<size_t>((size_t)256 << 20, std::min<size_t>((size_t)24 << 30, free_b / 2));
+    const int64_t n_units = (int64_t)all.size();
+    int64_t begin = 0;
+    while (begin < n_units) {
+        int64_t cand_e = 0, beta_b = 0, end = begin;
+        while (end < n_units) {
+            const int M = models[all[(size_t)end].model]->d.M;
+            int64_t ce = (int64_t)M * K, bb = (int64_t)(M - 2) * K * K;
+            int64_t need = (cand_e + ce) * (int64_t)(sizeof(int32_t) * 2) + (cand_e + ce) / K * 4 + beta_b + bb;
+            if (end > begin && (size_t)need > budget) break;
+            all[(size_t)end].cand = cand_e;
+            all[(size_t)end].beta = beta_b;
+            cand_e += ce;
+            beta_b += bb;
+            ++end;
+        }
+        const int64_t n = end - begin;
+        CK(g_ws.cand_idx.ensure((size_t)cand_e * sizeof(int32_t)), "workspace (candidates)");
+        CK(g_ws.cand_u.ensure((size_t)cand_e * sizeof(float)), "workspace (candidates)");
+        CK(g_ws.cand_cnt.ensure((size_t)(cand_e / K) * sizeof(int32_t)), "workspace (candidates)");
+        CK(g_ws.beta.ensure((size_t)beta_b), "workspace (argmin tables)");
+        CK(g_ws.units.ensure((size_t)n * sizeof(Unit)), "workspace (units)");
+        CK(g_ws.res.ensure((size_t)n * sizeof(UnitResult)), "workspace (results)");
+        CK(g_ws.counter.ensure(sizeof(int)), "workspace");
+        CK(cudaMemcpyAsync(g_ws.units.p, all.data() + begin, (size_t)n * sizeof(Unit), cudaMemcpyHostToDevice, st),
+           "upload units");
+        const Unit *du = g_ws.units.as<Unit>();
+        const ModelRec *dm = g_ws.mrec.as<ModelRec>();
+        const SceneRec *ds = g_ws.srec.as<SceneRec>();
+        CK(launch_select(du, n, dm, ds, p, max_M, g_ws.cand_idx.as<int32_t>(), g_ws.cand_u.as<float>(),
+                         g_ws.cand_cnt.as<int32_t>(), st),
+           "select kernel");
+        CK(launch_recurse(du, n, dm, ds, p, g_ws.cand_idx.as<int32_t>(), g_ws.cand_u.as<float>(),
+                          g_ws.cand_cnt.as<int32_t>(), g_ws.beta.as<uint8_t>(), g_ws.res.as<UnitResult>(),
+                          g_ws.counter.as<int>(), st),
+           "recursion kernel");
+        CK(launch_backtrack(du, n, dm, ds, p, g_ws.cand_idx.as<int32_t>(), g_ws.beta.as<uint8_t>(),
+                            g_ws.res.as<UnitResult>(), d_energy, d_assign, st),
+           "backtrack kernel");
+        begin = end;
+    }
+    if (energy && !e_dev)
+        CK(cudaMemcpyAsync(energy, d_energy, (size_t)n_out * sizeof(float), cudaMemcpyDeviceToHost, st), "energy D2H");
+    if (assign && !a_dev)
+        CK(cudaMemcpyAsync(assign, d_assign, (size_t)n_assign * sizeof(int32_t), cudaMemcpyDeviceToHost, st),
+           "assign D2H");
+    if ((energy && !e_dev) || (assign && !a_dev)) CK(cudaStreamSynchronize(st), "synchronise outputs");
+    else CK(cudaGetLastError(), "launch");
+    return HGM_OK;
+}
+
+// Units for offsets [first, first+n) of one pair in offset order (kernel-level entry points).
+hgm_status single_pair_units(const hgm_model *m, const hgm_scene *s, const hgm_params *hp, int32_t first,
+                             int32_t n, cudaStream_t st, Params &p, int &R)
+{
+    hgm_status rc = check_params(hp);
+    if (rc) return rc;
+    if (!valid_model(m) || !valid_scene(s)) return fail(HGM_EINVAL, "invalid handle");
+    if (m->F_user != s->F_user) return fail(HGM_EINVAL, "descriptor width differs between model and scene");
+    int32_t nall, f0;
+    hgm_params all = *hp;
+    all.offset_lo = INT32_MIN;
+    all.offset_hi = INT32_MAX;
+    pair_offsets(m, s, &all, &nall, &f0);
+    if (n < 0 || first < f0 || (int64_t)first + n > (int64_t)f0 + nall)
+        return fail(HGM_EINVAL, "offsets [%d, %d) outside the valid range [%d, %d)", first, first + n, f0, f0 + nall);
+    p = to_params(hp);
+    R = m->d.M;
+    const int K = p.K;
+    const int64_t pitch = round_up4(std::max(s->d.S, 1));
+    CK(g_ws.U.ensure((size_t)R * pitch * sizeof(float)), "workspace (unary table)");
+    ModelRec mr{m->d.xy, m->d.t, m->d.perm, m->d.M, 0};
+    SceneRec sr{s->d.xy, s->d.t, s->d.frame_start, s->d.perm, g_ws.U.as<float>(), pitch, s->d.S, s->d.n_frames};
+    CK(g_ws.mrec.ensure(sizeof(ModelRec)), "workspace");
+    CK(g_ws.srec.ensure(sizeof(SceneRec)), "workspace");
+    CK(cudaMemcpyAsync(g_ws.mrec.p, &mr, sizeof mr, cudaMemcpyHostToDevice, st), "upload");
+    CK(cudaMemcpyAsync(g_ws.srec.p, &sr, sizeof sr, cudaMemcpyHostToDevice, st), "upload");
+    CK(launch_unary(m->d.f, R, s->d.f, s->d.S, m->d.F, p.lambda1, g_ws.U.as<float>(), (int)pitch, st), "unary kernel");
+    std::vector<Unit> units((size_t)n);
+    for (int32_t k = 0; k < n; ++k) {
+        Unit u{};
+        u.model = 0;
+        u.scene = 0;
+        u.offset = first + k;
+        u.cand = (int64_t)k * m->d.M * K;
+        u.beta = (int64_t)k * (m->d.M - 2) * K * K;
+        u.out_e = k;
+        u.out_a = (int64_t)k * m->d.M;
+        units[(size_t)k] = u;
+    }
+    CK(g_ws.units.ensure(std::max<size_t>(1, units.size()) * sizeof(Unit)), "workspace (units)");
+    if (n) CK(cudaMemcpyAsync(g_ws.units.p, units.data(), units.size() * sizeof(Unit), cudaMemcpyHostToDevice, st),
+              "upload units");
+    CK(cudaStreamSynchronize(st), "synchronise");   // host vector goes out of scope
+    return HGM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void hgm_default_params(hgm_params *p)
+{
+    if (!p) return;
+    p->lambda1 = 0.6f;
+    p->lambda2 = 0.2f;
+    p->lambda3 = 5.0f;
+    p->T = 10;
+    p->window = 3;
+    p->K = 64;
+    p->precision = 0;
+    p->offset_lo = INT32_MIN;
+    p->offset_hi = INT32_MAX;
+}
+
+const char *hgm_last_error(void) { return g_err.c_str(); }
+
+hgm_status hgm_create_model(const float *xy, const int32_t *t, const float *desc, int32_t M, int32_t F, void *stream,
+                            hgm_model **out)
+{
+    std::lock_guard<std::mutex> lk(g_mu);
+    g_err.clear();
+    if (!out) return fail(HGM_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (M < 3) return fail(HGM_EINVAL, "a model needs M >= 3 points (got %d)", M);
+    if (F < 1 || F > 4096) return fail(HGM_EINVAL, "F must be in 1..4096 (got %d)", F);
+    if (!xy || !t || !desc) return fail(HGM_EINVAL, "NULL input array");
+    cudaStream_t st = (cudaStream_t)stream;
+    std::vector<float> hxy, hf;
+    std::vector<int32_t> ht;
+    hgm_status rc;
+    if ((rc = fetch(xy, (size_t)M * 2, hxy, st)) || (rc = fetch(t, (size_t)M, ht, st)) ||
+        (rc = fetch(desc, (size_t)M * F, hf, st)))
+        return rc;
+    for (float v : hxy)
+        if (!std::isfinite(v)) return fail(HGM_EINVAL, "non-finite model coordinate");
+    for (float v : hf)
+        if (!std::isfinite(v)) return fail(HGM_EINVAL, "non-finite model descriptor");
+    for (int32_t v : ht)
+        if (v < 0) return fail(HGM_EINVAL, "negative model frame");
+    std::vector<int32_t> perm;
+    sort_points(ht, perm);
+    const int Fp = round_up4(F);
+    std::vector<float2> sxy((size_t)M);
+    std::vector<int32_t> stt((size_t)M);
+    std::vector<float> sf((size_t)M * Fp, 0.0f);
+    for (int k = 0; k < M; ++k) {
+        int q = perm[(size_t)k];
+        sxy[(size_t)k] = make_float2(hxy[(size_t)q * 2], hxy[(size_t)q * 2 + 1]);
+        stt[(size_t)k] = ht[(size_t)q];
+        std::memcpy(&sf[(size_t)k * Fp], &hf[(size_t)q * F], (size_t)F * sizeof(float));
+    }
+    hgm_model *m = new hgm_model();
+    m->magic = kModelMagic;
+    m->d = ModelDev{M, Fp, nullptr, nullptr, nullptr, nullptr};
+    m->F_user = F;
+    m->t_sorted = stt;
+    m->perm = perm;
+    if ((rc = upload(&m->d.xy, sxy, st)) || (rc = upload(&m->d.t, stt, st)) || (rc = upload(&m->d.f, sf, st)) ||
+        (rc = upload(&m->d.perm, perm, st))) {
+        free_model(m);
+        delete m;
+        return rc;
+    }
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+        free_model(m);
+        delete m;
+        return cuda_fail(e, "create model");
+    }
+    *out = m;
+    return HGM_OK;
+}
+
+hgm_status hgm_create_scene(const float *xy, const int32_t *t, const float *desc, int32_t S, int32_t F,
+                            int32_t n_frames, void *stream, hgm_scene **out)
+{
+    std::lock_guard<std::mutex> lk(g_mu);
+    g_err.clear();
+    if (!out) return fail(HGM_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (S < 0) return fail(HGM_EINVAL, "S must be >= 0");
+    if (F < 1 || F > 4096) return fail(HGM_EINVAL, "F must be in 1..4096 (got %d)", F);
+    if (S > 0 && (!xy || !t || !desc)) return fail(HGM_EINVAL, "NULL input array");
+    cudaStream_t st = (cudaStream_t)stream;
+    std::vector<float> hxy, hf;
+    std::vector<int32_t> ht;
+    hgm_status rc;
+    if ((rc = fetch(xy, (size_t)S * 2, hxy, st)) || (rc = fetch(t, (size_t)S, ht, st)) ||
+        (rc = fetch(desc, (size_t)S * F, hf, st)))
+        return rc;
+    int32_t tmax = -1;
+    for (int32_t v : ht) {
+        if (v < 0) return fail(HGM_EINVAL, "negative scene frame");
+        tmax = std::max(tmax, v);
+    }
+    if (n_frames <= 0) n_frames = tmax + 1;
+    if (tmax >= n_frames) return fail(HGM_EINVAL, "scene frame %d outside [0, %d)", tmax, n_frames);
+    if (n_frames <= 0) n_frames = 0;
+    for (float v : hxy)
+        if (!std::isfinite(v)) return fail(HGM_EINVAL, "non-finite scene coordinate");
+    for (float v : hf)
+        if (!std::isfinite(v)) return fail(HGM_EINVAL, "non-finite scene descriptor");
+    // stable counting sort by frame; minnode(f) = first sorted index with frame >= f
+    std::vector<int32_t> fs((size_t)n_frames + 1, 0);
+    for (int32_t v : ht) fs[(size_t)v + 1]++;
+    for (int32_t f = 0; f < n_frames; ++f) fs[(size_t)f + 1] += fs[(size_t)f];
+    std::vector<int32_t> perm((size_t)S);
+    {
+        std::vector<int32_t> w(fs.begin(), fs.end() - 1);
+        for (int32_t k = 0; k < S; ++k) perm[(size_t)w[(size_t)ht[(size_t)k]]++] = k;
+    }
+    const int Fp = round_up4(F);
+    std::vector<float2> sxy((size_t)S);
+    std::vector<int32_t> stt((size_t)S);
+    std::vector<float> sf((size_t)S * Fp, 0.0f);
+    for (int32_t k = 0; k < S; ++k) {
+        int32_t q = perm[(size_t)k];
+        sxy[(size_t)k] = make_float2(hxy[(size_t)q * 2], hxy[(size_t)q * 2 + 1]);
+        stt[(size_t)k] = ht[(size_t)q];
+        std::memcpy(&sf[(size_t)k * Fp], &hf[(size_t)q * F], (size_t)F * sizeof(float));
+    }
+    hgm_scene *s = new hgm_scene();
+    s->magic = kSceneMagic;
+    s->d = SceneDev{S, Fp, n_frames, nullptr, nullptr, nullptr, nullptr, nullptr};
+    s->F_user = F;
+    s->perm = perm;
+    if ((rc = upload(&s->d.xy, sxy, st)) || (rc = upload(&s->d.t, stt, st)) || (rc = upload(&s->d.f, sf, st)) ||
+        (rc = upload(&s->d.frame_start, fs, st)) || (rc = upload(&s->d.perm, perm, st))) {
+        free_scene(s);
+        delete s;
+        return rc;
+    }
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+        free_scene(s);
+        delete s;
+        return cuda_fail(e, "create scene");
+    }
+    *out = s;
+    return HGM_OK;
+}
+
+void hgm_destroy(void *handle)
+{
+    if (!handle) return;
+    std::lock_guard<std::mutex> lk(g_mu);
+    uint32_t magic = *static_cast<uint32_t *>(handle);
+    if (magic == kModelMagic) {
+        hgm_model *m = static_cast<hgm_model *>(handle);
+        cudaDeviceSynchronize();
+        free_model(m);
+        m->magic = kDeadMagic;
+        delete m;
+    } else if (magic == kSceneMagic) {
+        hgm_scene *s = static_cast<hgm_scene *>(handle);
+        cudaDeviceSynchronize();
+        free_scene(s);
+        s->magic = kDeadMagic;
+        delete s;
+    }
+}
+
+hgm_status hgm_offsets(const hgm_model *model, const hgm_scene *scene, const hgm_params *params, int32_t *n_offsets,
+                       int32_t *first_offset)
+{
+    g_err.clear();
+    hgm_status rc = check_params(params);
+    if (rc) return rc;
+    if (!valid_model(model) || !valid_scene(scene)) return fail(HGM_EINVAL, "invalid handle");
+    int32_t n, f;
+    pair_offsets(model, scene, params, &n, &f);
+    if (n_offsets) *n_offsets = n;
+    if (first_offset) *first_offset = f;
+    return HGM_OK;
+}
+
+hgm_status hgm_batch_layout(const hgm_model *const *models, int32_t n_models, const hgm_scene *const *scenes,
+                            int32_t n_scenes, const hgm_params *params, int32_t *first_offset,
+                            int64_t *energy_start, int64_t *assign_start)
+{
+    g_err.clear();
+    hgm_status rc = check_params(params);
+    if (rc) return rc;
+    if (n_models < 0 || n_scenes < 0 || (n_models && !models) || (n_scenes && !scenes))
+        return fail(HGM_EINVAL, "bad model/scene arrays");
+    Plan pl;
+    rc = build_plan(models, n_models, scenes, n_scenes, params, pl);
+    if (rc) return rc;
+    size_t np = (size_t)n_models * n_scenes;
+    if (first_offset) std::copy(pl.first.begin(), pl.first.end(), first_offset);
+    if (energy_start) std::copy(pl.e_start.begin(), pl.e_start.begin() + np + 1, energy_start);
+    if (assign_start) std::copy(pl.a_start.begin(), pl.a_start.begin() + np + 1, assign_start);
+    return HGM_OK;
+}
+
+hgm_status hgm_match(const hgm_model *model, const hgm_scene *scene, const hgm_params *params, void *stream,
+                     int32_t *n_offsets, int32_t *first_offset, float *energy, int32_t *assign)
+{
+    std::lock_guard<std::mutex> lk(g_mu);
+    g_err.clear();
+    hgm_status rc = check_params(params);
+    if (rc) return rc;
+    if (!valid_model(model) || !valid_scene(scene)) return fail(HGM_EINVAL, "invalid handle");
+    if (model->F_user != scene->F_user) return fail(HGM_EINVAL, "descriptor width differs between model and scene");
+    int32_t n, f;
+    pair_offsets(model, scene, params, &n, &f);
+    if (n_offsets) *n_offsets = n;
+    if (first_offset) *first_offset = f;
+    if (!energy && !assign) return HGM_OK;
+    return run_batch(&model, 1, &scene, 1, params, (cudaStream_t)stream, energy, assign);
+}
+
+hgm_status hgm_match_batch(const hgm_model *const *models, int32_t n_models, const hgm_scene *const *scenes,
+                           int32_t n_scenes, const hgm_params *params, void *stream, float *energy, int32_t *assign)
+{
+    std::lock_guard<std::mutex> lk(g_mu);
+    g_err.clear();
+    if (n_models < 0 || n_scenes < 0 || (n_models && !models) || (n_scenes && !scenes))
+        return fail(HGM_EINVAL, "bad model/scene arrays");
+    return run_batch(models, n_models, scenes, n_scenes, params, (cudaStream_t)stream, energy, assign);
+}
+
+hgm_status hgm_model_order(const hgm_model *model, int32_t *perm)
+{
+    g_err.clear();
+    if (!valid_model(model) || !perm) return fail(HGM_EINVAL, "invalid argument");
+    std::copy(model->perm.begin(), model->perm.end(), perm);
+    return HGM_OK;
+}
+
+hgm_status hgm_scene_order(const hgm_scene *scene, int32_t *perm)
+{
+    g_err.clear();
+    if (!valid_scene(scene) || !perm) return fail(HGM_EINVAL, "invalid argument");
+    std::copy(scene->perm.begin(), scene->perm.end(), perm);
+    return HGM_OK;
+}
+
+hgm_status hgm_unary(const hgm_model *model, const hgm_scene *scene, float lambda1, void *stream, float *U)
+{
+    std::lock_guard<std::mutex> lk(g_mu);
+    g_err.clear();
+    if (!valid_model(model) || !valid_scene(scene)) return fail(HGM_EINVAL, "invalid handle");
+    if (model->F_user != scene->F_user) return fail(HGM_EINVAL, "descriptor width differs between model and scene");
+    if (!U || !is_device_ptr(U)) return fail(HGM_EINVAL, "U must be a device pointer");
+    if (!std::isfinite(lambda1) || lambda1 < 0) return fail(HGM_EINVAL, "lambda1 must be finite and >= 0");
+    cudaStream_t st = (cudaStream_t)stream;
+    CK(launch_unary(model->d.f, model->d.M, scene->d.f, scene->d.S, model->d.F, lambda1, U, scene->d.S, st),
+       "unary kernel");
+    return HGM_OK;
+}
+
+hgm_status hgm_candidates(const hgm_model *model, const hgm_scene *scene, const hgm_params *params, int32_t first,
+                          int32_t n, void *stream, int32_t *idx, int32_t *cnt)
+{
+    std::lock_guard<std::mutex> lk(g_mu);
+    g_err.clear();
+    if (!idx || !cnt || !is_device_ptr(idx) || !is_device_ptr(cnt)) return fail(HGM_EINVAL, "outputs must be device pointers");
+    cudaStream_t st = (cudaStream_t)stream;
+    Params p;
+    int R;
+    hgm_status rc = single_pair_units(model, scene, params, first, n, st, p, R);
+    if (rc) return rc;
+    if (n == 0) return HGM_OK;
+    CK(g_ws.cand_u.ensure((size_t)n * model->d.M * p.K * sizeof(float)), "workspace (candidates)");
+    CK(launch_select(g_ws.units.as<Unit>(), n, g_ws.mrec.as<ModelRec>(), g_ws.srec.as<SceneRec>(), p, model->d.M, idx,
+                     g_ws.cand_u.as<float>(), cnt, st),
+       "select kernel");
+    return HGM_OK;
+}
+
+hgm_status hgm_count_triples(const hgm_model *model, const hgm_scene *scene, const hgm_params *params, int32_t first,
+                             int32_t n, void *stream, int64_t *triples)
+{
+    std::lock_guard<std::mutex> lk(g_mu);
+    g_err.clear();
+    if (!triples || !is_device_ptr(triples)) return fail(HGM_EINVAL, "triples must be a device pointer");
+    cudaStream_t st = (cudaStream_t)stream;
+    Params p;
+    int R;
+    hgm_status rc = single_pair_units(model, scene, params, first, n, st, p, R);
+    if (rc) return rc;
+    if (n == 0) return HGM_OK;
+    const size_t ce = (size_t)n * model->d.M * p.K;
+    CK(g_ws.cand_idx.ensure(ce * sizeof(int32_t)), "workspace (candidates)");
+    CK(g_ws.cand_u.ensure(ce * sizeof(float)), "workspace (candidates)");
+    CK(g_ws.cand_cnt.ensure((size_t)n * model->d.M * sizeof(int32_t)), "workspace (candidates)");
+    CK(launch_select(g_ws.units.as<Unit>(), n, g_ws.mrec.as<ModelRec>(), g_ws.srec.as<SceneRec>(), p, model->d.M,
+                     g_ws.cand_idx.as<int32_t>(), g_ws.cand_u.as<float>(), g_ws.cand_cnt.as<int32_t>(), st),
+       "select kernel");
+    CK(launch_count(g_ws.units.as<Unit>(), n, g_ws.mrec.as<ModelRec>(), g_ws.srec.as<SceneRec>(), p,
+                    g_ws.cand_idx.as<int32_t>(), g_ws.cand_cnt.as<int32_t>(), triples, st),
+       "count kernel");
+    return HGM_OK;
+}
+
+hgm_status hgm_profile_enable(int32_t on)
+{
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    g_prof_on = on != 0;
+    return HGM_OK;
+}
+
+hgm_status hgm_profile_read(double *ms, int64_t *launches, int32_t n_kernels)
+{
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    g_err.clear();
+    for (ProfRec &r : g_prof_pending) {
+        cudaError_t e = cudaEventSynchronize(r.b);
+        if (e != cudaSuccess) return cuda_fail(e, "profile event");
+        float t = 0.0f;
+        cudaEventElapsedTime(&t, r.a, r.b);
+        g_prof_ms[r.kernel] += t;
+        g_prof_n[r.kernel] += 1;
+        g_prof_free.push_back(r.a);
+        g_prof_free.push_back(r.b);
+    }
+    g_prof_pending.clear();
+    for (int k = 0; k < n_kernels && k < kProfCount; ++k) {
+        if (ms) ms[k] = g_prof_ms[k];
+        if (launches) launches[k] = g_prof_n[k];
+    }
+    return HGM_OK;
+}
+
+hgm_status hgm_profile_reset(void)
+{
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    for (ProfRec &r : g_prof_pending) {
+        cudaEventSynchronize(r.b);
+        g_prof_free.push_back(r.a);
+        g_prof_free.push_back(r.b);
+    }
+    g_prof_pending.clear();
+    for (int k = 0; k < kProfCount; ++k) {
+        g_prof_ms[k] = 0;
+        g_prof_n[k] = 0;
+    }
+    return HGM_OK;
+}
+
+}  // extern "C"

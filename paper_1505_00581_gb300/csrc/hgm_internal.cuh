@@ -1,0 +1,101 @@
+// hgm_internal.cuh -- shared declarations of libhgm's host runtime and kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "hgm.h"
+
+namespace hgm {
+
+constexpr int kMaxK = 64;          // candidate cap supported by the kernels
+constexpr int kNoSlot = 255;       // beta entry of a cell without a feasible z_i
+constexpr float kTwoPi = 6.28318530717958647692f;
+constexpr float kPi = 3.14159265358979323846f;
+
+// Device-resident model (points sorted stably by frame).
+struct ModelDev {
+    int32_t M, F;
+    float2 *xy;          // [M]
+    int32_t *t;          // [M]
+    float *f;            // [M*F]
+    int32_t *perm;       // [M] caller index of sorted point k
+};
+
+// Device-resident scene (points sorted stably by frame) with its minnode table.
+struct SceneDev {
+    int32_t S, F, n_frames;
+    float2 *xy;          // [S]
+    int32_t *t;          // [S]
+    float *f;            // [S*F]
+    int32_t *frame_start;  // [n_frames+1], minnode of Sec. 3.4
+    int32_t *perm;       // [S] caller index of sorted point k
+};
+
+// Per-model record the kernels read (device array indexed by model slot).
+struct ModelRec {
+    const float2 *xy;
+    const int32_t *t;
+    const int32_t *perm;
+    int32_t M;
+    int32_t urow;        // first row of this model in the unary table
+};
+
+// Per-scene record the kernels read.
+struct SceneRec {
+    const float2 *xy;
+    const int32_t *t;
+    const int32_t *frame_start;
+    const int32_t *perm;
+    const float *U;      // unary table block of this scene: [R x upitch]
+    int64_t upitch;      // row pitch of U in floats (>= S)
+    int32_t S, n_frames;
+};
+
+// One matching problem: a (model, scene, offset) triple.
+struct Unit {
+    int32_t model, scene, offset, pad;
+    int64_t cand;        // base of this unit's candidate lists (entries), M*K
+    int64_t beta;        // base of this unit's argmin tables (bytes), (M-2)*K*K
+    int64_t out_e;       // index into the energy output
+    int64_t out_a;       // index into the assignment output
+};
+
+// Result of the recursion for one unit, consumed by the backtrack kernel.
+struct UnitResult {
+    float energy;
+    int32_t z1, z2;      // slots of z_1 and z_2 in C_1, C_2 (-1 if infeasible)
+    int32_t pad;
+};
+
+struct Params {
+    float lambda1, lambda2, lambda3;
+    int32_t T, window, K;
+};
+
+enum ProfKernel { kProfUnary = 0, kProfSelect = 1, kProfRecurse = 2, kProfBacktrack = 3, kProfCount = 4 };
+
+// ---- kernel launchers (each checks its own launch error) --------------------
+cudaError_t launch_unary(const float *A, int R, const float *B, int S, int F, float lambda1, float *U,
+                         int ldu, cudaStream_t st);
+cudaError_t launch_select(const Unit *units, int64_t n_units, const ModelRec *models, const SceneRec *scenes,
+                          Params p, int max_M, int32_t *cand_idx, float *cand_u, int32_t *cand_cnt,
+                          cudaStream_t st);
+cudaError_t launch_recurse(const Unit *units, int64_t n_units, const ModelRec *models, const SceneRec *scenes,
+                           Params p, const int32_t *cand_idx, const float *cand_u, const int32_t *cand_cnt,
+                           uint8_t *beta, UnitResult *res, int *work_counter, cudaStream_t st);
+cudaError_t launch_backtrack(const Unit *units, int64_t n_units, const ModelRec *models, const SceneRec *scenes,
+                             Params p, const int32_t *cand_idx, const uint8_t *beta, const UnitResult *res,
+                             float *energy, int32_t *assign, cudaStream_t st);
+cudaError_t launch_count(const Unit *units, int64_t n_units, const ModelRec *models, const SceneRec *scenes,
+                         Params p, const int32_t *cand_idx, const int32_t *cand_cnt, int64_t *triples,
+                         cudaStream_t st);
+
+// Profiling hooks (api.cu).
+void prof_begin(int kernel, cudaStream_t st);
+void prof_end(int kernel, cudaStream_t st);
+
+}  // namespace hgm

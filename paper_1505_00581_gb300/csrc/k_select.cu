@@ -1,0 +1,146 @@
+// k_select.cu -- candidate lists C_i(o): window + top-K cap.
+//
+// For unit (model m, scene s, offset o) and model point i, the window is the
+// frame range [t_i+o-w, t_i+o+w] clipped to the scene; through the minnode
+// table of Sec. 3.4 it is the contiguous sorted-scene range
+// [minnode(f0), minnode(f1+1)). If it holds more than K points, the K with
+// the smallest unary cost are kept (ties to the lower scene index), and the
+// kept points are listed in ascending scene index (hence ascending frame).
+//
+// One warp per (unit, i). The K-th smallest key is found exactly by a 4-pass
+// radix select on the IEEE bit patterns (unary costs are >= 0, so the bit
+// pattern orders like the value); a final ballot pass keeps every key below
+// the threshold plus the first equal ones in index order. Integer decisions
+// therefore depend only on the FP32 keys of kernel (a), bit for bit.
+#include "hgm_internal.cuh"
+
+namespace hgm {
+namespace {
+
+constexpr int kWarps = 8;
+
+__device__ __forceinline__ uint32_t lanemask_lt()
+{
+    uint32_t m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+__global__ void __launch_bounds__(kWarps * 32) select_kernel(const Unit *__restrict__ units, int64_t n_units,
+                                                             const ModelRec *__restrict__ models,
+                                                             const SceneRec *__restrict__ scenes, Params p,
+                                                             int32_t *__restrict__ cand_idx,
+                                                             float *__restrict__ cand_u,
+                                                             int32_t *__restrict__ cand_cnt)
+{
+    __shared__ uint32_t hist[kWarps][256];
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const int K = p.K;
+    for (int64_t u = blockIdx.x; u < n_units; u += gridDim.x) {
+        const Unit un = units[u];
+        const ModelRec md = models[un.model];
+        const SceneRec sc = scenes[un.scene];
+        for (int i = warp; i < md.M; i += kWarps) {
+            int32_t *oidx = cand_idx + un.cand + (int64_t)i * K;
+            float *ou = cand_u + un.cand + (int64_t)i * K;
+            const int ti = md.t[i];
+            int f0 = ti + un.offset - p.window, f1 = ti + un.offset + p.window;
+            f0 = max(f0, 0);
+            f1 = min(f1, sc.n_frames - 1);
+            int j0 = 0, n = 0;
+            if (f0 <= f1) {
+                j0 = sc.frame_start[f0];
+                n = sc.frame_start[f1 + 1] - j0;
+            }
+            const float *key = sc.U + (int64_t)(md.urow + i) * sc.upitch + j0;
+            int kept = n < K ? n : K;
+            if (n <= K) {
+                for (int e = lane; e < K; e += 32) {
+                    oidx[e] = e < n ? j0 + e : -1;
+                    ou[e] = e < n ? key[e] : __int_as_float(0x7f800000);
+                }
+            } else {
+                // radix select of the K-th smallest key (1-based rank kk)
+                uint32_t prefix = 0, mask = 0;
+                int kk = K;
+                for (int shift = 24; shift >= 0; shift -= 8) {
+                    for (int d = lane; d < 256; d += 32) hist[warp][d] = 0;
+                    __syncwarp();
+                    for (int e = lane; e < n; e += 32) {
+                        uint32_t b = __float_as_uint(key[e]);
+                        if ((b & mask) == prefix) atomicAdd(&hist[warp][(b >> shift) & 255u], 1u);
+                    }
+                    __syncwarp();
+                    uint32_t c[8];
+                    uint32_t sum = 0;
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) { c[q] = hist[warp][lane * 8 + q]; sum += c[q]; }
+                    uint32_t incl = sum;
+#pragma unroll
+                    for (int off = 1; off < 32; off <<= 1) {
+                        uint32_t v = __shfl_up_sync(0xffffffffu, incl, off);
+                        if (lane >= off) incl += v;
+                    }
+                    uint32_t excl = incl - sum;
+                    bool mine = excl < (uint32_t)kk && (uint32_t)kk <= incl;
+                    int digit = 0;
+                    uint32_t below = excl;
+                    if (mine) {
+#pragma unroll
+                        for (int q = 0; q < 8; ++q) {
+                            if (below + c[q] >= (uint32_t)kk) { digit = lane * 8 + q; break; }
+                            below += c[q];
+                        }
+                    }
+                    uint32_t ball = __ballot_sync(0xffffffffu, mine);
+                    int src = __ffs(ball) - 1;
+                    digit = __shfl_sync(0xffffffffu, digit, src);
+                    below = __shfl_sync(0xffffffffu, below, src);
+                    prefix |= (uint32_t)digit << shift;
+                    mask |= 255u << shift;
+                    kk -= (int)below;
+                    __syncwarp();
+                }
+                // keep keys < tau, plus the first kk keys == tau in index order
+                const uint32_t tau = prefix;
+                int base = 0, eqseen = 0;
+                for (int c0 = 0; c0 < n; c0 += 32) {
+                    int e = c0 + lane;
+                    bool valid = e < n;
+                    float kv = valid ? key[e] : 0.0f;
+                    uint32_t b = __float_as_uint(kv);
+                    bool lt = valid && b < tau;
+                    bool eq = valid && b == tau;
+                    uint32_t eqm = __ballot_sync(0xffffffffu, eq);
+                    int eqrank = eqseen + __popc(eqm & lanemask_lt());
+                    bool keep = lt || (eq && eqrank < kk);
+                    uint32_t km = __ballot_sync(0xffffffffu, keep);
+                    int pos = base + __popc(km & lanemask_lt());
+                    if (keep && pos < K) { oidx[pos] = j0 + e; ou[pos] = kv; }
+                    base += __popc(km);
+                    eqseen += __popc(eqm);
+                }
+            }
+            if (lane == 0) cand_cnt[un.cand / K + i] = kept;
+        }
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_select(const Unit *units, int64_t n_units, const ModelRec *models, const SceneRec *scenes,
+                          Params p, int max_M, int32_t *cand_idx, float *cand_u, int32_t *cand_cnt,
+                          cudaStream_t st)
+{
+    (void)max_M;
+    if (n_units <= 0) return cudaSuccess;
+    int64_t blocks = n_units < (int64_t)1 << 20 ? n_units : (int64_t)1 << 20;
+    prof_begin(kProfSelect, st);
+    select_kernel<<<(unsigned)blocks, kWarps * 32, 0, st>>>(units, n_units, models, scenes, p, cand_idx, cand_u,
+                                                            cand_cnt);
+    prof_end(kProfSelect, st);
+    return cudaGetLastError();
+}
+
+}  // namespace hgm

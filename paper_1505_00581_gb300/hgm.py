@@ -1,0 +1,282 @@
+"""Thin Python binding of libhgm (include/hgm.h): argument marshalling only.
+
+Every step of the matching runs inside libhgm's CUDA kernels; this module
+converts numpy arrays / torch tensors into pointers, passes torch's current
+CUDA stream, and raises on a non-zero status. There is no CPU fallback: if
+``_build/libhgm.so`` is missing or cannot be loaded, ``load()`` raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import dataclasses
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libhgm.so")
+
+HGM_OK, HGM_EINVAL, HGM_ENOMEM, HGM_ECUDA, HGM_ETIMEOUT, HGM_EUNSUPPORTED = range(6)
+KERNELS = ("unary", "select", "recurse", "backtrack")
+
+# Every function declared in include/hgm.h, with (restype, argtypes).
+_vp = ctypes.c_void_p
+_i32 = ctypes.c_int32
+_i64 = ctypes.c_int64
+_f32 = ctypes.c_float
+_p32 = ctypes.POINTER(ctypes.c_int32)
+_p64 = ctypes.POINTER(ctypes.c_int64)
+_pf = ctypes.POINTER(ctypes.c_float)
+_pd = ctypes.POINTER(ctypes.c_double)
+
+
+class Params(ctypes.Structure):
+    """hgm_params (include/hgm.h)."""
+    _fields_ = [("lambda1", ctypes.c_float), ("lambda2", ctypes.c_float), ("lambda3", ctypes.c_float),
+                ("T", ctypes.c_int32), ("window", ctypes.c_int32), ("K", ctypes.c_int32),
+                ("precision", ctypes.c_int32), ("offset_lo", ctypes.c_int32), ("offset_hi", ctypes.c_int32)]
+
+
+_PP = ctypes.POINTER(Params)
+SIGNATURES = {
+    "hgm_default_params": (None, [_PP]),
+    "hgm_create_model": (_i32, [_vp, _vp, _vp, _i32, _i32, _vp, ctypes.POINTER(_vp)]),
+    "hgm_create_scene": (_i32, [_vp, _vp, _vp, _i32, _i32, _i32, _vp, ctypes.POINTER(_vp)]),
+    "hgm_destroy": (None, [_vp]),
+    "hgm_last_error": (ctypes.c_char_p, []),
+    "hgm_offsets": (_i32, [_vp, _vp, _PP, _p32, _p32]),
+    "hgm_match": (_i32, [_vp, _vp, _PP, _vp, _p32, _p32, _vp, _vp]),
+    "hgm_batch_layout": (_i32, [ctypes.POINTER(_vp), _i32, ctypes.POINTER(_vp), _i32, _PP, _p32, _p64, _p64]),
+    "hgm_match_batch": (_i32, [ctypes.POINTER(_vp), _i32, ctypes.POINTER(_vp), _i32, _PP, _vp, _vp, _vp]),
+    "hgm_model_order": (_i32, [_vp, _p32]),
+    "hgm_scene_order": (_i32, [_vp, _p32]),
+    "hgm_unary": (_i32, [_vp, _vp, _f32, _vp, _vp]),
+    "hgm_candidates": (_i32, [_vp, _vp, _PP, _i32, _i32, _vp, _vp, _vp]),
+    "hgm_count_triples": (_i32, [_vp, _vp, _PP, _i32, _i32, _vp, _vp]),
+    "hgm_profile_enable": (_i32, [_i32]),
+    "hgm_profile_read": (_i32, [_pd, _p64, _i32]),
+    "hgm_profile_reset": (_i32, []),
+}
+
+_lib = None
+
+
+class HgmError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"hgm status {status}: {msg}")
+        self.status = status
+
+
+def load(path: str = LIB_PATH):
+    """Loads libhgm.so (built by __graft_entry__.build() / paper_1505_00581_gb300.build). No fallback."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"libhgm.so not found at {path}: build it first (python -c 'import __graft_entry__ as g; "
+                          f"g.build()'); there is no CPU fallback")
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(status: int):
+    if status != HGM_OK:
+        msg = _lib.hgm_last_error()
+        raise HgmError(status, msg.decode() if msg else "")
+
+
+def default_params(**over) -> Params:
+    lib = load()
+    p = Params()
+    lib.hgm_default_params(ctypes.byref(p))
+    for k, v in over.items():
+        setattr(p, k, v)
+    return p
+
+
+def _stream(stream=None) -> int:
+    if stream is not None:
+        return int(stream)
+    try:
+        import torch
+        if torch.cuda.is_available() and torch.cuda.is_initialized():
+            return int(torch.cuda.current_stream().cuda_stream)
+    except ImportError:
+        pass
+    return 0
+
+
+def _ptr(a):
+    """(pointer, keepalive) for a torch tensor (CPU/CUDA) or numpy array, contiguous."""
+    if a is None:
+        return None, None
+    try:
+        import torch
+        if isinstance(a, torch.Tensor):
+            a = a.contiguous()
+            return a.data_ptr(), a
+    except ImportError:
+        pass
+    a = np.ascontiguousarray(a)
+    return a.ctypes.data, a
+
+
+class Model:
+    """A model handle: M points (xy float32 [M,2], t int32 [M], f float32 [M,F]), host or device."""
+
+    def __init__(self, xy, t, f, stream=None):
+        self.lib = load()
+        xy = _as(xy, np.float32)
+        t = _as(t, np.int32)
+        f = _as(f, np.float32)
+        (pxy, kxy), (pt, kt), (pf, kf) = _ptr(xy), _ptr(t), _ptr(f)
+        h = ctypes.c_void_p()
+        M, F = int(f.shape[0]), int(f.shape[1])
+        _check(self.lib.hgm_create_model(pxy, pt, pf, M, F, _stream(stream), ctypes.byref(h)))
+        self.handle, self.M, self.F = h, M, F
+
+    def order(self) -> np.ndarray:
+        out = np.zeros(self.M, np.int32)
+        _check(self.lib.hgm_model_order(self.handle, out.ctypes.data_as(_p32)))
+        return out
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self.lib.hgm_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Scene:
+    """A scene handle: S points (xy [S,2], t [S], f [S,F]) over n_frames frames, host or device."""
+
+    def __init__(self, xy, t, f, n_frames: int = 0, stream=None):
+        self.lib = load()
+        xy = _as(xy, np.float32)
+        t = _as(t, np.int32)
+        f = _as(f, np.float32)
+        (pxy, kxy), (pt, kt), (pf, kf) = _ptr(xy), _ptr(t), _ptr(f)
+        h = ctypes.c_void_p()
+        S, F = int(f.shape[0]), int(f.shape[1])
+        _check(self.lib.hgm_create_scene(pxy, pt, pf, S, F, int(n_frames), _stream(stream), ctypes.byref(h)))
+        self.handle, self.S, self.F, self.n_frames = h, S, F, int(n_frames)
+
+    def order(self) -> np.ndarray:
+        out = np.zeros(self.S, np.int32)
+        _check(self.lib.hgm_scene_order(self.handle, out.ctypes.data_as(_p32)))
+        return out
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self.lib.hgm_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _as(a, dtype):
+    try:
+        import torch
+        if isinstance(a, torch.Tensor):
+            tdt = {np.float32: torch.float32, np.int32: torch.int32}[dtype]
+            return a.to(tdt).contiguous()
+    except ImportError:
+        pass
+    return np.ascontiguousarray(a, dtype=dtype)
+
+
+def offsets(model: Model, scene: Scene, params: Params):
+    n, f = ctypes.c_int32(), ctypes.c_int32()
+    _check(load().hgm_offsets(model.handle, scene.handle, ctypes.byref(params), ctypes.byref(n), ctypes.byref(f)))
+    return int(f.value), int(n.value)
+
+
+def match(model: Model, scene: Scene, params: Params, energy=None, assign=None, stream=None):
+    """Solves all offsets of one pair. energy/assign: preallocated outputs (torch CUDA tensors or numpy), or
+    None to get numpy arrays back. Returns (first_offset, energy, assign)."""
+    lib = load()
+    first, n = offsets(model, scene, params)
+    if energy is None and assign is None:
+        energy = np.zeros(n, np.float32)
+        assign = np.zeros((n, model.M), np.int32)
+    (pe, ke), (pa, ka) = _ptr(energy), _ptr(assign)
+    nn, ff = ctypes.c_int32(), ctypes.c_int32()
+    _check(lib.hgm_match(model.handle, scene.handle, ctypes.byref(params), _stream(stream), ctypes.byref(nn),
+                         ctypes.byref(ff), pe, pa))
+    return first, ke if energy is not None else None, ka if assign is not None else None
+
+
+def batch_layout(models: Sequence[Model], scenes: Sequence[Scene], params: Params):
+    lib = load()
+    nm, ns = len(models), len(scenes)
+    mh = (ctypes.c_void_p * max(nm, 1))(*[m.handle for m in models])
+    sh = (ctypes.c_void_p * max(ns, 1))(*[s.handle for s in scenes])
+    first = np.zeros(max(nm * ns, 1), np.int32)
+    es = np.zeros(nm * ns + 1, np.int64)
+    as_ = np.zeros(nm * ns + 1, np.int64)
+    _check(lib.hgm_batch_layout(mh, nm, sh, ns, ctypes.byref(params), first.ctypes.data_as(_p32),
+                                es.ctypes.data_as(_p64), as_.ctypes.data_as(_p64)))
+    return first[:nm * ns], es, as_
+
+
+def match_batch(models: Sequence[Model], scenes: Sequence[Scene], params: Params, energy=None, assign=None,
+                stream=None):
+    """All offsets of all (model, scene) pairs in one pass; outputs in the batch_layout order."""
+    lib = load()
+    nm, ns = len(models), len(scenes)
+    mh = (ctypes.c_void_p * max(nm, 1))(*[m.handle for m in models])
+    sh = (ctypes.c_void_p * max(ns, 1))(*[s.handle for s in scenes])
+    (pe, ke), (pa, ka) = _ptr(energy), _ptr(assign)
+    _check(lib.hgm_match_batch(mh, nm, sh, ns, ctypes.byref(params), _stream(stream), pe, pa))
+    return ke, ka
+
+
+def unary(model: Model, scene: Scene, lambda1: float, out, stream=None):
+    (po, ko) = _ptr(out)
+    _check(load().hgm_unary(model.handle, scene.handle, float(lambda1), _stream(stream), po))
+    return ko
+
+
+def candidates(model: Model, scene: Scene, params: Params, first: int, n: int, idx, cnt, stream=None):
+    (pi, ki), (pc, kc) = _ptr(idx), _ptr(cnt)
+    _check(load().hgm_candidates(model.handle, scene.handle, ctypes.byref(params), int(first), int(n),
+                                 _stream(stream), pi, pc))
+    return ki, kc
+
+
+def count_triples(model: Model, scene: Scene, params: Params, first: int, n: int, out, stream=None):
+    (po, ko) = _ptr(out)
+    _check(load().hgm_count_triples(model.handle, scene.handle, ctypes.byref(params), int(first), int(n),
+                                    _stream(stream), po))
+    return ko
+
+
+def profile_enable(on: bool = True):
+    _check(load().hgm_profile_enable(1 if on else 0))
+
+
+def profile_reset():
+    _check(load().hgm_profile_reset())
+
+
+def profile_read():
+    """{kernel: (total ms, launches)} since the last reset."""
+    ms = np.zeros(len(KERNELS), np.float64)
+    n = np.zeros(len(KERNELS), np.int64)
+    _check(load().hgm_profile_read(ms.ctypes.data_as(_pd), n.ctypes.data_as(_p64), len(KERNELS)))
+    return {k: (float(ms[i]), int(n[i])) for i, k in enumerate(KERNELS)}

@@ -92,7 +92,8 @@ def _tiny_oracle(seed, oracle_mod, T=10, lambda2=0.2, **kw):
     n_frames = int(rng.integers(6, 14))
     K = int(rng.integers(2, 6))
     window = int(rng.integers(0, 3))
-    wl = synth.tiny_case(seed, M=M, n_frames=n_frames, per_frame=per_frame, K=K, window=window, T=max(T, 1))
+    wl = synth.tiny_case(seed, M=M, n_frames=n_frames, per_frame=per_frame, K=K, window=window,
+                         T=T if T > 0 else 1000)
     return oracle_mod.Oracle.from_workload(wl, T=T, lambda2=lambda2, **kw)
 
 
