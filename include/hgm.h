@@ -147,6 +147,30 @@ HGM_API hgm_status hgm_match_batch(const hgm_model *const *models, int32_t n_mod
                            int32_t n_scenes, const hgm_params *params, void *stream, float *energy,
                            int32_t *assign);
 
+/* ---- matching without device allocation --------------------------------- */
+
+/* The paper has no counterpart to this entry point; it exists for callers
+ * that may not allocate device memory while they run: a real-time video loop
+ * that cannot afford the device-wide synchronisation cudaMalloc/cudaFree may
+ * cause, or a host framework that reserves all GPU memory at start-up.
+ * Same result as hgm_match for one (model, scene) pair and all its offsets
+ * (params->offset_lo/hi respected), but every intermediate (unary table,
+ * candidate lists, argmin tables, unit records) lives in one fixed 64 MiB
+ * scratch array compiled into the library, which each GPU that loads the
+ * library holds until the process exits. Offsets are processed in chunks that
+ * fit the scratch. No cudaMalloc, cudaFree or allocating library call is made.
+ *  energy [n_offsets] float, assign [n_offsets x M] int32: DEVICE pointers
+ *         (the layout of hgm_match; n_offsets from hgm_offsets).
+ * Errors: HGM_EUNSUPPORTED (with the byte counts in the message) when one
+ * offset of this pair does not fit the scratch -- the unary table alone needs
+ * M x S x 4 bytes; HGM_EINVAL for host outputs or bad arguments.
+ * The first call on a device looks up the scratch's device address
+ * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * All calls share the scratch: calls whose GPU work may overlap (other
+ * streams, other threads) race and must be serialised by the caller. */
+HGM_API hgm_status hgm_match_noalloc(const hgm_model *model, const hgm_scene *scene, const hgm_params *params,
+                                     void *stream, float *energy, int32_t *assign);
+
 /* ---- kernel-level entry points (used by the parity tests) -------------- */
 
 /* Stable frame order of a handle's points: perm[k] = caller index of the

@@ -23,8 +23,6 @@
 namespace hgm {
 namespace {
 
-constexpr uint32_t kModelMagic = 0x4d4f444cu;   // "MODL"
-constexpr uint32_t kSceneMagic = 0x53434e45u;   // "SCNE"
 constexpr uint32_t kDeadMagic = 0xdeadbeefu;
 
 thread_local std::string g_err;
@@ -170,25 +168,18 @@ void prof_end(int kernel, cudaStream_t st)
 
 using namespace hgm;
 
-struct hgm_model {
-    uint32_t magic;
-    ModelDev d;
-    int32_t F_user;
-    std::vector<int32_t> t_sorted;   // host copy of sorted frames
-    std::vector<int32_t> perm;       // host copy of the order
-};
-
-struct hgm_scene {
-    uint32_t magic;
-    SceneDev d;
-    int32_t F_user;
-    std::vector<int32_t> perm;
-};
-
-namespace {
-
+namespace hgm {
+// Error reporting for other translation units of the library.
+hgm_status set_error(hgm_status s, const char *msg)
+{
+    g_err = msg;
+    return s;
+}
 bool valid_model(const hgm_model *m) { return m && m->magic == kModelMagic; }
 bool valid_scene(const hgm_scene *s) { return s && s->magic == kSceneMagic; }
+}  // namespace hgm
+
+namespace {
 
 hgm_status check_params(const hgm_params *p)
 {

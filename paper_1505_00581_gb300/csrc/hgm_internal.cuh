@@ -98,4 +98,30 @@ cudaError_t launch_count(const Unit *units, int64_t n_units, const ModelRec *mod
 void prof_begin(int kernel, cudaStream_t st);
 void prof_end(int kernel, cudaStream_t st);
 
+constexpr uint32_t kModelMagic = 0x4d4f444cu;   // "MODL"
+constexpr uint32_t kSceneMagic = 0x53434e45u;   // "SCNE"
+
+}  // namespace hgm
+
+// Handle layouts (opaque to callers of include/hgm.h).
+struct hgm_model {
+    uint32_t magic;
+    hgm::ModelDev d;
+    int32_t F_user;
+    std::vector<int32_t> t_sorted;   // host copy of sorted frames
+    std::vector<int32_t> perm;       // host copy of the order
+};
+
+struct hgm_scene {
+    uint32_t magic;
+    hgm::SceneDev d;
+    int32_t F_user;
+    std::vector<int32_t> perm;
+};
+
+namespace hgm {
+// api.cu: sets the thread's hgm_last_error() message and returns s.
+hgm_status set_error(hgm_status s, const char *msg);
+bool valid_model(const hgm_model *m);
+bool valid_scene(const hgm_scene *s);
 }  // namespace hgm

@@ -49,6 +49,7 @@ SIGNATURES = {
     "hgm_match": (_i32, [_vp, _vp, _PP, _vp, _p32, _p32, _vp, _vp]),
     "hgm_batch_layout": (_i32, [ctypes.POINTER(_vp), _i32, ctypes.POINTER(_vp), _i32, _PP, _p32, _p64, _p64]),
     "hgm_match_batch": (_i32, [ctypes.POINTER(_vp), _i32, ctypes.POINTER(_vp), _i32, _PP, _vp, _vp, _vp]),
+    "hgm_match_noalloc": (_i32, [_vp, _vp, _PP, _vp, _vp, _vp]),
     "hgm_model_order": (_i32, [_vp, _p32]),
     "hgm_scene_order": (_i32, [_vp, _p32]),
     "hgm_unary": (_i32, [_vp, _vp, _f32, _vp, _vp]),
@@ -219,6 +220,13 @@ def match(model: Model, scene: Scene, params: Params, energy=None, assign=None, 
     _check(lib.hgm_match(model.handle, scene.handle, ctypes.byref(params), _stream(stream), ctypes.byref(nn),
                          ctypes.byref(ff), pe, pa))
     return first, ke if energy is not None else None, ka if assign is not None else None
+
+
+def match_noalloc(model: Model, scene: Scene, params: Params, energy, assign, stream=None):
+    """hgm_match_noalloc: like match() with device outputs, but allocates no device memory (fixed scratch)."""
+    (pe, ke), (pa, ka) = _ptr(energy), _ptr(assign)
+    _check(load().hgm_match_noalloc(model.handle, scene.handle, ctypes.byref(params), _stream(stream), pe, pa))
+    return ke, ka
 
 
 def batch_layout(models: Sequence[Model], scenes: Sequence[Scene], params: Params):
