@@ -147,6 +147,22 @@ HGM_API hgm_status hgm_match_batch(const hgm_model *const *models, int32_t n_mod
                            int32_t n_scenes, const hgm_params *params, void *stream, float *energy,
                            int32_t *assign);
 
+/* ---- tuning ---------------------------------------------------------------- */
+
+/* The recursion kernel (Eq. 10) comes in tile variants that differ only in how
+ * many z_{i-2} cells one thread carries (0: 4, 1: 2, 2: 8); results are
+ * identical. hgm_autotune times every variant on this batch restricted to
+ * offsets [max(offset_lo, 0), +sample_offsets) (full pipeline, CUDA events,
+ * best of two after a warm-up), makes the fastest the process-wide choice and
+ * returns it; ms_per_variant (host, may be NULL) receives each variant's time
+ * (3 entries). hgm_set_recurse_variant restores
+ * a cached choice. */
+HGM_API hgm_status hgm_autotune(const hgm_model *const *models, int32_t n_models, const hgm_scene *const *scenes,
+                                int32_t n_scenes, const hgm_params *params, void *stream, int32_t sample_offsets,
+                                int32_t *best_variant, float *ms_per_variant);
+HGM_API hgm_status hgm_set_recurse_variant(int32_t variant);
+HGM_API int32_t hgm_get_recurse_variant(void);
+
 /* ---- matching without device allocation --------------------------------- */
 
 /* The paper has no counterpart to this entry point; it exists for callers
@@ -197,14 +213,35 @@ HGM_API hgm_status hgm_candidates(const hgm_model *model, const hgm_scene *scene
 HGM_API hgm_status hgm_count_triples(const hgm_model *model, const hgm_scene *scene, const hgm_params *params,
                              int32_t first, int32_t n, void *stream, int64_t *triples);
 
+/* The FP32 two-argument arctangent the recursion kernel uses for the angle
+ * tables of Eq. 6 (reading R1: atan2(0,0) = 0), applied elementwise:
+ * out[k] = atan2(y[k], x[k]). y, x, out: device arrays of n floats. A test
+ * hook, so that the function's error bound can be checked against FP64. */
+HGM_API hgm_status hgm_atan2_f32(const float *y, const float *x, int64_t n, void *stream, float *out);
+
+/* C = bf16(A) * bf16(B)^T, FP32 accumulation on the 5th-generation tensor cores
+ * (tcgen05.mma, accumulator in tensor memory): A [M x K], B [N x K], C [M x N],
+ * row-major FP32 device arrays; K a multiple of 16 in 16..256. A test hook
+ * that pins the shared-memory operand layout and the descriptors used by the
+ * BF16 kernels. *status (device int, caller-zeroed) becomes 1 if a bounded
+ * wait for the tensor core gave up (C is then incomplete). */
+HGM_API hgm_status hgm_gemm_bf16(const float *A, const float *B, int32_t M, int32_t N, int32_t K, void *stream,
+                                 float *C, int32_t *status);
+
 /* ---- profiling ----------------------------------------------------------- */
 
-/* When on, every launch of the four kernels below is bracketed by CUDA
+/* on = 1: every launch of the four kernels below is bracketed by CUDA
  * events on its stream and its duration accumulated:
  *   0 = unary distance, 1 = candidate selection, 2 = recursion, 3 = backtrack.
  * hgm_profile_read synchronises on the recorded events and returns, per
- * kernel, total milliseconds and launch count since the last reset. */
+ * kernel, total milliseconds and launch count since the last reset.
+ * on = 2: batch calls instead run the accounting variant of the recursion
+ * kernel (same results), which adds the number of (z_i, z_{i-1}, z_{i-2})
+ * evaluations its triple loop performs to a counter read by
+ * hgm_profile_evaluated. on = 0: off. */
 HGM_API hgm_status hgm_profile_enable(int32_t on);
+/* Reads (and with reset != 0, then clears) the evaluation counter of on = 2. */
+HGM_API hgm_status hgm_profile_evaluated(int64_t *evaluated, int32_t reset);
 HGM_API hgm_status hgm_profile_read(double *ms, int64_t *launches, int32_t n_kernels);
 HGM_API hgm_status hgm_profile_reset(void);
 

@@ -135,9 +135,10 @@ struct Buffer {
 };
 
 struct Workspace {
-    Buffer modelcat, U, cand_idx, cand_u, cand_cnt, beta, units, res, mrec, srec, counter, out_e, out_a;
+    Buffer modelcat, U, cand_idx, cand_u, cand_cnt, beta, units, res, mrec, srec, counter, out_e, out_a, evaluated;
 };
 Workspace g_ws;
+bool g_count_mode = false;   // hgm_profile_enable(2): batch runs use the accounting recursion variant
 
 }  // namespace
 
@@ -421,10 +422,18 @@ hgm_status run_batch(const hgm_model *const *models, int nm, const hgm_scene *co
         CK(launch_select(du, n, dm, ds, p, max_M, g_ws.cand_idx.as<int32_t>(), g_ws.cand_u.as<float>(),
                          g_ws.cand_cnt.as<int32_t>(), st),
            "select kernel");
-        CK(launch_recurse(du, n, dm, ds, p, g_ws.cand_idx.as<int32_t>(), g_ws.cand_u.as<float>(),
-                          g_ws.cand_cnt.as<int32_t>(), g_ws.beta.as<uint8_t>(), g_ws.res.as<UnitResult>(),
-                          g_ws.counter.as<int>(), st),
-           "recursion kernel");
+        if (g_count_mode) {
+            CK(g_ws.evaluated.ensure(sizeof(unsigned long long)), "workspace");
+            CK(launch_recurse_count(du, n, dm, ds, p, g_ws.cand_idx.as<int32_t>(), g_ws.cand_u.as<float>(),
+                                    g_ws.cand_cnt.as<int32_t>(), g_ws.beta.as<uint8_t>(), g_ws.res.as<UnitResult>(),
+                                    g_ws.counter.as<int>(), g_ws.evaluated.as<unsigned long long>(), st),
+               "recursion kernel (accounting)");
+        } else {
+            CK(launch_recurse(du, n, dm, ds, p, g_ws.cand_idx.as<int32_t>(), g_ws.cand_u.as<float>(),
+                              g_ws.cand_cnt.as<int32_t>(), g_ws.beta.as<uint8_t>(), g_ws.res.as<UnitResult>(),
+                              g_ws.counter.as<int>(), st),
+               "recursion kernel");
+        }
         CK(launch_backtrack(du, n, dm, ds, p, g_ws.cand_idx.as<int32_t>(), g_ws.beta.as<uint8_t>(),
                             g_ws.res.as<UnitResult>(), d_energy, d_assign, st),
            "backtrack kernel");
@@ -786,10 +795,83 @@ hgm_status hgm_count_triples(const hgm_model *model, const hgm_scene *scene, con
     return HGM_OK;
 }
 
+hgm_status hgm_set_recurse_variant(int32_t variant)
+{
+    g_err.clear();
+    if (variant < 0 || variant >= recurse_variant_count()) return fail(HGM_EINVAL, "variant out of range");
+    set_recurse_variant(variant);
+    return HGM_OK;
+}
+
+int32_t hgm_get_recurse_variant(void) { return get_recurse_variant(); }
+
+hgm_status hgm_autotune(const hgm_model *const *models, int32_t n_models, const hgm_scene *const *scenes,
+                        int32_t n_scenes, const hgm_params *params, void *stream, int32_t sample_offsets,
+                        int32_t *best_variant, float *ms_per_variant)
+{
+    std::lock_guard<std::mutex> lk(g_mu);
+    g_err.clear();
+    if (n_models < 1 || n_scenes < 1 || !models || !scenes || sample_offsets < 1)
+        return fail(HGM_EINVAL, "bad autotune arguments");
+    hgm_status rc = check_params(params);
+    if (rc) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    hgm_params ps = *params;
+    ps.offset_lo = std::max(params->offset_lo, 0);
+    ps.offset_hi = (int32_t)std::min<int64_t>(params->offset_hi, (int64_t)ps.offset_lo + sample_offsets - 1);
+    const int nv = recurse_variant_count();
+    const int keep = get_recurse_variant();
+    cudaEvent_t a = nullptr, b = nullptr;
+    CK(cudaEventCreate(&a), "event");
+    CK(cudaEventCreate(&b), "event");
+    float best_ms = 3.0e38f;
+    int best = keep;
+    for (int v = 0; v < nv; ++v) {
+        set_recurse_variant(v);
+        float vbest = 3.0e38f;
+        for (int rep = 0; rep < 3; ++rep) {          // first repetition is a warm-up
+            CK(cudaEventRecord(a, st), "event");
+            rc = run_batch(models, n_models, scenes, n_scenes, &ps, st, nullptr, nullptr);
+            if (rc) { set_recurse_variant(keep); cudaEventDestroy(a); cudaEventDestroy(b); return rc; }
+            CK(cudaEventRecord(b, st), "event");
+            CK(cudaEventSynchronize(b), "event");
+            float ms = 0.0f;
+            CK(cudaEventElapsedTime(&ms, a, b), "event");
+            if (rep > 0) vbest = std::min(vbest, ms);
+        }
+        if (ms_per_variant) ms_per_variant[v] = vbest;
+        if (vbest < best_ms) { best_ms = vbest; best = v; }
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    set_recurse_variant(best);
+    if (best_variant) *best_variant = best;
+    return HGM_OK;
+}
+
 hgm_status hgm_profile_enable(int32_t on)
 {
     std::lock_guard<std::mutex> lk(g_prof_mu);
-    g_prof_on = on != 0;
+    g_prof_on = on == 1;
+    g_count_mode = on == 2;
+    return HGM_OK;
+}
+
+hgm_status hgm_profile_evaluated(int64_t *evaluated, int32_t reset)
+{
+    std::lock_guard<std::mutex> lk(g_mu);
+    g_err.clear();
+    if (!evaluated) return fail(HGM_EINVAL, "evaluated is NULL");
+    *evaluated = 0;
+    if (!g_ws.evaluated.p) {
+        if (reset) CK(g_ws.evaluated.ensure(sizeof(unsigned long long)), "workspace");
+        else return HGM_OK;
+    }
+    CK(cudaDeviceSynchronize(), "synchronise");
+    unsigned long long v = 0;
+    CK(cudaMemcpy(&v, g_ws.evaluated.p, sizeof v, cudaMemcpyDeviceToHost), "read counter");
+    *evaluated = (int64_t)v;
+    if (reset) CK(cudaMemset(g_ws.evaluated.p, 0, sizeof v), "reset counter");
     return HGM_OK;
 }
 

@@ -87,6 +87,16 @@ cudaError_t launch_select(const Unit *units, int64_t n_units, const ModelRec *mo
 cudaError_t launch_recurse(const Unit *units, int64_t n_units, const ModelRec *models, const SceneRec *scenes,
                            Params p, const int32_t *cand_idx, const float *cand_u, const int32_t *cand_cnt,
                            uint8_t *beta, UnitResult *res, int *work_counter, cudaStream_t st);
+// Tile variant of the recursion kernel used by launch_recurse (autotuned): 0..count-1.
+int recurse_variant_count();
+void set_recurse_variant(int v);
+int get_recurse_variant();
+// Same as launch_recurse, additionally adding the number of (a, b, c) evaluations of
+// the triple loop to *evaluated (work accounting; not used on the timed path).
+cudaError_t launch_recurse_count(const Unit *units, int64_t n_units, const ModelRec *models, const SceneRec *scenes,
+                                 Params p, const int32_t *cand_idx, const float *cand_u, const int32_t *cand_cnt,
+                                 uint8_t *beta, UnitResult *res, int *work_counter, unsigned long long *evaluated,
+                                 cudaStream_t st);
 cudaError_t launch_backtrack(const Unit *units, int64_t n_units, const ModelRec *models, const SceneRec *scenes,
                              Params p, const int32_t *cand_idx, const uint8_t *beta, const UnitResult *res,
                              float *energy, int32_t *assign, cudaStream_t st);

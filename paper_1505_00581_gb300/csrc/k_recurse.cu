@@ -10,32 +10,38 @@
 // the CPU as global barrier, Sec. 3.1): one CTA owns a whole unit for its
 // lifetime and steps i with CTA barriers; CTAs are persistent and take units
 // from a global counter in decreasing-size order. Everything a step touches
-// lives in shared memory (Sec. 3.5's local-memory rows, extended to the
-// whole alpha_{i+1} table and the geometry):
-//   sAB[a][b] = (U(a) + lambda2*Delta(i,i-1) + alpha_{i+1}(a,b),  wrap(A1 + theta(b->a)))
-//   sR [a][c] = theta(a->c)
-//   per cell (b,c) in registers: theta(b->c)
-// where theta(p->q) = atan2(q-p) and A1, A2 are the model's angles at i-1 and
-// at i. The angle differences of Eq. 6 become
+// lives in shared memory (Sec. 3.5's local-memory rows, extended to the whole
+// alpha table and the geometry). Writing theta(p->q) = atan2(q-p) and A1, A2
+// for the model's angles at i-1 and at i, the angle differences of Eq. 6 are
 //   d1 = wrap(A1 + theta(b->a) - theta(b->c)),  d2 = wrap(A2 + theta(a->b) - theta(a->c))
-// so a triple costs two subtractions, two circular folds, one FMA for the
-// squared norm, one square root and one FMA -- every pair-only term is hoisted
-// into the tables (Sec. 3.3's look-up idea applied to the geometry too).
-// Infeasible pairs carry +inf in the tables (causality t'(c)<=t'(b)<=t'(a),
-// closeness t'(a)-t'(c) < T, distinct points; Eqs. 7-8, Sec. 3.2's validity
-// mask) and the a-loop starts at the first a with t'(a) >= t'(b) (Sec. 3.4's
-// minnode bound on a list sorted by frame).
+// so that, with every pair-only term hoisted (Sec. 3.3's look-up idea applied
+// to the geometry), a triple costs two subtractions, two circular folds, a
+// squared norm, a square root and an FMA:
+//   base(a,b) = U(a) + lambda2 Delta(i,i-1) + alpha_{i+1}(a,b),  p1(a,b) = wrap(A1 + theta(b->a))
+//   v(a,b,c)  = base(a,b) + lambda2 lambda3 sqrt(d1^2 + d2^2)   [+ lambda2 Delta(i-1,i-2), after the min]
+// Infeasible pairs are +inf (causality t'(c)<=t'(b)<=t'(a), closeness
+// t'(a)-t'(c) < T, distinct points; Eqs. 7-8, Sec. 3.2's validity mask).
 //
-// Work split per step: tiles of one b and CT consecutive c (a register tile),
-// only for c with t'(c) <= t'(b), flattened across the CTA's threads. Each
-// thread loops a in increasing slot order with a strict '<', so the lowest
-// slot wins exact ties, as in the oracle.
+// Exact branch and bound: the geometric term is bounded, 0 <= D^g <= pi*sqrt(2),
+// so v(a,b,c) >= base(a,b), and any a with base(a,b) > base(w,b) + lambda2
+// lambda3 pi sqrt(2) (plus rounding slack) can never beat a feasible witness w.
+// Per b, the witness is the a of smallest base; for the rare c where it is
+// infeasible, the smallest base feasible with c raises the threshold. Only the
+// kept a (about a quarter on the paper-shaped workloads) enter the triple
+// loop, in increasing slot order with a strict '<', so the lowest slot still
+// wins exact ties -- the result is bit-identical to the full minimisation.
+//
+// Work split per step: warps build the kept lists of one b each; then tiles
+// of one b and CT consecutive c with t'(c) <= t'(b) are flattened across the
+// CTA's threads, each thread looping over the kept a of its b.
+#include "fast_math.cuh"
 #include "hgm_internal.cuh"
 
 namespace hgm {
 namespace {
 
 constexpr float kInf = __builtin_huge_valf();
+constexpr float kGeoMax = 4.45f;   // > pi*sqrt(2) = 4.4429, bound of the FP32 D^g
 
 __device__ __forceinline__ float sqrt_fast(float x)
 {
@@ -52,6 +58,13 @@ __device__ __forceinline__ float wrap_pi(float v)
     return v;
 }
 
+__device__ __forceinline__ uint32_t lanemask_lt()
+{
+    uint32_t m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
 template <int KM>
 struct List {
     float2 xy[KM];
@@ -61,17 +74,22 @@ struct List {
     int32_t n;
 };
 
-template <int KM, int NT, int CT>
+template <int KM, int NT>
 struct Smem {
-    static constexpr int RS = KM + 4;     // row stride of sR (bank skew, 16-byte rows)
-    float2 ab[KM * KM];                   // (base, p1) indexed a*KM + b
-    float r[KM * RS];                     // theta(a->c), indexed a*RS + c
-    float alpha[KM * KM];                 // alpha_{i+1}(a,b) at a*KM+b; alpha_i(b,c) written at b*KM+c
-    List<KM> list[3];
-    int32_t lo[KM];                       // first a with t'(a) >= t'(b)
+    static constexpr int RS = KM + 4;     // row stride of r (16-byte rows, bank skew)
+    float2 fb[KM * KM];                   // per b: kept (base, p1) in increasing a, at b*KM + k
+    float r[KM * RS];                     // theta(a->c) or +inf, at a*RS + c
+    static constexpr int AS = KM + 1;     // row stride of alpha (conflict-free row and column access)
+    float alpha[KM * AS];                 // alpha_{i+1}(a,b) at b*AS + a; alpha_i(b,c) written at c*AS + b
+    uint8_t fs[KM * KM];                  // slot a of each kept entry
+    uint8_t used[KM];                     // a kept for some b (its r row is needed)
+    int32_t fn[KM];                       // number of kept a per b
     int32_t pre[KM + 1];                  // tile prefix over b
+    List<KM> list[3];
     float red_v[NT / 32];
     int32_t red_k[NT / 32];
+    float A1, k2;
+    int32_t dt_ab, dt_bc;
     int32_t unit;
 };
 
@@ -96,36 +114,49 @@ __device__ void load_list(List<KM> &L, const SceneRec &sc, const int32_t *cidx, 
     if (tid == 0) L.n = n;
 }
 
-__device__ __forceinline__ float model_angle(float2 v, float2 p, float2 q)
+__device__ __forceinline__ float signed_angle(float2 v, float2 p, float2 q)
 {
-    // signed angle at v from v->p to v->q (reading R1), wrapped to [-pi, pi]
-    float a = atan2f(q.y - v.y, q.x - v.x) - atan2f(p.y - v.y, p.x - v.x);
-    return wrap_pi(a);
+    // angle at v from v->p to v->q (reading R1), wrapped to [-pi, pi]
+    return wrap_pi(fast_atan2(q.y - v.y, q.x - v.x) - fast_atan2(p.y - v.y, p.x - v.x));
 }
 
-template <int KM, int NT, int CT>
-__global__ void __launch_bounds__(NT) recurse_kernel(const Unit *__restrict__ units, int64_t n_units,
-                                                     const ModelRec *__restrict__ models,
-                                                     const SceneRec *__restrict__ scenes, Params p,
-                                                     const int32_t *__restrict__ cand_idx,
-                                                     const float *__restrict__ cand_u,
-                                                     const int32_t *__restrict__ cand_cnt,
-                                                     uint8_t *__restrict__ beta, UnitResult *__restrict__ res,
-                                                     int *__restrict__ work_counter)
+// (value, slot) minimum with ties to the lower slot
+__device__ __forceinline__ void argmin_merge(float &v, int &k, float ov, int ok)
 {
+    if (ov < v || (ov == v && ok < k)) { v = ov; k = ok; }
+}
+
+// kCount = true builds the accounting variant: identical work, plus a count of
+// the (a, b, c) evaluations the triple loop performs (kept a x CT per tile).
+template <int KM, int NT, int CT, bool kCount>
+__global__ void __launch_bounds__(NT, (KM > 32 ? 3 : 4))
+recurse_kernel(const Unit *__restrict__ units, int64_t n_units, const ModelRec *__restrict__ models,
+               const SceneRec *__restrict__ scenes, Params p, const int32_t *__restrict__ cand_idx,
+               const float *__restrict__ cand_u, const int32_t *__restrict__ cand_cnt, uint8_t *__restrict__ beta,
+               UnitResult *__restrict__ res, int *__restrict__ work_counter, unsigned long long *__restrict__ evaluated)
+{
+    unsigned long long n_eval = 0;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    Smem<KM, NT, CT> &sm = *reinterpret_cast<Smem<KM, NT, CT> *>(smem_raw);
-    constexpr int RS = Smem<KM, NT, CT>::RS;
-    const int tid = threadIdx.x;
+    Smem<KM, NT> &sm = *reinterpret_cast<Smem<KM, NT> *>(smem_raw);
+    constexpr int RS = Smem<KM, NT>::RS;
+    constexpr int AS = Smem<KM, NT>::AS;
+    constexpr int AQ = KM / 32;            // slots per lane in warp-wide passes
+    constexpr int NW = NT / 32;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int K = p.K;
+    const int T = p.T;
     const float lam2 = p.lambda2;
     const float lam23 = p.lambda2 * p.lambda3;
+    const float gmax = lam23 * kGeoMax;
 
     for (;;) {
         if (tid == 0) sm.unit = atomicAdd(work_counter, 1);
         __syncthreads();
         const int64_t u = sm.unit;
-        if (u >= n_units) break;
+        if (u >= n_units) {
+            if constexpr (kCount) atomicAdd(evaluated, n_eval);
+            break;
+        }
         const Unit un = units[u];
         const ModelRec md = models[un.model];
         const SceneRec sc = scenes[un.scene];
@@ -136,7 +167,7 @@ __global__ void __launch_bounds__(NT) recurse_kernel(const Unit *__restrict__ un
         uint8_t *ubeta = beta + un.beta;
 
         // alpha_{M+1} == 0 (Eq. 11)
-        for (int e = tid; e < KM * KM; e += NT) sm.alpha[e] = 0.0f;
+        for (int e = tid; e < KM * AS; e += NT) sm.alpha[e] = 0.0f;
         load_list<KM>(sm.list[(M - 1) % 3], sc, cidx + (int64_t)(M - 1) * K, cu + (int64_t)(M - 1) * K,
                       ccnt[M - 1], tid, NT);
         load_list<KM>(sm.list[(M - 2) % 3], sc, cidx + (int64_t)(M - 2) * K, cu + (int64_t)(M - 2) * K,
@@ -146,147 +177,222 @@ __global__ void __launch_bounds__(NT) recurse_kernel(const Unit *__restrict__ un
             List<KM> &LA = sm.list[i % 3];
             List<KM> &LB = sm.list[(i - 1) % 3];
             List<KM> &LC = sm.list[(i - 2) % 3];
+            // ---- phase 0: new list, model constants of hyperedge (i, i-1, i-2)
             load_list<KM>(LC, sc, cidx + (int64_t)(i - 2) * K, cu + (int64_t)(i - 2) * K, ccnt[i - 2], tid, NT);
+            if (tid < KM) sm.used[tid] = 0;
+            if (tid == 0) {
+                const float2 mi = md.xy[i], mj = md.xy[i - 1], mk = md.xy[i - 2];
+                const float A1 = signed_angle(mj, mi, mk);   // at i-1, from ->i to ->i-2
+                const float A2 = signed_angle(mi, mj, mk);   // at i, from ->i-1 to ->i-2
+                sm.A1 = A1;
+                sm.k2 = wrap_pi(A2 - A1 + kPi);              // p2 = p1 + k2 (mod 2pi)
+                sm.dt_ab = md.t[i] - md.t[i - 1];
+                sm.dt_bc = md.t[i - 1] - md.t[i - 2];
+            }
             __syncthreads();
             const int na = LA.n, nb = LB.n, nc = LC.n;
+            const float A1 = sm.A1, k2 = sm.k2;
+            const int dt_ab = sm.dt_ab, dt_bc = sm.dt_bc;
 
-            // per-b loop bound and number of c-tiles (c with t'(c) <= t'(b) form a prefix)
-            if (tid < KM) {
-                int b = tid, lo = 0, nq = 0;
-                if (b < nb) {
-                    int tb = LB.t[b];
-                    while (lo < na && LA.t[lo] < tb) ++lo;
-                    int cc = 0;
-                    while (cc < nc && LC.t[cc] <= tb) ++cc;
-                    nq = (cc + CT - 1) / CT;
-                }
-                sm.lo[b] = lo;
-                sm.pre[b + 1] = nq;
+            // ---- phase 1: per b (one warp each) the kept a list and the tile count
+            // per-lane data of the lane's a and c slots, shared by every b of the warp
+            int la_t[AQ], la_i[AQ], lc_t[AQ], lc_i[AQ];
+            float la_u[AQ];
+#pragma unroll
+            for (int q = 0; q < AQ; ++q) {
+                const int a = lane + 32 * q;
+                la_t[q] = LA.t[a];
+                la_i[q] = LA.idx[a];
+                la_u[q] = LA.u[a];
+                lc_t[q] = a < nc ? LC.t[a] : 0x7fffffff;   // c outside the list never qualifies
+                lc_i[q] = LC.idx[a];
             }
-            // model geometry of hyperedge (i, i-1, i-2)
-            const float2 mi = md.xy[i], mj = md.xy[i - 1], mk = md.xy[i - 2];
-            const float A1 = model_angle(mj, mi, mk);   // at i-1, from ->i to ->i-2
-            const float A2 = model_angle(mi, mj, mk);   // at i, from ->i-1 to ->i-2
-            const float k2 = wrap_pi(A2 - A1 + kPi);    // p2 = p1 + k2 (mod 2pi)
-            const int dt_ab = md.t[i] - md.t[i - 1];
-            const int dt_bc = md.t[i - 1] - md.t[i - 2];
+            for (int b = warp; b < KM; b += NW) {
+                if (b >= nb) {
+                    if (lane == 0) { sm.fn[b] = 0; sm.pre[b + 1] = 0; }
+                    continue;
+                }
+                const float2 pb = LB.xy[b];
+                const int tb = LB.t[b], ib = LB.idx[b];
+                float base[AQ];
+                float bv = kInf;
+                int bk = 0x7fffffff;
+#pragma unroll
+                for (int q = 0; q < AQ; ++q) {
+                    const int a = lane + 32 * q;
+                    base[q] = kInf;
+                    if (a < na && la_t[q] >= tb && la_i[q] != ib)
+                        base[q] = la_u[q] + lam2 * fabsf((float)(dt_ab - (la_t[q] - tb))) + sm.alpha[b * AS + a];
+                    argmin_merge(bv, bk, base[q], a);
+                }
+#pragma unroll
+                for (int off = 16; off > 0; off >>= 1)
+                    argmin_merge(bv, bk, __shfl_xor_sync(0xffffffffu, bv, off), __shfl_xor_sync(0xffffffffu, bk, off));
+                // c with t'(c) <= t'(b) form a prefix of C: tiles cover it
+                uint32_t cm[AQ];
+                int ccount = 0;
+#pragma unroll
+                for (int q = 0; q < AQ; ++q) {
+                    cm[q] = __ballot_sync(0xffffffffu, lc_t[q] <= tb);
+                    ccount += __popc(cm[q]);
+                }
+                if (lane == 0) sm.pre[b + 1] = (ccount + CT - 1) / CT;
+                if (!(bv < kInf)) {
+                    if (lane == 0) sm.fn[b] = 0;
+                    continue;
+                }
+                float thr = bv + gmax + 1e-6f * bv;
+                // cells (b,c) whose witness bk is infeasible: raise thr by their own best feasible base
+                const int tw = LA.t[bk], iw = LA.idx[bk];
+                uint32_t bad[AQ];
+#pragma unroll
+                for (int q = 0; q < AQ; ++q) {
+                    const bool bd = lc_t[q] <= tb && lc_i[q] != ib && ((T > 0 && tw - lc_t[q] >= T) || iw == lc_i[q]);
+                    bad[q] = __ballot_sync(0xffffffffu, bd);
+                }
+#pragma unroll
+                for (int q = 0; q < AQ; ++q) {
+                    while (bad[q]) {
+                        const int c = __ffs(bad[q]) - 1 + 32 * q;
+                        bad[q] &= bad[q] - 1;
+                        const int tc = LC.t[c], ic = LC.idx[c];
+                        float mv = kInf;
+#pragma unroll
+                        for (int qa = 0; qa < AQ; ++qa) {
+                            if (!((T > 0 && la_t[qa] - tc >= T) || la_i[qa] == ic)) mv = fminf(mv, base[qa]);
+                        }
+#pragma unroll
+                        for (int off = 16; off > 0; off >>= 1) mv = fminf(mv, __shfl_xor_sync(0xffffffffu, mv, off));
+                        if (mv < kInf) thr = fmaxf(thr, mv + gmax + 1e-6f * mv);
+                    }
+                }
+                // keep base <= thr, compacted in increasing a
+                int kept = 0;
+#pragma unroll
+                for (int q = 0; q < AQ; ++q) {
+                    const int a = lane + 32 * q;
+                    const bool keep = base[q] <= thr;
+                    const uint32_t km = __ballot_sync(0xffffffffu, keep);
+                    if (keep) {
+                        const int pos = kept + __popc(km & lanemask_lt());
+                        const float2 pa = LA.xy[a];
+                        const float p1 = wrap_pi(A1 + fast_atan2(pa.y - pb.y, pa.x - pb.x));   // theta(b->a)
+                        sm.fb[b * KM + pos] = make_float2(base[q], p1);
+                        sm.fs[b * KM + pos] = (uint8_t)a;
+                        sm.used[a] = 1;
+                    }
+                    kept += __popc(km);
+                }
+                if (lane == 0) sm.fn[b] = kept;
+            }
             __syncthreads();
-            if (tid < 32) {
-                // exclusive scan of tile counts over b (KM <= 64: two per lane)
-                int v0 = (2 * tid + 1 <= KM) ? sm.pre[2 * tid + 1] : 0;
-                int v1 = (2 * tid + 2 <= KM) ? sm.pre[2 * tid + 2] : 0;
-                int s = v0 + v1, incl = s;
+
+            // ---- phase 2: tile prefix; theta(a->c) rows of the kept a
+            if (warp == 0) {
+                int v[AQ], s = 0;
+#pragma unroll
+                for (int q = 0; q < AQ; ++q) { v[q] = sm.pre[1 + lane * AQ + q]; s += v[q]; }
+                int incl = s;
 #pragma unroll
                 for (int off = 1; off < 32; off <<= 1) {
                     int w = __shfl_up_sync(0xffffffffu, incl, off);
-                    if (tid >= off) incl += w;
+                    if (lane >= off) incl += w;
                 }
-                int excl = incl - s;
-                if (2 * tid + 1 <= KM) sm.pre[2 * tid + 1] = excl + v0;
-                if (2 * tid + 2 <= KM) sm.pre[2 * tid + 2] = excl + v0 + v1;
-                if (tid == 0) sm.pre[0] = 0;
+                int run = incl - s;
+#pragma unroll
+                for (int q = 0; q < AQ; ++q) { run += v[q]; sm.pre[1 + lane * AQ + q] = run; }
+                if (lane == 0) sm.pre[0] = 0;
             }
-            // tables
-            for (int e = tid; e < KM * KM; e += NT) {
-                int a = e / KM, b = e % KM;
-                if (a < na && b < nb) {
-                    float2 pa = LA.xy[a], pb = LB.xy[b];
-                    float th = atan2f(pa.y - pb.y, pa.x - pb.x);            // theta(b->a)
-                    float p1 = wrap_pi(A1 + th);
-                    int ta = LA.t[a], tb = LB.t[b];
-                    float base = kInf;
-                    if (ta >= tb && LA.idx[a] != LB.idx[b]) {
-                        float dt = fabsf((float)(dt_ab - (ta - tb)));
-                        base = LA.u[a] + lam2 * dt + sm.alpha[a * KM + b];
+            for (int e = tid; e < na * KM; e += NT) {
+                const int a = e / KM, c = e % KM;
+                if (!sm.used[a]) continue;
+                float r = kInf;
+                if (c < nc) {
+                    const int ta = LA.t[a], tc = LC.t[c];
+                    if (!(T > 0 && ta - tc >= T) && LA.idx[a] != LC.idx[c]) {
+                        const float2 pa = LA.xy[a], pc = LC.xy[c];
+                        r = fast_atan2(pc.y - pa.y, pc.x - pa.x);           // theta(a->c)
                     }
-                    sm.ab[a * KM + b] = make_float2(base, p1);
                 }
-                int c = b;
-                if (a < na && c < nc) {
-                    int ta = LA.t[a], tc = LC.t[c];
-                    float r = kInf;
-                    if (!(p.T > 0 && ta - tc >= p.T) && LA.idx[a] != LC.idx[c]) {
-                        float2 pa = LA.xy[a], pc = LC.xy[c];
-                        r = atan2f(pc.y - pa.y, pc.x - pa.x);               // theta(a->c)
-                    }
-                    sm.r[a * RS + c] = r;
-                } else if (a < KM && c < KM) {
-                    sm.r[a * RS + c] = kInf;
-                }
+                sm.r[a * RS + c] = r;
             }
             __syncthreads();
 
-            const int ntile = nb > 0 ? sm.pre[nb] : 0;
+            // ---- phase 3: tiles (b, CT consecutive c)
+            const int ntile = sm.pre[nb];
             uint8_t *bstep = ubeta + (int64_t)(i - 2) * K * K;
             for (int tile = tid; tile < ntile; tile += NT) {
-                // b = last index with pre[b] <= tile
                 int lo_b = 0, hi_b = nb;
                 while (hi_b - lo_b > 1) {
-                    int mid = (lo_b + hi_b) >> 1;
+                    const int mid = (lo_b + hi_b) >> 1;
                     if (sm.pre[mid] <= tile) lo_b = mid; else hi_b = mid;
                 }
                 const int b = lo_b;
                 const int c0 = (tile - sm.pre[b]) * CT;
                 const float2 pb = LB.xy[b];
-                const int tb = LB.t[b];
-                const int ib = LB.idx[b];
+                const int tb = LB.t[b], ib = LB.idx[b];
                 float q1[CT], best[CT];
                 int arg[CT];
 #pragma unroll
                 for (int k = 0; k < CT; ++k) {
-                    int c = c0 + k;
-                    bool ok = c < nc && LC.t[c] <= tb && LC.idx[c] != ib;
-                    q1[k] = ok ? atan2f(LC.xy[c].y - pb.y, LC.xy[c].x - pb.x) : kInf;   // theta(b->c)
+                    const int c = c0 + k;
+                    const bool ok = c < nc && LC.t[c] <= tb && LC.idx[c] != ib;
+                    q1[k] = ok ? fast_atan2(LC.xy[c].y - pb.y, LC.xy[c].x - pb.x) : kInf;   // theta(b->c)
                     best[k] = kInf;
                     arg[k] = kNoSlot;
                 }
-                for (int a = sm.lo[b]; a < na; ++a) {
-                    const float2 abv = sm.ab[a * KM + b];
-                    const float p2 = abv.y + k2;
+                const int nf = sm.fn[b];
+                if constexpr (kCount) n_eval += (unsigned long long)nf * CT;
+                const float2 *fbb = sm.fb + b * KM;
+                const uint8_t *fsb = sm.fs + b * KM;
+#pragma unroll 2
+                for (int k = 0; k < nf; ++k) {
+                    const float2 e = fbb[k];
+                    const int a = fsb[k];
+                    const float p2 = e.y + k2;
                     float rv[CT];
-                    if constexpr (CT == 4) {
-                        float4 r4 = *reinterpret_cast<const float4 *>(&sm.r[a * RS + c0]);
-                        rv[0] = r4.x; rv[1] = r4.y; rv[2] = r4.z; rv[3] = r4.w;
-                    } else {
 #pragma unroll
-                        for (int k = 0; k < CT; ++k) rv[k] = sm.r[a * RS + c0 + k];
+                    for (int q4 = 0; q4 < CT; q4 += 4) {
+                        if constexpr (CT >= 4) {
+                            const float4 r4 = *reinterpret_cast<const float4 *>(&sm.r[a * RS + c0 + q4]);
+                            rv[q4] = r4.x; rv[q4 + 1] = r4.y; rv[q4 + 2] = r4.z; rv[q4 + 3] = r4.w;
+                        }
+                    }
+                    if constexpr (CT == 2) {
+                        const float2 r2 = *reinterpret_cast<const float2 *>(&sm.r[a * RS + c0]);
+                        rv[0] = r2.x; rv[1] = r2.y;
                     }
 #pragma unroll
-                    for (int k = 0; k < CT; ++k) {
-                        float d1 = abv.y - q1[k];
-                        float d2 = p2 - rv[k];
-                        float w1 = fminf(fabsf(d1), kTwoPi - fabsf(d1));
-                        float w2 = fminf(fabsf(d2), kTwoPi - fabsf(d2));
-                        float s = fmaf(w2, w2, w1 * w1);
-                        float v = fmaf(lam23, sqrt_fast(s), abv.x);
-                        if (v < best[k]) { best[k] = v; arg[k] = a; }
+                    for (int q = 0; q < CT; ++q) {
+                        const float d1 = e.y - q1[q];
+                        const float d2 = p2 - rv[q];
+                        const float w1 = fminf(fabsf(d1), kTwoPi - fabsf(d1));
+                        const float w2 = fminf(fabsf(d2), kTwoPi - fabsf(d2));
+                        const float v = fmaf(lam23, sqrt_fast(fmaf(w2, w2, w1 * w1)), e.x);
+                        if (v < best[q]) { best[q] = v; arg[q] = a; }
                     }
                 }
 #pragma unroll
-                for (int k = 0; k < CT; ++k) {
-                    int c = c0 + k;
+                for (int q = 0; q < CT; ++q) {
+                    const int c = c0 + q;
                     if (c < nc) {
                         float al = kInf;
                         int bt = kNoSlot;
-                        if (best[k] < kInf) {
-                            float dt = fabsf((float)(dt_bc - (tb - LC.t[c])));
-                            al = best[k] + lam2 * dt;
-                            bt = arg[k];
+                        if (best[q] < kInf) {
+                            al = best[q] + lam2 * fabsf((float)(dt_bc - (tb - LC.t[c])));
+                            bt = arg[q];
                         }
-                        sm.alpha[b * KM + c] = al;
+                        sm.alpha[c * AS + b] = al;
                         bstep[b * K + c] = (uint8_t)bt;
                     }
                 }
             }
             // cells (b, c) beyond the tiled prefix are infeasible
-            for (int e = tid; e < KM * KM; e += NT) {
-                int b = e / KM, c = e % KM;
-                if (b < nb && c < nc) {
-                    int covered = (sm.pre[b + 1] - sm.pre[b]) * CT;
-                    if (c >= covered) {
-                        sm.alpha[b * KM + c] = kInf;
-                        bstep[b * K + c] = (uint8_t)kNoSlot;
-                    }
+            for (int b = warp; b < nb; b += NW) {
+                const int covered = (sm.pre[b + 1] - sm.pre[b]) * CT;
+                for (int c = covered + lane; c < nc; c += 32) {
+                    sm.alpha[c * AS + b] = kInf;
+                    bstep[b * K + c] = (uint8_t)kNoSlot;
                 }
             }
             __syncthreads();
@@ -300,27 +406,16 @@ __global__ void __launch_bounds__(NT) recurse_kernel(const Unit *__restrict__ un
             float bv = kInf;
             int bk = 0x7fffffff;
             for (int e = tid; e < KM * KM; e += NT) {
-                int c = e / KM, b = e % KM;    // e = z1 * KM + z2: lexicographic order
-                if (c < n0 && b < n1) {
-                    float v = L0.u[c] + L1.u[b] + sm.alpha[b * KM + c];
-                    if (v < bv || (v == bv && e < bk)) { bv = v; bk = e; }
-                }
+                const int c = e / KM, b = e % KM;    // e = z1 * KM + z2: lexicographic order
+                if (c < n0 && b < n1) argmin_merge(bv, bk, L0.u[c] + L1.u[b] + sm.alpha[c * AS + b], e);
             }
 #pragma unroll
-            for (int off = 16; off > 0; off >>= 1) {
-                float ov = __shfl_xor_sync(0xffffffffu, bv, off);
-                int ok = __shfl_xor_sync(0xffffffffu, bk, off);
-                if (ov < bv || (ov == bv && ok < bk)) { bv = ov; bk = ok; }
-            }
-            if ((tid & 31) == 0) { sm.red_v[tid >> 5] = bv; sm.red_k[tid >> 5] = bk; }
+            for (int off = 16; off > 0; off >>= 1)
+                argmin_merge(bv, bk, __shfl_xor_sync(0xffffffffu, bv, off), __shfl_xor_sync(0xffffffffu, bk, off));
+            if (lane == 0) { sm.red_v[warp] = bv; sm.red_k[warp] = bk; }
             __syncthreads();
             if (tid == 0) {
-                for (int w = 1; w < NT / 32; ++w) {
-                    float ov = sm.red_v[w];
-                    int ok = sm.red_k[w];
-                    if (ov < bv || (ov == bv && ok < bk)) { bv = ov; bk = ok; }
-                }
-                sm.red_v[0] = bv; sm.red_k[0] = bk;
+                for (int w = 1; w < NW; ++w) argmin_merge(bv, bk, sm.red_v[w], sm.red_k[w]);
                 UnitResult r;
                 r.pad = 0;
                 if (bv < kInf) {
@@ -339,44 +434,78 @@ __global__ void __launch_bounds__(NT) recurse_kernel(const Unit *__restrict__ un
     }
 }
 
-template <int KM, int NT, int CT>
+template <int KM, int NT, int CT, bool kCount>
 cudaError_t launch_recurse_t(const Unit *units, int64_t n_units, const ModelRec *models, const SceneRec *scenes,
                              Params p, const int32_t *cand_idx, const float *cand_u, const int32_t *cand_cnt,
-                             uint8_t *beta, UnitResult *res, int *work_counter, cudaStream_t st)
+                             uint8_t *beta, UnitResult *res, int *work_counter, unsigned long long *evaluated,
+                             cudaStream_t st)
 {
-    auto kern = recurse_kernel<KM, NT, CT>;
-    const size_t smem = sizeof(Smem<KM, NT, CT>);
+    auto kern = recurse_kernel<KM, NT, CT, kCount>;
+    const size_t smem = sizeof(Smem<KM, NT>);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int dev = 0, sms = 0, per_sm = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, smem);
-    if (e != cudaSuccess) return e;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, smem)) != cudaSuccess) return e;
     if (per_sm < 1) per_sm = 1;
     int64_t grid = (int64_t)sms * per_sm;
     if (grid > n_units) grid = n_units;
-    e = cudaMemsetAsync(work_counter, 0, sizeof(int), st);
-    if (e != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(work_counter, 0, sizeof(int), st)) != cudaSuccess) return e;
     prof_begin(kProfRecurse, st);
     kern<<<(unsigned)grid, NT, smem, st>>>(units, n_units, models, scenes, p, cand_idx, cand_u, cand_cnt, beta, res,
-                                           work_counter);
+                                           work_counter, evaluated);
     prof_end(kProfRecurse, st);
     return cudaGetLastError();
 }
 
+template <bool kCount>
+cudaError_t dispatch(int variant, const Unit *units, int64_t n_units, const ModelRec *models, const SceneRec *scenes,
+                     Params p, const int32_t *cand_idx, const float *cand_u, const int32_t *cand_cnt, uint8_t *beta,
+                     UnitResult *res, int *work_counter, unsigned long long *evaluated, cudaStream_t st)
+{
+    if (p.K <= 32) {
+        if (variant == 1)
+            return launch_recurse_t<32, 128, 2, kCount>(units, n_units, models, scenes, p, cand_idx, cand_u, cand_cnt,
+                                                        beta, res, work_counter, evaluated, st);
+        return launch_recurse_t<32, 128, 4, kCount>(units, n_units, models, scenes, p, cand_idx, cand_u, cand_cnt,
+                                                    beta, res, work_counter, evaluated, st);
+    }
+    if (variant == 1)
+        return launch_recurse_t<64, 256, 2, kCount>(units, n_units, models, scenes, p, cand_idx, cand_u, cand_cnt,
+                                                    beta, res, work_counter, evaluated, st);
+    if (variant == 2)
+        return launch_recurse_t<64, 256, 8, kCount>(units, n_units, models, scenes, p, cand_idx, cand_u, cand_cnt,
+                                                    beta, res, work_counter, evaluated, st);
+    return launch_recurse_t<64, 256, 4, kCount>(units, n_units, models, scenes, p, cand_idx, cand_u, cand_cnt, beta,
+                                                res, work_counter, evaluated, st);
+}
+
+int g_variant = 0;   // recursion tile variant: 0 = 4 c per tile, 1 = 2, 2 = 8 (K > 32 only)
+
 }  // namespace
+
+int recurse_variant_count() { return 3; }
+void set_recurse_variant(int v) { g_variant = (v >= 0 && v < 3) ? v : 0; }
+int get_recurse_variant() { return g_variant; }
 
 cudaError_t launch_recurse(const Unit *units, int64_t n_units, const ModelRec *models, const SceneRec *scenes,
                            Params p, const int32_t *cand_idx, const float *cand_u, const int32_t *cand_cnt,
                            uint8_t *beta, UnitResult *res, int *work_counter, cudaStream_t st)
 {
     if (n_units <= 0) return cudaSuccess;
-    if (p.K <= 32)
-        return launch_recurse_t<32, 128, 4>(units, n_units, models, scenes, p, cand_idx, cand_u, cand_cnt, beta,
-                                            res, work_counter, st);
-    return launch_recurse_t<64, 256, 4>(units, n_units, models, scenes, p, cand_idx, cand_u, cand_cnt, beta, res,
-                                        work_counter, st);
+    return dispatch<false>(g_variant, units, n_units, models, scenes, p, cand_idx, cand_u, cand_cnt, beta, res,
+                           work_counter, nullptr, st);
+}
+
+cudaError_t launch_recurse_count(const Unit *units, int64_t n_units, const ModelRec *models, const SceneRec *scenes,
+                                 Params p, const int32_t *cand_idx, const float *cand_u, const int32_t *cand_cnt,
+                                 uint8_t *beta, UnitResult *res, int *work_counter, unsigned long long *evaluated,
+                                 cudaStream_t st)
+{
+    if (n_units <= 0) return cudaSuccess;
+    return dispatch<true>(g_variant, units, n_units, models, scenes, p, cand_idx, cand_u, cand_cnt, beta, res,
+                          work_counter, evaluated, st);
 }
 
 }  // namespace hgm

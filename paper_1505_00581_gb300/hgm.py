@@ -50,13 +50,19 @@ SIGNATURES = {
     "hgm_batch_layout": (_i32, [ctypes.POINTER(_vp), _i32, ctypes.POINTER(_vp), _i32, _PP, _p32, _p64, _p64]),
     "hgm_match_batch": (_i32, [ctypes.POINTER(_vp), _i32, ctypes.POINTER(_vp), _i32, _PP, _vp, _vp, _vp]),
     "hgm_match_noalloc": (_i32, [_vp, _vp, _PP, _vp, _vp, _vp]),
+    "hgm_autotune": (_i32, [ctypes.POINTER(_vp), _i32, ctypes.POINTER(_vp), _i32, _PP, _vp, _i32, _p32, _pf]),
+    "hgm_set_recurse_variant": (_i32, [_i32]),
+    "hgm_get_recurse_variant": (_i32, []),
     "hgm_model_order": (_i32, [_vp, _p32]),
     "hgm_scene_order": (_i32, [_vp, _p32]),
     "hgm_unary": (_i32, [_vp, _vp, _f32, _vp, _vp]),
     "hgm_candidates": (_i32, [_vp, _vp, _PP, _i32, _i32, _vp, _vp, _vp]),
     "hgm_count_triples": (_i32, [_vp, _vp, _PP, _i32, _i32, _vp, _vp]),
+    "hgm_atan2_f32": (_i32, [_vp, _vp, _i64, _vp, _vp]),
+    "hgm_gemm_bf16": (_i32, [_vp, _vp, _i32, _i32, _i32, _vp, _vp, _vp]),
     "hgm_profile_enable": (_i32, [_i32]),
     "hgm_profile_read": (_i32, [_pd, _p64, _i32]),
+    "hgm_profile_evaluated": (_i32, [_p64, _i32]),
     "hgm_profile_reset": (_i32, []),
 }
 
@@ -229,6 +235,61 @@ def match_noalloc(model: Model, scene: Scene, params: Params, energy, assign, st
     return ke, ka
 
 
+N_VARIANTS = 3
+
+
+def _tune_cache_path():
+    return os.environ.get("HGM_TUNE_CACHE", os.path.join(os.path.expanduser("~"), ".cache", "hgm_autotune.json"))
+
+
+def _tune_key(params: Params) -> str:
+    try:
+        import torch
+        dev = torch.cuda.get_device_name() if torch.cuda.is_available() else "none"
+    except ImportError:
+        dev = "unknown"
+    return f"{dev}|K{'<=32' if params.K <= 32 else '<=64'}|precision{params.precision}"
+
+
+def autotune(models: Sequence[Model], scenes: Sequence[Scene], params: Params, sample_offsets: int = 128,
+             use_cache: bool = True, stream=None):
+    """Picks the fastest recursion tile variant for this workload (hgm_autotune) and caches the choice
+    in a JSON file keyed by device name and K bucket. Returns (variant, {variant: ms} or None)."""
+    import json
+    lib = load()
+    key, path = _tune_key(params), _tune_cache_path()
+    cache = {}
+    if use_cache and os.path.exists(path):
+        try:
+            cache = json.load(open(path))
+        except (OSError, ValueError):
+            cache = {}
+        if key in cache:
+            _check(lib.hgm_set_recurse_variant(int(cache[key]["variant"])))
+            return int(cache[key]["variant"]), None
+    nm, ns = len(models), len(scenes)
+    mh = (ctypes.c_void_p * nm)(*[m.handle for m in models])
+    sh = (ctypes.c_void_p * ns)(*[s.handle for s in scenes])
+    best = ctypes.c_int32()
+    ms = np.zeros(N_VARIANTS, np.float32)
+    _check(lib.hgm_autotune(mh, nm, sh, ns, ctypes.byref(params), _stream(stream), int(sample_offsets),
+                            ctypes.byref(best), ms.ctypes.data_as(_pf)))
+    times = {v: float(ms[v]) for v in range(N_VARIANTS)}
+    if use_cache:
+        cache[key] = {"variant": int(best.value), "ms": times, "sample_offsets": int(sample_offsets)}
+        try:
+            os.makedirs(os.path.dirname(path), exist_ok=True)
+            with open(path, "w") as fh:
+                json.dump(cache, fh, indent=1)
+        except OSError:
+            pass
+    return int(best.value), times
+
+
+def set_recurse_variant(v: int):
+    _check(load().hgm_set_recurse_variant(int(v)))
+
+
 def batch_layout(models: Sequence[Model], scenes: Sequence[Scene], params: Params):
     lib = load()
     nm, ns = len(models), len(scenes)
@@ -274,8 +335,31 @@ def count_triples(model: Model, scene: Scene, params: Params, first: int, n: int
     return ko
 
 
-def profile_enable(on: bool = True):
-    _check(load().hgm_profile_enable(1 if on else 0))
+def atan2_f32(y, x, out, stream=None):
+    """The recursion kernel's FP32 atan2 applied elementwise (device tensors)."""
+    (py, ky), (px, kx), (po, ko) = _ptr(y), _ptr(x), _ptr(out)
+    _check(load().hgm_atan2_f32(py, px, int(ko.numel() if hasattr(ko, "numel") else ko.size), _stream(stream), po))
+    return ko
+
+
+def gemm_bf16(A, B, C, status, stream=None):
+    """C = bf16(A) @ bf16(B).T on the tensor cores (test hook); all device tensors, status int32[1] zeroed."""
+    M, K = A.shape
+    N = B.shape[0]
+    _check(load().hgm_gemm_bf16(_ptr(A)[0], _ptr(B)[0], int(M), int(N), int(K), _stream(stream), _ptr(C)[0],
+                                _ptr(status)[0]))
+    return C
+
+
+def profile_enable(on=True):
+    """True/1: CUDA-event timing of the kernels; 2: accounting variant of the recursion; False/0: off."""
+    _check(load().hgm_profile_enable(int(on)))
+
+
+def profile_evaluated(reset: bool = False) -> int:
+    v = ctypes.c_int64()
+    _check(load().hgm_profile_evaluated(ctypes.byref(v), 1 if reset else 0))
+    return int(v.value)
 
 
 def profile_reset():

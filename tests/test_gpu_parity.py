@@ -351,3 +351,62 @@ def test_full_batched_workload_sampled(env):
     for (ok, tie, why), smp in zip(results, samples):
         assert ok, (smp, why)
     assert np.all(np.isfinite(e)) or np.any(np.isfinite(e))
+
+
+def test_accounting_variant_gives_identical_results(env):
+    """hgm_profile_enable(2) runs the recursion's accounting variant: same energies and assignments
+    bit for bit, and a positive evaluation count no larger than the unpruned loop's."""
+    torch, hgm, oracle = env
+    wl = synth.batched_exact(seed=7, n_models=2, n_scenes=1, frames_range=(80, 80))
+    ms = [handles(hgm, mod, wl.scenes[0], torch)[0] for mod in wl.models]
+    ss = [handles(hgm, wl.models[0], sc, torch)[1] for sc in wl.scenes]
+    p = hgm.default_params(K=wl.K, window=wl.window)
+    first, es, as_ = hgm.batch_layout(ms, ss, p)
+    outs = []
+    for mode in (0, 2):
+        e = torch.empty(int(es[-1]), dtype=torch.float32, device="cuda")
+        a = torch.empty(int(as_[-1]), dtype=torch.int32, device="cuda")
+        hgm.profile_evaluated(reset=True)
+        hgm.profile_enable(mode)
+        hgm.match_batch(ms, ss, p, e, a)
+        hgm.profile_enable(0)
+        torch.cuda.synchronize()
+        outs.append((e.cpu().numpy(), a.cpu().numpy(), hgm.profile_evaluated(reset=True)))
+    assert np.array_equal(outs[0][0], outs[1][0]) and np.array_equal(outs[0][1], outs[1][1])
+    ev = outs[1][2]
+    full = 0
+    for mi, m in enumerate(ms):
+        q = mi
+        n = int(es[q + 1] - es[q])
+        buf = torch.empty(n, dtype=torch.int64, device="cuda")
+        hgm.count_triples(m, ss[0], p, int(first[q]), n, buf)
+        full += int(buf.sum().item())
+    assert 0 < ev, ev
+    assert ev < 4 * full, (ev, full)
+
+
+def test_tile_variants_identical_and_autotune(env, tmp_path, monkeypatch):
+    """Every recursion tile variant gives the same energies and assignments bit for bit;
+    the autotuner picks one of them and records it in its JSON cache."""
+    torch, hgm, oracle = env
+    monkeypatch.setenv("HGM_TUNE_CACHE", str(tmp_path / "tune.json"))
+    for K, wl in ((64, synth.batched_exact(seed=8, n_models=2, n_scenes=2, frames_range=(70, 90))),
+                  (32, synth.single_match(3))):
+        ms = [handles(hgm, mod, wl.scenes[0], torch)[0] for mod in wl.models]
+        ss = [handles(hgm, wl.models[0], sc, torch)[1] for sc in wl.scenes]
+        p = hgm.default_params(K=wl.K, window=wl.window)
+        first, es, as_ = hgm.batch_layout(ms, ss, p)
+        outs = []
+        for v in range(hgm.N_VARIANTS):
+            hgm.set_recurse_variant(v)
+            e = torch.empty(int(es[-1]), dtype=torch.float32, device="cuda")
+            a = torch.empty(int(as_[-1]), dtype=torch.int32, device="cuda")
+            hgm.match_batch(ms, ss, p, e, a)
+            torch.cuda.synchronize()
+            outs.append((e.cpu().numpy(), a.cpu().numpy()))
+        for e, a in outs[1:]:
+            assert np.array_equal(e, outs[0][0]) and np.array_equal(a, outs[0][1])
+        best, times = hgm.autotune(ms, ss, p, sample_offsets=16)
+        assert 0 <= best < hgm.N_VARIANTS and times is not None and len(times) == hgm.N_VARIANTS
+        assert hgm.autotune(ms, ss, p)[0] == best      # served from the cache
+    hgm.set_recurse_variant(0)
