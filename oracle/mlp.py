@@ -1,0 +1,94 @@
+"""FP64 reference of the candidate-proposal MLP -- TEST INFRASTRUCTURE ONLY.
+
+The proposal network is not part of the paper: it is the learned pruning
+stage layered on the exact method (a small MLP that scores each window
+candidate so that only the best few enter the recursion). This module is the
+plain numpy definition its CUDA training and inference kernels are checked
+against:
+
+  x  = [f_i (F), f'_j (F), dx/100, dy/100, dt/w]        (input, 2F + 3)
+  z1 = W1 x + b1,  h1 = relu(z1)                         (hidden 128)
+  z2 = W2 h1 + b2, h2 = relu(z2)                         (hidden 128)
+  z3 = w3 . h2 + b3,  s = sigmoid(z3)                    (keep score)
+  loss = mean over the batch of softplus(z3) - y z3      (binary cross-entropy with logits)
+
+with dx = x'_j - x_i, dy = y'_j - y_i, dt = t'_j - (t_i + o) and w the window
+half-width. Gradients are written out by the chain rule; Adam follows Kingma
+and Ba (2015), bias-corrected. Only tests/ and bench.py's CPU legs import it.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+H = 128
+
+
+def init(rng: np.random.Generator, d_in: int, hidden: int = H):
+    """He-style initialisation; returns a dict of FP64 arrays."""
+    return {
+        "W1": rng.standard_normal((hidden, d_in)) * np.sqrt(2.0 / d_in),
+        "b1": np.zeros(hidden),
+        "W2": rng.standard_normal((hidden, hidden)) * np.sqrt(2.0 / hidden),
+        "b2": np.zeros(hidden),
+        "w3": rng.standard_normal(hidden) * np.sqrt(1.0 / hidden),
+        "b3": np.zeros(1),
+    }
+
+
+def features(model_f, scene_f, model_xy, scene_xy, model_t, scene_t, i, j, o, window):
+    """Input rows for (model point i, scene point j, offset o) triples (arrays of equal length)."""
+    i, j, o = np.asarray(i), np.asarray(j), np.asarray(o)
+    d = np.stack([(scene_xy[j, 0] - model_xy[i, 0]) / 100.0,
+                  (scene_xy[j, 1] - model_xy[i, 1]) / 100.0,
+                  (scene_t[j] - (model_t[i] + o)) / float(max(window, 1))], axis=1)
+    return np.concatenate([model_f[i], scene_f[j], d], axis=1).astype(np.float64)
+
+
+def forward(p, x):
+    z1 = x @ p["W1"].T + p["b1"]
+    h1 = np.maximum(z1, 0.0)
+    z2 = h1 @ p["W2"].T + p["b2"]
+    h2 = np.maximum(z2, 0.0)
+    z3 = h2 @ p["w3"] + p["b3"][0]
+    return {"z1": z1, "h1": h1, "z2": z2, "h2": h2, "z3": z3}
+
+
+def score(p, x):
+    return 1.0 / (1.0 + np.exp(-forward(p, x)["z3"]))
+
+
+def loss(p, x, y):
+    z3 = forward(p, x)["z3"]
+    return float(np.mean(np.logaddexp(0.0, z3) - y * z3))
+
+
+def backward(p, x, y):
+    """Gradients of loss() with respect to every parameter."""
+    c = forward(p, x)
+    B = x.shape[0]
+    dz3 = (1.0 / (1.0 + np.exp(-c["z3"])) - y) / B
+    g = {"w3": c["h2"].T @ dz3, "b3": np.array([dz3.sum()])}
+    dz2 = np.outer(dz3, p["w3"]) * (c["z2"] > 0)
+    g["W2"] = dz2.T @ c["h1"]
+    g["b2"] = dz2.sum(axis=0)
+    dz1 = (dz2 @ p["W2"]) * (c["z1"] > 0)
+    g["W1"] = dz1.T @ x
+    g["b1"] = dz1.sum(axis=0)
+    return g
+
+
+def adam(p, g, state, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8):
+    """One Adam step in place; state holds m, v and the step count t."""
+    state["t"] = state.get("t", 0) + 1
+    t = state["t"]
+    for k in p:
+        m = state.setdefault("m_" + k, np.zeros_like(p[k]))
+        v = state.setdefault("v_" + k, np.zeros_like(p[k]))
+        m *= b1
+        m += (1 - b1) * g[k]
+        v *= b2
+        v += (1 - b2) * g[k] ** 2
+        mh = m / (1 - b1 ** t)
+        vh = v / (1 - b2 ** t)
+        p[k] -= lr * mh / (np.sqrt(vh) + eps)
+    return p
