@@ -59,6 +59,7 @@ extern "C" {
 
 typedef struct hgm_model hgm_model;
 typedef struct hgm_scene hgm_scene;
+typedef struct hgm_prop hgm_prop;
 
 typedef enum {
     HGM_OK = 0,
@@ -80,7 +81,9 @@ typedef struct {
                            t'(a) - t'(c) < T; T <= 0 means no limit */
     int32_t window;     /* candidate window half-width w in frames, >= 0 */
     int32_t K;          /* candidate cap, 1..64 (1..255 is valid; > 64 is HGM_EUNSUPPORTED) */
-    int32_t precision;  /* 0 = FP32 exact path (the only one in this build) */
+    int32_t precision;  /* 0 = FP32 exact path; 1 = unary table as a BF16 tensor-core contraction
+                           (|a|^2 + |b|^2 - 2 a.b, FP32 accumulation) with the 8 smallest candidates
+                           of every list re-scored from the FP32 descriptors */
     int32_t offset_lo;  /* restrict offsets to [offset_lo, offset_hi] (inclusive); */
     int32_t offset_hi;  /* INT32_MIN / INT32_MAX (the defaults) mean all offsets */
 } hgm_params;
@@ -147,6 +150,37 @@ HGM_API hgm_status hgm_match_batch(const hgm_model *const *models, int32_t n_mod
                            int32_t n_scenes, const hgm_params *params, void *stream, float *energy,
                            int32_t *assign);
 
+/* ---- learned candidate proposal ---------------------------------------------- */
+
+/* The paper has no learned component; this small network is layered on the
+ * exact method as a pruning stage. For descriptors of width F it scores a
+ * candidate scene point j of model point i at offset o from
+ *   x = [f_i (F), f'_j (F), (x'_j - x_i)/100, (y'_j - y_i)/100, (t'_j - t_i - o)/w]   (d_in = 2F + 3)
+ * as z3 = w3 . relu(W2 relu(W1 x + b1) + b2) + b3 (hidden width 128), keep
+ * score sigmoid(z3). Every contraction runs in BF16 on the tensor cores with
+ * FP32 accumulation; weights, gradients and Adam moments are FP32.
+ * Weights cross the ABI in one host array, in this order: W1 [128 x d_in]
+ * row-major, b1 [128], W2 [128 x 128], b2 [128], w3 [128], b3 [1]
+ * (hgm_prop_size(F) floats). hgm_destroy releases a handle. */
+HGM_API hgm_status hgm_prop_create(int32_t F, const float *weights /* host or NULL: He init from seed */,
+                                   uint64_t seed, hgm_prop **out);
+HGM_API int64_t hgm_prop_size(int32_t F);
+HGM_API hgm_status hgm_prop_get(const hgm_prop *prop, float *weights /* host */, int64_t *step /* or NULL */);
+/* Replaces the weights (host array) and resets the Adam moments; step is the
+ * optimizer step count to resume from. */
+HGM_API hgm_status hgm_prop_set(hgm_prop *prop, const float *weights, int64_t step);
+/* Logits z3 [B] (device) of the rows of X [B x d_in] (device, row-major). */
+HGM_API hgm_status hgm_prop_forward(hgm_prop *prop, const float *X, int32_t B, void *stream, float *logits);
+/* Mean binary cross-entropy of labels y [B] (device, 0/1) and its gradient
+ * with respect to every weight, in the weight order above (host array). */
+HGM_API hgm_status hgm_prop_gradients(hgm_prop *prop, const float *X, const float *y, int32_t B, void *stream,
+                                      float *loss /* host, or NULL */, float *grad /* host */);
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8, bias-corrected) on batch
+ * (X, y); loss (host or device float, or NULL) receives the batch loss before
+ * the step. Asynchronous on the stream when loss is NULL or a device pointer. */
+HGM_API hgm_status hgm_prop_train_step(hgm_prop *prop, const float *X, const float *y, int32_t B, float lr,
+                                       void *stream, float *loss);
+
 /* ---- tuning ---------------------------------------------------------------- */
 
 /* The recursion kernel (Eq. 10) comes in tile variants that differ only in how
@@ -199,6 +233,13 @@ HGM_API hgm_status hgm_scene_order(const hgm_scene *scene, int32_t *perm);
  * order with fused multiply-add and an IEEE square root (the same value as
  * the candidate ranking key). U: device, M x S floats. */
 HGM_API hgm_status hgm_unary(const hgm_model *model, const hgm_scene *scene, float lambda1, void *stream, float *U);
+
+/* The same table in the precision mode: U[i*S + j] = lambda1 * sqrt(max(0,
+ * |f~_i|^2 + |f~'_j|^2 - 2 f~_i . f~'_j)) with f~ the BF16-rounded descriptors,
+ * products accumulated in FP32 on the tensor cores (tcgen05). U: device,
+ * M x S floats. Synchronous; HGM_ETIMEOUT if a bounded tensor-core wait gave up. */
+HGM_API hgm_status hgm_unary_bf16(const hgm_model *model, const hgm_scene *scene, float lambda1, void *stream,
+                                  float *U);
 
 /* Candidate lists for offsets first..first+n-1 (all must be valid offsets):
  *  idx [n x M x K] int32 (device): sorted scene indices of C_i(o) in

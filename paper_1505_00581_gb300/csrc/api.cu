@@ -19,6 +19,7 @@
 #include <vector>
 
 #include "hgm_internal.cuh"
+#include "prop.cuh"
 
 namespace hgm {
 namespace {
@@ -136,6 +137,7 @@ struct Buffer {
 
 struct Workspace {
     Buffer modelcat, U, cand_idx, cand_u, cand_cnt, beta, units, res, mrec, srec, counter, out_e, out_a, evaluated;
+    Buffer mnorm, snorm, status;
 };
 Workspace g_ws;
 bool g_count_mode = false;   // hgm_profile_enable(2): batch runs use the accounting recursion variant
@@ -191,7 +193,9 @@ hgm_status check_params(const hgm_params *p)
     if (p->window < 0) return fail(HGM_EINVAL, "window must be >= 0");
     if (p->K < 1 || p->K > 255) return fail(HGM_EINVAL, "K must be in 1..255 (got %d)", p->K);
     if (p->K > kMaxK) return fail(HGM_EUNSUPPORTED, "K > %d is not supported by this build", kMaxK);
-    if (p->precision != 0) return fail(HGM_EUNSUPPORTED, "precision %d not available", p->precision);
+    if (p->precision != 0 && p->precision != 1)
+        return fail(HGM_EUNSUPPORTED, "precision %d not available (0 = FP32 exact, 1 = BF16 + FP32 re-score)",
+                    p->precision);
     if (p->offset_lo > p->offset_hi) return fail(HGM_EINVAL, "offset_lo > offset_hi");
     return HGM_OK;
 }
@@ -205,6 +209,7 @@ Params to_params(const hgm_params *p)
     q.T = p->T;
     q.window = p->window;
     q.K = p->K;
+    q.rescore = p->precision == 1 ? kRescore : 0;
     return q;
 }
 
@@ -291,12 +296,13 @@ hgm_status run_batch(const hgm_model *const *models, int nm, const hgm_scene *co
     Plan pl;
     rc = build_plan(models, nm, scenes, ns, hp, pl);
     if (rc) return rc;
-    const Params p = to_params(hp);
+    Params p = to_params(hp);
     const int64_t n_out = pl.e_start.back();
     const int64_t n_assign = pl.a_start.back();
     if (n_out == 0 || nm == 0 || ns == 0) return HGM_OK;
     const int K = p.K;
     const int F = models[0]->d.F;
+    p.F = F;
 
     // unary table: all model rows x every scene (row pitch padded to 4)
     int R = 0, max_M = 0;
@@ -320,22 +326,42 @@ hgm_status run_batch(const hgm_model *const *models, int nm, const hgm_scene *co
            "gather model descriptors");
     std::vector<ModelRec> mrec(nm);
     for (int m = 0; m < nm; ++m)
-        mrec[m] = ModelRec{models[m]->d.xy, models[m]->d.t, models[m]->d.perm, models[m]->d.M, urow[m]};
+        mrec[m] = ModelRec{models[m]->d.xy, models[m]->d.t, models[m]->d.perm, models[m]->d.M, urow[m],
+                           models[m]->d.f};
     std::vector<SceneRec> srec(ns);
     for (int s = 0; s < ns; ++s) {
         const SceneDev &d = scenes[s]->d;
         srec[s] = SceneRec{d.xy, d.t, d.frame_start, d.perm, g_ws.U.as<float>() + ubase[s],
-                           (int64_t)round_up4(std::max(d.S, 1)), d.S, d.n_frames};
+                           (int64_t)round_up4(std::max(d.S, 1)), d.S, d.n_frames, d.f};
     }
     CK(g_ws.mrec.ensure(nm * sizeof(ModelRec)), "workspace");
     CK(g_ws.srec.ensure(ns * sizeof(SceneRec)), "workspace");
     CK(cudaMemcpyAsync(g_ws.mrec.p, mrec.data(), nm * sizeof(ModelRec), cudaMemcpyHostToDevice, st), "upload");
     CK(cudaMemcpyAsync(g_ws.srec.p, srec.data(), ns * sizeof(SceneRec), cudaMemcpyHostToDevice, st), "upload");
-    for (int s = 0; s < ns; ++s) {
-        const SceneDev &d = scenes[s]->d;
-        CK(launch_unary(g_ws.modelcat.as<float>(), R, d.f, d.S, F, p.lambda1, g_ws.U.as<float>() + ubase[s],
-                        (int)srec[s].upitch, st),
-           "unary kernel");
+    if (hp->precision == 1) {
+        // BF16 tensor-core unary table (norms of the BF16-rounded rows in FP32)
+        int64_t smax = 0;
+        for (int s = 0; s < ns; ++s) smax = std::max<int64_t>(smax, scenes[s]->d.S);
+        CK(g_ws.mnorm.ensure((size_t)R * sizeof(float)), "workspace (norms)");
+        CK(g_ws.snorm.ensure((size_t)std::max<int64_t>(smax, 1) * sizeof(float)), "workspace (norms)");
+        CK(g_ws.status.ensure(sizeof(int)), "workspace");
+        CK(cudaMemsetAsync(g_ws.status.p, 0, sizeof(int), st), "memset");
+        CK(launch_sqnorm_bf16(g_ws.modelcat.as<float>(), R, F, F, g_ws.mnorm.as<float>(), st), "norm kernel");
+        for (int s = 0; s < ns; ++s) {
+            const SceneDev &d = scenes[s]->d;
+            CK(launch_sqnorm_bf16(d.f, d.S, F, F, g_ws.snorm.as<float>(), st), "norm kernel");
+            CK(launch_unary_bf16(g_ws.modelcat.as<float>(), R, d.f, d.S, F, F, g_ws.mnorm.as<float>(),
+                                 g_ws.snorm.as<float>(), p.lambda1, g_ws.U.as<float>() + ubase[s], srec[s].upitch,
+                                 g_ws.status.as<int>(), st),
+               "BF16 unary kernel");
+        }
+    } else {
+        for (int s = 0; s < ns; ++s) {
+            const SceneDev &d = scenes[s]->d;
+            CK(launch_unary(g_ws.modelcat.as<float>(), R, d.f, d.S, F, p.lambda1, g_ws.U.as<float>() + ubase[s],
+                            (int)srec[s].upitch, st),
+               "unary kernel");
+        }
     }
 
     // outputs: device pointers are written in place, host ones through staging
@@ -465,17 +491,32 @@ hgm_status single_pair_units(const hgm_model *m, const hgm_scene *s, const hgm_p
     if (n < 0 || first < f0 || (int64_t)first + n > (int64_t)f0 + nall)
         return fail(HGM_EINVAL, "offsets [%d, %d) outside the valid range [%d, %d)", first, first + n, f0, f0 + nall);
     p = to_params(hp);
+    p.F = m->d.F;
     R = m->d.M;
     const int K = p.K;
     const int64_t pitch = round_up4(std::max(s->d.S, 1));
     CK(g_ws.U.ensure((size_t)R * pitch * sizeof(float)), "workspace (unary table)");
-    ModelRec mr{m->d.xy, m->d.t, m->d.perm, m->d.M, 0};
-    SceneRec sr{s->d.xy, s->d.t, s->d.frame_start, s->d.perm, g_ws.U.as<float>(), pitch, s->d.S, s->d.n_frames};
+    ModelRec mr{m->d.xy, m->d.t, m->d.perm, m->d.M, 0, m->d.f};
+    SceneRec sr{s->d.xy, s->d.t, s->d.frame_start, s->d.perm, g_ws.U.as<float>(), pitch, s->d.S, s->d.n_frames,
+                s->d.f};
     CK(g_ws.mrec.ensure(sizeof(ModelRec)), "workspace");
     CK(g_ws.srec.ensure(sizeof(SceneRec)), "workspace");
     CK(cudaMemcpyAsync(g_ws.mrec.p, &mr, sizeof mr, cudaMemcpyHostToDevice, st), "upload");
     CK(cudaMemcpyAsync(g_ws.srec.p, &sr, sizeof sr, cudaMemcpyHostToDevice, st), "upload");
-    CK(launch_unary(m->d.f, R, s->d.f, s->d.S, m->d.F, p.lambda1, g_ws.U.as<float>(), (int)pitch, st), "unary kernel");
+    if (hp->precision == 1) {
+        CK(g_ws.mnorm.ensure((size_t)R * sizeof(float)), "workspace (norms)");
+        CK(g_ws.snorm.ensure((size_t)std::max(s->d.S, 1) * sizeof(float)), "workspace (norms)");
+        CK(g_ws.status.ensure(sizeof(int)), "workspace");
+        CK(cudaMemsetAsync(g_ws.status.p, 0, sizeof(int), st), "memset");
+        CK(launch_sqnorm_bf16(m->d.f, R, m->d.F, m->d.F, g_ws.mnorm.as<float>(), st), "norm kernel");
+        CK(launch_sqnorm_bf16(s->d.f, s->d.S, m->d.F, m->d.F, g_ws.snorm.as<float>(), st), "norm kernel");
+        CK(launch_unary_bf16(m->d.f, R, s->d.f, s->d.S, m->d.F, m->d.F, g_ws.mnorm.as<float>(), g_ws.snorm.as<float>(),
+                             p.lambda1, g_ws.U.as<float>(), pitch, g_ws.status.as<int>(), st),
+           "BF16 unary kernel");
+    } else {
+        CK(launch_unary(m->d.f, R, s->d.f, s->d.S, m->d.F, p.lambda1, g_ws.U.as<float>(), (int)pitch, st),
+           "unary kernel");
+    }
     std::vector<Unit> units((size_t)n);
     for (int32_t k = 0; k < n; ++k) {
         Unit u{};
@@ -658,6 +699,12 @@ void hgm_destroy(void *handle)
         free_scene(s);
         s->magic = kDeadMagic;
         delete s;
+    } else if (magic == kPropMagic) {
+        hgm_prop *p = static_cast<hgm_prop *>(handle);
+        cudaDeviceSynchronize();
+        prop_free(p);
+        p->magic = kDeadMagic;
+        delete p;
     }
 }
 
@@ -748,6 +795,32 @@ hgm_status hgm_unary(const hgm_model *model, const hgm_scene *scene, float lambd
     cudaStream_t st = (cudaStream_t)stream;
     CK(launch_unary(model->d.f, model->d.M, scene->d.f, scene->d.S, model->d.F, lambda1, U, scene->d.S, st),
        "unary kernel");
+    return HGM_OK;
+}
+
+hgm_status hgm_unary_bf16(const hgm_model *model, const hgm_scene *scene, float lambda1, void *stream, float *U)
+{
+    std::lock_guard<std::mutex> lk(g_mu);
+    g_err.clear();
+    if (!valid_model(model) || !valid_scene(scene)) return fail(HGM_EINVAL, "invalid handle");
+    if (model->F_user != scene->F_user) return fail(HGM_EINVAL, "descriptor width differs between model and scene");
+    if (!U || !is_device_ptr(U)) return fail(HGM_EINVAL, "U must be a device pointer");
+    if (!std::isfinite(lambda1) || lambda1 < 0) return fail(HGM_EINVAL, "lambda1 must be finite and >= 0");
+    cudaStream_t st = (cudaStream_t)stream;
+    const int F = model->d.F, M = model->d.M, S = scene->d.S;
+    CK(g_ws.mnorm.ensure((size_t)M * sizeof(float)), "workspace (norms)");
+    CK(g_ws.snorm.ensure((size_t)std::max(S, 1) * sizeof(float)), "workspace (norms)");
+    CK(g_ws.status.ensure(sizeof(int)), "workspace");
+    CK(cudaMemsetAsync(g_ws.status.p, 0, sizeof(int), st), "memset");
+    CK(launch_sqnorm_bf16(model->d.f, M, F, F, g_ws.mnorm.as<float>(), st), "norm kernel");
+    CK(launch_sqnorm_bf16(scene->d.f, S, F, F, g_ws.snorm.as<float>(), st), "norm kernel");
+    CK(launch_unary_bf16(model->d.f, M, scene->d.f, S, F, F, g_ws.mnorm.as<float>(), g_ws.snorm.as<float>(), lambda1,
+                         U, S, g_ws.status.as<int>(), st),
+       "BF16 unary kernel");
+    int status = 0;
+    CK(cudaMemcpyAsync(&status, g_ws.status.p, sizeof(int), cudaMemcpyDeviceToHost, st), "status");
+    CK(cudaStreamSynchronize(st), "synchronise");
+    if (status) return fail(HGM_ETIMEOUT, "a bounded wait for the tensor core gave up");
     return HGM_OK;
 }
 

@@ -42,6 +42,7 @@ struct ModelRec {
     const int32_t *perm;
     int32_t M;
     int32_t urow;        // first row of this model in the unary table
+    const float *f;      // sorted descriptors, row stride Params::F (used to re-score in FP32)
 };
 
 // Per-scene record the kernels read.
@@ -53,6 +54,7 @@ struct SceneRec {
     const float *U;      // unary table block of this scene: [R x upitch]
     int64_t upitch;      // row pitch of U in floats (>= S)
     int32_t S, n_frames;
+    const float *f;      // sorted descriptors, row stride Params::F
 };
 
 // One matching problem: a (model, scene, offset) triple.
@@ -74,13 +76,24 @@ struct UnitResult {
 struct Params {
     float lambda1, lambda2, lambda3;
     int32_t T, window, K;
+    int32_t F = 0;       // descriptor row stride (padded width)
+    int32_t rescore = 0; // 0, or: recompute the U of the `rescore` smallest candidates per list in FP32
 };
+
+constexpr int kRescore = 8;   // candidates per list re-scored in FP32 by the BF16 precision mode
 
 enum ProfKernel { kProfUnary = 0, kProfSelect = 1, kProfRecurse = 2, kProfBacktrack = 3, kProfCount = 4 };
 
 // ---- kernel launchers (each checks its own launch error) --------------------
 cudaError_t launch_unary(const float *A, int R, const float *B, int S, int F, float lambda1, float *U,
                          int ldu, cudaStream_t st);
+// k_rowdot.cu: BF16 tensor-core products.
+cudaError_t launch_sqnorm_bf16(const float *X, int64_t n, int ld, int F, float *out, cudaStream_t st);
+cudaError_t launch_unary_bf16(const float *model, int R, const float *scene, int S, int F, int ld,
+                              const float *mnorm, const float *snorm, float lambda1, float *U, int64_t ldu,
+                              int *status, cudaStream_t st);
+cudaError_t launch_rowdot_plain(const float *X, int64_t nrows, int ldx, const float *W, int ncols, int ldw, int F,
+                                const float *bias, float *Y, int64_t ldy, int *status, cudaStream_t st);
 cudaError_t launch_select(const Unit *units, int64_t n_units, const ModelRec *models, const SceneRec *scenes,
                           Params p, int max_M, int32_t *cand_idx, float *cand_u, int32_t *cand_cnt,
                           cudaStream_t st);

@@ -123,6 +123,39 @@ __global__ void __launch_bounds__(kWarps * 32) select_kernel(const Unit *__restr
                 }
             }
             if (lane == 0) cand_cnt[un.cand / K + i] = kept;
+            if (p.rescore > 0 && kept > 0) {
+                // precision mode: the p.rescore smallest approximate costs (ties: lower slot) are
+                // recomputed from the FP32 descriptors in the exact kernel's fixed FMA order
+                __syncwarp();
+                float kv[2];
+                kv[0] = lane < kept ? ou[lane] : __int_as_float(0x7f800000);
+                kv[1] = lane + 32 < kept ? ou[lane + 32] : __int_as_float(0x7f800000);
+                int mine = -1;
+                const int rounds = p.rescore < kept ? p.rescore : kept;
+                for (int q = 0; q < rounds; ++q) {
+                    float bv = kv[0] <= kv[1] ? kv[0] : kv[1];
+                    int bs = kv[0] <= kv[1] ? lane : lane + 32;
+#pragma unroll
+                    for (int off = 16; off > 0; off >>= 1) {
+                        const float ov = __shfl_xor_sync(0xffffffffu, bv, off);
+                        const int os = __shfl_xor_sync(0xffffffffu, bs, off);
+                        if (ov < bv || (ov == bv && os < bs)) { bv = ov; bs = os; }
+                    }
+                    if (lane == q) mine = bs;
+                    if (bs == lane) kv[0] = __int_as_float(0x7f800000);
+                    if (bs == lane + 32) kv[1] = __int_as_float(0x7f800000);
+                }
+                if (mine >= 0 && mine < kept) {
+                    const float *a = md.f + (int64_t)i * p.F;
+                    const float *b = sc.f + (int64_t)oidx[mine] * p.F;
+                    float s2 = 0.0f;
+                    for (int k = 0; k < p.F; ++k) {
+                        const float d = __fsub_rn(a[k], b[k]);
+                        s2 = __fmaf_rn(d, d, s2);
+                    }
+                    ou[mine] = __fmul_rn(p.lambda1, __fsqrt_rn(s2));
+                }
+            }
         }
     }
 }

@@ -50,12 +50,20 @@ SIGNATURES = {
     "hgm_batch_layout": (_i32, [ctypes.POINTER(_vp), _i32, ctypes.POINTER(_vp), _i32, _PP, _p32, _p64, _p64]),
     "hgm_match_batch": (_i32, [ctypes.POINTER(_vp), _i32, ctypes.POINTER(_vp), _i32, _PP, _vp, _vp, _vp]),
     "hgm_match_noalloc": (_i32, [_vp, _vp, _PP, _vp, _vp, _vp]),
+    "hgm_prop_create": (_i32, [_i32, _vp, ctypes.c_uint64, ctypes.POINTER(_vp)]),
+    "hgm_prop_size": (_i64, [_i32]),
+    "hgm_prop_get": (_i32, [_vp, _vp, _p64]),
+    "hgm_prop_set": (_i32, [_vp, _vp, _i64]),
+    "hgm_prop_forward": (_i32, [_vp, _vp, _i32, _vp, _vp]),
+    "hgm_prop_gradients": (_i32, [_vp, _vp, _vp, _i32, _vp, _vp, _vp]),
+    "hgm_prop_train_step": (_i32, [_vp, _vp, _vp, _i32, _f32, _vp, _vp]),
     "hgm_autotune": (_i32, [ctypes.POINTER(_vp), _i32, ctypes.POINTER(_vp), _i32, _PP, _vp, _i32, _p32, _pf]),
     "hgm_set_recurse_variant": (_i32, [_i32]),
     "hgm_get_recurse_variant": (_i32, []),
     "hgm_model_order": (_i32, [_vp, _p32]),
     "hgm_scene_order": (_i32, [_vp, _p32]),
     "hgm_unary": (_i32, [_vp, _vp, _f32, _vp, _vp]),
+    "hgm_unary_bf16": (_i32, [_vp, _vp, _f32, _vp, _vp]),
     "hgm_candidates": (_i32, [_vp, _vp, _PP, _i32, _i32, _vp, _vp, _vp]),
     "hgm_count_triples": (_i32, [_vp, _vp, _PP, _i32, _i32, _vp, _vp]),
     "hgm_atan2_f32": (_i32, [_vp, _vp, _i64, _vp, _vp]),
@@ -207,6 +215,71 @@ def _as(a, dtype):
     return np.ascontiguousarray(a, dtype=dtype)
 
 
+class Proposal:
+    """Candidate-proposal network handle (hgm_prop_*). weights: flat FP32 host array in the ABI order."""
+
+    def __init__(self, F: int, weights=None, seed: int = 0):
+        self.lib = load()
+        self.F = int(F)
+        self.size = int(self.lib.hgm_prop_size(self.F))
+        h = ctypes.c_void_p()
+        w = None if weights is None else np.ascontiguousarray(weights, dtype=np.float32)
+        if w is not None and w.size != self.size:
+            raise ValueError(f"expected {self.size} weights, got {w.size}")
+        _check(self.lib.hgm_prop_create(self.F, None if w is None else w.ctypes.data, int(seed), ctypes.byref(h)))
+        self.handle = h
+
+    @property
+    def d_in(self):
+        return 2 * self.F + 3
+
+    def get(self):
+        w = np.zeros(self.size, np.float32)
+        st = ctypes.c_int64()
+        _check(self.lib.hgm_prop_get(self.handle, w.ctypes.data, ctypes.byref(st)))
+        return w, int(st.value)
+
+    def set(self, weights, step: int = 0):
+        w = np.ascontiguousarray(weights, dtype=np.float32)
+        _check(self.lib.hgm_prop_set(self.handle, w.ctypes.data, int(step)))
+
+    def unflatten(self, w):
+        H, d = 128, self.d_in
+        o = 0
+        out = {}
+        for name, shape in (("W1", (H, d)), ("b1", (H,)), ("W2", (H, H)), ("b2", (H,)), ("w3", (H,)), ("b3", (1,))):
+            n = int(np.prod(shape))
+            out[name] = np.asarray(w[o:o + n]).reshape(shape)
+            o += n
+        return out
+
+    def forward(self, X, out, stream=None):
+        _check(self.lib.hgm_prop_forward(self.handle, _ptr(X)[0], int(X.shape[0]), _stream(stream), _ptr(out)[0]))
+        return out
+
+    def gradients(self, X, y, stream=None):
+        g = np.zeros(self.size, np.float32)
+        loss = ctypes.c_float()
+        _check(self.lib.hgm_prop_gradients(self.handle, _ptr(X)[0], _ptr(y)[0], int(X.shape[0]), _stream(stream),
+                                           ctypes.byref(loss), g.ctypes.data))
+        return float(loss.value), g
+
+    def train_step(self, X, y, lr: float, loss_out=None, stream=None):
+        _check(self.lib.hgm_prop_train_step(self.handle, _ptr(X)[0], _ptr(y)[0], int(X.shape[0]), float(lr),
+                                            _stream(stream), None if loss_out is None else _ptr(loss_out)[0]))
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self.lib.hgm_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 def offsets(model: Model, scene: Scene, params: Params):
     n, f = ctypes.c_int32(), ctypes.c_int32()
     _check(load().hgm_offsets(model.handle, scene.handle, ctypes.byref(params), ctypes.byref(n), ctypes.byref(f)))
@@ -318,6 +391,12 @@ def match_batch(models: Sequence[Model], scenes: Sequence[Scene], params: Params
 def unary(model: Model, scene: Scene, lambda1: float, out, stream=None):
     (po, ko) = _ptr(out)
     _check(load().hgm_unary(model.handle, scene.handle, float(lambda1), _stream(stream), po))
+    return ko
+
+
+def unary_bf16(model: Model, scene: Scene, lambda1: float, out, stream=None):
+    (po, ko) = _ptr(out)
+    _check(load().hgm_unary_bf16(model.handle, scene.handle, float(lambda1), _stream(stream), po))
     return ko
 
 
