@@ -166,6 +166,72 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def _time_form(torch, hgm, models, scenes, p, energy, assign, steps, warmup, stream, flush):
+    for _ in range(warmup):
+        hgm.match_batch(models, scenes, p, energy, assign)
+    torch.cuda.synchronize()
+    hgm.profile_reset()
+    hgm.profile_enable(True)
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    for k in range(steps):
+        flush.zero_()
+        starts[k].record(stream)
+        hgm.match_batch(models, scenes, p, energy, assign)
+        ends[k].record(stream)
+    torch.cuda.synchronize()
+    hgm.profile_enable(False)
+    return sum(a.elapsed_time(b) for a, b in zip(starts, ends)) / steps, hgm.profile_read()
+
+
+def run_pruned(args, torch, hgm, wl, models, scenes, energy, assign, es, as_, dev, stream, world):
+    """The pruned + BF16 form on the same workload: BF16 tensor-core unary table, the proposal network
+    keeps 8 of the 64 candidates per list, recursion on the short lists, exact fallback for infeasible
+    units. Quality is measured against this run's exact results (energy/assign hold them)."""
+    from paper_1505_00581_gb300 import prop_train
+    e_ref = energy.cpu().numpy().copy()
+    a_ref = assign.cpu().numpy().copy()
+    t0 = time.time()
+    if args.checkpoint:
+        prop, info = prop_train.load_checkpoint(args.checkpoint), {"checkpoint": args.checkpoint}
+    else:
+        prop, info = prop_train.train_default(torch, wl, steps=args.train_steps, seed=101 + 1000 * int(
+            os.environ.get("RANK", "0")))
+    train_s = time.time() - t0
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+    p = hgm.default_params(K=wl.K, window=wl.window, T=wl.T, precision=1, prune=prop, keep=8)
+    e2 = torch.empty_like(energy)
+    a2 = torch.empty_like(assign)
+    hgm.prune_counters(reset=True)
+    ms, prof = _time_form(torch, hgm, models, scenes, p, e2, a2, args.steps, args.warmup, stream, flush)
+    n_pruned, n_fb = hgm.prune_counters(reset=True)
+    blocks = []
+    for mi, m in enumerate(wl.models):
+        for si in range(len(wl.scenes)):
+            q = mi * len(wl.scenes) + si
+            blocks.append((int(as_[q]), int(es[q + 1] - es[q]), m.n))
+    first_, es_, _ = hgm.batch_layout(models, scenes, hgm.default_params(K=wl.K, window=wl.window, T=wl.T))
+    masks = prop_train.implant_masks(wl, first_, es_)
+    erows = [int(es_[q]) for q in range(len(blocks))]
+    quality = prop_train.compare(e_ref, a_ref, e2.cpu().numpy(), a2.cpu().numpy(), blocks, erows, masks)
+    # the same pruning without the network: the 8 smallest unary costs (K = 8 window cap), BF16 + re-score
+    pb = hgm.default_params(K=8, window=wl.window, T=wl.T, precision=1)
+    first8, es8, as8 = hgm.batch_layout(models, scenes, pb)
+    e8 = torch.empty(int(es8[-1]), dtype=torch.float32, device=dev)
+    a8 = torch.empty(int(as8[-1]), dtype=torch.int32, device=dev)
+    ms8, _ = _time_form(torch, hgm, models, scenes, pb, e8, a8, max(1, args.steps // 2), 1, stream, flush)
+    base_q = prop_train.compare(e_ref, a_ref, e8.cpu().numpy(), a8.cpu().numpy(), blocks, erows, masks)
+    frames = wl.total_frames * world
+    return {"value": frames / (ms / 1e3), "unit": "frames/s", "ms_per_step": ms,
+            "kernel_ms_per_step": {k: v[0] / args.steps for k, v in prof.items()},
+            "keep": 8, "K": wl.K, "precision": "BF16 unary + FP32 re-score of kept candidates",
+            "fallback_units_per_step": n_fb / max(1, args.steps + args.warmup),
+            "units_per_step": n_pruned / max(1, args.steps + args.warmup), **quality,
+            "top8_by_unary_baseline": {"value": frames / (ms8 / 1e3), "unit": "frames/s", **base_q},
+            "training": {k: v for k, v in info.items() if k != "loss"}, "final_loss": (info.get("loss") or [[0, None]])[-1][1],
+            "train_s": train_s}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -177,6 +243,9 @@ def main():
     ap.add_argument("--cpu-units", type=int, default=48)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-pruned", action="store_true", help="skip the pruned+BF16 form")
+    ap.add_argument("--train-steps", type=int, default=2000)
+    ap.add_argument("--checkpoint", default=None, help="load the proposal network from <path>.bin/.json")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -319,6 +388,10 @@ def main():
                "sample": f"{n} seeded units of {total_units(wl)} ({t:.1f} s on {threads} threads), "
                          f"projected to the whole workload"}
 
+    pruned = None
+    if not args.no_pruned:
+        pruned = run_pruned(args, torch, hgm, wl, models, scenes, energy, assign, es, as_, dev, stream, world)
+
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "frames/s", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
@@ -331,7 +404,7 @@ def main():
                            "recurse_variant": variant, "autotune_ms": variant_ms,
                            "parallelism": f"replicas x{world}"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-                "clocks": clk_sum, "finite_offsets": int(fin)}
+                "clocks": clk_sum, "finite_offsets": int(fin), "pruned_bf16": pruned}
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()

@@ -86,9 +86,13 @@ typedef struct {
                            of every list re-scored from the FP32 descriptors */
     int32_t offset_lo;  /* restrict offsets to [offset_lo, offset_hi] (inclusive); */
     int32_t offset_hi;  /* INT32_MIN / INT32_MAX (the defaults) mean all offsets */
+    const struct hgm_prop *prune;  /* NULL: exact path. Else the proposal network keeps the `keep` best
+                                      candidates of every list (ties: lower slot) before the recursion; units
+                                      whose pruned optimum is infeasible are re-solved on the full lists. */
+    int32_t keep;       /* candidates kept per list when pruning, 1..K (default 8) */
 } hgm_params;
 
-/* Fills *p with the defaults above. */
+/* Fills *p with the defaults above (prune = NULL, keep = 8). */
 HGM_API void hgm_default_params(hgm_params *p);
 
 /* Creates a model from M points (host or device pointers; copied). The chain
@@ -271,9 +275,10 @@ HGM_API hgm_status hgm_gemm_bf16(const float *A, const float *B, int32_t M, int3
 
 /* ---- profiling ----------------------------------------------------------- */
 
-/* on = 1: every launch of the four kernels below is bracketed by CUDA
- * events on its stream and its duration accumulated:
- *   0 = unary distance, 1 = candidate selection, 2 = recursion, 3 = backtrack.
+/* on = 1: every launch of the kernels below is bracketed by CUDA events on
+ * its stream and its duration accumulated:
+ *   0 = unary distance, 1 = candidate selection, 2 = recursion, 3 = backtrack,
+ *   4 = proposal-network pruning.
  * hgm_profile_read synchronises on the recorded events and returns, per
  * kernel, total milliseconds and launch count since the last reset.
  * on = 2: batch calls instead run the accounting variant of the recursion
@@ -283,6 +288,9 @@ HGM_API hgm_status hgm_gemm_bf16(const float *A, const float *B, int32_t M, int3
 HGM_API hgm_status hgm_profile_enable(int32_t on);
 /* Reads (and with reset != 0, then clears) the evaluation counter of on = 2. */
 HGM_API hgm_status hgm_profile_evaluated(int64_t *evaluated, int32_t reset);
+/* Units solved on the pruned lists and units re-solved on the full lists
+ * (fallback) by batch calls with pruning, since the last reset. */
+HGM_API hgm_status hgm_prune_counters(int64_t *pruned_units, int64_t *fallback_units, int32_t reset);
 HGM_API hgm_status hgm_profile_read(double *ms, int64_t *launches, int32_t n_kernels);
 HGM_API hgm_status hgm_profile_reset(void);
 

@@ -138,9 +138,11 @@ struct Buffer {
 struct Workspace {
     Buffer modelcat, U, cand_idx, cand_u, cand_cnt, beta, units, res, mrec, srec, counter, out_e, out_a, evaluated;
     Buffer mnorm, snorm, status;
+    Buffer P, Q, cand2_idx, cand2_u, cand2_cnt, units2, beta2, fb_units, fb_count, beta_fb, res_fb, scores;
 };
 Workspace g_ws;
 bool g_count_mode = false;   // hgm_profile_enable(2): batch runs use the accounting recursion variant
+int64_t g_pruned_units = 0, g_fallback_units = 0;
 
 }  // namespace
 
@@ -197,6 +199,10 @@ hgm_status check_params(const hgm_params *p)
         return fail(HGM_EUNSUPPORTED, "precision %d not available (0 = FP32 exact, 1 = BF16 + FP32 re-score)",
                     p->precision);
     if (p->offset_lo > p->offset_hi) return fail(HGM_EINVAL, "offset_lo > offset_hi");
+    if (p->prune) {
+        if (p->prune->magic != kPropMagic) return fail(HGM_EINVAL, "prune is not a proposal-network handle");
+        if (p->keep < 1 || p->keep > p->K) return fail(HGM_EINVAL, "keep must be in 1..K (got %d)", p->keep);
+    }
     return HGM_OK;
 }
 
@@ -334,6 +340,45 @@ hgm_status run_batch(const hgm_model *const *models, int nm, const hgm_scene *co
         srec[s] = SceneRec{d.xy, d.t, d.frame_start, d.perm, g_ws.U.as<float>() + ubase[s],
                            (int64_t)round_up4(std::max(d.S, 1)), d.S, d.n_frames, d.f};
     }
+    // proposal network: per-point projections of its first layer (tensor cores)
+    const hgm_prop *prop = hp->prune;
+    const bool pruning = prop != nullptr;
+    const int keep = pruning ? hp->keep : K;
+    PropInfer pi{};
+    if (pruning) {
+        const int Fu = models[0]->F_user;
+        if (prop->L.F != Fu) return fail(HGM_EINVAL, "proposal network built for F = %d, descriptors have F = %d",
+                                         prop->L.F, Fu);
+        std::vector<int64_t> qbase(ns);
+        int64_t qtot = 0;
+        for (int s = 0; s < ns; ++s) { qbase[s] = qtot; qtot += (int64_t)scenes[s]->d.S * kPropHidden; }
+        CK(g_ws.P.ensure((size_t)R * kPropHidden * sizeof(float)), "workspace (projections)");
+        CK(g_ws.Q.ensure((size_t)std::max<int64_t>(qtot, 1) * sizeof(float)), "workspace (projections)");
+        CK(g_ws.status.ensure(sizeof(int)), "workspace");
+        CK(cudaMemsetAsync(g_ws.status.p, 0, sizeof(int), st), "memset");
+        const float *th = prop->theta;
+        CK(launch_rowdot_plain(g_ws.modelcat.as<float>(), R, F, th + prop->L.o_W1, kPropHidden, prop->L.dp, Fu,
+                               th + prop->L.o_b1, g_ws.P.as<float>(), kPropHidden, g_ws.status.as<int>(), st),
+           "projection kernel");
+        for (int s = 0; s < ns; ++s) {
+            const SceneDev &d = scenes[s]->d;
+            CK(launch_rowdot_plain(d.f, d.S, F, th + prop->L.o_W1 + Fu, kPropHidden, prop->L.dp, Fu, nullptr,
+                                   g_ws.Q.as<float>() + qbase[s], kPropHidden, g_ws.status.as<int>(), st),
+               "projection kernel");
+            srec[s].pq = g_ws.Q.as<float>() + qbase[s];
+        }
+        pi.P = g_ws.P.as<float>();
+        pi.W2 = th + prop->L.o_W2;
+        pi.b2 = th + prop->L.o_b2;
+        pi.w3 = th + prop->L.o_w3;
+        pi.b3 = th + prop->L.o_b3;
+        pi.w1c = th + prop->L.o_W1 + 2 * Fu;
+        pi.dp = prop->L.dp;
+        pi.inv_window = 1.0f / (float)std::max(hp->window, 1);
+        pi.keep = keep;
+        pi.rescore = hp->precision == 1 ? 1 : 0;
+        p.rescore = 0;   // the kept candidates are re-scored by the pruning kernel instead
+    }
     CK(g_ws.mrec.ensure(nm * sizeof(ModelRec)), "workspace");
     CK(g_ws.srec.ensure(ns * sizeof(SceneRec)), "workspace");
     CK(cudaMemcpyAsync(g_ws.mrec.p, mrec.data(), nm * sizeof(ModelRec), cudaMemcpyHostToDevice, st), "upload");
@@ -424,7 +469,9 @@ hgm_status run_batch(const hgm_model *const *models, int nm, const hgm_scene *co
         while (end < n_units) {
             const int M = models[all[(size_t)end].model]->d.M;
             int64_t ce = (int64_t)M * K, bb = (int64_t)(M - 2) * K * K;
-            int64_t need = (cand_e + ce) * (int64_t)(sizeof(int32_t) * 2) + (cand_e + ce) / K * 4 + beta_b + bb;
+            const int64_t bb_need = pruning ? (int64_t)(M - 2) * keep * keep : bb;
+            const int64_t need = (cand_e + ce) * (int64_t)(sizeof(int32_t) * 2) + (cand_e + ce) / K * 4 +
+                                 (beta_b + bb) / (K * K) * (bb_need / std::max<int64_t>(M - 2, 1));
             if (end > begin && (size_t)need > budget) break;
             all[(size_t)end].cand = cand_e;
             all[(size_t)end].beta = beta_b;
@@ -436,7 +483,7 @@ hgm_status run_batch(const hgm_model *const *models, int nm, const hgm_scene *co
         CK(g_ws.cand_idx.ensure((size_t)cand_e * sizeof(int32_t)), "workspace (candidates)");
         CK(g_ws.cand_u.ensure((size_t)cand_e * sizeof(float)), "workspace (candidates)");
         CK(g_ws.cand_cnt.ensure((size_t)(cand_e / K) * sizeof(int32_t)), "workspace (candidates)");
-        CK(g_ws.beta.ensure((size_t)beta_b), "workspace (argmin tables)");
+        if (!pruning) CK(g_ws.beta.ensure((size_t)beta_b), "workspace (argmin tables)");
         CK(g_ws.units.ensure((size_t)n * sizeof(Unit)), "workspace (units)");
         CK(g_ws.res.ensure((size_t)n * sizeof(UnitResult)), "workspace (results)");
         CK(g_ws.counter.ensure(sizeof(int)), "workspace");
@@ -448,6 +495,58 @@ hgm_status run_batch(const hgm_model *const *models, int nm, const hgm_scene *co
         CK(launch_select(du, n, dm, ds, p, max_M, g_ws.cand_idx.as<int32_t>(), g_ws.cand_u.as<float>(),
                          g_ws.cand_cnt.as<int32_t>(), st),
            "select kernel");
+        if (pruning) {
+            const int64_t n_lists = cand_e / K;
+            CK(g_ws.cand2_idx.ensure((size_t)n_lists * keep * sizeof(int32_t)), "workspace (pruned lists)");
+            CK(g_ws.cand2_u.ensure((size_t)n_lists * keep * sizeof(float)), "workspace (pruned lists)");
+            CK(g_ws.cand2_cnt.ensure((size_t)n_lists * sizeof(int32_t)), "workspace (pruned lists)");
+            CK(g_ws.units2.ensure((size_t)n * sizeof(Unit)), "workspace (units)");
+            CK(g_ws.beta2.ensure((size_t)(beta_b / ((int64_t)K * K) * keep * keep) + 1), "workspace (argmin tables)");
+            CK(g_ws.scores.ensure((size_t)cand_e * sizeof(float)), "workspace (scores)");
+            CK(launch_prop_prune(du, n, dm, ds, p, pi, g_ws.cand_idx.as<int32_t>(), g_ws.cand_u.as<float>(),
+                                 g_ws.cand_cnt.as<int32_t>(), g_ws.scores.as<float>(), g_ws.cand2_idx.as<int32_t>(),
+                                 g_ws.cand2_u.as<float>(), g_ws.cand2_cnt.as<int32_t>(), g_ws.status.as<int>(), st),
+               "pruning kernels");
+            CK(launch_derive_units(du, n, K, keep, g_ws.units2.as<Unit>(), st), "derive units");
+            Params pk = p;
+            pk.K = keep;
+            pk.rescore = 0;
+            const Unit *du2 = g_ws.units2.as<Unit>();
+            CK(launch_recurse(du2, n, dm, ds, pk, g_ws.cand2_idx.as<int32_t>(), g_ws.cand2_u.as<float>(),
+                              g_ws.cand2_cnt.as<int32_t>(), g_ws.beta2.as<uint8_t>(), g_ws.res.as<UnitResult>(),
+                              g_ws.counter.as<int>(), st),
+               "recursion kernel (pruned lists)");
+            CK(launch_backtrack(du2, n, dm, ds, pk, g_ws.cand2_idx.as<int32_t>(), g_ws.beta2.as<uint8_t>(),
+                                g_ws.res.as<UnitResult>(), d_energy, d_assign, st),
+               "backtrack kernel (pruned lists)");
+            // fallback: units whose pruned optimum is infeasible are solved again on the full lists
+            const int bstride = (max_M - 2) * K * K;
+            CK(g_ws.fb_units.ensure((size_t)n * sizeof(Unit)), "workspace (fallback)");
+            CK(g_ws.fb_count.ensure(sizeof(int)), "workspace");
+            CK(cudaMemsetAsync(g_ws.fb_count.p, 0, sizeof(int), st), "memset");
+            CK(launch_collect_infeasible(g_ws.res.as<UnitResult>(), du, n, bstride, g_ws.fb_units.as<Unit>(),
+                                         g_ws.fb_count.as<int>(), st),
+               "collect infeasible");
+            int n_fb = 0;
+            CK(cudaMemcpyAsync(&n_fb, g_ws.fb_count.p, sizeof(int), cudaMemcpyDeviceToHost, st), "fallback count");
+            CK(cudaStreamSynchronize(st), "synchronise");
+            g_pruned_units += n;
+            g_fallback_units += n_fb;
+            if (n_fb > 0) {
+                CK(g_ws.beta_fb.ensure((size_t)n_fb * bstride), "workspace (fallback)");
+                CK(g_ws.res_fb.ensure((size_t)n_fb * sizeof(UnitResult)), "workspace (fallback)");
+                const Unit *dfb = g_ws.fb_units.as<Unit>();
+                CK(launch_recurse(dfb, n_fb, dm, ds, p, g_ws.cand_idx.as<int32_t>(), g_ws.cand_u.as<float>(),
+                                  g_ws.cand_cnt.as<int32_t>(), g_ws.beta_fb.as<uint8_t>(), g_ws.res_fb.as<UnitResult>(),
+                                  g_ws.counter.as<int>(), st),
+                   "recursion kernel (fallback)");
+                CK(launch_backtrack(dfb, n_fb, dm, ds, p, g_ws.cand_idx.as<int32_t>(), g_ws.beta_fb.as<uint8_t>(),
+                                    g_ws.res_fb.as<UnitResult>(), d_energy, d_assign, st),
+                   "backtrack kernel (fallback)");
+            }
+            begin = end;
+            continue;
+        }
         if (g_count_mode) {
             CK(g_ws.evaluated.ensure(sizeof(unsigned long long)), "workspace");
             CK(launch_recurse_count(du, n, dm, ds, p, g_ws.cand_idx.as<int32_t>(), g_ws.cand_u.as<float>(),
@@ -552,6 +651,8 @@ void hgm_default_params(hgm_params *p)
     p->precision = 0;
     p->offset_lo = INT32_MIN;
     p->offset_hi = INT32_MAX;
+    p->prune = nullptr;
+    p->keep = 8;
 }
 
 const char *hgm_last_error(void) { return g_err.c_str(); }
@@ -927,6 +1028,15 @@ hgm_status hgm_profile_enable(int32_t on)
     std::lock_guard<std::mutex> lk(g_prof_mu);
     g_prof_on = on == 1;
     g_count_mode = on == 2;
+    return HGM_OK;
+}
+
+hgm_status hgm_prune_counters(int64_t *pruned_units, int64_t *fallback_units, int32_t reset)
+{
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (pruned_units) *pruned_units = g_pruned_units;
+    if (fallback_units) *fallback_units = g_fallback_units;
+    if (reset) g_pruned_units = g_fallback_units = 0;
     return HGM_OK;
 }
 

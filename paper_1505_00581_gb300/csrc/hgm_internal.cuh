@@ -55,6 +55,7 @@ struct SceneRec {
     int64_t upitch;      // row pitch of U in floats (>= S)
     int32_t S, n_frames;
     const float *f;      // sorted descriptors, row stride Params::F
+    const float *pq;     // proposal network: W1b f'_j per sorted point [S x 128] (pruned mode only)
 };
 
 // One matching problem: a (model, scene, offset) triple.
@@ -82,7 +83,26 @@ struct Params {
 
 constexpr int kRescore = 8;   // candidates per list re-scored in FP32 by the BF16 precision mode
 
-enum ProfKernel { kProfUnary = 0, kProfSelect = 1, kProfRecurse = 2, kProfBacktrack = 3, kProfCount = 4 };
+enum ProfKernel { kProfUnary = 0, kProfSelect = 1, kProfRecurse = 2, kProfBacktrack = 3, kProfPrune = 4, kProfCount = 5 };
+
+// Proposal network operands for the pruning kernel (device pointers into the weights).
+struct PropInfer {
+    const float *P;      // [R x 128]: W1a f_i + b1 per model row of the batch
+    const float *W2, *b2, *w3, *b3;
+    const float *w1c;    // W1 columns 2F..2F+2 (row stride dp)
+    int dp;
+    float inv_window;    // 1 / max(w, 1)
+    int keep;            // candidates kept per list
+    int rescore;         // 1: kept candidates' U recomputed in FP32 (precision mode)
+};
+// Scores every candidate (scores [n_lists x K] scratch) and keeps the pi.keep best per list.
+cudaError_t launch_prop_prune(const Unit *units, int64_t n_units, const ModelRec *models, const SceneRec *scenes,
+                              Params p, const PropInfer &pi, const int32_t *cand_idx, const float *cand_u,
+                              const int32_t *cand_cnt, float *scores, int32_t *out_idx, float *out_u,
+                              int32_t *out_cnt, int *status, cudaStream_t st);
+cudaError_t launch_derive_units(const Unit *in, int64_t n, int K, int keep, Unit *out, cudaStream_t st);
+cudaError_t launch_collect_infeasible(const UnitResult *res, const Unit *units, int64_t n, int beta_stride, Unit *list,
+                                      int *count, cudaStream_t st);
 
 // ---- kernel launchers (each checks its own launch error) --------------------
 cudaError_t launch_unary(const float *A, int R, const float *B, int S, int F, float lambda1, float *U,
@@ -100,6 +120,10 @@ cudaError_t launch_select(const Unit *units, int64_t n_units, const ModelRec *mo
 cudaError_t launch_recurse(const Unit *units, int64_t n_units, const ModelRec *models, const SceneRec *scenes,
                            Params p, const int32_t *cand_idx, const float *cand_u, const int32_t *cand_cnt,
                            uint8_t *beta, UnitResult *res, int *work_counter, cudaStream_t st);
+// k_recurse_small.cu: warp-per-unit recursion for lists of at most 16 candidates.
+cudaError_t launch_recurse_small(const Unit *units, int64_t n_units, const ModelRec *models, const SceneRec *scenes,
+                                 Params p, const int32_t *cand_idx, const float *cand_u, const int32_t *cand_cnt,
+                                 uint8_t *beta, UnitResult *res, cudaStream_t st);
 // Tile variant of the recursion kernel used by launch_recurse (autotuned): 0..count-1.
 int recurse_variant_count();
 void set_recurse_variant(int v);

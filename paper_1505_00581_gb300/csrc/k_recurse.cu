@@ -34,29 +34,13 @@
 // Work split per step: warps build the kept lists of one b each; then tiles
 // of one b and CT consecutive c with t'(c) <= t'(b) are flattened across the
 // CTA's threads, each thread looping over the kept a of its b.
-#include "fast_math.cuh"
-#include "hgm_internal.cuh"
+#include "recurse_common.cuh"
 
 namespace hgm {
 namespace {
 
 constexpr float kInf = __builtin_huge_valf();
 constexpr float kGeoMax = 4.45f;   // > pi*sqrt(2) = 4.4429, bound of the FP32 D^g
-
-__device__ __forceinline__ float sqrt_fast(float x)
-{
-    float r;
-    asm("sqrt.approx.f32 %0, %1;" : "=f"(r) : "f"(x));
-    return r;
-}
-
-__device__ __forceinline__ float wrap_pi(float v)
-{
-    // argument in [-3pi, 3pi]: one fold to [-pi, pi]
-    if (v > kPi) v -= kTwoPi;
-    else if (v < -kPi) v += kTwoPi;
-    return v;
-}
 
 __device__ __forceinline__ uint32_t lanemask_lt()
 {
@@ -112,12 +96,6 @@ __device__ void load_list(List<KM> &L, const SceneRec &sc, const int32_t *cidx, 
         }
     }
     if (tid == 0) L.n = n;
-}
-
-__device__ __forceinline__ float signed_angle(float2 v, float2 p, float2 q)
-{
-    // angle at v from v->p to v->q (reading R1), wrapped to [-pi, pi]
-    return wrap_pi(fast_atan2(q.y - v.y, q.x - v.x) - fast_atan2(p.y - v.y, p.x - v.x));
 }
 
 // (value, slot) minimum with ties to the lower slot
@@ -185,7 +163,7 @@ recurse_kernel(const Unit *__restrict__ units, int64_t n_units, const ModelRec *
                 const float A1 = signed_angle(mj, mi, mk);   // at i-1, from ->i to ->i-2
                 const float A2 = signed_angle(mi, mj, mk);   // at i, from ->i-1 to ->i-2
                 sm.A1 = A1;
-                sm.k2 = wrap_pi(A2 - A1 + kPi);              // p2 = p1 + k2 (mod 2pi)
+                sm.k2 = wrap_pi(__fadd_rn(__fsub_rn(A2, A1), kPi));   // p2 = p1 + k2 (mod 2pi)
                 sm.dt_ab = md.t[i] - md.t[i - 1];
                 sm.dt_bc = md.t[i - 1] - md.t[i - 2];
             }
@@ -222,7 +200,7 @@ recurse_kernel(const Unit *__restrict__ units, int64_t n_units, const ModelRec *
                     const int a = lane + 32 * q;
                     base[q] = kInf;
                     if (a < na && la_t[q] >= tb && la_i[q] != ib)
-                        base[q] = la_u[q] + lam2 * fabsf((float)(dt_ab - (la_t[q] - tb))) + sm.alpha[b * AS + a];
+                        base[q] = base_cost(la_u[q], lam2, dt_ab, la_t[q], tb, sm.alpha[b * AS + a]);
                     argmin_merge(bv, bk, base[q], a);
                 }
 #pragma unroll
@@ -276,7 +254,7 @@ recurse_kernel(const Unit *__restrict__ units, int64_t n_units, const ModelRec *
                     if (keep) {
                         const int pos = kept + __popc(km & lanemask_lt());
                         const float2 pa = LA.xy[a];
-                        const float p1 = wrap_pi(A1 + fast_atan2(pa.y - pb.y, pa.x - pb.x));   // theta(b->a)
+                        const float p1 = wrap_pi(__fadd_rn(A1, direction(pb, pa)));   // A1 + theta(b->a)
                         sm.fb[b * KM + pos] = make_float2(base[q], p1);
                         sm.fs[b * KM + pos] = (uint8_t)a;
                         sm.used[a] = 1;
@@ -310,8 +288,7 @@ recurse_kernel(const Unit *__restrict__ units, int64_t n_units, const ModelRec *
                 if (c < nc) {
                     const int ta = LA.t[a], tc = LC.t[c];
                     if (!(T > 0 && ta - tc >= T) && LA.idx[a] != LC.idx[c]) {
-                        const float2 pa = LA.xy[a], pc = LC.xy[c];
-                        r = fast_atan2(pc.y - pa.y, pc.x - pa.x);           // theta(a->c)
+                        r = direction(LA.xy[a], LC.xy[c]);                   // theta(a->c)
                     }
                 }
                 sm.r[a * RS + c] = r;
@@ -337,7 +314,7 @@ recurse_kernel(const Unit *__restrict__ units, int64_t n_units, const ModelRec *
                 for (int k = 0; k < CT; ++k) {
                     const int c = c0 + k;
                     const bool ok = c < nc && LC.t[c] <= tb && LC.idx[c] != ib;
-                    q1[k] = ok ? fast_atan2(LC.xy[c].y - pb.y, LC.xy[c].x - pb.x) : kInf;   // theta(b->c)
+                    q1[k] = ok ? direction(pb, LC.xy[c]) : kInf;   // theta(b->c)
                     best[k] = kInf;
                     arg[k] = kNoSlot;
                 }
@@ -349,7 +326,7 @@ recurse_kernel(const Unit *__restrict__ units, int64_t n_units, const ModelRec *
                 for (int k = 0; k < nf; ++k) {
                     const float2 e = fbb[k];
                     const int a = fsb[k];
-                    const float p2 = e.y + k2;
+                    const float p2 = __fadd_rn(e.y, k2);
                     float rv[CT];
 #pragma unroll
                     for (int q4 = 0; q4 < CT; q4 += 4) {
@@ -364,11 +341,7 @@ recurse_kernel(const Unit *__restrict__ units, int64_t n_units, const ModelRec *
                     }
 #pragma unroll
                     for (int q = 0; q < CT; ++q) {
-                        const float d1 = e.y - q1[q];
-                        const float d2 = p2 - rv[q];
-                        const float w1 = fminf(fabsf(d1), kTwoPi - fabsf(d1));
-                        const float w2 = fminf(fabsf(d2), kTwoPi - fabsf(d2));
-                        const float v = fmaf(lam23, sqrt_fast(fmaf(w2, w2, w1 * w1)), e.x);
+                        const float v = triple_cost(e.x, e.y, p2, q1[q], rv[q], lam23);
                         if (v < best[q]) { best[q] = v; arg[q] = a; }
                     }
                 }
@@ -379,7 +352,7 @@ recurse_kernel(const Unit *__restrict__ units, int64_t n_units, const ModelRec *
                         float al = kInf;
                         int bt = kNoSlot;
                         if (best[q] < kInf) {
-                            al = best[q] + lam2 * fabsf((float)(dt_bc - (tb - LC.t[c])));
+                            al = cell_alpha(best[q], lam2, dt_bc, tb, LC.t[c]);
                             bt = arg[q];
                         }
                         sm.alpha[c * AS + b] = al;
@@ -494,6 +467,8 @@ cudaError_t launch_recurse(const Unit *units, int64_t n_units, const ModelRec *m
                            uint8_t *beta, UnitResult *res, int *work_counter, cudaStream_t st)
 {
     if (n_units <= 0) return cudaSuccess;
+    if (p.K <= 16)   // short lists (pruned form): one warp per unit
+        return launch_recurse_small(units, n_units, models, scenes, p, cand_idx, cand_u, cand_cnt, beta, res, st);
     return dispatch<false>(g_variant, units, n_units, models, scenes, p, cand_idx, cand_u, cand_cnt, beta, res,
                            work_counter, nullptr, st);
 }

@@ -18,7 +18,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libhgm.so")
 
 HGM_OK, HGM_EINVAL, HGM_ENOMEM, HGM_ECUDA, HGM_ETIMEOUT, HGM_EUNSUPPORTED = range(6)
-KERNELS = ("unary", "select", "recurse", "backtrack")
+KERNELS = ("unary", "select", "recurse", "backtrack", "prune")
 
 # Every function declared in include/hgm.h, with (restype, argtypes).
 _vp = ctypes.c_void_p
@@ -35,7 +35,8 @@ class Params(ctypes.Structure):
     """hgm_params (include/hgm.h)."""
     _fields_ = [("lambda1", ctypes.c_float), ("lambda2", ctypes.c_float), ("lambda3", ctypes.c_float),
                 ("T", ctypes.c_int32), ("window", ctypes.c_int32), ("K", ctypes.c_int32),
-                ("precision", ctypes.c_int32), ("offset_lo", ctypes.c_int32), ("offset_hi", ctypes.c_int32)]
+                ("precision", ctypes.c_int32), ("offset_lo", ctypes.c_int32), ("offset_hi", ctypes.c_int32),
+                ("prune", ctypes.c_void_p), ("keep", ctypes.c_int32)]
 
 
 _PP = ctypes.POINTER(Params)
@@ -71,6 +72,7 @@ SIGNATURES = {
     "hgm_profile_enable": (_i32, [_i32]),
     "hgm_profile_read": (_i32, [_pd, _p64, _i32]),
     "hgm_profile_evaluated": (_i32, [_p64, _i32]),
+    "hgm_prune_counters": (_i32, [_p64, _p64, _i32]),
     "hgm_profile_reset": (_i32, []),
 }
 
@@ -111,6 +113,8 @@ def default_params(**over) -> Params:
     p = Params()
     lib.hgm_default_params(ctypes.byref(p))
     for k, v in over.items():
+        if k == "prune" and v is not None and hasattr(v, "handle"):
+            v = v.handle.value    # a Proposal object
         setattr(p, k, v)
     return p
 
@@ -433,6 +437,12 @@ def gemm_bf16(A, B, C, status, stream=None):
 def profile_enable(on=True):
     """True/1: CUDA-event timing of the kernels; 2: accounting variant of the recursion; False/0: off."""
     _check(load().hgm_profile_enable(int(on)))
+
+
+def prune_counters(reset: bool = False):
+    a, b = ctypes.c_int64(), ctypes.c_int64()
+    _check(load().hgm_prune_counters(ctypes.byref(a), ctypes.byref(b), 1 if reset else 0))
+    return int(a.value), int(b.value)
 
 
 def profile_evaluated(reset: bool = False) -> int:

@@ -157,22 +157,37 @@ def single_match(seed: int = 0) -> Workload:
     return Workload("single_match_M16_F60_K32", [mod], [sc], K=32, window=2)
 
 
-def batched_exact(seed: int = 1, n_models: int = 10, n_scenes: int = 8, M_range=(16, 64),
-                  frames_range=(300, 1500), lam: float = 30.0, implants_per_scene: int = 3) -> Workload:
-    """10 models (M in 16..64) vs 8 scenes of 300-1500 frames, Poisson(30)/frame at 320x240; K=64, w=3."""
-    rng = np.random.default_rng(seed)
-    models = [make_model(rng, int(rng.integers(M_range[0], M_range[1] + 1))) for _ in range(n_models)]
+def batched_scenes(rng: np.random.Generator, models: Sequence[PointSet], n_scenes: int, frames_range=(300, 1500),
+                   lam: float = 30.0, implants_per_scene: int = 3, frame=(320.0, 240.0)) -> List[Scene]:
+    """Scenes of the batched workload for a given model set: clutter from the models' centres, implants of
+    random models at random offsets."""
     pool = np.concatenate([m.centres for m in models])
     scenes = []
     for _ in range(n_scenes):
         nf = int(rng.integers(frames_range[0], frames_range[1] + 1))
         imp = []
         for _ in range(implants_per_scene):
-            m = int(rng.integers(0, n_models))
+            m = int(rng.integers(0, len(models)))
             span = int(models[m].t.max())
             imp.append((m, int(rng.integers(0, max(1, nf - span)))))
-        scenes.append(make_scene(rng, nf, (320.0, 240.0), ("poisson", lam), pool, models, imp))
+        scenes.append(make_scene(rng, nf, frame, ("poisson", lam), pool, models, imp))
+    return scenes
+
+
+def batched_exact(seed: int = 1, n_models: int = 10, n_scenes: int = 8, M_range=(16, 64),
+                  frames_range=(300, 1500), lam: float = 30.0, implants_per_scene: int = 3) -> Workload:
+    """10 models (M in 16..64) vs 8 scenes of 300-1500 frames, Poisson(30)/frame at 320x240; K=64, w=3."""
+    rng = np.random.default_rng(seed)
+    models = [make_model(rng, int(rng.integers(M_range[0], M_range[1] + 1))) for _ in range(n_models)]
+    scenes = batched_scenes(rng, models, n_scenes, frames_range, lam, implants_per_scene)
     return Workload(f"batched_exact_{n_models}x{n_scenes}_K64", models, scenes, K=64, window=3)
+
+
+def training_scenes(wl: Workload, seed: int, n_scenes: int = 3) -> Workload:
+    """The same models with separately seeded scenes (the proposal network's training data)."""
+    rng = np.random.default_rng(seed)
+    scenes = batched_scenes(rng, wl.models, n_scenes)
+    return Workload(wl.name + f"_train{seed}", wl.models, scenes, K=wl.K, window=wl.window, T=wl.T)
 
 
 def precision_long(seed: int = 2, n_models: int = 50, n_frames: int = 30000, M_range=(32, 128),
