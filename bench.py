@@ -203,7 +203,9 @@ def run_pruned(args, torch, hgm, wl, models, scenes, energy, assign, es, as_, de
     e2 = torch.empty_like(energy)
     a2 = torch.empty_like(assign)
     hgm.prune_counters(reset=True)
+    torch.cuda.profiler.start()
     ms, prof = _time_form(torch, hgm, models, scenes, p, e2, a2, args.steps, args.warmup, stream, flush)
+    torch.cuda.profiler.stop()
     n_pruned, n_fb = hgm.prune_counters(reset=True)
     blocks = []
     for mi, m in enumerate(wl.models):

@@ -147,7 +147,10 @@ HGM_API hgm_status hgm_batch_layout(const hgm_model *const *models, int32_t n_mo
 
 /* Solves every offset of every (model, scene) pair in one pass: the unit
  * list (model, scene, offset) is ordered by decreasing model size and run by
- * persistent kernels, in chunks bounded by the workspace budget.
+ * persistent kernels, in chunks bounded by the workspace budget. Scenes whose
+ * unary table (model points x scene points x 4 bytes) exceeds the budget are
+ * cut into offset segments (each with the frames its windows reach), solved
+ * group by group; results do not depend on the segmentation.
  * energy (host or device, or NULL) and assign (host or device, or NULL) use
  * the layout of hgm_batch_layout. */
 HGM_API hgm_status hgm_match_batch(const hgm_model *const *models, int32_t n_models, const hgm_scene *const *scenes,
@@ -188,7 +191,8 @@ HGM_API hgm_status hgm_prop_train_step(hgm_prop *prop, const float *X, const flo
 /* ---- tuning ---------------------------------------------------------------- */
 
 /* The recursion kernel (Eq. 10) comes in tile variants that differ only in how
- * many z_{i-2} cells one thread carries (0: 4, 1: 2, 2: 8); results are
+ * the work is split (0: 4 z_{i-2} cells per thread, 1: 8 cells per thread,
+ * 2: 4 cells per thread with half the threads per unit); results are
  * identical. hgm_autotune times every variant on this batch restricted to
  * offsets [max(offset_lo, 0), +sample_offsets) (full pipeline, CUDA events,
  * best of two after a warm-up), makes the fastest the process-wide choice and
@@ -224,6 +228,11 @@ HGM_API int32_t hgm_get_recurse_variant(void);
  * streams, other threads) race and must be serialised by the caller. */
 HGM_API hgm_status hgm_match_noalloc(const hgm_model *model, const hgm_scene *scene, const hgm_params *params,
                                      void *stream, float *energy, int32_t *assign);
+
+/* Workspace budget in bytes for one segment group's unary table and for one
+ * chunk's candidate lists and argmin tables (0 = automatic: a third of the
+ * free device memory, at most 24 GiB). */
+HGM_API hgm_status hgm_set_workspace_budget(int64_t bytes);
 
 /* ---- kernel-level entry points (used by the parity tests) -------------- */
 

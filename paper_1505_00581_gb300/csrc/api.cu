@@ -142,6 +142,7 @@ struct Workspace {
 };
 Workspace g_ws;
 bool g_count_mode = false;   // hgm_profile_enable(2): batch runs use the accounting recursion variant
+size_t g_budget_override = 0;   // hgm_set_workspace_budget: bytes for the unary table and for a chunk (0 = auto)
 int64_t g_pruned_units = 0, g_fallback_units = 0;
 
 }  // namespace
@@ -294,174 +295,12 @@ hgm_status build_plan(const hgm_model *const *models, int nm, const hgm_scene *c
     return HGM_OK;
 }
 
-hgm_status run_batch(const hgm_model *const *models, int nm, const hgm_scene *const *scenes, int ns,
-                     const hgm_params *hp, cudaStream_t st, float *energy, int32_t *assign)
+// Runs a list of units (one segment group): chunks bounded by the budget for candidate lists and
+// argmin tables; per chunk selection -> (pruning ->) recursion -> backtrack (-> fallback).
+hgm_status run_units(const hgm_model *const *models, std::vector<Unit> &all, int max_M, int K, int keep, bool pruning,
+                     const Params &p, const PropInfer &pi, cudaStream_t st, float *d_energy, int32_t *d_assign,
+                     size_t budget)
 {
-    hgm_status rc = check_params(hp);
-    if (rc) return rc;
-    Plan pl;
-    rc = build_plan(models, nm, scenes, ns, hp, pl);
-    if (rc) return rc;
-    Params p = to_params(hp);
-    const int64_t n_out = pl.e_start.back();
-    const int64_t n_assign = pl.a_start.back();
-    if (n_out == 0 || nm == 0 || ns == 0) return HGM_OK;
-    const int K = p.K;
-    const int F = models[0]->d.F;
-    p.F = F;
-
-    // unary table: all model rows x every scene (row pitch padded to 4)
-    int R = 0, max_M = 0;
-    std::vector<int> urow(nm);
-    for (int m = 0; m < nm; ++m) {
-        urow[m] = R;
-        R += models[m]->d.M;
-        max_M = std::max(max_M, models[m]->d.M);
-    }
-    std::vector<int64_t> ubase(ns);
-    int64_t utot = 0;
-    for (int s = 0; s < ns; ++s) {
-        ubase[s] = utot;
-        utot += (int64_t)R * round_up4(std::max(scenes[s]->d.S, 1));
-    }
-    CK(g_ws.modelcat.ensure((size_t)R * F * sizeof(float)), "workspace (models)");
-    CK(g_ws.U.ensure((size_t)utot * sizeof(float)), "workspace (unary table)");
-    for (int m = 0; m < nm; ++m)
-        CK(cudaMemcpyAsync(g_ws.modelcat.as<float>() + (size_t)urow[m] * F, models[m]->d.f,
-                           (size_t)models[m]->d.M * F * sizeof(float), cudaMemcpyDeviceToDevice, st),
-           "gather model descriptors");
-    std::vector<ModelRec> mrec(nm);
-    for (int m = 0; m < nm; ++m)
-        mrec[m] = ModelRec{models[m]->d.xy, models[m]->d.t, models[m]->d.perm, models[m]->d.M, urow[m],
-                           models[m]->d.f};
-    std::vector<SceneRec> srec(ns);
-    for (int s = 0; s < ns; ++s) {
-        const SceneDev &d = scenes[s]->d;
-        srec[s] = SceneRec{d.xy, d.t, d.frame_start, d.perm, g_ws.U.as<float>() + ubase[s],
-                           (int64_t)round_up4(std::max(d.S, 1)), d.S, d.n_frames, d.f};
-    }
-    // proposal network: per-point projections of its first layer (tensor cores)
-    const hgm_prop *prop = hp->prune;
-    const bool pruning = prop != nullptr;
-    const int keep = pruning ? hp->keep : K;
-    PropInfer pi{};
-    if (pruning) {
-        const int Fu = models[0]->F_user;
-        if (prop->L.F != Fu) return fail(HGM_EINVAL, "proposal network built for F = %d, descriptors have F = %d",
-                                         prop->L.F, Fu);
-        std::vector<int64_t> qbase(ns);
-        int64_t qtot = 0;
-        for (int s = 0; s < ns; ++s) { qbase[s] = qtot; qtot += (int64_t)scenes[s]->d.S * kPropHidden; }
-        CK(g_ws.P.ensure((size_t)R * kPropHidden * sizeof(float)), "workspace (projections)");
-        CK(g_ws.Q.ensure((size_t)std::max<int64_t>(qtot, 1) * sizeof(float)), "workspace (projections)");
-        CK(g_ws.status.ensure(sizeof(int)), "workspace");
-        CK(cudaMemsetAsync(g_ws.status.p, 0, sizeof(int), st), "memset");
-        const float *th = prop->theta;
-        CK(launch_rowdot_plain(g_ws.modelcat.as<float>(), R, F, th + prop->L.o_W1, kPropHidden, prop->L.dp, Fu,
-                               th + prop->L.o_b1, g_ws.P.as<float>(), kPropHidden, g_ws.status.as<int>(), st),
-           "projection kernel");
-        for (int s = 0; s < ns; ++s) {
-            const SceneDev &d = scenes[s]->d;
-            CK(launch_rowdot_plain(d.f, d.S, F, th + prop->L.o_W1 + Fu, kPropHidden, prop->L.dp, Fu, nullptr,
-                                   g_ws.Q.as<float>() + qbase[s], kPropHidden, g_ws.status.as<int>(), st),
-               "projection kernel");
-            srec[s].pq = g_ws.Q.as<float>() + qbase[s];
-        }
-        pi.P = g_ws.P.as<float>();
-        pi.W2 = th + prop->L.o_W2;
-        pi.b2 = th + prop->L.o_b2;
-        pi.w3 = th + prop->L.o_w3;
-        pi.b3 = th + prop->L.o_b3;
-        pi.w1c = th + prop->L.o_W1 + 2 * Fu;
-        pi.dp = prop->L.dp;
-        pi.inv_window = 1.0f / (float)std::max(hp->window, 1);
-        pi.keep = keep;
-        pi.rescore = hp->precision == 1 ? 1 : 0;
-        p.rescore = 0;   // the kept candidates are re-scored by the pruning kernel instead
-    }
-    CK(g_ws.mrec.ensure(nm * sizeof(ModelRec)), "workspace");
-    CK(g_ws.srec.ensure(ns * sizeof(SceneRec)), "workspace");
-    CK(cudaMemcpyAsync(g_ws.mrec.p, mrec.data(), nm * sizeof(ModelRec), cudaMemcpyHostToDevice, st), "upload");
-    CK(cudaMemcpyAsync(g_ws.srec.p, srec.data(), ns * sizeof(SceneRec), cudaMemcpyHostToDevice, st), "upload");
-    if (hp->precision == 1) {
-        // BF16 tensor-core unary table (norms of the BF16-rounded rows in FP32)
-        int64_t smax = 0;
-        for (int s = 0; s < ns; ++s) smax = std::max<int64_t>(smax, scenes[s]->d.S);
-        CK(g_ws.mnorm.ensure((size_t)R * sizeof(float)), "workspace (norms)");
-        CK(g_ws.snorm.ensure((size_t)std::max<int64_t>(smax, 1) * sizeof(float)), "workspace (norms)");
-        CK(g_ws.status.ensure(sizeof(int)), "workspace");
-        CK(cudaMemsetAsync(g_ws.status.p, 0, sizeof(int), st), "memset");
-        CK(launch_sqnorm_bf16(g_ws.modelcat.as<float>(), R, F, F, g_ws.mnorm.as<float>(), st), "norm kernel");
-        for (int s = 0; s < ns; ++s) {
-            const SceneDev &d = scenes[s]->d;
-            CK(launch_sqnorm_bf16(d.f, d.S, F, F, g_ws.snorm.as<float>(), st), "norm kernel");
-            CK(launch_unary_bf16(g_ws.modelcat.as<float>(), R, d.f, d.S, F, F, g_ws.mnorm.as<float>(),
-                                 g_ws.snorm.as<float>(), p.lambda1, g_ws.U.as<float>() + ubase[s], srec[s].upitch,
-                                 g_ws.status.as<int>(), st),
-               "BF16 unary kernel");
-        }
-    } else {
-        for (int s = 0; s < ns; ++s) {
-            const SceneDev &d = scenes[s]->d;
-            CK(launch_unary(g_ws.modelcat.as<float>(), R, d.f, d.S, F, p.lambda1, g_ws.U.as<float>() + ubase[s],
-                            (int)srec[s].upitch, st),
-               "unary kernel");
-        }
-    }
-
-    // outputs: device pointers are written in place, host ones through staging
-    const bool e_dev = energy && is_device_ptr(energy);
-    const bool a_dev = assign && is_device_ptr(assign);
-    float *d_energy = nullptr;
-    int32_t *d_assign = nullptr;
-    if (energy) {
-        if (e_dev) d_energy = energy;
-        else {
-            CK(g_ws.out_e.ensure((size_t)n_out * sizeof(float)), "workspace (energy)");
-            d_energy = g_ws.out_e.as<float>();
-        }
-    }
-    if (assign) {
-        if (a_dev) d_assign = assign;
-        else {
-            CK(g_ws.out_a.ensure((size_t)n_assign * sizeof(int32_t)), "workspace (assign)");
-            d_assign = g_ws.out_a.as<int32_t>();
-        }
-    }
-
-    // units, longest first (counting sort by model size, stable)
-    std::vector<Unit> all;
-    all.reserve((size_t)n_out);
-    std::vector<int64_t> bucket((size_t)max_M + 2, 0);
-    for (int m = 0; m < nm; ++m)
-        for (int s = 0; s < ns; ++s) {
-            size_t q = (size_t)m * ns + s;
-            bucket[(size_t)(max_M - models[m]->d.M)] += pl.e_start[q + 1] - pl.e_start[q];
-        }
-    std::vector<int64_t> pos(bucket.size() + 1, 0);
-    for (size_t k = 0; k < bucket.size(); ++k) pos[k + 1] = pos[k] + bucket[k];
-    all.resize((size_t)n_out);
-    for (int m = 0; m < nm; ++m)
-        for (int s = 0; s < ns; ++s) {
-            size_t q = (size_t)m * ns + s;
-            int64_t n = pl.e_start[q + 1] - pl.e_start[q];
-            const int M = models[m]->d.M;
-            int64_t &w = pos[(size_t)(max_M - M)];
-            for (int64_t k = 0; k < n; ++k) {
-                Unit u{};
-                u.model = m;
-                u.scene = s;
-                u.offset = pl.first[q] + (int32_t)k;
-                u.out_e = pl.e_start[q] + k;
-                u.out_a = pl.a_start[q] + k * M;
-                all[(size_t)w++] = u;
-            }
-        }
-
-    // chunks bounded by the workspace budget for candidate lists and argmin tables
-    size_t free_b = 0, total_b = 0;
-    CK(cudaMemGetInfo(&free_b, &total_b), "cudaMemGetInfo");
-    const size_t budget = std::max<size_t>((size_t)256 << 20, std::min<size_t>((size_t)24 << 30, free_b / 2));
     const int64_t n_units = (int64_t)all.size();
     int64_t begin = 0;
     while (begin < n_units) {
@@ -563,6 +402,243 @@ hgm_status run_batch(const hgm_model *const *models, int nm, const hgm_scene *co
                             g_ws.res.as<UnitResult>(), d_energy, d_assign, st),
            "backtrack kernel");
         begin = end;
+    }
+    return HGM_OK;
+}
+
+// A scene segment: offsets [oa, ob) of scene s; its unary-table block covers the
+// sorted points [j0, j1) of the frames every model's windows can reach from them.
+struct Segment {
+    int s;
+    int32_t oa, ob;
+    int64_t j0, j1;
+};
+
+hgm_status run_batch(const hgm_model *const *models, int nm, const hgm_scene *const *scenes, int ns,
+                     const hgm_params *hp, cudaStream_t st, float *energy, int32_t *assign)
+{
+    hgm_status rc = check_params(hp);
+    if (rc) return rc;
+    Plan pl;
+    rc = build_plan(models, nm, scenes, ns, hp, pl);
+    if (rc) return rc;
+    Params p = to_params(hp);
+    const int64_t n_out = pl.e_start.back();
+    const int64_t n_assign = pl.a_start.back();
+    if (n_out == 0 || nm == 0 || ns == 0) return HGM_OK;
+    const int K = p.K;
+    const int F = models[0]->d.F;
+    p.F = F;
+
+    // model rows of the unary table (all models of the batch)
+    int R = 0, max_M = 0, tmin_all = INT32_MAX, tmax_all = INT32_MIN;
+    std::vector<int> urow(nm);
+    for (int m = 0; m < nm; ++m) {
+        urow[m] = R;
+        R += models[m]->d.M;
+        max_M = std::max(max_M, models[m]->d.M);
+        tmin_all = std::min(tmin_all, models[m]->t_sorted.front());
+        tmax_all = std::max(tmax_all, models[m]->t_sorted.back());
+    }
+    CK(g_ws.modelcat.ensure((size_t)R * F * sizeof(float)), "workspace (models)");
+    for (int m = 0; m < nm; ++m)
+        CK(cudaMemcpyAsync(g_ws.modelcat.as<float>() + (size_t)urow[m] * F, models[m]->d.f,
+                           (size_t)models[m]->d.M * F * sizeof(float), cudaMemcpyDeviceToDevice, st),
+           "gather model descriptors");
+    std::vector<ModelRec> mrec(nm);
+    for (int m = 0; m < nm; ++m)
+        mrec[m] = ModelRec{models[m]->d.xy, models[m]->d.t, models[m]->d.perm, models[m]->d.M, urow[m],
+                           models[m]->d.f};
+    CK(g_ws.mrec.ensure(nm * sizeof(ModelRec)), "workspace");
+    CK(cudaMemcpyAsync(g_ws.mrec.p, mrec.data(), nm * sizeof(ModelRec), cudaMemcpyHostToDevice, st), "upload");
+    CK(g_ws.status.ensure(sizeof(int)), "workspace");
+    CK(cudaMemsetAsync(g_ws.status.p, 0, sizeof(int), st), "memset");
+
+    // proposal network: first-layer projections of the model points (the scene points' per segment)
+    const hgm_prop *prop = hp->prune;
+    const bool pruning = prop != nullptr;
+    const int keep = pruning ? hp->keep : K;
+    const int Fu = models[0]->F_user;
+    PropInfer pi{};
+    if (pruning) {
+        if (prop->L.F != Fu) return fail(HGM_EINVAL, "proposal network built for F = %d, descriptors have F = %d",
+                                         prop->L.F, Fu);
+        const float *th = prop->theta;
+        CK(g_ws.P.ensure((size_t)R * kPropHidden * sizeof(float)), "workspace (projections)");
+        CK(launch_rowdot_plain(g_ws.modelcat.as<float>(), R, F, th + prop->L.o_W1, kPropHidden, prop->L.dp, Fu,
+                               th + prop->L.o_b1, g_ws.P.as<float>(), kPropHidden, g_ws.status.as<int>(), st),
+           "projection kernel");
+        pi.P = g_ws.P.as<float>();
+        pi.W2 = th + prop->L.o_W2;
+        pi.b2 = th + prop->L.o_b2;
+        pi.w3 = th + prop->L.o_w3;
+        pi.b3 = th + prop->L.o_b3;
+        pi.w1c = th + prop->L.o_W1 + 2 * Fu;
+        pi.dp = prop->L.dp;
+        pi.inv_window = 1.0f / (float)std::max(hp->window, 1);
+        pi.keep = keep;
+        pi.rescore = hp->precision == 1 ? 1 : 0;
+        p.rescore = 0;   // the kept candidates are re-scored by the pruning kernel instead
+    }
+    if (hp->precision == 1) {
+        CK(g_ws.mnorm.ensure((size_t)R * sizeof(float)), "workspace (norms)");
+        CK(launch_sqnorm_bf16(g_ws.modelcat.as<float>(), R, F, F, g_ws.mnorm.as<float>(), st), "norm kernel");
+    }
+
+    // outputs: device pointers are written in place, host ones through staging
+    const bool e_dev = energy && is_device_ptr(energy);
+    const bool a_dev = assign && is_device_ptr(assign);
+    float *d_energy = nullptr;
+    int32_t *d_assign = nullptr;
+    if (energy) {
+        if (e_dev) d_energy = energy;
+        else {
+            CK(g_ws.out_e.ensure((size_t)n_out * sizeof(float)), "workspace (energy)");
+            d_energy = g_ws.out_e.as<float>();
+        }
+    }
+    if (assign) {
+        if (a_dev) d_assign = assign;
+        else {
+            CK(g_ws.out_a.ensure((size_t)n_assign * sizeof(int32_t)), "workspace (assign)");
+            d_assign = g_ws.out_a.as<int32_t>();
+        }
+    }
+
+    // budgets: unary table (+ projections) per segment group, and candidate lists + argmin tables per chunk
+    size_t free_b = 0, total_b = 0;
+    CK(cudaMemGetInfo(&free_b, &total_b), "cudaMemGetInfo");
+    const size_t budget = g_budget_override ? g_budget_override
+                                            : std::max<size_t>((size_t)256 << 20,
+                                                               std::min<size_t>((size_t)24 << 30, free_b / 3));
+    const int64_t per_point = (int64_t)R * 4 + (pruning ? (int64_t)kPropHidden * 4 : 0);
+    const int64_t max_points = std::max<int64_t>(1, (int64_t)budget / per_point);
+
+    // segments: per scene, runs of offsets whose reachable frames hold at most max_points points
+    std::vector<Segment> segs;
+    for (int s = 0; s < ns; ++s) {
+        int64_t o_lo = INT64_MAX, o_hi = INT64_MIN;
+        for (int m = 0; m < nm; ++m) {
+            const size_t q = (size_t)m * ns + s;
+            const int64_t n = pl.e_start[q + 1] - pl.e_start[q];
+            if (n > 0) {
+                o_lo = std::min<int64_t>(o_lo, pl.first[q]);
+                o_hi = std::max<int64_t>(o_hi, (int64_t)pl.first[q] + n - 1);
+            }
+        }
+        if (o_lo > o_hi) continue;
+        const std::vector<int32_t> &fs = scenes[s]->fs_host;
+        const int nf = scenes[s]->d.n_frames;
+        auto frame_lo = [&](int64_t oa) { return (int)std::max<int64_t>(0, oa + tmin_all - hp->window); };
+        auto frame_hi = [&](int64_t ob) { return (int)std::min<int64_t>(nf - 1, ob - 1 + tmax_all + hp->window); };
+        int64_t oa = o_lo;
+        while (oa <= o_hi) {
+            int64_t ob = oa + 1;
+            const int64_t j0 = fs[(size_t)frame_lo(oa)];
+            while (ob <= o_hi && fs[(size_t)frame_hi(ob + 1) + 1] - j0 <= max_points) ++ob;
+            segs.push_back(Segment{s, (int32_t)oa, (int32_t)ob, j0, (int64_t)fs[(size_t)frame_hi(ob) + 1]});
+            oa = ob;
+        }
+    }
+
+    size_t gbegin = 0;
+    while (gbegin < segs.size()) {
+        // a group of consecutive segments whose unary tables fit together
+        size_t gend = gbegin;
+        int64_t gpoints = 0;
+        while (gend < segs.size()) {
+            const int64_t pts = round_up4((int)std::max<int64_t>(segs[gend].j1 - segs[gend].j0, 1));
+            if (gend > gbegin && gpoints + pts > max_points) break;
+            gpoints += pts;
+            ++gend;
+        }
+        const int ng = (int)(gend - gbegin);
+        CK(g_ws.U.ensure((size_t)R * gpoints * sizeof(float)), "workspace (unary table)");
+        if (pruning) CK(g_ws.Q.ensure((size_t)gpoints * kPropHidden * sizeof(float)), "workspace (projections)");
+        std::vector<SceneRec> srec((size_t)ng);
+        int64_t off = 0, smax = 0;
+        for (int g = 0; g < ng; ++g) {
+            const Segment &sg = segs[gbegin + g];
+            const SceneDev &d = scenes[sg.s]->d;
+            const int64_t pts = sg.j1 - sg.j0, pitch = round_up4((int)std::max<int64_t>(pts, 1));
+            SceneRec r{d.xy, d.t, d.frame_start, d.perm, g_ws.U.as<float>() + (size_t)R * off, pitch, d.S, d.n_frames,
+                       d.f};
+            r.ucol0 = sg.j0;
+            if (pruning) r.pq = g_ws.Q.as<float>() + (size_t)off * kPropHidden;
+            srec[(size_t)g] = r;
+            off += pitch;
+            smax = std::max(smax, pts);
+        }
+        CK(g_ws.srec.ensure((size_t)ng * sizeof(SceneRec)), "workspace");
+        CK(cudaMemcpyAsync(g_ws.srec.p, srec.data(), (size_t)ng * sizeof(SceneRec), cudaMemcpyHostToDevice, st),
+           "upload");
+        if (hp->precision == 1) CK(g_ws.snorm.ensure((size_t)std::max<int64_t>(smax, 1) * sizeof(float)), "workspace");
+        for (int g = 0; g < ng; ++g) {
+            const Segment &sg = segs[gbegin + g];
+            const SceneDev &d = scenes[sg.s]->d;
+            const float *segf = d.f + (size_t)sg.j0 * F;
+            const int pts = (int)(sg.j1 - sg.j0);
+            float *U = const_cast<float *>(srec[(size_t)g].U);
+            if (hp->precision == 1) {
+                CK(launch_sqnorm_bf16(segf, pts, F, F, g_ws.snorm.as<float>(), st), "norm kernel");
+                CK(launch_unary_bf16(g_ws.modelcat.as<float>(), R, segf, pts, F, F, g_ws.mnorm.as<float>(),
+                                     g_ws.snorm.as<float>(), p.lambda1, U, srec[(size_t)g].upitch,
+                                     g_ws.status.as<int>(), st),
+                   "BF16 unary kernel");
+            } else {
+                CK(launch_unary(g_ws.modelcat.as<float>(), R, segf, pts, F, p.lambda1, U, (int)srec[(size_t)g].upitch,
+                                st),
+                   "unary kernel");
+            }
+            if (pruning) {
+                const float *th = prop->theta;
+                CK(launch_rowdot_plain(segf, pts, F, th + prop->L.o_W1 + Fu, kPropHidden, prop->L.dp, Fu, nullptr,
+                                       const_cast<float *>(srec[(size_t)g].pq), kPropHidden, g_ws.status.as<int>(),
+                                       st),
+                   "projection kernel");
+            }
+        }
+
+        // units of the group, longest first (counting sort by model size, stable)
+        std::vector<int64_t> bucket((size_t)max_M + 2, 0);
+        auto span = [&](int m, int g, int64_t &lo, int64_t &hi) {
+            const Segment &sg = segs[gbegin + g];
+            const size_t q = (size_t)m * ns + sg.s;
+            const int64_t n = pl.e_start[q + 1] - pl.e_start[q];
+            lo = std::max<int64_t>(sg.oa, pl.first[q]);
+            hi = std::min<int64_t>(sg.ob, (int64_t)pl.first[q] + n);
+        };
+        int64_t n_units = 0;
+        for (int m = 0; m < nm; ++m)
+            for (int g = 0; g < ng; ++g) {
+                int64_t lo, hi;
+                span(m, g, lo, hi);
+                if (hi > lo) { bucket[(size_t)(max_M - models[m]->d.M)] += hi - lo; n_units += hi - lo; }
+            }
+        std::vector<int64_t> pos(bucket.size() + 1, 0);
+        for (size_t k = 0; k < bucket.size(); ++k) pos[k + 1] = pos[k] + bucket[k];
+        std::vector<Unit> all((size_t)n_units);
+        for (int m = 0; m < nm; ++m)
+            for (int g = 0; g < ng; ++g) {
+                int64_t lo, hi;
+                span(m, g, lo, hi);
+                const Segment &sg = segs[gbegin + g];
+                const size_t q = (size_t)m * ns + sg.s;
+                const int M = models[m]->d.M;
+                int64_t &w = pos[(size_t)(max_M - M)];
+                for (int64_t o = lo; o < hi; ++o) {
+                    Unit u{};
+                    u.model = m;
+                    u.scene = g;
+                    u.offset = (int32_t)o;
+                    u.out_e = pl.e_start[q] + (o - pl.first[q]);
+                    u.out_a = pl.a_start[q] + (o - pl.first[q]) * M;
+                    all[(size_t)w++] = u;
+                }
+            }
+        rc = run_units(models, all, max_M, K, keep, pruning, p, pi, st, d_energy, d_assign, budget);
+        if (rc) return rc;
+        gbegin = gend;
     }
     if (energy && !e_dev)
         CK(cudaMemcpyAsync(energy, d_energy, (size_t)n_out * sizeof(float), cudaMemcpyDeviceToHost, st), "energy D2H");
@@ -767,6 +843,7 @@ hgm_status hgm_create_scene(const float *xy, const int32_t *t, const float *desc
     s->d = SceneDev{S, Fp, n_frames, nullptr, nullptr, nullptr, nullptr, nullptr};
     s->F_user = F;
     s->perm = perm;
+    s->fs_host = fs;
     if ((rc = upload(&s->d.xy, sxy, st)) || (rc = upload(&s->d.t, stt, st)) || (rc = upload(&s->d.f, sf, st)) ||
         (rc = upload(&s->d.frame_start, fs, st)) || (rc = upload(&s->d.perm, perm, st))) {
         free_scene(s);
@@ -1028,6 +1105,15 @@ hgm_status hgm_profile_enable(int32_t on)
     std::lock_guard<std::mutex> lk(g_prof_mu);
     g_prof_on = on == 1;
     g_count_mode = on == 2;
+    return HGM_OK;
+}
+
+hgm_status hgm_set_workspace_budget(int64_t bytes)
+{
+    std::lock_guard<std::mutex> lk(g_mu);
+    g_err.clear();
+    if (bytes < 0) return fail(HGM_EINVAL, "budget must be >= 0");
+    g_budget_override = (size_t)bytes;
     return HGM_OK;
 }
 

@@ -55,7 +55,8 @@ struct SceneRec {
     int64_t upitch;      // row pitch of U in floats (>= S)
     int32_t S, n_frames;
     const float *f;      // sorted descriptors, row stride Params::F
-    const float *pq;     // proposal network: W1b f'_j per sorted point [S x 128] (pruned mode only)
+    const float *pq;     // proposal network: W1b f'_j per point of the block [.. x 128] (pruned mode only)
+    int64_t ucol0;       // first sorted scene point of the U / pq blocks (a segment of the scene)
 };
 
 // One matching problem: a (model, scene, offset) triple.
@@ -164,6 +165,7 @@ struct hgm_scene {
     hgm::SceneDev d;
     int32_t F_user;
     std::vector<int32_t> perm;
+    std::vector<int32_t> fs_host;    // host copy of the minnode table (segment planning)
 };
 
 namespace hgm {

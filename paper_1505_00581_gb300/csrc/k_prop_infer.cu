@@ -108,7 +108,7 @@ __global__ void __launch_bounds__(256) prop_score_kernel(const Unit *__restrict_
                 const float dx = (sxy.x - mxy.x) * 0.01f, dy = (sxy.y - mxy.y) * 0.01f;
                 const float dt = (float)(sc.t[j] - md.t[list] - un.offset) * pi.inv_window;
                 const float4 *P4 = reinterpret_cast<const float4 *>(pi.P + (int64_t)(md.urow + list) * H + h0);
-                const float4 *Q4 = reinterpret_cast<const float4 *>(sc.pq + (int64_t)j * H + h0);
+                const float4 *Q4 = reinterpret_cast<const float4 *>(sc.pq + (int64_t)(j - sc.ucol0) * H + h0);
 #pragma unroll 2
                 for (int h = 0; h < 64; h += 8) {
                     const float4 pa = P4[h / 4], pb = P4[h / 4 + 1], qa = Q4[h / 4], qb = Q4[h / 4 + 1];

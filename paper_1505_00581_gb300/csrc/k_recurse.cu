@@ -68,7 +68,10 @@ struct Smem {
     uint8_t fs[KM * KM];                  // slot a of each kept entry
     uint8_t used[KM];                     // a kept for some b (its r row is needed)
     int32_t fn[KM];                       // number of kept a per b
-    int32_t pre[KM + 1];                  // tile prefix over b
+    uint8_t tile_b[KM * KM / 4];          // b of every tile of the step (tiles of >= 4 cells)
+    uint16_t tbase[KM];                   // first tile of b
+    uint8_t tcount[KM];                   // tiles of b
+    int32_t ntile;                        // tiles of the step (shared-memory counter)
     List<KM> list[3];
     float red_v[NT / 32];
     int32_t red_k[NT / 32];
@@ -158,6 +161,7 @@ recurse_kernel(const Unit *__restrict__ units, int64_t n_units, const ModelRec *
             // ---- phase 0: new list, model constants of hyperedge (i, i-1, i-2)
             load_list<KM>(LC, sc, cidx + (int64_t)(i - 2) * K, cu + (int64_t)(i - 2) * K, ccnt[i - 2], tid, NT);
             if (tid < KM) sm.used[tid] = 0;
+            if (tid == 0) sm.ntile = 0;
             if (tid == 0) {
                 const float2 mi = md.xy[i], mj = md.xy[i - 1], mk = md.xy[i - 2];
                 const float A1 = signed_angle(mj, mi, mk);   // at i-1, from ->i to ->i-2
@@ -187,25 +191,29 @@ recurse_kernel(const Unit *__restrict__ units, int64_t n_units, const ModelRec *
             }
             for (int b = warp; b < KM; b += NW) {
                 if (b >= nb) {
-                    if (lane == 0) { sm.fn[b] = 0; sm.pre[b + 1] = 0; }
+                    if (lane == 0) { sm.fn[b] = 0; sm.tcount[b] = 0; }
                     continue;
                 }
                 const float2 pb = LB.xy[b];
                 const int tb = LB.t[b], ib = LB.idx[b];
                 float base[AQ];
                 float bv = kInf;
-                int bk = 0x7fffffff;
 #pragma unroll
                 for (int q = 0; q < AQ; ++q) {
                     const int a = lane + 32 * q;
                     base[q] = kInf;
                     if (a < na && la_t[q] >= tb && la_i[q] != ib)
                         base[q] = base_cost(la_u[q], lam2, dt_ab, la_t[q], tb, sm.alpha[b * AS + a]);
-                    argmin_merge(bv, bk, base[q], a);
+                    bv = fminf(bv, base[q]);
                 }
 #pragma unroll
-                for (int off = 16; off > 0; off >>= 1)
-                    argmin_merge(bv, bk, __shfl_xor_sync(0xffffffffu, bv, off), __shfl_xor_sync(0xffffffffu, bk, off));
+                for (int off = 16; off > 0; off >>= 1) bv = fminf(bv, __shfl_xor_sync(0xffffffffu, bv, off));
+                int bk = 0;   // witness: the lowest slot with the smallest base
+#pragma unroll
+                for (int q = AQ - 1; q >= 0; --q) {
+                    const uint32_t hit = __ballot_sync(0xffffffffu, base[q] == bv);
+                    if (hit) bk = __ffs(hit) - 1 + 32 * q;
+                }
                 // c with t'(c) <= t'(b) form a prefix of C: tiles cover it
                 uint32_t cm[AQ];
                 int ccount = 0;
@@ -214,7 +222,14 @@ recurse_kernel(const Unit *__restrict__ units, int64_t n_units, const ModelRec *
                     cm[q] = __ballot_sync(0xffffffffu, lc_t[q] <= tb);
                     ccount += __popc(cm[q]);
                 }
-                if (lane == 0) sm.pre[b + 1] = (ccount + CT - 1) / CT;
+                {
+                    const int nq = (ccount + CT - 1) / CT;
+                    int t0 = 0;
+                    if (lane == 0) t0 = atomicAdd(&sm.ntile, nq);
+                    t0 = __shfl_sync(0xffffffffu, t0, 0);
+                    for (int t = lane; t < nq; t += 32) sm.tile_b[t0 + t] = (uint8_t)b;
+                    if (lane == 0) { sm.tbase[b] = (uint16_t)t0; sm.tcount[b] = (uint8_t)nq; }
+                }
                 if (!(bv < kInf)) {
                     if (lane == 0) sm.fn[b] = 0;
                     continue;
@@ -265,22 +280,7 @@ recurse_kernel(const Unit *__restrict__ units, int64_t n_units, const ModelRec *
             }
             __syncthreads();
 
-            // ---- phase 2: tile prefix; theta(a->c) rows of the kept a
-            if (warp == 0) {
-                int v[AQ], s = 0;
-#pragma unroll
-                for (int q = 0; q < AQ; ++q) { v[q] = sm.pre[1 + lane * AQ + q]; s += v[q]; }
-                int incl = s;
-#pragma unroll
-                for (int off = 1; off < 32; off <<= 1) {
-                    int w = __shfl_up_sync(0xffffffffu, incl, off);
-                    if (lane >= off) incl += w;
-                }
-                int run = incl - s;
-#pragma unroll
-                for (int q = 0; q < AQ; ++q) { run += v[q]; sm.pre[1 + lane * AQ + q] = run; }
-                if (lane == 0) sm.pre[0] = 0;
-            }
+            // ---- phase 2: theta(a->c) rows of the kept a
             for (int e = tid; e < na * KM; e += NT) {
                 const int a = e / KM, c = e % KM;
                 if (!sm.used[a]) continue;
@@ -296,16 +296,11 @@ recurse_kernel(const Unit *__restrict__ units, int64_t n_units, const ModelRec *
             __syncthreads();
 
             // ---- phase 3: tiles (b, CT consecutive c)
-            const int ntile = sm.pre[nb];
+            const int ntile = sm.ntile;
             uint8_t *bstep = ubeta + (int64_t)(i - 2) * K * K;
             for (int tile = tid; tile < ntile; tile += NT) {
-                int lo_b = 0, hi_b = nb;
-                while (hi_b - lo_b > 1) {
-                    const int mid = (lo_b + hi_b) >> 1;
-                    if (sm.pre[mid] <= tile) lo_b = mid; else hi_b = mid;
-                }
-                const int b = lo_b;
-                const int c0 = (tile - sm.pre[b]) * CT;
+                const int b = sm.tile_b[tile];
+                const int c0 = (tile - sm.tbase[b]) * CT;
                 const float2 pb = LB.xy[b];
                 const int tb = LB.t[b], ib = LB.idx[b];
                 float q1[CT], best[CT];
@@ -319,13 +314,14 @@ recurse_kernel(const Unit *__restrict__ units, int64_t n_units, const ModelRec *
                     arg[k] = kNoSlot;
                 }
                 const int nf = sm.fn[b];
-                if constexpr (kCount) n_eval += (unsigned long long)nf * CT;
+
                 const float2 *fbb = sm.fb + b * KM;
                 const uint8_t *fsb = sm.fs + b * KM;
 #pragma unroll 2
                 for (int k = 0; k < nf; ++k) {
                     const float2 e = fbb[k];
                     const int a = fsb[k];
+                    if constexpr (kCount) n_eval += CT;
                     const float p2 = __fadd_rn(e.y, k2);
                     float rv[CT];
 #pragma unroll
@@ -362,7 +358,7 @@ recurse_kernel(const Unit *__restrict__ units, int64_t n_units, const ModelRec *
             }
             // cells (b, c) beyond the tiled prefix are infeasible
             for (int b = warp; b < nb; b += NW) {
-                const int covered = (sm.pre[b + 1] - sm.pre[b]) * CT;
+                const int covered = sm.tcount[b] * CT;
                 for (int c = covered + lane; c < nc; c += 32) {
                     sm.alpha[c * AS + b] = kInf;
                     bstep[b * K + c] = (uint8_t)kNoSlot;
@@ -439,22 +435,22 @@ cudaError_t dispatch(int variant, const Unit *units, int64_t n_units, const Mode
 {
     if (p.K <= 32) {
         if (variant == 1)
-            return launch_recurse_t<32, 128, 2, kCount>(units, n_units, models, scenes, p, cand_idx, cand_u, cand_cnt,
+            return launch_recurse_t<32, 128, 8, kCount>(units, n_units, models, scenes, p, cand_idx, cand_u, cand_cnt,
                                                         beta, res, work_counter, evaluated, st);
         return launch_recurse_t<32, 128, 4, kCount>(units, n_units, models, scenes, p, cand_idx, cand_u, cand_cnt,
                                                     beta, res, work_counter, evaluated, st);
     }
     if (variant == 1)
-        return launch_recurse_t<64, 256, 2, kCount>(units, n_units, models, scenes, p, cand_idx, cand_u, cand_cnt,
+        return launch_recurse_t<64, 256, 8, kCount>(units, n_units, models, scenes, p, cand_idx, cand_u, cand_cnt,
                                                     beta, res, work_counter, evaluated, st);
     if (variant == 2)
-        return launch_recurse_t<64, 256, 8, kCount>(units, n_units, models, scenes, p, cand_idx, cand_u, cand_cnt,
+        return launch_recurse_t<64, 128, 4, kCount>(units, n_units, models, scenes, p, cand_idx, cand_u, cand_cnt,
                                                     beta, res, work_counter, evaluated, st);
     return launch_recurse_t<64, 256, 4, kCount>(units, n_units, models, scenes, p, cand_idx, cand_u, cand_cnt, beta,
                                                 res, work_counter, evaluated, st);
 }
 
-int g_variant = 0;   // recursion tile variant: 0 = 4 c per tile, 1 = 2, 2 = 8 (K > 32 only)
+int g_variant = 0;   // recursion variant: 0 = 4 c per tile, 1 = 8 c per tile, 2 = 4 c per tile on 128 threads
 
 }  // namespace
 

@@ -53,7 +53,7 @@ __global__ void __launch_bounds__(kWarps * 32) select_kernel(const Unit *__restr
                 j0 = sc.frame_start[f0];
                 n = sc.frame_start[f1 + 1] - j0;
             }
-            const float *key = sc.U + (int64_t)(md.urow + i) * sc.upitch + j0;
+            const float *key = sc.U + (int64_t)(md.urow + i) * sc.upitch + (j0 - sc.ucol0);
             int kept = n < K ? n : K;
             if (n <= K) {
                 for (int e = lane; e < K; e += 32) {

@@ -61,6 +61,7 @@ SIGNATURES = {
     "hgm_autotune": (_i32, [ctypes.POINTER(_vp), _i32, ctypes.POINTER(_vp), _i32, _PP, _vp, _i32, _p32, _pf]),
     "hgm_set_recurse_variant": (_i32, [_i32]),
     "hgm_get_recurse_variant": (_i32, []),
+    "hgm_set_workspace_budget": (_i32, [_i64]),
     "hgm_model_order": (_i32, [_vp, _p32]),
     "hgm_scene_order": (_i32, [_vp, _p32]),
     "hgm_unary": (_i32, [_vp, _vp, _f32, _vp, _vp]),
@@ -361,6 +362,11 @@ def autotune(models: Sequence[Model], scenes: Sequence[Scene], params: Params, s
         except OSError:
             pass
     return int(best.value), times
+
+
+def set_workspace_budget(nbytes: int):
+    """Bytes for a segment group's unary table and a chunk's lists/argmin tables (0 = automatic)."""
+    _check(load().hgm_set_workspace_budget(int(nbytes)))
 
 
 def set_recurse_variant(v: int):

@@ -410,3 +410,26 @@ def test_tile_variants_identical_and_autotune(env, tmp_path, monkeypatch):
         assert 0 <= best < hgm.N_VARIANTS and times is not None and len(times) == hgm.N_VARIANTS
         assert hgm.autotune(ms, ss, p)[0] == best      # served from the cache
     hgm.set_recurse_variant(0)
+
+
+@pytest.mark.parametrize("precision,prune", [(0, False), (1, False), (0, True)])
+def test_segmented_batches_equal_whole_scene_batches(env, precision, prune):
+    """A small workspace budget cuts the scenes into offset segments (several unary-table groups, several
+    chunks); energies and assignments are bit-identical to the unsegmented run."""
+    torch, hgm, oracle = env
+    wl = synth.batched_exact(seed=12, n_models=3, n_scenes=2, frames_range=(150, 260))
+    ms = [handles(hgm, mod, wl.scenes[0], torch)[0] for mod in wl.models]
+    ss = [handles(hgm, wl.models[0], sc, torch)[1] for sc in wl.scenes]
+    prop = hgm.Proposal(162, seed=4) if prune else None
+    p = hgm.default_params(K=wl.K, window=wl.window, precision=precision, prune=prop)
+    first, es, as_ = hgm.batch_layout(ms, ss, p)
+    outs = []
+    for budget in (0, 6 << 20):
+        hgm.set_workspace_budget(budget)
+        e = torch.empty(int(es[-1]), dtype=torch.float32, device="cuda")
+        a = torch.empty(int(as_[-1]), dtype=torch.int32, device="cuda")
+        hgm.match_batch(ms, ss, p, e, a)
+        torch.cuda.synchronize()
+        outs.append((e.cpu().numpy(), a.cpu().numpy()))
+    hgm.set_workspace_budget(0)
+    assert np.array_equal(outs[0][0], outs[1][0]) and np.array_equal(outs[0][1], outs[1][1])
