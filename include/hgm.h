@@ -261,6 +261,18 @@ HGM_API hgm_status hgm_unary_bf16(const hgm_model *model, const hgm_scene *scene
 HGM_API hgm_status hgm_candidates(const hgm_model *model, const hgm_scene *scene, const hgm_params *params,
                           int32_t first, int32_t n, void *stream, int32_t *idx, int32_t *cnt);
 
+/* The proposal network's logit for every candidate of offsets first..first+n-1
+ * of one pair, as the pruning pass computes it: the first layer from the
+ * per-point projections P and Q (position terms folded in), layer 2 on the
+ * tensor cores with BF16 operands and FP32 accumulation, relu, output layer in
+ * FP32. Candidates are those of hgm_candidates (params->prune is ignored; prop
+ * is used). scores [n x M x K] float (device): slot c of list (offset, sorted
+ * model index i); -inf for empty slots. HGM_EUNSUPPORTED if K > 64,
+ * HGM_ETIMEOUT if a bounded tensor-core wait gave up. Synchronous. The paper
+ * has no learned pruning; this checks the pruning pass's scores. */
+HGM_API hgm_status hgm_prop_scores(const hgm_prop *prop, const hgm_model *model, const hgm_scene *scene,
+                                   const hgm_params *params, int32_t first, int32_t n, void *stream, float *scores);
+
 /* Feasible (z_i, z_{i-1}, z_{i-2}) triples of the recursion at each offset
  * (the work Sec. 2.2 counts as O(S M T^2) after pruning):
  * triples [n] int64 (device). Used to state algorithmic work. */

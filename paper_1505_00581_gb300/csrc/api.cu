@@ -138,7 +138,7 @@ struct Buffer {
 struct Workspace {
     Buffer modelcat, U, cand_idx, cand_u, cand_cnt, beta, units, res, mrec, srec, counter, out_e, out_a, evaluated;
     Buffer mnorm, snorm, status;
-    Buffer P, Q, cand2_idx, cand2_u, cand2_cnt, units2, beta2, fb_units, fb_count, beta_fb, res_fb, scores;
+    Buffer P, Q, modelxy, cand2_idx, cand2_u, cand2_cnt, units2, beta2, fb_units, fb_count, beta_fb, res_fb, scores;
 };
 Workspace g_ws;
 bool g_count_mode = false;   // hgm_profile_enable(2): batch runs use the accounting recursion variant
@@ -245,6 +245,7 @@ void free_model(hgm_model *m)
     cudaFree(m->d.t);
     cudaFree(m->d.f);
     cudaFree(m->d.perm);
+    cudaFree(m->d.geo);
 }
 
 void free_scene(hgm_scene *s)
@@ -448,7 +449,7 @@ hgm_status run_batch(const hgm_model *const *models, int nm, const hgm_scene *co
     std::vector<ModelRec> mrec(nm);
     for (int m = 0; m < nm; ++m)
         mrec[m] = ModelRec{models[m]->d.xy, models[m]->d.t, models[m]->d.perm, models[m]->d.M, urow[m],
-                           models[m]->d.f};
+                           models[m]->d.f, models[m]->d.geo};
     CK(g_ws.mrec.ensure(nm * sizeof(ModelRec)), "workspace");
     CK(cudaMemcpyAsync(g_ws.mrec.p, mrec.data(), nm * sizeof(ModelRec), cudaMemcpyHostToDevice, st), "upload");
     CK(g_ws.status.ensure(sizeof(int)), "workspace");
@@ -467,6 +468,15 @@ hgm_status run_batch(const hgm_model *const *models, int nm, const hgm_scene *co
         CK(g_ws.P.ensure((size_t)R * kPropHidden * sizeof(float)), "workspace (projections)");
         CK(launch_rowdot_plain(g_ws.modelcat.as<float>(), R, F, th + prop->L.o_W1, kPropHidden, prop->L.dp, Fu,
                                th + prop->L.o_b1, g_ws.P.as<float>(), kPropHidden, g_ws.status.as<int>(), st),
+           "projection kernel");
+        // position terms of the model points folded into P (the scene points' into Q)
+        CK(g_ws.modelxy.ensure((size_t)R * 2 * sizeof(float)), "workspace (models)");
+        for (int m = 0; m < nm; ++m)
+            CK(cudaMemcpyAsync(g_ws.modelxy.as<float>() + (size_t)urow[m] * 2, models[m]->d.xy,
+                               (size_t)models[m]->d.M * 2 * sizeof(float), cudaMemcpyDeviceToDevice, st),
+               "gather model positions");
+        CK(launch_prop_fold_xy(g_ws.P.as<float>(), R, g_ws.modelxy.as<float>(), th + prop->L.o_W1 + 2 * Fu,
+                               prop->L.dp, -1.0f, st),
            "projection kernel");
         pi.P = g_ws.P.as<float>();
         pi.W2 = th + prop->L.o_W2;
@@ -596,6 +606,10 @@ hgm_status run_batch(const hgm_model *const *models, int nm, const hgm_scene *co
                                        const_cast<float *>(srec[(size_t)g].pq), kPropHidden, g_ws.status.as<int>(),
                                        st),
                    "projection kernel");
+                CK(launch_prop_fold_xy(const_cast<float *>(srec[(size_t)g].pq), pts,
+                                       reinterpret_cast<const float *>(d.xy) + (size_t)sg.j0 * 2,
+                                       th + prop->L.o_W1 + 2 * Fu, prop->L.dp, 1.0f, st),
+                   "projection kernel");
             }
         }
 
@@ -671,7 +685,7 @@ hgm_status single_pair_units(const hgm_model *m, const hgm_scene *s, const hgm_p
     const int K = p.K;
     const int64_t pitch = round_up4(std::max(s->d.S, 1));
     CK(g_ws.U.ensure((size_t)R * pitch * sizeof(float)), "workspace (unary table)");
-    ModelRec mr{m->d.xy, m->d.t, m->d.perm, m->d.M, 0, m->d.f};
+    ModelRec mr{m->d.xy, m->d.t, m->d.perm, m->d.M, 0, m->d.f, m->d.geo};
     SceneRec sr{s->d.xy, s->d.t, s->d.frame_start, s->d.perm, g_ws.U.as<float>(), pitch, s->d.S, s->d.n_frames,
                 s->d.f};
     CK(g_ws.mrec.ensure(sizeof(ModelRec)), "workspace");
@@ -770,7 +784,7 @@ hgm_status hgm_create_model(const float *xy, const int32_t *t, const float *desc
     }
     hgm_model *m = new hgm_model();
     m->magic = kModelMagic;
-    m->d = ModelDev{M, Fp, nullptr, nullptr, nullptr, nullptr};
+    m->d = ModelDev{M, Fp, nullptr, nullptr, nullptr, nullptr, nullptr};
     m->F_user = F;
     m->t_sorted = stt;
     m->perm = perm;
@@ -780,7 +794,9 @@ hgm_status hgm_create_model(const float *xy, const int32_t *t, const float *desc
         delete m;
         return rc;
     }
-    cudaError_t e = cudaStreamSynchronize(st);
+    cudaError_t e = cudaMalloc((void **)&m->d.geo, (size_t)M * sizeof(float4));
+    if (e == cudaSuccess) e = launch_model_geo(m->d.xy, m->d.t, M, m->d.geo, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) {
         free_model(m);
         delete m;
@@ -1018,6 +1034,72 @@ hgm_status hgm_candidates(const hgm_model *model, const hgm_scene *scene, const 
     CK(launch_select(g_ws.units.as<Unit>(), n, g_ws.mrec.as<ModelRec>(), g_ws.srec.as<SceneRec>(), p, model->d.M, idx,
                      g_ws.cand_u.as<float>(), cnt, st),
        "select kernel");
+    return HGM_OK;
+}
+
+hgm_status hgm_prop_scores(const hgm_prop *prop, const hgm_model *model, const hgm_scene *scene,
+                           const hgm_params *params, int32_t first, int32_t n, void *stream, float *scores)
+{
+    std::lock_guard<std::mutex> lk(g_mu);
+    g_err.clear();
+    if (!prop || prop->magic != kPropMagic) return fail(HGM_EINVAL, "prop is not a proposal-network handle");
+    if (!scores || !is_device_ptr(scores)) return fail(HGM_EINVAL, "scores must be a device pointer");
+    if (params && params->K > 64) return fail(HGM_EUNSUPPORTED, "proposal scoring needs K <= 64");
+    cudaStream_t st = (cudaStream_t)stream;
+    Params p;
+    int R;
+    hgm_status rc = single_pair_units(model, scene, params, first, n, st, p, R);
+    if (rc) return rc;
+    const int Fu = model->F_user, F = model->d.F, M = model->d.M, S = scene->d.S;
+    if (prop->L.F != Fu) return fail(HGM_EINVAL, "proposal network built for F = %d, descriptors have F = %d",
+                                     prop->L.F, Fu);
+    if (n == 0) return HGM_OK;
+    const size_t ce = (size_t)n * M * p.K;
+    CK(g_ws.cand_idx.ensure(ce * sizeof(int32_t)), "workspace (candidates)");
+    CK(g_ws.cand_u.ensure(ce * sizeof(float)), "workspace (candidates)");
+    CK(g_ws.cand_cnt.ensure((size_t)n * M * sizeof(int32_t)), "workspace (candidates)");
+    CK(launch_select(g_ws.units.as<Unit>(), n, g_ws.mrec.as<ModelRec>(), g_ws.srec.as<SceneRec>(), p, M,
+                     g_ws.cand_idx.as<int32_t>(), g_ws.cand_u.as<float>(), g_ws.cand_cnt.as<int32_t>(), st),
+       "select kernel");
+    const float *th = prop->theta;
+    CK(g_ws.P.ensure((size_t)M * kPropHidden * sizeof(float)), "workspace (projections)");
+    CK(g_ws.Q.ensure((size_t)std::max(S, 1) * kPropHidden * sizeof(float)), "workspace (projections)");
+    CK(g_ws.status.ensure(sizeof(int)), "workspace");
+    CK(cudaMemsetAsync(g_ws.status.p, 0, sizeof(int), st), "memset");
+    CK(launch_rowdot_plain(model->d.f, M, F, th + prop->L.o_W1, kPropHidden, prop->L.dp, Fu, th + prop->L.o_b1,
+                           g_ws.P.as<float>(), kPropHidden, g_ws.status.as<int>(), st),
+       "projection kernel");
+    CK(launch_prop_fold_xy(g_ws.P.as<float>(), M, reinterpret_cast<const float *>(model->d.xy),
+                           th + prop->L.o_W1 + 2 * Fu, prop->L.dp, -1.0f, st),
+       "projection kernel");
+    CK(launch_rowdot_plain(scene->d.f, S, F, th + prop->L.o_W1 + Fu, kPropHidden, prop->L.dp, Fu, nullptr,
+                           g_ws.Q.as<float>(), kPropHidden, g_ws.status.as<int>(), st),
+       "projection kernel");
+    CK(launch_prop_fold_xy(g_ws.Q.as<float>(), S, reinterpret_cast<const float *>(scene->d.xy),
+                           th + prop->L.o_W1 + 2 * Fu, prop->L.dp, 1.0f, st),
+       "projection kernel");
+    const int64_t pitch = round_up4(std::max(S, 1));
+    SceneRec sr{scene->d.xy, scene->d.t, scene->d.frame_start, scene->d.perm, g_ws.U.as<float>(), pitch, S,
+                scene->d.n_frames, scene->d.f};
+    sr.pq = g_ws.Q.as<float>();
+    CK(cudaMemcpyAsync(g_ws.srec.p, &sr, sizeof sr, cudaMemcpyHostToDevice, st), "upload");
+    PropInfer pi{};
+    pi.P = g_ws.P.as<float>();
+    pi.W2 = th + prop->L.o_W2;
+    pi.b2 = th + prop->L.o_b2;
+    pi.w3 = th + prop->L.o_w3;
+    pi.b3 = th + prop->L.o_b3;
+    pi.w1c = th + prop->L.o_W1 + 2 * Fu;
+    pi.dp = prop->L.dp;
+    pi.inv_window = 1.0f / (float)std::max(params->window, 1);
+    pi.keep = p.K;
+    CK(launch_prop_score(g_ws.units.as<Unit>(), n, g_ws.mrec.as<ModelRec>(), g_ws.srec.as<SceneRec>(), p, pi,
+                         g_ws.cand_idx.as<int32_t>(), g_ws.cand_cnt.as<int32_t>(), scores, g_ws.status.as<int>(), st),
+       "scoring kernel");
+    int status = 0;
+    CK(cudaMemcpyAsync(&status, g_ws.status.p, sizeof(int), cudaMemcpyDeviceToHost, st), "status");
+    CK(cudaStreamSynchronize(st), "synchronise");
+    if (status) return fail(HGM_ETIMEOUT, "a bounded tensor-core wait gave up");
     return HGM_OK;
 }
 

@@ -23,6 +23,7 @@ struct ModelDev {
     int32_t *t;          // [M]
     float *f;            // [M*F]
     int32_t *perm;       // [M] caller index of sorted point k
+    float4 *geo;         // [M] per chain step i >= 2: (A1, k2, t_i - t_{i-1}, t_{i-1} - t_{i-2}) (ints as bits)
 };
 
 // Device-resident scene (points sorted stably by frame) with its minnode table.
@@ -43,6 +44,7 @@ struct ModelRec {
     int32_t M;
     int32_t urow;        // first row of this model in the unary table
     const float *f;      // sorted descriptors, row stride Params::F (used to re-score in FP32)
+    const float4 *geo;   // per-step model constants of the recursion (ModelDev::geo)
 };
 
 // Per-scene record the kernels read.
@@ -97,6 +99,16 @@ struct PropInfer {
     int rescore;         // 1: kept candidates' U recomputed in FP32 (precision mode)
 };
 // Scores every candidate (scores [n_lists x K] scratch) and keeps the pi.keep best per list.
+// Per-step model constants of the recursion: geo[i] = (A1, k2, dt_ab, dt_bc) for i >= 2 (zero for i < 2),
+// A1 = signed angle at i-1 (->i to ->i-2), k2 = wrap(A2 - A1 + pi) with A2 the angle at i (->i-1 to ->i-2).
+cudaError_t launch_model_geo(const float2 *xy, const int32_t *t, int M, float4 *geo, cudaStream_t st);
+// rows[r][h] += sign * (W1c[h][0] x_r + W1c[h][1] y_r) / 100 (the first layer's position terms), r < n.
+cudaError_t launch_prop_fold_xy(float *rows, int64_t n, const float *xy, const float *w1c, int dp, float sign,
+                                cudaStream_t st);
+// The proposal network's logit of every candidate of every list (scores [n_lists x K], -inf for empty slots).
+cudaError_t launch_prop_score(const Unit *units, int64_t n_units, const ModelRec *models, const SceneRec *scenes,
+                              Params p, const PropInfer &pi, const int32_t *cand_idx, const int32_t *cand_cnt,
+                              float *scores, int *status, cudaStream_t st);
 cudaError_t launch_prop_prune(const Unit *units, int64_t n_units, const ModelRec *models, const SceneRec *scenes,
                               Params p, const PropInfer &pi, const int32_t *cand_idx, const float *cand_u,
                               const int32_t *cand_cnt, float *scores, int32_t *out_idx, float *out_u,

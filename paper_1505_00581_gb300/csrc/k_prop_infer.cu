@@ -4,13 +4,19 @@
 // network scores every candidate j and keeps the `keep` best (ties: lower
 // slot), listed in slot order (ascending scene index, as the recursion
 // expects). The first layer is decomposed as
-//   W1 x + b1 = (W1a f_i + b1) + W1b f'_j + W1c (dx, dy, dt)
-// where the two point projections P (per model point) and Q (per scene point)
-// are computed once per batch by the tensor-core row-product kernel; here each
-// thread builds one candidate's 128 hidden units, the CTA stages 128 candidates
-// (two lists) as BF16, and layer 2 (128 x 128) runs as tcgen05.mma with W2
-// resident in shared memory and the accumulator in tensor memory. The epilogue
-// applies relu(+b2), the dot with w3 (+b3) and the per-list top-keep.
+//   W1 x + b1 = (W1a f_i + b1 - W1c.(x_i, y_i, 0) / 100) + (W1b f'_j + W1c.(x'_j, y'_j, 0) / 100)
+//             + W1c_t (t'_j - t_i - o) / w
+// (x = [f_i, f'_j, dx / 100, dy / 100, dt / w]): the two point projections P
+// (per model point) and Q (per scene point) are computed once per batch by the
+// tensor-core row-product kernel with the linear position terms folded in, so
+// a candidate's 128 hidden units cost one add and one fma each.
+//
+// The scoring kernel stages 128 candidates per tile (128 / 2^ceil(log2 K)
+// lists) as BF16 and runs layer 2 (128 x 128) as tcgen05.mma with W2 resident
+// in shared memory. Tiles are double-buffered in shared memory and in tensor
+// memory: tile k is gathered while the MMA of tile k - 1 runs, its epilogue
+// (relu(+b2), dot with w3) follows the issue of tile k, and the two column
+// halves of a row are summed one tile later, so one barrier per tile suffices.
 #include "hgm_internal.cuh"
 #include "prop.cuh"
 #include "tc05.cuh"
@@ -26,15 +32,13 @@ constexpr uint32_t kPolls = 1u << 26;
 constexpr float kNegInf = -__builtin_huge_valf();
 
 struct Smem {
-    unsigned char a[TM * H * 2];     // hidden layer 1 of 128 candidates, BF16, canonical K-major
+    unsigned char a[2][TM * H * 2];  // hidden layer 1 of two tiles, BF16, canonical K-major
     unsigned char w2[H * H * 2];     // W2 (rows = output units), BF16
-    float part[2][TM];               // half-sums of the last layer
-    float b2[H], w3[H];
-    float w1c[3][H];
+    float part[2][2][TM];            // [buffer][column half][row]: half-sums of the last layer
+    float b2[H], w3[H], w1t[H];      // layer-2 bias, output weights, dt column of W1
     float b3;
-    uint64_t mbar;
+    uint64_t mbar[2];
     uint32_t tslot;
-    int bad;
 };
 
 __device__ __forceinline__ float exact_u(const float *a, const float *b, int F, float lambda1)
@@ -47,22 +51,39 @@ __device__ __forceinline__ float exact_u(const float *a, const float *b, int F, 
     return __fmul_rn(lambda1, __fsqrt_rn(s));
 }
 
-// Logits of every candidate of every list: scores [n_lists x K] (-inf for empty slots).
+// rows[r][h] += sign * (W1c[h][0] x_r + W1c[h][1] y_r) / 100: the position terms of the first layer.
+__global__ void fold_xy_kernel(float *__restrict__ rows, int64_t n, const float2 *__restrict__ xy,
+                               const float *__restrict__ w1c, int dp, float sign)
+{
+    const int64_t total = n * H;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = e / H;
+        const int h = (int)(e % H);
+        const float2 p = xy[r];
+        const float t = fmaf(w1c[(int64_t)h * dp], p.x, w1c[(int64_t)h * dp + 1] * p.y);
+        rows[e] = fmaf(sign * 0.01f, t, rows[e]);
+    }
+}
+
+// Final logit of every candidate of every list: scores [n_lists x K] (-inf for empty slots).
 // 256 threads: row r = tid % 128 of the tile, half = tid / 128 owns hidden units [64 half, 64 half + 64).
-__global__ void __launch_bounds__(256) prop_score_kernel(const Unit *__restrict__ units, int64_t n_units,
-                                                         const ModelRec *__restrict__ models,
-                                                         const SceneRec *__restrict__ scenes, Params p, PropInfer pi,
-                                                         const int32_t *__restrict__ cand_idx,
-                                                         const int32_t *__restrict__ cand_cnt,
-                                                         float *__restrict__ scores, int *__restrict__ status)
+__global__ void __launch_bounds__(256, 2) prop_score_kernel(const Unit *__restrict__ units, int64_t n_units,
+                                                            const ModelRec *__restrict__ models,
+                                                            const SceneRec *__restrict__ scenes, Params p,
+                                                            PropInfer pi, int kp_log2,
+                                                            const int32_t *__restrict__ cand_idx,
+                                                            const int32_t *__restrict__ cand_cnt,
+                                                            float *__restrict__ scores, int *__restrict__ status)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     Smem &sm = *reinterpret_cast<Smem *>(smem_raw);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int row = tid & (TM - 1), half = tid >> 7;
+    const int row = tid & (TM - 1), half = tid >> 7, h0 = 64 * half;
     const int K = p.K;
+    const int lpt = TM >> kp_log2;                                  // lists per tile
+    const int lsub = row >> kp_log2, slot = row & ((1 << kp_log2) - 1);
 
-    if (warp == 0) tc05::tmem_alloc<H>(&sm.tslot);
+    if (warp == 0) tc05::tmem_alloc<2 * H>(&sm.tslot);
     for (int e = tid; e < H * (H / 8); e += 256) {          // W2 -> BF16, canonical layout
         const int r = e / (H / 8), k = (e % (H / 8)) * 8;
         __align__(16) __nv_bfloat162 h[4];
@@ -74,108 +95,141 @@ __global__ void __launch_bounds__(256) prop_score_kernel(const Unit *__restrict_
     for (int h = tid; h < H; h += 256) {
         sm.b2[h] = pi.b2[h];
         sm.w3[h] = pi.w3[h];
-#pragma unroll
-        for (int c = 0; c < 3; ++c) sm.w1c[c][h] = pi.w1c[(int64_t)h * pi.dp + c];
+        sm.w1t[h] = pi.w1c[(int64_t)h * pi.dp + 2] * pi.inv_window;
     }
     if (tid == 0) {
         sm.b3 = pi.b3[0];
-        sm.bad = 0;
-        tc05::mbar_init(&sm.mbar, 1);
+        tc05::mbar_init(&sm.mbar[0], 1);
+        tc05::mbar_init(&sm.mbar[1], 1);
     }
     tc05::fence_before_sync();
     __syncthreads();
     tc05::fence_after_sync();
     const uint32_t taddr = sm.tslot;
-    // warp w reads TMEM lanes 32 (w % 4) .. + 31, columns [64 half, 64 half + 64)
-    const uint32_t tlane = taddr + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(64 * half);
+    // warp w reads TMEM lanes 32 (w % 4) .. + 31, columns [64 half, 64 half + 64) of either accumulator
+    const uint32_t tlane = taddr + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)h0;
     constexpr uint32_t idesc = tc05::idesc_bf16_f32(TM, H);
-    uint32_t phase = 0;
 
-    for (int64_t u = blockIdx.x; u < n_units && !sm.bad; u += gridDim.x) {
+    uint32_t parity = 0;      // bit b: phase parity of the next completion of mbar[b]
+    uint32_t pending = 0;     // bit b: an MMA committed to mbar[b] whose completion was not yet observed
+    int64_t o1 = -1, o2 = -1; // score index of this row in tiles k-1 and k-2 (half 0 only; -1 none)
+    bool v1 = false, v2 = false;
+    bool bad = false, stop = false;
+    int64_t k = 0;
+
+    // epilogue of the tile in accumulator b: relu(z + b2) . w3 over this thread's 64 columns
+    auto epilogue = [&](int b) {
+        bool ok = tc05::mbar_wait(&sm.mbar[b], (parity >> b) & 1u, kPolls);
+        ok = __all_sync(0xffffffffu, ok);
+        float acc = 0.0f;
+        if (ok) {
+            parity ^= 1u << b;
+            pending &= ~(1u << b);
+            tc05::fence_after_sync();
+#pragma unroll
+            for (int c0 = 0; c0 < 64; c0 += 32) {
+                float v[32];
+                tc05::tmem_ld32(tlane + (uint32_t)(H * b + c0), v);
+#pragma unroll
+                for (int q = 0; q < 32; ++q) acc = fmaf(fmaxf(v[q] + sm.b2[h0 + c0 + q], 0.0f), sm.w3[h0 + c0 + q], acc);
+            }
+        } else {
+            bad = true;
+            if (lane == 0) atomicExch(status, 1);
+        }
+        sm.part[b][half][row] = acc;
+        tc05::fence_before_sync();
+    };
+    auto final_score = [&](int64_t o, bool v, int b) {
+        if (o >= 0) scores[o] = v ? sm.b3 + sm.part[b][0][row] + sm.part[b][1][row] : kNegInf;
+    };
+
+    for (int64_t u = blockIdx.x; u < n_units && !stop; u += gridDim.x) {
         const Unit un = units[u];
         const ModelRec md = models[un.model];
         const SceneRec sc = scenes[un.scene];
         const int M = md.M;
         const int64_t lbase = un.cand / K;
-        for (int i0 = 0; i0 < M && !sm.bad; i0 += 2) {
-            const int list = i0 + (row >= 64 ? 1 : 0), slot = row & 63;
+        for (int i0 = 0; i0 < M; i0 += lpt) {
+            const int buf = (int)(k & 1);
+            const int list = i0 + lsub;
             const int n = list < M ? cand_cnt[lbase + list] : 0;
             const bool valid = slot < n;
-            const int h0 = 64 * half;
+            unsigned char *arow = sm.a[buf];
             if (valid) {
                 const int j = cand_idx[un.cand + (int64_t)list * K + slot];
-                const float2 mxy = md.xy[list], sxy = sc.xy[j];
-                const float dx = (sxy.x - mxy.x) * 0.01f, dy = (sxy.y - mxy.y) * 0.01f;
-                const float dt = (float)(sc.t[j] - md.t[list] - un.offset) * pi.inv_window;
-                const float4 *P4 = reinterpret_cast<const float4 *>(pi.P + (int64_t)(md.urow + list) * H + h0);
                 const float4 *Q4 = reinterpret_cast<const float4 *>(sc.pq + (int64_t)(j - sc.ucol0) * H + h0);
-#pragma unroll 2
-                for (int h = 0; h < 64; h += 8) {
-                    const float4 pa = P4[h / 4], pb = P4[h / 4 + 1], qa = Q4[h / 4], qb = Q4[h / 4 + 1];
-                    float v[8] = {pa.x + qa.x, pa.y + qa.y, pa.z + qa.z, pa.w + qa.w,
-                                  pb.x + qb.x, pb.y + qb.y, pb.z + qb.z, pb.w + qb.w};
+                const float4 *P4 = reinterpret_cast<const float4 *>(pi.P + (int64_t)(md.urow + list) * H + h0);
+                float4 q[16];
+#pragma unroll
+                for (int c = 0; c < 16; ++c) q[c] = __ldg(Q4 + c);
+                const float dt = (float)(sc.t[j] - md.t[list] - un.offset);
+#pragma unroll
+                for (int c = 0; c < 16; c += 2) {
+                    const float4 pa = __ldg(P4 + c), pb = __ldg(P4 + c + 1);
+                    float v[8] = {pa.x + q[c].x,     pa.y + q[c].y,     pa.z + q[c].z,     pa.w + q[c].w,
+                                  pb.x + q[c + 1].x, pb.y + q[c + 1].y, pb.z + q[c + 1].z, pb.w + q[c + 1].w};
                     __align__(16) __nv_bfloat162 hh[4];
 #pragma unroll
-                    for (int q = 0; q < 8; ++q) {
-                        v[q] = fmaf(sm.w1c[0][h0 + h + q], dx, v[q]);
-                        v[q] = fmaf(sm.w1c[1][h0 + h + q], dy, v[q]);
-                        v[q] = fmaxf(fmaf(sm.w1c[2][h0 + h + q], dt, v[q]), 0.0f);
-                    }
+                    for (int e = 0; e < 8; ++e) v[e] = fmaxf(fmaf(sm.w1t[h0 + 4 * c + e], dt, v[e]), 0.0f);
 #pragma unroll
-                    for (int q = 0; q < 4; ++q) hh[q] = __floats2bfloat162_rn(v[2 * q], v[2 * q + 1]);
-                    *reinterpret_cast<uint4 *>(sm.a + tc05::kmajor_offset(row, h0 + h, kLBO, kSBO)) =
+                    for (int e = 0; e < 4; ++e) hh[e] = __floats2bfloat162_rn(v[2 * e], v[2 * e + 1]);
+                    *reinterpret_cast<uint4 *>(arow + tc05::kmajor_offset(row, h0 + 4 * c, kLBO, kSBO)) =
                         *reinterpret_cast<uint4 *>(hh);
                 }
             } else {
-                for (int h = 0; h < 64; h += 8)
-                    *reinterpret_cast<uint4 *>(sm.a + tc05::kmajor_offset(row, h0 + h, kLBO, kSBO)) =
+#pragma unroll
+                for (int c = 0; c < 64; c += 8)
+                    *reinterpret_cast<uint4 *>(arow + tc05::kmajor_offset(row, h0 + c, kLBO, kSBO)) =
                         make_uint4(0, 0, 0, 0);
             }
+            const int64_t o0 = (half == 0 && list < M && slot < K) ? (lbase + list) * K + slot : -1;
             tc05::fence_proxy_async_smem();
             tc05::fence_before_sync();
-            __syncthreads();
+            stop = __syncthreads_or(bad) != 0;
             tc05::fence_after_sync();
+            if (stop) break;
+            final_score(o2, v2, buf);   // tile k-2: both halves were written in the previous iteration
             if (tid == 0) {
-                const uint32_t a0 = tc05::smem_u32(sm.a), b0 = tc05::smem_u32(sm.w2);
+                const uint32_t a0 = tc05::smem_u32(arow), b0 = tc05::smem_u32(sm.w2);
                 for (int ks = 0; ks < H / 16; ++ks)
-                    tc05::mma_bf16(taddr, tc05::smem_desc(a0 + ks * 2 * kLBO, kLBO, kSBO),
+                    tc05::mma_bf16(taddr + (uint32_t)(H * buf), tc05::smem_desc(a0 + ks * 2 * kLBO, kLBO, kSBO),
                                    tc05::smem_desc(b0 + ks * 2 * kLBO, kLBO, kSBO), idesc, ks > 0);
-                tc05::mma_commit(&sm.mbar);
+                tc05::mma_commit(&sm.mbar[buf]);
             }
-            const bool ok = tc05::mbar_wait(&sm.mbar, phase, kPolls);
-            phase ^= 1u;
-            if (!ok && lane == 0) { atomicExch(status, 1); sm.bad = 1; }
-            tc05::fence_after_sync();
-            float acc = 0.0f;
-            if (ok) {
-#pragma unroll
-                for (int c0 = 0; c0 < 64; c0 += 32) {
-                    float v[32];
-                    tc05::tmem_ld32(tlane + (uint32_t)c0, v);
-#pragma unroll
-                    for (int q = 0; q < 32; ++q)
-                        acc = fmaf(fmaxf(v[q] + sm.b2[h0 + c0 + q], 0.0f), sm.w3[h0 + c0 + q], acc);
-                }
-            }
-            sm.part[half][row] = acc;
-            tc05::fence_before_sync();
-            __syncthreads();
-            tc05::fence_after_sync();
-            if (half == 0 && list < M && slot < K)
-                scores[(lbase + list) * K + slot] = valid ? sm.b3 + sm.part[0][row] + sm.part[1][row] : kNegInf;
+            pending |= 1u << buf;
+            if (k >= 1) epilogue(buf ^ 1);
+            o2 = o1; v2 = v1;
+            o1 = o0; v1 = valid;
+            ++k;
         }
+    }
+    // drain: the last iteration's reads of part[] (tile k-3) come before the last tile's epilogue writes
+    tc05::fence_before_sync();
+    stop = __syncthreads_or(bad) != 0;
+    tc05::fence_after_sync();
+    if (!stop && k >= 1) epilogue((int)((k - 1) & 1));
+    tc05::fence_before_sync();
+    stop = __syncthreads_or(bad) != 0;
+    tc05::fence_after_sync();
+    if (!stop) {
+        if (k >= 2) final_score(o2, v2, (int)(k & 1));
+        if (k >= 1) final_score(o1, v1, (int)((k - 1) & 1));
+    } else {
+        // a wait gave up: give the MMAs still in flight a bounded time before the accumulators are freed
+        for (int b = 0; b < 2; ++b)
+            if ((pending >> b) & 1u) tc05::mbar_wait(&sm.mbar[b], (parity >> b) & 1u, kPolls);
     }
     tc05::fence_before_sync();
     __syncthreads();
-    if (warp == 0) tc05::tmem_dealloc<H>(taddr);
+    if (warp == 0) tc05::tmem_dealloc<2 * H>(taddr);
 }
 
-// Per (unit, i) list: keep the `keep` best scores (ties: lower slot), in slot order; precision mode
-// re-scores the kept candidates' unary costs in FP32. One warp per list.
+// Per (unit, i) list: keep the `keep` best scores (ties: lower slot), in slot order, with their FP32 unary
+// costs from the candidate list (re-scored afterwards in the precision mode). One warp per list.
 __global__ void __launch_bounds__(256) prop_keep_kernel(const Unit *__restrict__ units, int64_t n_units,
-                                                        const ModelRec *__restrict__ models,
-                                                        const SceneRec *__restrict__ scenes, Params p, int keep,
-                                                        int rescore, const float *__restrict__ scores,
+                                                        const ModelRec *__restrict__ models, Params p, int keep,
+                                                        const float *__restrict__ scores,
                                                         const int32_t *__restrict__ cand_idx,
                                                         const float *__restrict__ cand_u,
                                                         const int32_t *__restrict__ cand_cnt,
@@ -188,10 +242,9 @@ __global__ void __launch_bounds__(256) prop_keep_kernel(const Unit *__restrict__
     asm("mov.u32 %0, %%lanemask_lt;" : "=r"(lt));
     for (int64_t u = blockIdx.x; u < n_units; u += gridDim.x) {
         const Unit un = units[u];
-        const ModelRec md = models[un.model];
-        const SceneRec sc = scenes[un.scene];
+        const int M = models[un.model].M;
         const int64_t lbase = un.cand / K;
-        for (int li = warp; li < md.M; li += 8) {
+        for (int li = warp; li < M; li += 8) {
             const int nl = cand_cnt[lbase + li];
             const int kk = nl < keep ? nl : keep;
             const float *sl = scores + (lbase + li) * K;
@@ -216,22 +269,41 @@ __global__ void __launch_bounds__(256) prop_keep_kernel(const Unit *__restrict__
             const int64_t ibase = un.cand + (int64_t)li * K;
             if (c0) {
                 const int pos = __popc(m0 & lt);
-                const int j = cand_idx[ibase + lane];
-                out_idx[obase + pos] = j;
-                out_u[obase + pos] = rescore ? exact_u(md.f + (int64_t)li * p.F, sc.f + (int64_t)j * p.F, p.F,
-                                                       p.lambda1)
-                                             : cand_u[ibase + lane];
+                out_idx[obase + pos] = cand_idx[ibase + lane];
+                out_u[obase + pos] = cand_u[ibase + lane];
             }
             if (c1) {
                 const int pos = __popc(m0) + __popc(m1 & lt);
-                const int j = cand_idx[ibase + lane + 32];
-                out_idx[obase + pos] = j;
-                out_u[obase + pos] = rescore ? exact_u(md.f + (int64_t)li * p.F, sc.f + (int64_t)j * p.F, p.F,
-                                                       p.lambda1)
-                                             : cand_u[ibase + lane + 32];
+                out_idx[obase + pos] = cand_idx[ibase + lane + 32];
+                out_u[obase + pos] = cand_u[ibase + lane + 32];
             }
             for (int q = kk + lane; q < keep; q += 32) out_idx[obase + q] = -1;
             if (lane == 0) out_cnt[lbase + li] = kk;
+        }
+    }
+}
+
+// Precision mode: the kept candidates' unary costs in FP32 (components in order, IEEE sqrt, times lambda1 --
+// the same value as the FP32 table). One thread per kept slot; lists in unit order.
+__global__ void __launch_bounds__(256) prop_rescore_kernel(const Unit *__restrict__ units, int64_t n_units,
+                                                           const ModelRec *__restrict__ models,
+                                                           const SceneRec *__restrict__ scenes, Params p, int keep,
+                                                           const int32_t *__restrict__ out_idx,
+                                                           const int32_t *__restrict__ out_cnt,
+                                                           float *__restrict__ out_u)
+{
+    const int K = p.K;
+    for (int64_t u = blockIdx.x; u < n_units; u += gridDim.x) {
+        const Unit un = units[u];
+        const ModelRec md = models[un.model];
+        const SceneRec sc = scenes[un.scene];
+        const int64_t lbase = un.cand / K;
+        for (int e = threadIdx.x; e < md.M * keep; e += blockDim.x) {
+            const int li = e / keep, c = e - li * keep;
+            if (c >= out_cnt[lbase + li]) continue;
+            const int64_t o = (lbase + li) * keep + c;
+            const int j = out_idx[o];
+            out_u[o] = exact_u(md.f + (int64_t)li * p.F, sc.f + (int64_t)j * p.F, p.F, p.lambda1);
         }
     }
 }
@@ -263,30 +335,54 @@ __global__ void collect_infeasible_kernel(const UnitResult *__restrict__ res, co
 
 }  // namespace
 
+cudaError_t launch_prop_fold_xy(float *rows, int64_t n, const float *xy, const float *w1c, int dp, float sign,
+                                cudaStream_t st)
+{
+    if (n <= 0) return cudaSuccess;
+    const int64_t blocks = std::min<int64_t>((n * H + 255) / 256, 8192);
+    fold_xy_kernel<<<(unsigned)blocks, 256, 0, st>>>(rows, n, reinterpret_cast<const float2 *>(xy), w1c, dp, sign);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_prop_score(const Unit *units, int64_t n_units, const ModelRec *models, const SceneRec *scenes,
+                              Params p, const PropInfer &pi, const int32_t *cand_idx, const int32_t *cand_cnt,
+                              float *scores, int *status, cudaStream_t st)
+{
+    if (n_units <= 0) return cudaSuccess;
+    if (p.K < 1 || p.K > 64) return cudaErrorInvalidValue;
+    int kp_log2 = 0;
+    while ((1 << kp_log2) < p.K) ++kp_log2;
+    const size_t smem = sizeof(Smem);
+    cudaError_t e = cudaFuncSetAttribute(prop_score_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int dev = 0, sms = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    // two CTAs per SM: 2 x ~101 KB of shared memory, 2 x 256 of the SM's 512 TMEM columns
+    const int64_t grid = std::min<int64_t>(n_units, (int64_t)sms * 2);
+    prop_score_kernel<<<(unsigned)grid, 256, smem, st>>>(units, n_units, models, scenes, p, pi, kp_log2, cand_idx,
+                                                         cand_cnt, scores, status);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_prop_prune(const Unit *units, int64_t n_units, const ModelRec *models, const SceneRec *scenes,
                               Params p, const PropInfer &pi, const int32_t *cand_idx, const float *cand_u,
                               const int32_t *cand_cnt, float *scores, int32_t *out_idx, float *out_u,
                               int32_t *out_cnt, int *status, cudaStream_t st)
 {
     if (n_units <= 0) return cudaSuccess;
-    const size_t smem = sizeof(Smem);
-    cudaError_t e = cudaFuncSetAttribute(prop_score_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    int dev = 0, sms = 0, per_sm = 0;
-    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
-    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, prop_score_kernel, 256, smem)) != cudaSuccess)
-        return e;
-    per_sm = per_sm < 1 ? 1 : (per_sm > 4 ? 4 : per_sm);   // 4 x 128 TMEM columns
-    const int64_t grid = std::min<int64_t>(n_units, (int64_t)sms * per_sm);
     prof_begin(kProfPrune, st);
-    prop_score_kernel<<<(unsigned)grid, 256, smem, st>>>(units, n_units, models, scenes, p, pi, cand_idx, cand_cnt,
-                                                         scores, status);
-    if ((e = cudaGetLastError()) == cudaSuccess) {
+    cudaError_t e = launch_prop_score(units, n_units, models, scenes, p, pi, cand_idx, cand_cnt, scores, status, st);
+    if (e == cudaSuccess) {
         const int64_t blocks = std::min<int64_t>(n_units, (int64_t)1 << 20);
-        prop_keep_kernel<<<(unsigned)blocks, 256, 0, st>>>(units, n_units, models, scenes, p, pi.keep, pi.rescore,
-                                                           scores, cand_idx, cand_u, cand_cnt, out_idx, out_u,
-                                                           out_cnt);
+        prop_keep_kernel<<<(unsigned)blocks, 256, 0, st>>>(units, n_units, models, p, pi.keep, scores, cand_idx,
+                                                           cand_u, cand_cnt, out_idx, out_u, out_cnt);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess && pi.rescore) {
+        const int64_t blocks = std::min<int64_t>(n_units, (int64_t)1 << 20);
+        prop_rescore_kernel<<<(unsigned)blocks, 256, 0, st>>>(units, n_units, models, scenes, p, pi.keep, out_idx,
+                                                                  out_cnt, out_u);
         e = cudaGetLastError();
     }
     prof_end(kProfPrune, st);

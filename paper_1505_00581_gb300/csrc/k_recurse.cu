@@ -31,9 +31,15 @@
 // loop, in increasing slot order with a strict '<', so the lowest slot still
 // wins exact ties -- the result is bit-identical to the full minimisation.
 //
-// Work split per step: warps build the kept lists of one b each; then tiles
-// of one b and CT consecutive c with t'(c) <= t'(b) are flattened across the
-// CTA's threads, each thread looping over the kept a of its b.
+// Work split per step (two CTA barriers): phase 1, warps build the kept lists
+// of one b each; phase 2, the theta(a->c) rows of the kept a, then warp 0
+// orders the b by decreasing kept count and lays out the tile table; phase 3,
+// tiles of one b and CT consecutive c with t'(c) <= t'(b) are flattened across
+// the CTA's threads in that order (similar loop lengths within a warp), each
+// thread looping over the kept a of its b. The per-step model constants come
+// from a table built at model creation, and the list C of the next step is
+// fetched from global memory during phases 1-2 and stored in the buffer of the
+// list A, which phase 3 no longer reads, so no step waits on a global load.
 #include "recurse_common.cuh"
 
 namespace hgm {
@@ -71,12 +77,12 @@ struct Smem {
     uint8_t tile_b[KM * KM / 4];          // b of every tile of the step (tiles of >= 4 cells)
     uint16_t tbase[KM];                   // first tile of b
     uint8_t tcount[KM];                   // tiles of b
-    int32_t ntile;                        // tiles of the step (shared-memory counter)
+    int32_t hist[KM + 1];                 // tiles per kept count (counting sort of the b), then bucket starts
+    int32_t ntile;                        // tiles of the step
     List<KM> list[3];
+    float4 geo[2];                        // model constants of step i at geo[i & 1]
     float red_v[NT / 32];
     int32_t red_k[NT / 32];
-    float A1, k2;
-    int32_t dt_ab, dt_bc;
     int32_t unit;
 };
 
@@ -147,34 +153,33 @@ recurse_kernel(const Unit *__restrict__ units, int64_t n_units, const ModelRec *
         const int32_t *ccnt = cand_cnt + un.cand / K;
         uint8_t *ubeta = beta + un.beta;
 
-        // alpha_{M+1} == 0 (Eq. 11)
+        // alpha_{M+1} == 0 (Eq. 11); the three lists and the constants of the first step
         for (int e = tid; e < KM * AS; e += NT) sm.alpha[e] = 0.0f;
-        load_list<KM>(sm.list[(M - 1) % 3], sc, cidx + (int64_t)(M - 1) * K, cu + (int64_t)(M - 1) * K,
-                      ccnt[M - 1], tid, NT);
-        load_list<KM>(sm.list[(M - 2) % 3], sc, cidx + (int64_t)(M - 2) * K, cu + (int64_t)(M - 2) * K,
-                      ccnt[M - 2], tid, NT);
+        for (int q = 1; q <= 3 && q <= M; ++q)
+            load_list<KM>(sm.list[(M - q) % 3], sc, cidx + (int64_t)(M - q) * K, cu + (int64_t)(M - q) * K,
+                          ccnt[M - q], tid, NT);
+        if (tid < KM) sm.used[tid] = 0;
+        if (tid == 0 && M >= 3) sm.geo[(M - 1) & 1] = md.geo[M - 1];
+        __syncthreads();
 
         for (int i = M - 1; i >= 2; --i) {
             List<KM> &LA = sm.list[i % 3];
             List<KM> &LB = sm.list[(i - 1) % 3];
             List<KM> &LC = sm.list[(i - 2) % 3];
-            // ---- phase 0: new list, model constants of hyperedge (i, i-1, i-2)
-            load_list<KM>(LC, sc, cidx + (int64_t)(i - 2) * K, cu + (int64_t)(i - 2) * K, ccnt[i - 2], tid, NT);
-            if (tid < KM) sm.used[tid] = 0;
-            if (tid == 0) sm.ntile = 0;
-            if (tid == 0) {
-                const float2 mi = md.xy[i], mj = md.xy[i - 1], mk = md.xy[i - 2];
-                const float A1 = signed_angle(mj, mi, mk);   // at i-1, from ->i to ->i-2
-                const float A2 = signed_angle(mi, mj, mk);   // at i, from ->i-1 to ->i-2
-                sm.A1 = A1;
-                sm.k2 = wrap_pi(__fadd_rn(__fsub_rn(A2, A1), kPi));   // p2 = p1 + k2 (mod 2pi)
-                sm.dt_ab = md.t[i] - md.t[i - 1];
-                sm.dt_bc = md.t[i - 1] - md.t[i - 2];
-            }
-            __syncthreads();
+            const float4 g = sm.geo[i & 1];
+            const float A1 = g.x, k2 = g.y;
+            const int dt_ab = __float_as_int(g.z), dt_bc = __float_as_int(g.w);
             const int na = LA.n, nb = LB.n, nc = LC.n;
-            const float A1 = sm.A1, k2 = sm.k2;
-            const int dt_ab = sm.dt_ab, dt_bc = sm.dt_bc;
+
+            // list C of the next step (chain index i-3): first half of the fetch
+            const bool pf = i >= 3 && tid < K;
+            int pf_n = 0, pf_j = -1;
+            float pf_u = kInf;
+            if (pf) {
+                pf_n = ccnt[i - 3];
+                pf_j = cidx[(int64_t)(i - 3) * K + tid];
+                pf_u = cu[(int64_t)(i - 3) * K + tid];
+            }
 
             // ---- phase 1: per b (one warp each) the kept a list and the tile count
             // per-lane data of the lane's a and c slots, shared by every b of the warp
@@ -215,21 +220,10 @@ recurse_kernel(const Unit *__restrict__ units, int64_t n_units, const ModelRec *
                     if (hit) bk = __ffs(hit) - 1 + 32 * q;
                 }
                 // c with t'(c) <= t'(b) form a prefix of C: tiles cover it
-                uint32_t cm[AQ];
                 int ccount = 0;
 #pragma unroll
-                for (int q = 0; q < AQ; ++q) {
-                    cm[q] = __ballot_sync(0xffffffffu, lc_t[q] <= tb);
-                    ccount += __popc(cm[q]);
-                }
-                {
-                    const int nq = (ccount + CT - 1) / CT;
-                    int t0 = 0;
-                    if (lane == 0) t0 = atomicAdd(&sm.ntile, nq);
-                    t0 = __shfl_sync(0xffffffffu, t0, 0);
-                    for (int t = lane; t < nq; t += 32) sm.tile_b[t0 + t] = (uint8_t)b;
-                    if (lane == 0) { sm.tbase[b] = (uint16_t)t0; sm.tcount[b] = (uint8_t)nq; }
-                }
+                for (int q = 0; q < AQ; ++q) ccount += __popc(__ballot_sync(0xffffffffu, lc_t[q] <= tb));
+                if (lane == 0) sm.tcount[b] = (uint8_t)((ccount + CT - 1) / CT);
                 if (!(bv < kInf)) {
                     if (lane == 0) sm.fn[b] = 0;
                     continue;
@@ -261,6 +255,7 @@ recurse_kernel(const Unit *__restrict__ units, int64_t n_units, const ModelRec *
                 }
                 // keep base <= thr, compacted in increasing a
                 int kept = 0;
+                float *fbf = reinterpret_cast<float *>(sm.fb + b * KM);
 #pragma unroll
                 for (int q = 0; q < AQ; ++q) {
                     const int a = lane + 32 * q;
@@ -268,32 +263,111 @@ recurse_kernel(const Unit *__restrict__ units, int64_t n_units, const ModelRec *
                     const uint32_t km = __ballot_sync(0xffffffffu, keep);
                     if (keep) {
                         const int pos = kept + __popc(km & lanemask_lt());
-                        const float2 pa = LA.xy[a];
-                        const float p1 = wrap_pi(__fadd_rn(A1, direction(pb, pa)));   // A1 + theta(b->a)
-                        sm.fb[b * KM + pos] = make_float2(base[q], p1);
+                        fbf[2 * pos] = base[q];
                         sm.fs[b * KM + pos] = (uint8_t)a;
                         sm.used[a] = 1;
                     }
                     kept += __popc(km);
                 }
+                __syncwarp();
+                // p1 = A1 + theta(b->a) of the kept entries, one lane per entry
+                for (int pos = lane; pos < kept; pos += 32) {
+                    const float2 pa = LA.xy[sm.fs[b * KM + pos]];
+                    fbf[2 * pos + 1] = wrap_pi(__fadd_rn(A1, direction(pb, pa)));
+                }
                 if (lane == 0) sm.fn[b] = kept;
             }
             __syncthreads();
 
-            // ---- phase 2: theta(a->c) rows of the kept a
+            // list C of the next step: second half of the fetch (positions and frames)
+            float2 pf_xy = make_float2(0.f, 0.f);
+            int pf_t = 0x3fffffff;
+            const bool pf_ok = pf && tid < pf_n;
+            if (pf_ok) {
+                pf_xy = sc.xy[pf_j];
+                pf_t = sc.t[pf_j];
+            }
+
+            // ---- phase 2: theta(a->c) rows of the kept a; then warp 0 lays out the tile table
+            if (tid == 32 && i >= 3) sm.geo[(i - 1) & 1] = md.geo[i - 1];
             for (int e = tid; e < na * KM; e += NT) {
                 const int a = e / KM, c = e % KM;
                 if (!sm.used[a]) continue;
                 float r = kInf;
                 if (c < nc) {
                     const int ta = LA.t[a], tc = LC.t[c];
-                    if (!(T > 0 && ta - tc >= T) && LA.idx[a] != LC.idx[c]) {
+                    // kept pairs have t'(c) <= t'(b) <= t'(a): entries with t'(c) > t'(a) are never read
+                    if (tc <= ta && !(T > 0 && ta - tc >= T) && LA.idx[a] != LC.idx[c]) {
                         r = direction(LA.xy[a], LC.xy[c]);                   // theta(a->c)
                     }
                 }
                 sm.r[a * RS + c] = r;
             }
+            if (warp == 0) {
+                // tiles of b in decreasing kept count (counting sort; order inside a count is free):
+                // the lanes of a warp then loop over similar numbers of a
+                constexpr int HB = KM + 1, HE = (HB + 31) / 32;
+                for (int k = lane; k < HB; k += 32) sm.hist[k] = 0;
+                __syncwarp();
+                int key[AQ], cnt[AQ];
+#pragma unroll
+                for (int q = 0; q < AQ; ++q) {
+                    const int b = lane + 32 * q;
+                    cnt[q] = sm.tcount[b];
+                    key[q] = KM - sm.fn[b];
+                    if (cnt[q]) atomicAdd(&sm.hist[key[q]], cnt[q]);
+                }
+                __syncwarp();
+                int loc[HE], sum = 0;
+#pragma unroll
+                for (int e = 0; e < HE; ++e) {
+                    const int k = lane * HE + e;
+                    loc[e] = k < HB ? sm.hist[k] : 0;
+                    sum += loc[e];
+                }
+                int x = sum;
+#pragma unroll
+                for (int off = 1; off < 32; off <<= 1) {
+                    const int y = __shfl_up_sync(0xffffffffu, x, off);
+                    if (lane >= off) x += y;
+                }
+                int pre = x - sum;
+#pragma unroll
+                for (int e = 0; e < HE; ++e) {
+                    const int k = lane * HE + e;
+                    if (k < HB) sm.hist[k] = pre;
+                    pre += loc[e];
+                }
+                __syncwarp();
+#pragma unroll
+                for (int q = 0; q < AQ; ++q) {
+                    if (cnt[q]) {
+                        const int b = lane + 32 * q;
+                        const int t0 = atomicAdd(&sm.hist[key[q]], cnt[q]);
+                        sm.tbase[b] = (uint16_t)t0;
+                        for (int t = 0; t < cnt[q]; ++t) sm.tile_b[t0 + t] = (uint8_t)b;
+                    }
+                }
+                const int total = __shfl_sync(0xffffffffu, x, 31);
+                if (lane == 0) sm.ntile = total;
+            }
             __syncthreads();
+
+            // list A is not read from here on: its buffer receives list C of the next step
+            if (pf) {
+                LA.idx[tid] = pf_ok ? pf_j : -1;
+                LA.xy[tid] = pf_xy;
+                LA.t[tid] = pf_t;
+                LA.u[tid] = pf_ok ? pf_u : kInf;
+                if (tid == 0) LA.n = pf_n;
+            }
+            if (i >= 3 && tid >= K && tid < KM) {
+                LA.idx[tid] = -1;
+                LA.xy[tid] = make_float2(0.f, 0.f);
+                LA.t[tid] = 0x3fffffff;
+                LA.u[tid] = kInf;
+            }
+            if (tid < KM) sm.used[tid] = 0;
 
             // ---- phase 3: tiles (b, CT consecutive c)
             const int ntile = sm.ntile;
@@ -409,6 +483,9 @@ cudaError_t launch_recurse_t(const Unit *units, int64_t n_units, const ModelRec 
                              uint8_t *beta, UnitResult *res, int *work_counter, unsigned long long *evaluated,
                              cudaStream_t st)
 {
+    // three CTAs of 256 threads per SM: 3 x (shared memory + 1 KB reserved) <= 228 KB
+    static_assert(KM != 64 || NT != 256 || 3 * (sizeof(Smem<KM, NT>) + 1024) <= 228 * 1024,
+                  "recursion shared memory exceeds the three-CTA budget");
     auto kern = recurse_kernel<KM, NT, CT, kCount>;
     const size_t smem = sizeof(Smem<KM, NT>);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -453,6 +530,31 @@ cudaError_t dispatch(int variant, const Unit *units, int64_t n_units, const Mode
 int g_variant = 0;   // recursion variant: 0 = 4 c per tile, 1 = 8 c per tile, 2 = 4 c per tile on 128 threads
 
 }  // namespace
+
+namespace {
+__global__ void model_geo_kernel(const float2 *__restrict__ xy, const int32_t *__restrict__ t, int M,
+                                 float4 *__restrict__ geo)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < M; i += gridDim.x * blockDim.x) {
+        float4 g = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (i >= 2) {
+            const float2 mi = xy[i], mj = xy[i - 1], mk = xy[i - 2];
+            const float A1 = signed_angle(mj, mi, mk);   // at i-1, from ->i to ->i-2
+            const float A2 = signed_angle(mi, mj, mk);   // at i, from ->i-1 to ->i-2
+            g = make_float4(A1, wrap_pi(__fadd_rn(__fsub_rn(A2, A1), kPi)), __int_as_float(t[i] - t[i - 1]),
+                            __int_as_float(t[i - 1] - t[i - 2]));
+        }
+        geo[i] = g;
+    }
+}
+}  // namespace
+
+cudaError_t launch_model_geo(const float2 *xy, const int32_t *t, int M, float4 *geo, cudaStream_t st)
+{
+    if (M <= 0) return cudaSuccess;
+    model_geo_kernel<<<(M + 127) / 128, 128, 0, st>>>(xy, t, M, geo);
+    return cudaGetLastError();
+}
 
 int recurse_variant_count() { return 3; }
 void set_recurse_variant(int v) { g_variant = (v >= 0 && v < 3) ? v : 0; }

@@ -62,6 +62,7 @@ SIGNATURES = {
     "hgm_set_recurse_variant": (_i32, [_i32]),
     "hgm_get_recurse_variant": (_i32, []),
     "hgm_set_workspace_budget": (_i32, [_i64]),
+    "hgm_prop_scores": (_i32, [_vp, _vp, _vp, _vp, _i32, _i32, _vp, _vp]),
     "hgm_model_order": (_i32, [_vp, _p32]),
     "hgm_scene_order": (_i32, [_vp, _p32]),
     "hgm_unary": (_i32, [_vp, _vp, _f32, _vp, _vp]),
@@ -415,6 +416,14 @@ def candidates(model: Model, scene: Scene, params: Params, first: int, n: int, i
     _check(load().hgm_candidates(model.handle, scene.handle, ctypes.byref(params), int(first), int(n),
                                  _stream(stream), pi, pc))
     return ki, kc
+
+
+def prop_scores(prop: "Proposal", model: Model, scene: Scene, params: Params, first: int, n: int, out, stream=None):
+    """The pruning pass's logit of every candidate (out: device float [n, M, K]; -inf for empty slots)."""
+    (po, ko) = _ptr(out)
+    _check(load().hgm_prop_scores(prop.handle, model.handle, scene.handle, ctypes.byref(params), int(first), int(n),
+                                  _stream(stream), po))
+    return ko
 
 
 def count_triples(model: Model, scene: Scene, params: Params, first: int, n: int, out, stream=None):

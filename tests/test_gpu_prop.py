@@ -210,3 +210,79 @@ def test_pruning_is_a_restriction_with_fallback(env):
     for k in range(0, n, 7):
         if fin[k]:
             assert abs(orc.energy(a1[k]) - e1[k]) <= 1e-5 * e1[k]
+
+
+def _pair_features(mod, sc, m, s, first, idx, cnt, window):
+    """FP64 network inputs of every candidate slot: [f_i, f'_j, dx/100, dy/100, dt/w] with i, j the caller
+    indices behind the sorted indices of the candidate lists; mask of the filled slots."""
+    mperm, sperm = m.order(), s.order()
+    n, M, K = idx.shape
+    valid = np.arange(K)[None, None, :] < cnt[:, :, None]
+    i_c = np.broadcast_to(mperm[np.arange(M)][None, :, None], (n, M, K))
+    j_c = sperm[np.where(valid, idx, 0)]
+    o = (first + np.arange(n))[:, None, None]
+    d = np.stack([(sc.xy[j_c, 0].astype(np.float64) - mod.xy[i_c, 0]) / 100.0,
+                  (sc.xy[j_c, 1].astype(np.float64) - mod.xy[i_c, 1]) / 100.0,
+                  (sc.t[j_c].astype(np.float64) - mod.t[i_c] - o) / float(window)], axis=-1)
+    X = np.concatenate([mod.f[i_c].astype(np.float64), sc.f[j_c].astype(np.float64), d], axis=-1)
+    return X[valid], valid
+
+
+@pytest.mark.parametrize("K,window,precision", [(64, 0, 0), (24, 3, 1)])
+def test_scoring_kernel_matches_fp64(env, K, window, precision):
+    """The pruning pass's logits (first layer from the per-point projections with the position terms folded
+    in, layer 2 on the tensor cores) against the FP64 network on the same candidates: to 2e-3 of the logit
+    range against the emulation that rounds the tensor-core operands to BF16 (the descriptors and W1a/W1b
+    in the projections, h1 and W2 in layer 2); within 5% of the spread against plain FP64. Empty slots are
+    -inf. K = 64 with w = 0: lists of about 30 candidates (many empty slots); K = 24 with w = 3: full lists,
+    four lists of 32 rows (8 of them empty) in each 128-row tile."""
+    torch, hgm, _ = env
+    F = 162
+    wl = _pair(seed=5, frames=90)
+    mod, sc = wl.models[0], wl.scenes[0]
+    m, s = handles(hgm, mod, sc, torch)
+    prop = hgm.Proposal(F, seed=11)
+    ref = _ref_params(prop)
+    rng = np.random.default_rng(8)
+    ref["b1"] = rng.normal(size=128) * 0.1
+    ref["b2"] = rng.normal(size=128) * 0.1
+    ref["b3"] = np.array([-0.2])
+    ref["W1"][:, 2 * F:] = rng.normal(size=(128, 3)) * 0.5
+    w = np.concatenate([ref[k].reshape(-1) for k in ("W1", "b1", "W2", "b2", "w3", "b3")]).astype(np.float32)
+    prop.set(w)
+    ref = _ref_params(prop)
+    p = hgm.default_params(K=K, window=window, precision=precision)
+    first, n = hgm.offsets(m, s, p)
+    first, n = first + 7, min(n - 7, 9)
+    idx = torch.empty((n, mod.n, K), dtype=torch.int32, device="cuda")
+    cnt = torch.empty((n, mod.n), dtype=torch.int32, device="cuda")
+    hgm.candidates(m, s, p, first, n, idx, cnt)
+    out = torch.full((n, mod.n, K), 7.0, dtype=torch.float32, device="cuda")
+    hgm.prop_scores(prop, m, s, p, first, n, out)
+    torch.cuda.synchronize()
+    got = out.cpu().numpy()
+    X, valid = _pair_features(mod, sc, m, s, first, idx.cpu().numpy(), cnt.cpu().numpy(), max(window, 1))
+    assert valid.sum() > 1000 and (window > 0 or (~valid).sum() > 1000)
+    assert np.all(got[~valid] == -np.inf)
+    g = got[valid]
+    assert np.all(np.isfinite(g))
+    z64 = mlp.forward(ref, X)["z3"]
+    W1 = ref["W1"]
+    z1 = _bf16(X[:, :F]) @ _bf16(W1[:, :F]).T + ref["b1"] + _bf16(X[:, F:2 * F]) @ _bf16(W1[:, F:2 * F]).T \
+        + X[:, 2 * F:] @ W1[:, 2 * F:].T
+    z2 = _bf16(np.maximum(z1, 0.0)) @ _bf16(ref["W2"]).T + ref["b2"]
+    z_emu = np.maximum(z2, 0.0) @ ref["w3"] + ref["b3"][0]
+    assert np.max(np.abs(g - z_emu)) <= 2e-3 * max(1.0, np.max(np.abs(z_emu))), np.max(np.abs(g - z_emu))
+    assert np.max(np.abs(g - z64)) <= 0.05 * max(1.0, np.std(z64)), (np.max(np.abs(g - z64)), np.std(z64))
+
+
+def test_scoring_kernel_rejects_long_lists(env):
+    torch, hgm, _ = env
+    wl = _pair(seed=5, frames=60)
+    m, s = handles(hgm, wl.models[0], wl.scenes[0], torch)
+    prop = hgm.Proposal(162, seed=1)
+    p = hgm.default_params(K=65, window=3)
+    out = torch.empty(16, device="cuda")
+    with pytest.raises(hgm.HgmError) as err:
+        hgm.prop_scores(prop, m, s, p, 0, 1, out)
+    assert err.value.status == 5
