@@ -391,28 +391,28 @@ recurse_kernel(const Unit *__restrict__ units, int64_t n_units, const ModelRec *
 
                 const float2 *fbb = sm.fb + b * KM;
                 const uint8_t *fsb = sm.fs + b * KM;
+                // cells in pairs: packed FP32x2 arithmetic, same roundings as triple_cost
+                static_assert(CT % 4 == 0, "tiles of a multiple of 4 cells");
+                unsigned long long q1p[CT / 2];
+#pragma unroll
+                for (int q = 0; q < CT / 2; ++q) q1p[q] = pk2(q1[2 * q], q1[2 * q + 1]);
+                const unsigned long long lamp = pk2(lam23, lam23);
 #pragma unroll 2
                 for (int k = 0; k < nf; ++k) {
                     const float2 e = fbb[k];
                     const int a = fsb[k];
                     if constexpr (kCount) n_eval += CT;
                     const float p2 = __fadd_rn(e.y, k2);
-                    float rv[CT];
+                    const unsigned long long bp = pk2(e.x, e.x), p1p = pk2(e.y, e.y), p2p = pk2(p2, p2);
 #pragma unroll
                     for (int q4 = 0; q4 < CT; q4 += 4) {
-                        if constexpr (CT >= 4) {
-                            const float4 r4 = *reinterpret_cast<const float4 *>(&sm.r[a * RS + c0 + q4]);
-                            rv[q4] = r4.x; rv[q4 + 1] = r4.y; rv[q4 + 2] = r4.z; rv[q4 + 3] = r4.w;
-                        }
-                    }
-                    if constexpr (CT == 2) {
-                        const float2 r2 = *reinterpret_cast<const float2 *>(&sm.r[a * RS + c0]);
-                        rv[0] = r2.x; rv[1] = r2.y;
-                    }
+                        const float4 r4 = *reinterpret_cast<const float4 *>(&sm.r[a * RS + c0 + q4]);
+                        float v[4];
+                        triple_cost2(bp, p1p, p2p, q1p[q4 / 2], pk2(r4.x, r4.y), lamp, v[0], v[1]);
+                        triple_cost2(bp, p1p, p2p, q1p[q4 / 2 + 1], pk2(r4.z, r4.w), lamp, v[2], v[3]);
 #pragma unroll
-                    for (int q = 0; q < CT; ++q) {
-                        const float v = triple_cost(e.x, e.y, p2, q1[q], rv[q], lam23);
-                        if (v < best[q]) { best[q] = v; arg[q] = a; }
+                        for (int q = 0; q < 4; ++q)
+                            if (v[q] < best[q4 + q]) { best[q4 + q] = v[q]; arg[q4 + q] = a; }
                     }
                 }
 #pragma unroll

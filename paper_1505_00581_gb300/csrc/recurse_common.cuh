@@ -54,6 +54,56 @@ __device__ __forceinline__ float triple_cost(float base, float p1, float p2, flo
     return __fmaf_rn(lam23, sqrt_fast(__fmaf_rn(w2, w2, __fmul_rn(w1, w1))), base);
 }
 
+// ---- packed FP32 pairs (sm_100-family add/sub/mul/fma .f32x2: per element the same IEEE
+// round-to-nearest operation as the scalar form, two lanes of work per instruction) ----------
+__device__ __forceinline__ unsigned long long pk2(float lo, float hi)
+{
+    unsigned long long r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ void upk2(unsigned long long r, float &lo, float &hi)
+{
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(r));
+}
+__device__ __forceinline__ unsigned long long sub2(unsigned long long a, unsigned long long b)
+{
+    unsigned long long r;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ unsigned long long mul2(unsigned long long a, unsigned long long b)
+{
+    unsigned long long r;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ unsigned long long fma2(unsigned long long a, unsigned long long b, unsigned long long c)
+{
+    unsigned long long r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+    return r;
+}
+
+// triple_cost for two cells (same a, b; c and c'): bit-identical to two triple_cost calls.
+// p1p = (p1, p1), p2p = (p2, p2), basep = (base, base), lam = (lambda2 lambda3, lambda2 lambda3).
+__device__ __forceinline__ void triple_cost2(unsigned long long basep, unsigned long long p1p,
+                                             unsigned long long p2p, unsigned long long q1p, unsigned long long rp,
+                                             unsigned long long lam, float &va, float &vb)
+{
+    float d1a, d1b, d2a, d2b;
+    upk2(sub2(p1p, q1p), d1a, d1b);
+    upk2(sub2(p2p, rp), d2a, d2b);
+    const float w1a = fminf(fabsf(d1a), __fsub_rn(kTwoPi, fabsf(d1a)));
+    const float w1b = fminf(fabsf(d1b), __fsub_rn(kTwoPi, fabsf(d1b)));
+    const float w2a = fminf(fabsf(d2a), __fsub_rn(kTwoPi, fabsf(d2a)));
+    const float w2b = fminf(fabsf(d2b), __fsub_rn(kTwoPi, fabsf(d2b)));
+    const unsigned long long w1 = pk2(w1a, w1b), w2 = pk2(w2a, w2b);
+    float sa, sb;
+    upk2(fma2(w2, w2, mul2(w1, w1)), sa, sb);
+    upk2(fma2(lam, pk2(sqrt_fast(sa), sqrt_fast(sb)), basep), va, vb);
+}
+
 // alpha_i(b,c) = min_a v + lambda2 |dt_model - (t'(b) - t'(c))|
 __device__ __forceinline__ float cell_alpha(float best, float lam2, int dt_model, int tb, int tc)
 {
