@@ -23,23 +23,30 @@
 // t'(a)-t'(c) < T, distinct points; Eqs. 7-8, Sec. 3.2's validity mask).
 //
 // Exact branch and bound: the geometric term is bounded, 0 <= D^g <= pi*sqrt(2),
-// so v(a,b,c) >= base(a,b), and any a with base(a,b) > base(w,b) + lambda2
-// lambda3 pi sqrt(2) (plus rounding slack) can never beat a feasible witness w.
-// Per b, the witness is the a of smallest base; for the rare c where it is
-// infeasible, the smallest base feasible with c raises the threshold. Only the
-// kept a (about a quarter on the paper-shaped workloads) enter the triple
-// loop, in increasing slot order with a strict '<', so the lowest slot still
-// wins exact ties -- the result is bit-identical to the full minimisation.
+// so v(a,b,c) >= base(a,b), and an a with base(a,b) > m(b,c) + lambda2 lambda3
+// pi sqrt(2) (plus rounding slack), m(b,c) the smallest base among the a
+// feasible with the cell, can never beat the cell's best. Any threshold at or
+// above max_c m(b,c) + that bound is therefore exact. Per b the witness w is the
+// a of smallest base, m(b,c) = base(w) wherever w is feasible with c; for the
+// cells where it is not, m(b,c) is at most the runner-up's base when the
+// runner-up is feasible with c, and otherwise at most the second smallest base
+// among the a feasible with the earliest c (every later c admits a superset of
+// those a and excludes at most one of them, the same point as c). Only the kept
+// a (about a sixth of the feasible ones on the paper-shaped workloads) enter the
+// triple loop, in increasing slot order with a strict '<', so the lowest slot
+// still wins exact ties -- the result is bit-identical to the full minimisation.
 //
-// Work split per step (two CTA barriers): phase 1, warps build the kept lists
-// of one b each; phase 2, the theta(a->c) rows of the kept a, then warp 0
-// orders the b by decreasing kept count and lays out the tile table; phase 3,
-// tiles of one b and CT consecutive c with t'(c) <= t'(b) are flattened across
-// the CTA's threads in that order (similar loop lengths within a warp), each
-// thread looping over the kept a of its b. The per-step model constants come
-// from a table built at model creation, and the list C of the next step is
-// fetched from global memory during phases 1-2 and stored in the buffer of the
-// list A, which phase 3 no longer reads, so no step waits on a global load.
+// Work split per step (two CTA barriers): phase 1, NP threads per b (adjacent
+// lanes, interleaved a) build the kept lists with pairwise shuffles only, while
+// the other warps compute the theta(a->c) table; the list builders then meet on
+// a named barrier and warp 0 orders the b by decreasing kept count and lays out
+// the tile table; phase 3, tiles of one b and CT consecutive c with
+// t'(c) <= t'(b) are flattened across the CTA's threads in that order (similar
+// loop lengths within a warp), each thread looping over the kept a of its b.
+// The per-step model constants come from a table built at model creation, and
+// the list C of the next step is fetched from global memory during phase 2 and
+// stored in the buffer of the list A, which phase 3 no longer reads, so no step
+// waits on a global load.
 #include "recurse_common.cuh"
 
 namespace hgm {
@@ -64,20 +71,21 @@ struct List {
     int32_t n;
 };
 
-template <int KM, int NT>
+template <int KM, int NT, int NP>
 struct Smem {
     static constexpr int RS = KM + 4;     // row stride of r (16-byte rows, bank skew)
     float2 fb[KM * KM];                   // per b: kept (base, p1) in increasing a, at b*KM + k
     float r[KM * RS];                     // theta(a->c) or +inf, at a*RS + c
-    static constexpr int AS = KM + 1;     // row stride of alpha (conflict-free row and column access)
-    float alpha[KM * AS];                 // alpha_{i+1}(a,b) at b*AS + a; alpha_i(b,c) written at c*AS + b
+    // row stride of alpha: phase 1 reads row b at a = NP k + h with lanes (b, h); conflict-free when
+    // AS = NP (mod 32) and odd multiples are avoided: 65 for one thread per b, 66 for two
+    static constexpr int AS = KM + NP;
+    float alpha[KM * AS];                 // alpha_{i+1}(a,b) at b*AS + a (then base(a,b)); alpha_i(b,c) at c*AS + b
     uint8_t fs[KM * KM];                  // slot a of each kept entry
-    uint8_t used[KM];                     // a kept for some b (its r row is needed)
-    int32_t fn[KM];                       // number of kept a per b
+    uint8_t fn[KM];                       // number of kept a per b
     uint8_t tile_b[KM * KM / 4];          // b of every tile of the step (tiles of >= 4 cells)
     uint16_t tbase[KM];                   // first tile of b
     uint8_t tcount[KM];                   // tiles of b
-    int32_t hist[KM + 1];                 // tiles per kept count (counting sort of the b), then bucket starts
+    int32_t pw[KM];                       // per b: (sort key << 5) | tile count, key 0 for b without tiles
     int32_t ntile;                        // tiles of the step
     List<KM> list[3];
     float4 geo[2];                        // model constants of step i at geo[i & 1]
@@ -115,7 +123,7 @@ __device__ __forceinline__ void argmin_merge(float &v, int &k, float ov, int ok)
 
 // kCount = true builds the accounting variant: identical work, plus a count of
 // the (a, b, c) evaluations the triple loop performs (kept a x CT per tile).
-template <int KM, int NT, int CT, bool kCount>
+template <int KM, int NT, int CT, int NP, bool kCount>
 __global__ void __launch_bounds__(NT, (KM > 32 ? 3 : 4))
 recurse_kernel(const Unit *__restrict__ units, int64_t n_units, const ModelRec *__restrict__ models,
                const SceneRec *__restrict__ scenes, Params p, const int32_t *__restrict__ cand_idx,
@@ -124,11 +132,15 @@ recurse_kernel(const Unit *__restrict__ units, int64_t n_units, const ModelRec *
 {
     unsigned long long n_eval = 0;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    Smem<KM, NT> &sm = *reinterpret_cast<Smem<KM, NT> *>(smem_raw);
-    constexpr int RS = Smem<KM, NT>::RS;
-    constexpr int AS = Smem<KM, NT>::AS;
+    Smem<KM, NT, NP> &sm = *reinterpret_cast<Smem<KM, NT, NP> *>(smem_raw);
+    constexpr int RS = Smem<KM, NT, NP>::RS;
+    constexpr int AS = Smem<KM, NT, NP>::AS;
     constexpr int AQ = KM / 32;            // slots per lane in warp-wide passes
     constexpr int NW = NT / 32;
+    constexpr int P1 = KM * NP;            // threads building the kept lists (NP per b); the rest: theta table
+    constexpr int AH = KM / NP;            // a (and c) slots per list-building thread
+    static_assert(NP == 1 || NP == 2, "one or two threads per b");
+    static_assert(P1 % 32 == 0 && NT - P1 >= KM, "thread split");
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int K = p.K;
     const int T = p.T;
@@ -158,7 +170,6 @@ recurse_kernel(const Unit *__restrict__ units, int64_t n_units, const ModelRec *
         for (int q = 1; q <= 3 && q <= M; ++q)
             load_list<KM>(sm.list[(M - q) % 3], sc, cidx + (int64_t)(M - q) * K, cu + (int64_t)(M - q) * K,
                           ccnt[M - q], tid, NT);
-        if (tid < KM) sm.used[tid] = 0;
         if (tid == 0 && M >= 3) sm.geo[(M - 1) & 1] = md.geo[M - 1];
         __syncthreads();
 
@@ -171,203 +182,191 @@ recurse_kernel(const Unit *__restrict__ units, int64_t n_units, const ModelRec *
             const int dt_ab = __float_as_int(g.z), dt_bc = __float_as_int(g.w);
             const int na = LA.n, nb = LB.n, nc = LC.n;
 
-            // list C of the next step (chain index i-3): first half of the fetch
-            const bool pf = i >= 3 && tid < K;
+            // list C of the next step (chain index i-3) is fetched by the theta-table threads
+            const int pfi = tid - P1;
+            const bool pf = i >= 3 && pfi >= 0 && pfi < K;
             int pf_n = 0, pf_j = -1;
             float pf_u = kInf;
-            if (pf) {
-                pf_n = ccnt[i - 3];
-                pf_j = cidx[(int64_t)(i - 3) * K + tid];
-                pf_u = cu[(int64_t)(i - 3) * K + tid];
-            }
-
-            // ---- phase 1: per b (one warp each) the kept a list and the tile count
-            // per-lane data of the lane's a and c slots, shared by every b of the warp
-            int la_t[AQ], la_i[AQ], lc_t[AQ], lc_i[AQ];
-            float la_u[AQ];
-#pragma unroll
-            for (int q = 0; q < AQ; ++q) {
-                const int a = lane + 32 * q;
-                la_t[q] = LA.t[a];
-                la_i[q] = LA.idx[a];
-                la_u[q] = LA.u[a];
-                lc_t[q] = a < nc ? LC.t[a] : 0x7fffffff;   // c outside the list never qualifies
-                lc_i[q] = LC.idx[a];
-            }
-            for (int b = warp; b < KM; b += NW) {
-                if (b >= nb) {
-                    if (lane == 0) { sm.fn[b] = 0; sm.tcount[b] = 0; }
-                    continue;
-                }
-                const float2 pb = LB.xy[b];
-                const int tb = LB.t[b], ib = LB.idx[b];
-                float base[AQ];
-                float bv = kInf;
-#pragma unroll
-                for (int q = 0; q < AQ; ++q) {
-                    const int a = lane + 32 * q;
-                    base[q] = kInf;
-                    if (a < na && la_t[q] >= tb && la_i[q] != ib)
-                        base[q] = base_cost(la_u[q], lam2, dt_ab, la_t[q], tb, sm.alpha[b * AS + a]);
-                    bv = fminf(bv, base[q]);
-                }
-#pragma unroll
-                for (int off = 16; off > 0; off >>= 1) bv = fminf(bv, __shfl_xor_sync(0xffffffffu, bv, off));
-                int bk = 0;   // witness: the lowest slot with the smallest base
-#pragma unroll
-                for (int q = AQ - 1; q >= 0; --q) {
-                    const uint32_t hit = __ballot_sync(0xffffffffu, base[q] == bv);
-                    if (hit) bk = __ffs(hit) - 1 + 32 * q;
-                }
-                // c with t'(c) <= t'(b) form a prefix of C: tiles cover it
-                int ccount = 0;
-#pragma unroll
-                for (int q = 0; q < AQ; ++q) ccount += __popc(__ballot_sync(0xffffffffu, lc_t[q] <= tb));
-                if (lane == 0) sm.tcount[b] = (uint8_t)((ccount + CT - 1) / CT);
-                if (!(bv < kInf)) {
-                    if (lane == 0) sm.fn[b] = 0;
-                    continue;
-                }
-                float thr = bv + gmax + 1e-6f * bv;
-                // cells (b,c) whose witness bk is infeasible: raise thr by their own best feasible base
-                const int tw = LA.t[bk], iw = LA.idx[bk];
-                uint32_t bad[AQ];
-#pragma unroll
-                for (int q = 0; q < AQ; ++q) {
-                    const bool bd = lc_t[q] <= tb && lc_i[q] != ib && ((T > 0 && tw - lc_t[q] >= T) || iw == lc_i[q]);
-                    bad[q] = __ballot_sync(0xffffffffu, bd);
-                }
-#pragma unroll
-                for (int q = 0; q < AQ; ++q) {
-                    while (bad[q]) {
-                        const int c = __ffs(bad[q]) - 1 + 32 * q;
-                        bad[q] &= bad[q] - 1;
-                        const int tc = LC.t[c], ic = LC.idx[c];
-                        float mv = kInf;
-#pragma unroll
-                        for (int qa = 0; qa < AQ; ++qa) {
-                            if (!((T > 0 && la_t[qa] - tc >= T) || la_i[qa] == ic)) mv = fminf(mv, base[qa]);
-                        }
-#pragma unroll
-                        for (int off = 16; off > 0; off >>= 1) mv = fminf(mv, __shfl_xor_sync(0xffffffffu, mv, off));
-                        if (mv < kInf) thr = fmaxf(thr, mv + gmax + 1e-6f * mv);
-                    }
-                }
-                // keep base <= thr, compacted in increasing a
-                int kept = 0;
-                float *fbf = reinterpret_cast<float *>(sm.fb + b * KM);
-#pragma unroll
-                for (int q = 0; q < AQ; ++q) {
-                    const int a = lane + 32 * q;
-                    const bool keep = base[q] <= thr;
-                    const uint32_t km = __ballot_sync(0xffffffffu, keep);
-                    if (keep) {
-                        const int pos = kept + __popc(km & lanemask_lt());
-                        fbf[2 * pos] = base[q];
-                        sm.fs[b * KM + pos] = (uint8_t)a;
-                        sm.used[a] = 1;
-                    }
-                    kept += __popc(km);
-                }
-                __syncwarp();
-                // p1 = A1 + theta(b->a) of the kept entries, one lane per entry
-                for (int pos = lane; pos < kept; pos += 32) {
-                    const float2 pa = LA.xy[sm.fs[b * KM + pos]];
-                    fbf[2 * pos + 1] = wrap_pi(__fadd_rn(A1, direction(pb, pa)));
-                }
-                if (lane == 0) sm.fn[b] = kept;
-            }
-            __syncthreads();
-
-            // list C of the next step: second half of the fetch (positions and frames)
             float2 pf_xy = make_float2(0.f, 0.f);
             int pf_t = 0x3fffffff;
-            const bool pf_ok = pf && tid < pf_n;
-            if (pf_ok) {
-                pf_xy = sc.xy[pf_j];
-                pf_t = sc.t[pf_j];
-            }
+            bool pf_ok = false;
 
-            // ---- phase 2: theta(a->c) rows of the kept a; then warp 0 lays out the tile table
-            if (tid == 32 && i >= 3) sm.geo[(i - 1) & 1] = md.geo[i - 1];
-            for (int e = tid; e < na * KM; e += NT) {
-                const int a = e / KM, c = e % KM;
-                if (!sm.used[a]) continue;
-                float r = kInf;
-                if (c < nc) {
-                    const int ta = LA.t[a], tc = LC.t[c];
-                    // kept pairs have t'(c) <= t'(b) <= t'(a): entries with t'(c) > t'(a) are never read
-                    if (tc <= ta && !(T > 0 && ta - tc >= T) && LA.idx[a] != LC.idx[c]) {
-                        r = direction(LA.xy[a], LC.xy[c]);                   // theta(a->c)
+            if (tid < P1) {
+                // ---- phase 1: the kept a list of b, NP threads per b (lanes h of a pair; a = NP k + h)
+                const int b = tid / NP, h = tid % NP;
+                const bool inb = b < nb;
+                float2 pb = make_float2(0.f, 0.f);
+                int tb = 0, ib = -1;
+                if (inb) { pb = LB.xy[b]; tb = LB.t[b]; ib = LB.idx[b]; }
+                float *arow = sm.alpha + b * AS;
+                // smallest and second-smallest base (value, slot) over all feasible a, and the two smallest
+                // values over the a also feasible with the earliest c (t'(a) - t'(C_0) < T)
+                float m1 = kInf, m2 = kInf, q1v = kInf, q2v = kInf;
+                int s1 = 1 << 20, s2 = 1 << 20;
+                const int t0c = nc > 0 ? LC.t[0] : 0;
+                if (inb) {
+#pragma unroll 4
+                    for (int k = 0; k < AH; ++k) {
+                        const int a = NP * k + h;
+                        // slots past the list hold t = 0x3fffffff, idx = -1, u = inf: never feasible with b
+                        const int ta = LA.t[a];
+                        float bs = kInf;
+                        if (a < na && ta >= tb && LA.idx[a] != ib)
+                            bs = base_cost(LA.u[a], lam2, dt_ab, ta, tb, arow[a]);
+                        arow[a] = bs;   // base(a,b) replaces alpha_{i+1}(a,b): read once, by this thread
+                        if (bs < m1) { m2 = m1; s2 = s1; m1 = bs; s1 = a; }
+                        else if (bs < m2) { m2 = bs; s2 = a; }
+                        if (!(T > 0 && ta - t0c >= T)) {
+                            if (bs < q1v) { q2v = q1v; q1v = bs; }
+                            else if (bs < q2v) q2v = bs;
+                        }
                     }
                 }
-                sm.r[a * RS + c] = r;
-            }
-            if (warp == 0) {
-                // tiles of b in decreasing kept count (counting sort; order inside a count is free):
-                // the lanes of a warp then loop over similar numbers of a
-                constexpr int HB = KM + 1, HE = (HB + 31) / 32;
-                for (int k = lane; k < HB; k += 32) sm.hist[k] = 0;
-                __syncwarp();
-                int key[AQ], cnt[AQ];
-#pragma unroll
-                for (int q = 0; q < AQ; ++q) {
-                    const int b = lane + 32 * q;
-                    cnt[q] = sm.tcount[b];
-                    key[q] = KM - sm.fn[b];
-                    if (cnt[q]) atomicAdd(&sm.hist[key[q]], cnt[q]);
+                if constexpr (NP == 2) {
+                    // merge the pair's (value, slot) top-2 lists; ties go to the lower slot
+                    const float om1 = __shfl_xor_sync(0xffffffffu, m1, 1), om2 = __shfl_xor_sync(0xffffffffu, m2, 1);
+                    const int os1 = __shfl_xor_sync(0xffffffffu, s1, 1), os2 = __shfl_xor_sync(0xffffffffu, s2, 1);
+                    const float oq1 = __shfl_xor_sync(0xffffffffu, q1v, 1), oq2 = __shfl_xor_sync(0xffffffffu, q2v, 1);
+                    if (om1 < m1 || (om1 == m1 && os1 < s1)) {
+                        if (m1 < om2 || (m1 == om2 && s1 < os2)) { m2 = m1; s2 = s1; }
+                        else { m2 = om2; s2 = os2; }
+                        m1 = om1; s1 = os1;
+                    } else if (om1 < m2 || (om1 == m2 && os1 < s2)) {
+                        m2 = om1; s2 = os1;
+                    }
+                    q2v = fminf(fmaxf(q1v, oq1), fminf(q2v, oq2));
+                    q1v = fminf(q1v, oq1);
                 }
-                __syncwarp();
-                int loc[HE], sum = 0;
-#pragma unroll
-                for (int e = 0; e < HE; ++e) {
-                    const int k = lane * HE + e;
-                    loc[e] = k < HB ? sm.hist[k] : 0;
-                    sum += loc[e];
+                const float bv = m1;
+                // c with t'(c) <= t'(b) form a prefix of C (time order): its length by binary search
+                int ccount = 0;
+                if (inb) {
+                    int lo = 0, hi = nc;
+                    while (lo < hi) {
+                        const int mid = (lo + hi) >> 1;
+                        if (LC.t[mid] <= tb) lo = mid + 1;
+                        else hi = mid;
+                    }
+                    ccount = lo;
                 }
-                int x = sum;
-#pragma unroll
-                for (int off = 1; off < 32; off <<= 1) {
-                    const int y = __shfl_up_sync(0xffffffffu, x, off);
-                    if (lane >= off) x += y;
-                }
-                int pre = x - sum;
-#pragma unroll
-                for (int e = 0; e < HE; ++e) {
-                    const int k = lane * HE + e;
-                    if (k < HB) sm.hist[k] = pre;
-                    pre += loc[e];
-                }
-                __syncwarp();
-#pragma unroll
-                for (int q = 0; q < AQ; ++q) {
-                    if (cnt[q]) {
-                        const int b = lane + 32 * q;
-                        const int t0 = atomicAdd(&sm.hist[key[q]], cnt[q]);
-                        sm.tbase[b] = (uint16_t)t0;
-                        for (int t = 0; t < cnt[q]; ++t) sm.tile_b[t0 + t] = (uint8_t)b;
+                const bool live = inb && bv < kInf && ccount > 0;
+                // cells (b,c) where the witness s1 is infeasible: their best base is at most the second
+                // smallest over the a feasible with c -- exactly m2 when the runner-up s2 is feasible with
+                // c, else at most q2v (the a feasible with C_0 are feasible with every later c)
+                bool anybad = false, loose = false;
+                if (live) {
+                    const int tw = LA.t[s1], iw = LA.idx[s1];
+                    const int t2 = s2 < KM ? LA.t[s2] : 0, i2 = s2 < KM ? LA.idx[s2] : -2;
+#pragma unroll 4
+                    for (int k = 0; k < AH; ++k) {
+                        const int c = NP * k + h;
+                        const int tc = LC.t[c], ic = LC.idx[c];
+                        if (c < ccount && ic != ib && ((T > 0 && tw - tc >= T) || iw == ic)) {
+                            anybad = true;
+                            if (!(m2 < kInf) || (T > 0 && t2 - tc >= T) || i2 == ic) loose = true;
+                        }
                     }
                 }
-                const int total = __shfl_sync(0xffffffffu, x, 31);
-                if (lane == 0) sm.ntile = total;
+                if constexpr (NP == 2) {
+                    anybad |= __shfl_xor_sync(0xffffffffu, (int)anybad, 1) != 0;
+                    loose |= __shfl_xor_sync(0xffffffffu, (int)loose, 1) != 0;
+                }
+                float thr = bv + gmax + 1e-6f * bv;
+                if (anybad) {
+                    const float bb = loose ? q2v : m2;
+                    thr = bb < kInf ? fmaxf(thr, bb + gmax + 1e-6f * bb) : kInf;
+                }
+                // keep base <= thr, compacted in increasing a: positions from the pair's kept masks
+                unsigned long long mk = 0;
+                if (live) {
+#pragma unroll 8
+                    for (int k = 0; k < AH; ++k) {
+                        const float bs = arow[NP * k + h];   // +inf for a past the list
+                        if (bs < kInf && bs <= thr) mk |= 1ull << k;
+                    }
+                }
+                unsigned long long pmk = 0;
+                if constexpr (NP == 2) {
+                    const unsigned lo32 = __shfl_xor_sync(0xffffffffu, (unsigned)mk, 1);
+                    pmk = lo32;
+                }
+                const int kept = __popcll(mk) + __popcll(pmk);
+                float *fbf = reinterpret_cast<float *>(sm.fb + b * KM);
+                for (unsigned long long m = mk; m; m &= m - 1) {
+                    const int k = __ffsll((long long)m) - 1;
+                    const int a = NP * k + h;
+                    int pos = __popcll(mk & ((1ull << k) - 1));
+                    if constexpr (NP == 2) pos += __popcll(pmk & ((h ? 2ull << k : 1ull << k) - 1));
+                    fbf[2 * pos] = arow[a];
+                    sm.fs[b * KM + pos] = (uint8_t)a;
+                    fbf[2 * pos + 1] = wrap_pi(__fadd_rn(A1, direction(pb, LA.xy[a])));   // p1 = A1 + theta(b->a)
+                }
+                // tiles in decreasing kept count, then increasing b (the lanes of a warp then loop over
+                // similar numbers of a): b's first tile = sum of the tile counts of the b ranked before it
+                const int nt_b = inb ? (ccount + CT - 1) / CT : 0;
+                const int fnb = live ? kept : 0;
+                const int key = nt_b > 0 ? ((fnb + 1) << 8) | (255 - b) : 0;
+                if (h == 0) {
+                    sm.fn[b] = (uint8_t)fnb;
+                    sm.tcount[b] = (uint8_t)nt_b;
+                    sm.pw[b] = (key << 5) | nt_b;
+                }
+                asm volatile("bar.sync 1, %0;" ::"r"(P1) : "memory");
+                int before = 0, total = 0;
+                for (int b2 = h; b2 < KM; b2 += NP) {
+                    const int w = sm.pw[b2];
+                    total += w & 31;
+                    if ((w >> 5) > key) before += w & 31;
+                }
+                if constexpr (NP == 2) {
+                    before += __shfl_xor_sync(0xffffffffu, before, 1);
+                    total += __shfl_xor_sync(0xffffffffu, total, 1);
+                }
+                if (h == 0) sm.tbase[b] = (uint16_t)before;
+                for (int t = h; t < nt_b; t += NP) sm.tile_b[before + t] = (uint8_t)b;
+                if (tid == 0) sm.ntile = total;
+            } else {
+                // ---- phase 2 (concurrent): theta(a->c) for every a and the c with t'(c) <= t'(a)
+                if (pf) {
+                    pf_n = ccnt[i - 3];
+                    pf_j = cidx[(int64_t)(i - 3) * K + pfi];
+                    pf_u = cu[(int64_t)(i - 3) * K + pfi];
+                }
+                if (tid == P1 && i >= 3) sm.geo[(i - 1) & 1] = md.geo[i - 1];
+                for (int e = tid - P1; e < na * KM; e += NT - P1) {
+                    const int a = e / KM, c = e % KM;
+                    float r = kInf;
+                    if (c < nc) {
+                        const int ta = LA.t[a], tc = LC.t[c];
+                        // kept pairs have t'(c) <= t'(b) <= t'(a): entries with t'(c) > t'(a) are never read
+                        if (tc <= ta && !(T > 0 && ta - tc >= T) && LA.idx[a] != LC.idx[c]) {
+                            r = direction(LA.xy[a], LC.xy[c]);                   // theta(a->c)
+                        }
+                    }
+                    sm.r[a * RS + c] = r;
+                }
+                pf_ok = pf && pfi < pf_n;
+                if (pf_ok) {
+                    pf_xy = sc.xy[pf_j];
+                    pf_t = sc.t[pf_j];
+                }
             }
             __syncthreads();
 
             // list A is not read from here on: its buffer receives list C of the next step
             if (pf) {
-                LA.idx[tid] = pf_ok ? pf_j : -1;
-                LA.xy[tid] = pf_xy;
-                LA.t[tid] = pf_t;
-                LA.u[tid] = pf_ok ? pf_u : kInf;
-                if (tid == 0) LA.n = pf_n;
+                LA.idx[pfi] = pf_ok ? pf_j : -1;
+                LA.xy[pfi] = pf_xy;
+                LA.t[pfi] = pf_t;
+                LA.u[pfi] = pf_ok ? pf_u : kInf;
+                if (pfi == 0) LA.n = pf_n;
             }
-            if (i >= 3 && tid >= K && tid < KM) {
-                LA.idx[tid] = -1;
-                LA.xy[tid] = make_float2(0.f, 0.f);
-                LA.t[tid] = 0x3fffffff;
-                LA.u[tid] = kInf;
+            if (i >= 3 && pfi >= K && pfi < KM) {
+                LA.idx[pfi] = -1;
+                LA.xy[pfi] = make_float2(0.f, 0.f);
+                LA.t[pfi] = 0x3fffffff;
+                LA.u[pfi] = kInf;
             }
-            if (tid < KM) sm.used[tid] = 0;
 
             // ---- phase 3: tiles (b, CT consecutive c)
             const int ntile = sm.ntile;
@@ -477,17 +476,17 @@ recurse_kernel(const Unit *__restrict__ units, int64_t n_units, const ModelRec *
     }
 }
 
-template <int KM, int NT, int CT, bool kCount>
+template <int KM, int NT, int CT, int NP, bool kCount>
 cudaError_t launch_recurse_t(const Unit *units, int64_t n_units, const ModelRec *models, const SceneRec *scenes,
                              Params p, const int32_t *cand_idx, const float *cand_u, const int32_t *cand_cnt,
                              uint8_t *beta, UnitResult *res, int *work_counter, unsigned long long *evaluated,
                              cudaStream_t st)
 {
     // three CTAs of 256 threads per SM: 3 x (shared memory + 1 KB reserved) <= 228 KB
-    static_assert(KM != 64 || NT != 256 || 3 * (sizeof(Smem<KM, NT>) + 1024) <= 228 * 1024,
+    static_assert(KM != 64 || NT != 256 || 3 * (sizeof(Smem<KM, NT, NP>) + 1024) <= 228 * 1024,
                   "recursion shared memory exceeds the three-CTA budget");
-    auto kern = recurse_kernel<KM, NT, CT, kCount>;
-    const size_t smem = sizeof(Smem<KM, NT>);
+    auto kern = recurse_kernel<KM, NT, CT, NP, kCount>;
+    const size_t smem = sizeof(Smem<KM, NT, NP>);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int dev = 0, sms = 0, per_sm = 0;
@@ -510,24 +509,21 @@ cudaError_t dispatch(int variant, const Unit *units, int64_t n_units, const Mode
                      Params p, const int32_t *cand_idx, const float *cand_u, const int32_t *cand_cnt, uint8_t *beta,
                      UnitResult *res, int *work_counter, unsigned long long *evaluated, cudaStream_t st)
 {
+#define HGM_RECURSE(KM_, NT_, CT_, NP_)                                                                           \
+    return launch_recurse_t<KM_, NT_, CT_, NP_, kCount>(units, n_units, models, scenes, p, cand_idx, cand_u,    \
+                                                        cand_cnt, beta, res, work_counter, evaluated, st)
     if (p.K <= 32) {
-        if (variant == 1)
-            return launch_recurse_t<32, 128, 8, kCount>(units, n_units, models, scenes, p, cand_idx, cand_u, cand_cnt,
-                                                        beta, res, work_counter, evaluated, st);
-        return launch_recurse_t<32, 128, 4, kCount>(units, n_units, models, scenes, p, cand_idx, cand_u, cand_cnt,
-                                                    beta, res, work_counter, evaluated, st);
+        if (variant == 1) HGM_RECURSE(32, 128, 8, 2);
+        if (variant == 2) HGM_RECURSE(32, 128, 4, 1);
+        HGM_RECURSE(32, 128, 4, 2);
     }
-    if (variant == 1)
-        return launch_recurse_t<64, 256, 8, kCount>(units, n_units, models, scenes, p, cand_idx, cand_u, cand_cnt,
-                                                    beta, res, work_counter, evaluated, st);
-    if (variant == 2)
-        return launch_recurse_t<64, 128, 4, kCount>(units, n_units, models, scenes, p, cand_idx, cand_u, cand_cnt,
-                                                    beta, res, work_counter, evaluated, st);
-    return launch_recurse_t<64, 256, 4, kCount>(units, n_units, models, scenes, p, cand_idx, cand_u, cand_cnt, beta,
-                                                res, work_counter, evaluated, st);
+    if (variant == 1) HGM_RECURSE(64, 256, 8, 2);
+    if (variant == 2) HGM_RECURSE(64, 256, 4, 1);
+    HGM_RECURSE(64, 256, 4, 2);
+#undef HGM_RECURSE
 }
 
-int g_variant = 0;   // recursion variant: 0 = 4 c per tile, 1 = 8 c per tile, 2 = 4 c per tile on 128 threads
+int g_variant = 0;   // recursion variant: 0 = 4 c per tile, 1 = 8 c per tile, 2 = 4 c per tile and one list builder per b
 
 }  // namespace
 
