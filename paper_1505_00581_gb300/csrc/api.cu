@@ -90,6 +90,7 @@ hgm_status upload(T **dptr, const std::vector<T> &h, cudaStream_t st)
 
 int round_up4(int v) { return (v + 3) & ~3; }
 
+
 // ---- profiling --------------------------------------------------------------
 struct ProfRec {
     int kernel;
@@ -138,12 +139,65 @@ struct Buffer {
 struct Workspace {
     Buffer modelcat, U, cand_idx, cand_u, cand_cnt, beta, units, res, mrec, srec, counter, out_e, out_a, evaluated;
     Buffer mnorm, snorm, status;
-    Buffer P, Q, modelxy, cand2_idx, cand2_u, cand2_cnt, units2, beta2, fb_units, fb_count, beta_fb, res_fb, scores;
+    Buffer stage, perm_stage, flag;   // inputs of hgm_create_model / hgm_create_scene
+    Buffer P, Q, modelxy, cand2_idx, cand2_u, cand2_cnt, units2, beta2, fb_units, fb_count, beta_fb, scores;
+    Buffer fb_total;   // fallback units since the last hgm_prune_counters reset (device counter)
 };
 Workspace g_ws;
 bool g_count_mode = false;   // hgm_profile_enable(2): batch runs use the accounting recursion variant
 size_t g_budget_override = 0;   // hgm_set_workspace_budget: bytes for the unary table and for a chunk (0 = auto)
-int64_t g_pruned_units = 0, g_fallback_units = 0;
+int64_t g_pruned_units = 0;
+
+// dst[k][c] = src[perm[k]][c] for c < F, 0 for F <= c < Fp; flags a non-finite component.
+__global__ void gather_rows_kernel(const float *__restrict__ src, int F, const int32_t *__restrict__ perm, int64_t n,
+                                   int Fp, float *__restrict__ dst, int *__restrict__ bad)
+{
+    const int64_t total = n * Fp;
+    int nonfinite = 0;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t k = e / Fp;
+        const int c = (int)(e - k * Fp);
+        float v = 0.0f;
+        if (c < F) {
+            v = src[(int64_t)perm[k] * F + c];
+            nonfinite |= !isfinite(v);
+        }
+        dst[e] = v;
+    }
+    if (nonfinite) atomicOr(bad, 1);
+}
+
+// Sorted, padded device copy of a descriptor array (host or device, n x F row-major): the raw rows go to the
+// device in one copy (none for device input), then a gather kernel applies the permutation. Returns
+// HGM_EINVAL on a non-finite component. Synchronous on st.
+hgm_status upload_sorted_rows(const float *src, int64_t n, int F, int Fp, const std::vector<int32_t> &perm,
+                              float **dst, const char *what, cudaStream_t st)
+{
+    const size_t bytes = (size_t)std::max<int64_t>(n * Fp, 1) * sizeof(float);
+    CK(cudaMalloc((void **)dst, bytes), "cudaMalloc");
+    if (n == 0) return HGM_OK;
+    const float *dsrc = src;
+    if (!is_device_ptr(src)) {
+        CK(g_ws.stage.ensure((size_t)n * F * sizeof(float)), "workspace (input staging)");
+        CK(cudaMemcpyAsync(g_ws.stage.p, src, (size_t)n * F * sizeof(float), cudaMemcpyHostToDevice, st),
+           "upload descriptors");
+        dsrc = g_ws.stage.as<float>();
+    }
+    CK(g_ws.perm_stage.ensure((size_t)n * sizeof(int32_t)), "workspace (input staging)");
+    CK(cudaMemcpyAsync(g_ws.perm_stage.p, perm.data(), (size_t)n * sizeof(int32_t), cudaMemcpyHostToDevice, st),
+       "upload permutation");
+    CK(g_ws.flag.ensure(sizeof(int)), "workspace");
+    CK(cudaMemsetAsync(g_ws.flag.p, 0, sizeof(int), st), "memset");
+    const int64_t blocks = std::min<int64_t>((n * Fp + 255) / 256, 65536);
+    gather_rows_kernel<<<(unsigned)blocks, 256, 0, st>>>(dsrc, F, g_ws.perm_stage.as<int32_t>(), n, Fp, *dst,
+                                                         g_ws.flag.as<int>());
+    CK(cudaGetLastError(), "gather kernel");
+    int bad = 0;
+    CK(cudaMemcpyAsync(&bad, g_ws.flag.p, sizeof(int), cudaMemcpyDeviceToHost, st), "flag");
+    CK(cudaStreamSynchronize(st), "synchronise");
+    if (bad) return fail(HGM_EINVAL, "non-finite %s descriptor", what);
+    return HGM_OK;
+}
 
 }  // namespace
 
@@ -359,31 +413,22 @@ hgm_status run_units(const hgm_model *const *models, std::vector<Unit> &all, int
             CK(launch_backtrack(du2, n, dm, ds, pk, g_ws.cand2_idx.as<int32_t>(), g_ws.beta2.as<uint8_t>(),
                                 g_ws.res.as<UnitResult>(), d_energy, d_assign, st),
                "backtrack kernel (pruned lists)");
-            // fallback: units whose pruned optimum is infeasible are solved again on the full lists
-            const int bstride = (max_M - 2) * K * K;
+            // fallback: units whose pruned optimum is infeasible are solved again on the full lists, by the
+            // fused recursion + backtrack reading their number on the device (no host round trip)
             CK(g_ws.fb_units.ensure((size_t)n * sizeof(Unit)), "workspace (fallback)");
             CK(g_ws.fb_count.ensure(sizeof(int)), "workspace");
             CK(cudaMemsetAsync(g_ws.fb_count.p, 0, sizeof(int), st), "memset");
-            CK(launch_collect_infeasible(g_ws.res.as<UnitResult>(), du, n, bstride, g_ws.fb_units.as<Unit>(),
-                                         g_ws.fb_count.as<int>(), st),
+            CK(launch_collect_infeasible(g_ws.res.as<UnitResult>(), du, n, g_ws.fb_units.as<Unit>(),
+                                         g_ws.fb_count.as<int>(), g_ws.fb_total.as<unsigned long long>(), st),
                "collect infeasible");
-            int n_fb = 0;
-            CK(cudaMemcpyAsync(&n_fb, g_ws.fb_count.p, sizeof(int), cudaMemcpyDeviceToHost, st), "fallback count");
-            CK(cudaStreamSynchronize(st), "synchronise");
+            const int64_t scratch = recurse_fused_scratch(K, max_M);
+            if (scratch < 0) return fail(HGM_ECUDA, "device query failed");
+            CK(g_ws.beta_fb.ensure((size_t)scratch), "workspace (fallback)");
+            CK(launch_recurse_fused(g_ws.fb_units.as<Unit>(), n, g_ws.fb_count.as<int>(), dm, ds, p,
+                                    g_ws.cand_idx.as<int32_t>(), g_ws.cand_u.as<float>(), g_ws.cand_cnt.as<int32_t>(),
+                                    g_ws.beta_fb.as<uint8_t>(), max_M, d_energy, d_assign, g_ws.counter.as<int>(), st),
+               "recursion kernel (fallback)");
             g_pruned_units += n;
-            g_fallback_units += n_fb;
-            if (n_fb > 0) {
-                CK(g_ws.beta_fb.ensure((size_t)n_fb * bstride), "workspace (fallback)");
-                CK(g_ws.res_fb.ensure((size_t)n_fb * sizeof(UnitResult)), "workspace (fallback)");
-                const Unit *dfb = g_ws.fb_units.as<Unit>();
-                CK(launch_recurse(dfb, n_fb, dm, ds, p, g_ws.cand_idx.as<int32_t>(), g_ws.cand_u.as<float>(),
-                                  g_ws.cand_cnt.as<int32_t>(), g_ws.beta_fb.as<uint8_t>(), g_ws.res_fb.as<UnitResult>(),
-                                  g_ws.counter.as<int>(), st),
-                   "recursion kernel (fallback)");
-                CK(launch_backtrack(dfb, n_fb, dm, ds, p, g_ws.cand_idx.as<int32_t>(), g_ws.beta_fb.as<uint8_t>(),
-                                    g_ws.res_fb.as<UnitResult>(), d_energy, d_assign, st),
-                   "backtrack kernel (fallback)");
-            }
             begin = end;
             continue;
         }
@@ -489,6 +534,10 @@ hgm_status run_batch(const hgm_model *const *models, int nm, const hgm_scene *co
         pi.keep = keep;
         pi.rescore = hp->precision == 1 ? 1 : 0;
         p.rescore = 0;   // the kept candidates are re-scored by the pruning kernel instead
+        if (!g_ws.fb_total.p) {
+            CK(g_ws.fb_total.ensure(sizeof(unsigned long long)), "workspace");
+            CK(cudaMemsetAsync(g_ws.fb_total.p, 0, sizeof(unsigned long long), st), "memset");
+        }
     }
     if (hp->precision == 1) {
         CK(g_ws.mnorm.ensure((size_t)R * sizeof(float)), "workspace (norms)");
@@ -758,16 +807,14 @@ hgm_status hgm_create_model(const float *xy, const int32_t *t, const float *desc
     if (F < 1 || F > 4096) return fail(HGM_EINVAL, "F must be in 1..4096 (got %d)", F);
     if (!xy || !t || !desc) return fail(HGM_EINVAL, "NULL input array");
     cudaStream_t st = (cudaStream_t)stream;
-    std::vector<float> hxy, hf;
+    // positions and frames are sorted on the host (small); descriptors go to the device raw and are
+    // permuted there
+    std::vector<float> hxy;
     std::vector<int32_t> ht;
     hgm_status rc;
-    if ((rc = fetch(xy, (size_t)M * 2, hxy, st)) || (rc = fetch(t, (size_t)M, ht, st)) ||
-        (rc = fetch(desc, (size_t)M * F, hf, st)))
-        return rc;
+    if ((rc = fetch(xy, (size_t)M * 2, hxy, st)) || (rc = fetch(t, (size_t)M, ht, st))) return rc;
     for (float v : hxy)
         if (!std::isfinite(v)) return fail(HGM_EINVAL, "non-finite model coordinate");
-    for (float v : hf)
-        if (!std::isfinite(v)) return fail(HGM_EINVAL, "non-finite model descriptor");
     for (int32_t v : ht)
         if (v < 0) return fail(HGM_EINVAL, "negative model frame");
     std::vector<int32_t> perm;
@@ -775,12 +822,10 @@ hgm_status hgm_create_model(const float *xy, const int32_t *t, const float *desc
     const int Fp = round_up4(F);
     std::vector<float2> sxy((size_t)M);
     std::vector<int32_t> stt((size_t)M);
-    std::vector<float> sf((size_t)M * Fp, 0.0f);
     for (int k = 0; k < M; ++k) {
         int q = perm[(size_t)k];
         sxy[(size_t)k] = make_float2(hxy[(size_t)q * 2], hxy[(size_t)q * 2 + 1]);
         stt[(size_t)k] = ht[(size_t)q];
-        std::memcpy(&sf[(size_t)k * Fp], &hf[(size_t)q * F], (size_t)F * sizeof(float));
     }
     hgm_model *m = new hgm_model();
     m->magic = kModelMagic;
@@ -788,7 +833,8 @@ hgm_status hgm_create_model(const float *xy, const int32_t *t, const float *desc
     m->F_user = F;
     m->t_sorted = stt;
     m->perm = perm;
-    if ((rc = upload(&m->d.xy, sxy, st)) || (rc = upload(&m->d.t, stt, st)) || (rc = upload(&m->d.f, sf, st)) ||
+    if ((rc = upload(&m->d.xy, sxy, st)) || (rc = upload(&m->d.t, stt, st)) ||
+        (rc = upload_sorted_rows(desc, M, F, Fp, perm, &m->d.f, "model", st)) ||
         (rc = upload(&m->d.perm, perm, st))) {
         free_model(m);
         delete m;
@@ -817,12 +863,12 @@ hgm_status hgm_create_scene(const float *xy, const int32_t *t, const float *desc
     if (F < 1 || F > 4096) return fail(HGM_EINVAL, "F must be in 1..4096 (got %d)", F);
     if (S > 0 && (!xy || !t || !desc)) return fail(HGM_EINVAL, "NULL input array");
     cudaStream_t st = (cudaStream_t)stream;
-    std::vector<float> hxy, hf;
+    // positions and frames are sorted on the host (small); descriptors go to the device raw and are
+    // permuted there
+    std::vector<float> hxy;
     std::vector<int32_t> ht;
     hgm_status rc;
-    if ((rc = fetch(xy, (size_t)S * 2, hxy, st)) || (rc = fetch(t, (size_t)S, ht, st)) ||
-        (rc = fetch(desc, (size_t)S * F, hf, st)))
-        return rc;
+    if ((rc = fetch(xy, (size_t)S * 2, hxy, st)) || (rc = fetch(t, (size_t)S, ht, st))) return rc;
     int32_t tmax = -1;
     for (int32_t v : ht) {
         if (v < 0) return fail(HGM_EINVAL, "negative scene frame");
@@ -833,8 +879,6 @@ hgm_status hgm_create_scene(const float *xy, const int32_t *t, const float *desc
     if (n_frames <= 0) n_frames = 0;
     for (float v : hxy)
         if (!std::isfinite(v)) return fail(HGM_EINVAL, "non-finite scene coordinate");
-    for (float v : hf)
-        if (!std::isfinite(v)) return fail(HGM_EINVAL, "non-finite scene descriptor");
     // stable counting sort by frame; minnode(f) = first sorted index with frame >= f
     std::vector<int32_t> fs((size_t)n_frames + 1, 0);
     for (int32_t v : ht) fs[(size_t)v + 1]++;
@@ -847,12 +891,10 @@ hgm_status hgm_create_scene(const float *xy, const int32_t *t, const float *desc
     const int Fp = round_up4(F);
     std::vector<float2> sxy((size_t)S);
     std::vector<int32_t> stt((size_t)S);
-    std::vector<float> sf((size_t)S * Fp, 0.0f);
     for (int32_t k = 0; k < S; ++k) {
         int32_t q = perm[(size_t)k];
         sxy[(size_t)k] = make_float2(hxy[(size_t)q * 2], hxy[(size_t)q * 2 + 1]);
         stt[(size_t)k] = ht[(size_t)q];
-        std::memcpy(&sf[(size_t)k * Fp], &hf[(size_t)q * F], (size_t)F * sizeof(float));
     }
     hgm_scene *s = new hgm_scene();
     s->magic = kSceneMagic;
@@ -860,7 +902,8 @@ hgm_status hgm_create_scene(const float *xy, const int32_t *t, const float *desc
     s->F_user = F;
     s->perm = perm;
     s->fs_host = fs;
-    if ((rc = upload(&s->d.xy, sxy, st)) || (rc = upload(&s->d.t, stt, st)) || (rc = upload(&s->d.f, sf, st)) ||
+    if ((rc = upload(&s->d.xy, sxy, st)) || (rc = upload(&s->d.t, stt, st)) ||
+        (rc = upload_sorted_rows(desc, S, F, Fp, perm, &s->d.f, "scene", st)) ||
         (rc = upload(&s->d.frame_start, fs, st)) || (rc = upload(&s->d.perm, perm, st))) {
         free_scene(s);
         delete s;
@@ -1202,9 +1245,16 @@ hgm_status hgm_set_workspace_budget(int64_t bytes)
 hgm_status hgm_prune_counters(int64_t *pruned_units, int64_t *fallback_units, int32_t reset)
 {
     std::lock_guard<std::mutex> lk(g_mu);
+    g_err.clear();
+    unsigned long long fb = 0;
+    if (g_ws.fb_total.p) {
+        CK(cudaDeviceSynchronize(), "synchronise");
+        CK(cudaMemcpy(&fb, g_ws.fb_total.p, sizeof fb, cudaMemcpyDeviceToHost), "read counter");
+        if (reset) CK(cudaMemset(g_ws.fb_total.p, 0, sizeof fb), "reset counter");
+    }
     if (pruned_units) *pruned_units = g_pruned_units;
-    if (fallback_units) *fallback_units = g_fallback_units;
-    if (reset) g_pruned_units = g_fallback_units = 0;
+    if (fallback_units) *fallback_units = (int64_t)fb;
+    if (reset) g_pruned_units = 0;
     return HGM_OK;
 }
 

@@ -433,3 +433,48 @@ def test_segmented_batches_equal_whole_scene_batches(env, precision, prune):
         outs.append((e.cpu().numpy(), a.cpu().numpy()))
     hgm.set_workspace_budget(0)
     assert np.array_equal(outs[0][0], outs[1][0]) and np.array_equal(outs[0][1], outs[1][1])
+
+
+@pytest.mark.parametrize("where", ["host", "pinned", "device"])
+def test_inputs_from_host_pinned_or_device_give_identical_results(env, where):
+    """Handles created from pageable host arrays, pinned host tensors or device tensors (descriptors permuted
+    on the device in every case) give bit-identical energies and assignments."""
+    torch, hgm, _ = env
+    wl = synth.single_match(seed=4)
+    mod, sc = wl.models[0], wl.scenes[0]
+    p = hgm.default_params(K=wl.K, window=wl.window)
+    m0, s0 = handles(hgm, mod, sc)
+    _, e0, a0 = hgm.match(m0, s0, p)
+    if where == "host":
+        m, s = handles(hgm, mod, sc)
+    elif where == "pinned":
+        pin = lambda a: torch.from_numpy(a).pin_memory()
+        m = hgm.Model(pin(mod.xy), pin(mod.t), pin(mod.f))
+        s = hgm.Scene(pin(sc.xy), pin(sc.t), pin(sc.f), sc.n_frames)
+    else:
+        m, s = handles(hgm, mod, sc, torch)
+    _, e1, a1 = hgm.match(m, s, p)
+    assert np.array_equal(e0, e1) and np.array_equal(a0, a1)
+    assert np.array_equal(m.order(), m0.order()) and np.array_equal(s.order(), s0.order())
+
+
+@pytest.mark.parametrize("on_device", [False, True])
+def test_non_finite_descriptors_are_rejected(env, on_device):
+    torch, hgm, _ = env
+    wl = synth.single_match(seed=5)
+    mod, sc = wl.models[0], wl.scenes[0]
+    mf = mod.f.copy()
+    mf[2, 7] = np.nan
+    sf = sc.f.copy()
+    sf[sc.n // 2, 100] = np.inf
+    conv = (lambda a: torch.from_numpy(a).cuda()) if on_device else (lambda a: a)
+    with pytest.raises(hgm.HgmError) as err:
+        hgm.Model(conv(mod.xy), conv(mod.t), conv(mf))
+    assert err.value.status == hgm.HGM_EINVAL and "non-finite model descriptor" in str(err.value)
+    with pytest.raises(hgm.HgmError) as err:
+        hgm.Scene(conv(sc.xy), conv(sc.t), conv(sf), sc.n_frames)
+    assert err.value.status == hgm.HGM_EINVAL and "non-finite scene descriptor" in str(err.value)
+    # the library stays usable
+    m, s = handles(hgm, mod, sc)
+    first, e, a = hgm.match(m, s, hgm.default_params(K=wl.K, window=wl.window))
+    assert np.isfinite(e).any()
