@@ -114,8 +114,8 @@ cudaError_t launch_prop_prune(const Unit *units, int64_t n_units, const ModelRec
                               const int32_t *cand_cnt, float *scores, int32_t *out_idx, float *out_u,
                               int32_t *out_cnt, int *status, cudaStream_t st);
 cudaError_t launch_derive_units(const Unit *in, int64_t n, int K, int keep, Unit *out, cudaStream_t st);
-cudaError_t launch_collect_infeasible(const UnitResult *res, const Unit *units, int64_t n, int beta_stride, Unit *list,
-                                      int *count, cudaStream_t st);
+cudaError_t launch_collect_infeasible(const UnitResult *res, const Unit *units, int64_t n, Unit *list, int *count,
+                                      unsigned long long *total, cudaStream_t st);
 
 // ---- kernel launchers (each checks its own launch error) --------------------
 cudaError_t launch_unary(const float *A, int R, const float *B, int S, int F, float lambda1, float *U,
@@ -143,6 +143,14 @@ void set_recurse_variant(int v);
 int get_recurse_variant();
 // Same as launch_recurse, additionally adding the number of (a, b, c) evaluations of
 // the triple loop to *evaluated (work accounting; not used on the timed path).
+// Fused recursion + backtrack for the exact fallback of the pruned form: the unit count is read from n_dev
+// (at most n_max), argmin tables live in per-CTA scratch of recurse_fused_scratch(K, max_M) bytes, and
+// energies / assignments are written directly. No host synchronisation.
+int64_t recurse_fused_scratch(int K, int max_M);
+cudaError_t launch_recurse_fused(const Unit *units, int64_t n_max, const int *n_dev, const ModelRec *models,
+                                 const SceneRec *scenes, Params p, const int32_t *cand_idx, const float *cand_u,
+                                 const int32_t *cand_cnt, uint8_t *scratch, int max_M, float *energy,
+                                 int32_t *assign, int *work_counter, cudaStream_t st);
 cudaError_t launch_recurse_count(const Unit *units, int64_t n_units, const ModelRec *models, const SceneRec *scenes,
                                  Params p, const int32_t *cand_idx, const float *cand_u, const int32_t *cand_cnt,
                                  uint8_t *beta, UnitResult *res, int *work_counter, unsigned long long *evaluated,

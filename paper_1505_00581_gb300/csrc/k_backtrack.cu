@@ -7,6 +7,7 @@
 // and only energies and assignments leave the device. Slots are mapped to
 // sorted scene indices through the unit's candidate lists, then to the
 // caller's scene indices, and written in the caller's model order.
+#include "backtrack.cuh"
 #include "hgm_internal.cuh"
 
 namespace hgm {
@@ -24,32 +25,7 @@ __global__ void backtrack_kernel(const Unit *__restrict__ units, int64_t n_units
         const Unit un = units[u];
         const ModelRec md = models[un.model];
         const SceneRec sc = scenes[un.scene];
-        const UnitResult r = res[u];
-        const int M = md.M;
-        if (energy) energy[un.out_e] = r.energy;
-        if (!assign) continue;
-        int32_t *out = assign + un.out_a;
-        if (r.z1 < 0) {
-            for (int i = 0; i < M; ++i) out[i] = -1;
-            continue;
-        }
-        const int32_t *cidx = cand_idx + un.cand;
-        const uint8_t *ub = beta + un.beta;
-        int s2 = r.z1, s1 = r.z2;   // slots of z_{i-2}, z_{i-1}
-        out[md.perm[0]] = sc.perm[cidx[s2]];
-        out[md.perm[1]] = sc.perm[cidx[K + s1]];
-        bool ok = true;
-        for (int i = 2; i < M; ++i) {
-            int s0 = ok ? ub[((int64_t)(i - 2) * K + s1) * K + s2] : kNoSlot;
-            if (s0 == kNoSlot) {
-                ok = false;
-                out[md.perm[i]] = -1;
-                continue;
-            }
-            out[md.perm[i]] = sc.perm[cidx[(int64_t)i * K + s0]];
-            s2 = s1;
-            s1 = s0;
-        }
+        backtrack_unit(un, md, sc, K, cand_idx + un.cand, beta + un.beta, res[u], energy, assign);
     }
 }
 

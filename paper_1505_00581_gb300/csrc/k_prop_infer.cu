@@ -319,16 +319,17 @@ __global__ void derive_units_kernel(const Unit *__restrict__ in, int64_t n, int 
     }
 }
 
-// Units whose pruned optimum is infeasible, appended to `list` (fallback to the full lists).
+// Units whose pruned optimum is infeasible, appended to `list` (fallback to the full lists); `total`
+// accumulates their number across calls (read by hgm_prune_counters).
 __global__ void collect_infeasible_kernel(const UnitResult *__restrict__ res, const Unit *__restrict__ units,
-                                          int64_t n, int beta_stride, Unit *__restrict__ list, int *__restrict__ count)
+                                          int64_t n, Unit *__restrict__ list, int *__restrict__ count,
+                                          unsigned long long *__restrict__ total)
 {
     for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
         if (res[k].z1 < 0) {
             const int at = atomicAdd(count, 1);
-            Unit u = units[k];
-            u.beta = (int64_t)at * beta_stride;
-            list[at] = u;
+            atomicAdd(total, 1ull);
+            list[at] = units[k];
         }
     }
 }
@@ -396,13 +397,12 @@ cudaError_t launch_derive_units(const Unit *in, int64_t n, int K, int keep, Unit
     return cudaGetLastError();
 }
 
-cudaError_t launch_collect_infeasible(const UnitResult *res, const Unit *units, int64_t n, int beta_stride, Unit *list,
-                                      int *count, cudaStream_t st)
+cudaError_t launch_collect_infeasible(const UnitResult *res, const Unit *units, int64_t n, Unit *list, int *count,
+                                      unsigned long long *total, cudaStream_t st)
 {
     if (n <= 0) return cudaSuccess;
-    collect_infeasible_kernel<<<(unsigned)std::min<int64_t>((n + 255) / 256, 4096), 256, 0, st>>>(res, units, n,
-                                                                                                  beta_stride, list,
-                                                                                                  count);
+    collect_infeasible_kernel<<<(unsigned)std::min<int64_t>((n + 255) / 256, 4096), 256, 0, st>>>(res, units, n, list,
+                                                                                                  count, total);
     return cudaGetLastError();
 }
 

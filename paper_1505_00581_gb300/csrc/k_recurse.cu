@@ -47,6 +47,7 @@
 // the list C of the next step is fetched from global memory during phase 2 and
 // stored in the buffer of the list A, which phase 3 no longer reads, so no step
 // waits on a global load.
+#include "backtrack.cuh"
 #include "recurse_common.cuh"
 
 namespace hgm {
@@ -123,13 +124,25 @@ __device__ __forceinline__ void argmin_merge(float &v, int &k, float ov, int ok)
 
 // kCount = true builds the accounting variant: identical work, plus a count of
 // the (a, b, c) evaluations the triple loop performs (kept a x CT per tile).
-template <int KM, int NT, int CT, int NP, bool kCount>
+// kFused = true builds the self-contained variant used for the exact fallback
+// of the pruned form: the number of units is read from n_dev (written by an
+// earlier kernel, so nothing waits on the host), the argmin tables of a unit
+// live in a per-CTA scratch block (beta + blockIdx.x * beta_cta, reused unit
+// after unit), and the CTA backtracks its own unit and writes the energy and
+// the assignment itself.
+template <int KM, int NT, int CT, int NP, bool kCount, bool kFused>
 __global__ void __launch_bounds__(NT, (KM > 32 ? 3 : 4))
 recurse_kernel(const Unit *__restrict__ units, int64_t n_units, const ModelRec *__restrict__ models,
                const SceneRec *__restrict__ scenes, Params p, const int32_t *__restrict__ cand_idx,
                const float *__restrict__ cand_u, const int32_t *__restrict__ cand_cnt, uint8_t *__restrict__ beta,
-               UnitResult *__restrict__ res, int *__restrict__ work_counter, unsigned long long *__restrict__ evaluated)
+               UnitResult *__restrict__ res, int *__restrict__ work_counter, unsigned long long *__restrict__ evaluated,
+               const int *__restrict__ n_dev, int64_t beta_cta, float *__restrict__ energy_out,
+               int32_t *__restrict__ assign_out)
 {
+    if constexpr (kFused) {
+        const int64_t nd = *n_dev;
+        n_units = nd < n_units ? nd : n_units;
+    }
     unsigned long long n_eval = 0;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Smem<KM, NT, NP> &sm = *reinterpret_cast<Smem<KM, NT, NP> *>(smem_raw);
@@ -163,7 +176,7 @@ recurse_kernel(const Unit *__restrict__ units, int64_t n_units, const ModelRec *
         const int32_t *cidx = cand_idx + un.cand;
         const float *cu = cand_u + un.cand;
         const int32_t *ccnt = cand_cnt + un.cand / K;
-        uint8_t *ubeta = beta + un.beta;
+        uint8_t *ubeta = kFused ? beta + (int64_t)blockIdx.x * beta_cta : beta + un.beta;
 
         // alpha_{M+1} == 0 (Eq. 11); the three lists and the constants of the first step
         for (int e = tid; e < KM * AS; e += NT) sm.alpha[e] = 0.0f;
@@ -469,23 +482,33 @@ recurse_kernel(const Unit *__restrict__ units, int64_t n_units, const ModelRec *
                     r.z1 = -1;
                     r.z2 = -1;
                 }
-                res[u] = r;
+                if constexpr (kFused) backtrack_unit(un, md, sc, K, cidx, ubeta, r, energy_out, assign_out);
+                else res[u] = r;
             }
             __syncthreads();
         }
     }
 }
 
-template <int KM, int NT, int CT, int NP, bool kCount>
+constexpr int kFusedPerSm = 3;   // CTAs per SM of the fused variant (its argmin scratch is per CTA)
+
+struct FusedArgs {
+    const int *n_dev = nullptr;
+    int64_t beta_cta = 0;
+    float *energy = nullptr;
+    int32_t *assign = nullptr;
+};
+
+template <int KM, int NT, int CT, int NP, bool kCount, bool kFused>
 cudaError_t launch_recurse_t(const Unit *units, int64_t n_units, const ModelRec *models, const SceneRec *scenes,
                              Params p, const int32_t *cand_idx, const float *cand_u, const int32_t *cand_cnt,
                              uint8_t *beta, UnitResult *res, int *work_counter, unsigned long long *evaluated,
-                             cudaStream_t st)
+                             const FusedArgs &fa, cudaStream_t st)
 {
     // three CTAs of 256 threads per SM: 3 x (shared memory + 1 KB reserved) <= 228 KB
     static_assert(KM != 64 || NT != 256 || 3 * (sizeof(Smem<KM, NT, NP>) + 1024) <= 228 * 1024,
                   "recursion shared memory exceeds the three-CTA budget");
-    auto kern = recurse_kernel<KM, NT, CT, NP, kCount>;
+    auto kern = recurse_kernel<KM, NT, CT, NP, kCount, kFused>;
     const size_t smem = sizeof(Smem<KM, NT, NP>);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -498,20 +521,25 @@ cudaError_t launch_recurse_t(const Unit *units, int64_t n_units, const ModelRec 
     if (grid > n_units) grid = n_units;
     if ((e = cudaMemsetAsync(work_counter, 0, sizeof(int), st)) != cudaSuccess) return e;
     prof_begin(kProfRecurse, st);
+    if (kFused) {   // the per-CTA scratch was sized for sms * kFusedPerSm CTAs
+        grid = std::min<int64_t>((int64_t)sms * kFusedPerSm, n_units);
+    }
     kern<<<(unsigned)grid, NT, smem, st>>>(units, n_units, models, scenes, p, cand_idx, cand_u, cand_cnt, beta, res,
-                                           work_counter, evaluated);
+                                           work_counter, evaluated, fa.n_dev, fa.beta_cta, fa.energy, fa.assign);
     prof_end(kProfRecurse, st);
     return cudaGetLastError();
 }
 
-template <bool kCount>
+template <bool kCount, bool kFused>
 cudaError_t dispatch(int variant, const Unit *units, int64_t n_units, const ModelRec *models, const SceneRec *scenes,
                      Params p, const int32_t *cand_idx, const float *cand_u, const int32_t *cand_cnt, uint8_t *beta,
-                     UnitResult *res, int *work_counter, unsigned long long *evaluated, cudaStream_t st)
+                     UnitResult *res, int *work_counter, unsigned long long *evaluated, const FusedArgs &fa,
+                     cudaStream_t st)
 {
 #define HGM_RECURSE(KM_, NT_, CT_, NP_)                                                                           \
-    return launch_recurse_t<KM_, NT_, CT_, NP_, kCount>(units, n_units, models, scenes, p, cand_idx, cand_u,    \
-                                                        cand_cnt, beta, res, work_counter, evaluated, st)
+    return launch_recurse_t<KM_, NT_, CT_, NP_, kCount, kFused>(units, n_units, models, scenes, p, cand_idx,    \
+                                                                cand_u, cand_cnt, beta, res, work_counter,      \
+                                                                evaluated, fa, st)
     if (p.K <= 32) {
         if (variant == 1) HGM_RECURSE(32, 128, 8, 2);
         if (variant == 2) HGM_RECURSE(32, 128, 4, 1);
@@ -563,8 +591,33 @@ cudaError_t launch_recurse(const Unit *units, int64_t n_units, const ModelRec *m
     if (n_units <= 0) return cudaSuccess;
     if (p.K <= 16)   // short lists (pruned form): one warp per unit
         return launch_recurse_small(units, n_units, models, scenes, p, cand_idx, cand_u, cand_cnt, beta, res, st);
-    return dispatch<false>(g_variant, units, n_units, models, scenes, p, cand_idx, cand_u, cand_cnt, beta, res,
-                           work_counter, nullptr, st);
+    return dispatch<false, false>(g_variant, units, n_units, models, scenes, p, cand_idx, cand_u, cand_cnt, beta,
+                                  res, work_counter, nullptr, FusedArgs{}, st);
+}
+
+int64_t recurse_fused_scratch(int K, int max_M)
+{
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) !=
+                                                  cudaSuccess)
+        return -1;
+    const int64_t per = ((int64_t)std::max(max_M - 2, 1) * K * K + 255) / 256 * 256;
+    return (int64_t)sms * kFusedPerSm * per;
+}
+
+cudaError_t launch_recurse_fused(const Unit *units, int64_t n_max, const int *n_dev, const ModelRec *models,
+                                 const SceneRec *scenes, Params p, const int32_t *cand_idx, const float *cand_u,
+                                 const int32_t *cand_cnt, uint8_t *scratch, int max_M, float *energy,
+                                 int32_t *assign, int *work_counter, cudaStream_t st)
+{
+    if (n_max <= 0) return cudaSuccess;
+    FusedArgs fa;
+    fa.n_dev = n_dev;
+    fa.beta_cta = ((int64_t)std::max(max_M - 2, 1) * p.K * p.K + 255) / 256 * 256;
+    fa.energy = energy;
+    fa.assign = assign;
+    return dispatch<false, true>(0, units, n_max, models, scenes, p, cand_idx, cand_u, cand_cnt, scratch, nullptr,
+                                 work_counter, nullptr, fa, st);
 }
 
 cudaError_t launch_recurse_count(const Unit *units, int64_t n_units, const ModelRec *models, const SceneRec *scenes,
@@ -573,8 +626,8 @@ cudaError_t launch_recurse_count(const Unit *units, int64_t n_units, const Model
                                  cudaStream_t st)
 {
     if (n_units <= 0) return cudaSuccess;
-    return dispatch<true>(g_variant, units, n_units, models, scenes, p, cand_idx, cand_u, cand_cnt, beta, res,
-                          work_counter, evaluated, st);
+    return dispatch<true, false>(g_variant, units, n_units, models, scenes, p, cand_idx, cand_u, cand_cnt, beta,
+                                 res, work_counter, evaluated, FusedArgs{}, st);
 }
 
 }  // namespace hgm
