@@ -166,6 +166,24 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def _time_plan(torch, hgm, models, scenes, p, energy, assign, steps, warmup, stream, flush):
+    """The same batch as one CUDA-graph replay per step (hgm_plan): ms per step, CUDA events on the stream."""
+    plan = hgm.Plan(models, scenes, p, energy, assign, stream=stream)
+    for _ in range(warmup):
+        plan.run(stream)
+    plan.check(stream)
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    for k in range(steps):
+        flush.zero_()
+        starts[k].record(stream)
+        plan.run(stream)
+        ends[k].record(stream)
+    plan.check(stream)
+    plan.close()
+    return sum(a.elapsed_time(b) for a, b in zip(starts, ends)) / steps
+
+
 def _time_form(torch, hgm, models, scenes, p, energy, assign, steps, warmup, stream, flush):
     for _ in range(warmup):
         hgm.match_batch(models, scenes, p, energy, assign)
@@ -207,6 +225,9 @@ def run_pruned(args, torch, hgm, wl, models, scenes, energy, assign, es, as_, de
     ms, prof = _time_form(torch, hgm, models, scenes, p, e2, a2, args.steps, args.warmup, stream, flush)
     torch.cuda.profiler.stop()
     n_pruned, n_fb = hgm.prune_counters(reset=True)
+    g_ms = None if args.no_graph else _time_plan(torch, hgm, models, scenes, p, e2, a2, args.steps, args.warmup,
+                                                  stream, flush)
+    hgm.prune_counters(reset=True)
     blocks = []
     for mi, m in enumerate(wl.models):
         for si in range(len(wl.scenes)):
@@ -226,6 +247,7 @@ def run_pruned(args, torch, hgm, wl, models, scenes, energy, assign, es, as_, de
     frames = wl.total_frames * world
     return {"value": frames / (ms / 1e3), "unit": "frames/s", "ms_per_step": ms,
             "kernel_ms_per_step": {k: v[0] / args.steps for k, v in prof.items()},
+            "graph": None if g_ms is None else {"value": frames / (g_ms / 1e3), "unit": "frames/s", "ms_per_step": g_ms},
             "keep": 8, "K": wl.K, "precision": "BF16 unary + FP32 re-score of kept candidates",
             "fallback_units_per_step": n_fb / max(1, args.steps + args.warmup),
             "units_per_step": n_pruned / max(1, args.steps + args.warmup), **quality,
@@ -245,6 +267,7 @@ def main():
     ap.add_argument("--cpu-units", type=int, default=48)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-graph", action="store_true", help="skip the CUDA-graph replay lines")
     ap.add_argument("--no-pruned", action="store_true", help="skip the pruned+BF16 form")
     ap.add_argument("--train-steps", type=int, default=2000)
     ap.add_argument("--checkpoint", default=None, help="load the proposal network from <path>.bin/.json")
@@ -362,6 +385,13 @@ def main():
         e2e = {"value": frames_all / e2e_sec if world == 1 else wl.total_frames * world / e2e_sec,
                "unit": "frames/s", "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
 
+    # the same exact batch replayed as a CUDA graph (hgm_plan)
+    graph = None
+    if not args.no_graph:
+        g_ms = _time_plan(torch, hgm, models, scenes, p, energy, assign, args.steps, args.warmup, stream, flush)
+        graph = {"value": frames_all / (g_ms / 1e3), "unit": "frames/s", "ms_per_step": g_ms,
+                 "form": "plain exact FP32, one graph launch per step"}
+
     pk, pk_kind = peaks()
     sm_count = torch.cuda.get_device_properties(dev).multi_processor_count or SM_COUNT_FALLBACK
     clk_sum = clk.summary()
@@ -408,7 +438,7 @@ def main():
                            "form": "plain exact FP32", "l2": "flushed (512 MiB write) before every step",
                            "recurse_variant": variant, "autotune_ms": variant_ms,
                            "parallelism": f"replicas x{world}"},
-                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "graph": graph, "gpu_launches": launches,
                 "clocks": clk_sum, "finite_offsets": int(fin), "pruned_bf16": pruned}
         print(json.dumps(line), flush=True)
     if dist:

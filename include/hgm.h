@@ -60,6 +60,7 @@ extern "C" {
 typedef struct hgm_model hgm_model;
 typedef struct hgm_scene hgm_scene;
 typedef struct hgm_prop hgm_prop;
+typedef struct hgm_plan hgm_plan;
 
 typedef enum {
     HGM_OK = 0,
@@ -111,7 +112,8 @@ HGM_API hgm_status hgm_create_model(const float *xy, const int32_t *t, const flo
 HGM_API hgm_status hgm_create_scene(const float *xy, const int32_t *t, const float *desc, int32_t S, int32_t F,
                             int32_t n_frames, void *stream, hgm_scene **out);
 
-/* Releases a model or scene handle and its device memory. NULL is a no-op.
+/* Releases a model, scene, proposal-network or plan handle and its device
+ * memory. NULL is a no-op.
  * Work on the handle must be complete (or ordered before on the stream the
  * handle was used on) -- the call synchronises the device first. */
 HGM_API void hgm_destroy(void *handle);
@@ -156,6 +158,36 @@ HGM_API hgm_status hgm_batch_layout(const hgm_model *const *models, int32_t n_mo
 HGM_API hgm_status hgm_match_batch(const hgm_model *const *models, int32_t n_models, const hgm_scene *const *scenes,
                            int32_t n_scenes, const hgm_params *params, void *stream, float *energy,
                            int32_t *assign);
+
+/* Completion: hgm_match and hgm_match_batch return once their work is queued
+ * on `stream` when both outputs are device pointers and no tensor-core kernel
+ * runs (precision 0, no pruning); with a host output, precision 1 or pruning
+ * they return after the work has finished, so that HGM_ETIMEOUT (a bounded
+ * tensor-core wait gave up) can be reported. */
+
+/* Plans (the batch driver's replay form; the paper's one-launch-per-step
+ * OpenCL driver has no counterpart): the work of hgm_match_batch for fixed
+ * models, scenes, params and device outputs is laid out once -- segment
+ * groups, unit lists in decreasing model size, workspace -- and recorded as a
+ * CUDA graph that hgm_plan_run replays with a single launch.
+ * hgm_plan_create runs the batch once (sizing pass; results are written) and
+ * records a second pass without executing it. energy / assign must be device
+ * pointers (or NULL) in the hgm_batch_layout order. The model, scene and
+ * proposal-network handles and the outputs must outlive the plan: the graph
+ * holds their device addresses (their contents, e.g. retrained weights, may
+ * change between runs). The plan owns its workspace, so plans and ordinary
+ * calls do not share buffers. Release with hgm_destroy.
+ * HGM_EINVAL: bad arrays, params or host outputs. */
+HGM_API hgm_status hgm_plan_create(const hgm_model *const *models, int32_t n_models, const hgm_scene *const *scenes,
+                                   int32_t n_scenes, const hgm_params *params, float *energy, int32_t *assign,
+                                   void *stream, hgm_plan **out);
+
+/* Replays the plan on `stream` (asynchronous: one graph launch). */
+HGM_API hgm_status hgm_plan_run(hgm_plan *plan, void *stream);
+
+/* Waits for `stream` and reports HGM_ETIMEOUT if a bounded tensor-core wait
+ * gave up in a replay since the last run was issued. */
+HGM_API hgm_status hgm_plan_check(hgm_plan *plan, void *stream);
 
 /* ---- learned candidate proposal ---------------------------------------------- */
 

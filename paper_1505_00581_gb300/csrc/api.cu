@@ -118,12 +118,19 @@ cudaEvent_t prof_event()
 }
 
 // ---- workspace ------------------------------------------------------------------
+bool g_capturing = false;   // a plan's launch sequence is being recorded: no allocation, no events
+
 struct Buffer {
     void *p = nullptr;
     size_t bytes = 0;
+    Buffer() = default;
+    Buffer(const Buffer &) = delete;
+    Buffer &operator=(const Buffer &) = delete;
+    ~Buffer() { if (p) cudaFree(p); }
     cudaError_t ensure(size_t need)
     {
         if (need <= bytes) return cudaSuccess;
+        if (g_capturing) return cudaErrorStreamCaptureUnsupported;   // sizes were fixed by the sizing pass
         if (p) cudaFree(p);
         p = nullptr;
         bytes = 0;
@@ -147,6 +154,38 @@ Workspace g_ws;
 bool g_count_mode = false;   // hgm_profile_enable(2): batch runs use the accounting recursion variant
 size_t g_budget_override = 0;   // hgm_set_workspace_budget: bytes for the unary table and for a chunk (0 = auto)
 int64_t g_pruned_units = 0;
+
+// How run_batch issues its work: on the shared workspace (ordinary calls), or for a plan on the plan's own
+// workspace, first as a sizing pass (grows the workspace, keeps a pinned copy of every host upload) and then
+// as the recorded pass (no allocation, no host synchronisation, uploads from those pinned copies).
+struct Exec {
+    enum Mode { kNormal, kSizing, kCapture } mode = kNormal;
+    Workspace *ws = &g_ws;
+    size_t budget = 0;                                    // workspace budget fixed by the sizing pass
+    std::vector<std::pair<void *, size_t>> *pinned = nullptr;
+    size_t pin_next = 0;
+    int64_t pruned_units = 0;                             // units of the pruned pass issued
+    bool tensor = false;                                  // a tensor-core kernel ran (status flag is live)
+};
+
+hgm_status h2d(Exec &ex, void *dst, const void *src, size_t bytes, cudaStream_t st)
+{
+    if (!bytes) return HGM_OK;
+    if (ex.mode == Exec::kSizing) {
+        void *h = nullptr;
+        CK(cudaMallocHost(&h, bytes), "pinned staging");
+        ex.pinned->emplace_back(h, bytes);
+    }
+    if (ex.mode != Exec::kNormal) {
+        if (ex.pin_next >= ex.pinned->size() || (*ex.pinned)[ex.pin_next].second != bytes)
+            return fail(HGM_ECUDA, "plan: upload sequence differs between the sizing and the recorded pass");
+        void *h = (*ex.pinned)[ex.pin_next++].first;
+        std::memcpy(h, src, bytes);
+        src = h;
+    }
+    CK(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, st), "upload");
+    return HGM_OK;
+}
 
 // dst[k][c] = src[perm[k]][c] for c < F, 0 for F <= c < Fp; flags a non-finite component.
 __global__ void gather_rows_kernel(const float *__restrict__ src, int F, const int32_t *__restrict__ perm, int64_t n,
@@ -204,7 +243,7 @@ hgm_status upload_sorted_rows(const float *src, int64_t n, int F, int Fp, const 
 // Profiling hooks used by the kernel launchers.
 void prof_begin(int kernel, cudaStream_t st)
 {
-    if (!g_prof_on) return;
+    if (!g_prof_on || g_capturing) return;
     std::lock_guard<std::mutex> lk(g_prof_mu);
     ProfRec r{kernel, prof_event(), prof_event()};
     if (!r.a || !r.b) return;
@@ -215,7 +254,7 @@ void prof_begin(int kernel, cudaStream_t st)
 
 void prof_end(int kernel, cudaStream_t st)
 {
-    if (!g_prof_on) return;
+    if (!g_prof_on || g_capturing) return;
     std::lock_guard<std::mutex> lk(g_prof_mu);
     if (!g_prof_is_open[kernel]) return;
     ProfRec r = g_prof_open[kernel];
@@ -352,11 +391,13 @@ hgm_status build_plan(const hgm_model *const *models, int nm, const hgm_scene *c
 
 // Runs a list of units (one segment group): chunks bounded by the budget for candidate lists and
 // argmin tables; per chunk selection -> (pruning ->) recursion -> backtrack (-> fallback).
-hgm_status run_units(const hgm_model *const *models, std::vector<Unit> &all, int max_M, int K, int keep, bool pruning,
-                     const Params &p, const PropInfer &pi, cudaStream_t st, float *d_energy, int32_t *d_assign,
-                     size_t budget)
+hgm_status run_units(Exec &ex, const hgm_model *const *models, std::vector<Unit> &all, int max_M, int K, int keep,
+                     bool pruning, const Params &p, const PropInfer &pi, cudaStream_t st, float *d_energy,
+                     int32_t *d_assign, size_t budget)
 {
+    Workspace &ws = *ex.ws;
     const int64_t n_units = (int64_t)all.size();
+    hgm_status rc;
     int64_t begin = 0;
     while (begin < n_units) {
         int64_t cand_e = 0, beta_b = 0, end = begin;
@@ -374,78 +415,77 @@ hgm_status run_units(const hgm_model *const *models, std::vector<Unit> &all, int
             ++end;
         }
         const int64_t n = end - begin;
-        CK(g_ws.cand_idx.ensure((size_t)cand_e * sizeof(int32_t)), "workspace (candidates)");
-        CK(g_ws.cand_u.ensure((size_t)cand_e * sizeof(float)), "workspace (candidates)");
-        CK(g_ws.cand_cnt.ensure((size_t)(cand_e / K) * sizeof(int32_t)), "workspace (candidates)");
-        if (!pruning) CK(g_ws.beta.ensure((size_t)beta_b), "workspace (argmin tables)");
-        CK(g_ws.units.ensure((size_t)n * sizeof(Unit)), "workspace (units)");
-        CK(g_ws.res.ensure((size_t)n * sizeof(UnitResult)), "workspace (results)");
-        CK(g_ws.counter.ensure(sizeof(int)), "workspace");
-        CK(cudaMemcpyAsync(g_ws.units.p, all.data() + begin, (size_t)n * sizeof(Unit), cudaMemcpyHostToDevice, st),
-           "upload units");
-        const Unit *du = g_ws.units.as<Unit>();
-        const ModelRec *dm = g_ws.mrec.as<ModelRec>();
-        const SceneRec *ds = g_ws.srec.as<SceneRec>();
-        CK(launch_select(du, n, dm, ds, p, max_M, g_ws.cand_idx.as<int32_t>(), g_ws.cand_u.as<float>(),
-                         g_ws.cand_cnt.as<int32_t>(), st),
+        CK(ws.cand_idx.ensure((size_t)cand_e * sizeof(int32_t)), "workspace (candidates)");
+        CK(ws.cand_u.ensure((size_t)cand_e * sizeof(float)), "workspace (candidates)");
+        CK(ws.cand_cnt.ensure((size_t)(cand_e / K) * sizeof(int32_t)), "workspace (candidates)");
+        if (!pruning) CK(ws.beta.ensure((size_t)beta_b), "workspace (argmin tables)");
+        CK(ws.units.ensure((size_t)n * sizeof(Unit)), "workspace (units)");
+        CK(ws.res.ensure((size_t)n * sizeof(UnitResult)), "workspace (results)");
+        CK(ws.counter.ensure(sizeof(int)), "workspace");
+        if ((rc = h2d(ex, ws.units.p, all.data() + begin, (size_t)n * sizeof(Unit), st))) return rc;
+        const Unit *du = ws.units.as<Unit>();
+        const ModelRec *dm = ws.mrec.as<ModelRec>();
+        const SceneRec *ds = ws.srec.as<SceneRec>();
+        CK(launch_select(du, n, dm, ds, p, max_M, ws.cand_idx.as<int32_t>(), ws.cand_u.as<float>(),
+                         ws.cand_cnt.as<int32_t>(), st),
            "select kernel");
         if (pruning) {
             const int64_t n_lists = cand_e / K;
-            CK(g_ws.cand2_idx.ensure((size_t)n_lists * keep * sizeof(int32_t)), "workspace (pruned lists)");
-            CK(g_ws.cand2_u.ensure((size_t)n_lists * keep * sizeof(float)), "workspace (pruned lists)");
-            CK(g_ws.cand2_cnt.ensure((size_t)n_lists * sizeof(int32_t)), "workspace (pruned lists)");
-            CK(g_ws.units2.ensure((size_t)n * sizeof(Unit)), "workspace (units)");
-            CK(g_ws.beta2.ensure((size_t)(beta_b / ((int64_t)K * K) * keep * keep) + 1), "workspace (argmin tables)");
-            CK(g_ws.scores.ensure((size_t)cand_e * sizeof(float)), "workspace (scores)");
-            CK(launch_prop_prune(du, n, dm, ds, p, pi, g_ws.cand_idx.as<int32_t>(), g_ws.cand_u.as<float>(),
-                                 g_ws.cand_cnt.as<int32_t>(), g_ws.scores.as<float>(), g_ws.cand2_idx.as<int32_t>(),
-                                 g_ws.cand2_u.as<float>(), g_ws.cand2_cnt.as<int32_t>(), g_ws.status.as<int>(), st),
+            CK(ws.cand2_idx.ensure((size_t)n_lists * keep * sizeof(int32_t)), "workspace (pruned lists)");
+            CK(ws.cand2_u.ensure((size_t)n_lists * keep * sizeof(float)), "workspace (pruned lists)");
+            CK(ws.cand2_cnt.ensure((size_t)n_lists * sizeof(int32_t)), "workspace (pruned lists)");
+            CK(ws.units2.ensure((size_t)n * sizeof(Unit)), "workspace (units)");
+            CK(ws.beta2.ensure((size_t)(beta_b / ((int64_t)K * K) * keep * keep) + 1), "workspace (argmin tables)");
+            CK(ws.scores.ensure((size_t)cand_e * sizeof(float)), "workspace (scores)");
+            CK(launch_prop_prune(du, n, dm, ds, p, pi, ws.cand_idx.as<int32_t>(), ws.cand_u.as<float>(),
+                                 ws.cand_cnt.as<int32_t>(), ws.scores.as<float>(), ws.cand2_idx.as<int32_t>(),
+                                 ws.cand2_u.as<float>(), ws.cand2_cnt.as<int32_t>(), ws.status.as<int>(), st),
                "pruning kernels");
-            CK(launch_derive_units(du, n, K, keep, g_ws.units2.as<Unit>(), st), "derive units");
+            CK(launch_derive_units(du, n, K, keep, ws.units2.as<Unit>(), st), "derive units");
             Params pk = p;
             pk.K = keep;
             pk.rescore = 0;
-            const Unit *du2 = g_ws.units2.as<Unit>();
-            CK(launch_recurse(du2, n, dm, ds, pk, g_ws.cand2_idx.as<int32_t>(), g_ws.cand2_u.as<float>(),
-                              g_ws.cand2_cnt.as<int32_t>(), g_ws.beta2.as<uint8_t>(), g_ws.res.as<UnitResult>(),
-                              g_ws.counter.as<int>(), st),
+            const Unit *du2 = ws.units2.as<Unit>();
+            CK(launch_recurse(du2, n, dm, ds, pk, ws.cand2_idx.as<int32_t>(), ws.cand2_u.as<float>(),
+                              ws.cand2_cnt.as<int32_t>(), ws.beta2.as<uint8_t>(), ws.res.as<UnitResult>(),
+                              ws.counter.as<int>(), st),
                "recursion kernel (pruned lists)");
-            CK(launch_backtrack(du2, n, dm, ds, pk, g_ws.cand2_idx.as<int32_t>(), g_ws.beta2.as<uint8_t>(),
-                                g_ws.res.as<UnitResult>(), d_energy, d_assign, st),
+            CK(launch_backtrack(du2, n, dm, ds, pk, ws.cand2_idx.as<int32_t>(), ws.beta2.as<uint8_t>(),
+                                ws.res.as<UnitResult>(), d_energy, d_assign, st),
                "backtrack kernel (pruned lists)");
             // fallback: units whose pruned optimum is infeasible are solved again on the full lists, by the
             // fused recursion + backtrack reading their number on the device (no host round trip)
-            CK(g_ws.fb_units.ensure((size_t)n * sizeof(Unit)), "workspace (fallback)");
-            CK(g_ws.fb_count.ensure(sizeof(int)), "workspace");
-            CK(cudaMemsetAsync(g_ws.fb_count.p, 0, sizeof(int), st), "memset");
-            CK(launch_collect_infeasible(g_ws.res.as<UnitResult>(), du, n, g_ws.fb_units.as<Unit>(),
-                                         g_ws.fb_count.as<int>(), g_ws.fb_total.as<unsigned long long>(), st),
+            CK(ws.fb_units.ensure((size_t)n * sizeof(Unit)), "workspace (fallback)");
+            CK(ws.fb_count.ensure(sizeof(int)), "workspace");
+            CK(cudaMemsetAsync(ws.fb_count.p, 0, sizeof(int), st), "memset");
+            CK(launch_collect_infeasible(ws.res.as<UnitResult>(), du, n, ws.fb_units.as<Unit>(),
+                                         ws.fb_count.as<int>(), g_ws.fb_total.as<unsigned long long>(), st),
                "collect infeasible");
             const int64_t scratch = recurse_fused_scratch(K, max_M);
             if (scratch < 0) return fail(HGM_ECUDA, "device query failed");
-            CK(g_ws.beta_fb.ensure((size_t)scratch), "workspace (fallback)");
-            CK(launch_recurse_fused(g_ws.fb_units.as<Unit>(), n, g_ws.fb_count.as<int>(), dm, ds, p,
-                                    g_ws.cand_idx.as<int32_t>(), g_ws.cand_u.as<float>(), g_ws.cand_cnt.as<int32_t>(),
-                                    g_ws.beta_fb.as<uint8_t>(), max_M, d_energy, d_assign, g_ws.counter.as<int>(), st),
+            CK(ws.beta_fb.ensure((size_t)scratch), "workspace (fallback)");
+            CK(launch_recurse_fused(ws.fb_units.as<Unit>(), n, ws.fb_count.as<int>(), dm, ds, p,
+                                    ws.cand_idx.as<int32_t>(), ws.cand_u.as<float>(), ws.cand_cnt.as<int32_t>(),
+                                    ws.beta_fb.as<uint8_t>(), max_M, d_energy, d_assign, ws.counter.as<int>(), st),
                "recursion kernel (fallback)");
-            g_pruned_units += n;
+            ex.pruned_units += n;
             begin = end;
             continue;
         }
-        if (g_count_mode) {
-            CK(g_ws.evaluated.ensure(sizeof(unsigned long long)), "workspace");
-            CK(launch_recurse_count(du, n, dm, ds, p, g_ws.cand_idx.as<int32_t>(), g_ws.cand_u.as<float>(),
-                                    g_ws.cand_cnt.as<int32_t>(), g_ws.beta.as<uint8_t>(), g_ws.res.as<UnitResult>(),
-                                    g_ws.counter.as<int>(), g_ws.evaluated.as<unsigned long long>(), st),
+        if (g_count_mode && ex.mode == Exec::kNormal) {
+            CK(ws.evaluated.ensure(sizeof(unsigned long long)), "workspace");
+            CK(launch_recurse_count(du, n, dm, ds, p, ws.cand_idx.as<int32_t>(), ws.cand_u.as<float>(),
+                                    ws.cand_cnt.as<int32_t>(), ws.beta.as<uint8_t>(), ws.res.as<UnitResult>(),
+                                    ws.counter.as<int>(), ws.evaluated.as<unsigned long long>(), st),
                "recursion kernel (accounting)");
         } else {
-            CK(launch_recurse(du, n, dm, ds, p, g_ws.cand_idx.as<int32_t>(), g_ws.cand_u.as<float>(),
-                              g_ws.cand_cnt.as<int32_t>(), g_ws.beta.as<uint8_t>(), g_ws.res.as<UnitResult>(),
-                              g_ws.counter.as<int>(), st),
+            CK(launch_recurse(du, n, dm, ds, p, ws.cand_idx.as<int32_t>(), ws.cand_u.as<float>(),
+                              ws.cand_cnt.as<int32_t>(), ws.beta.as<uint8_t>(), ws.res.as<UnitResult>(),
+                              ws.counter.as<int>(), st),
                "recursion kernel");
         }
-        CK(launch_backtrack(du, n, dm, ds, p, g_ws.cand_idx.as<int32_t>(), g_ws.beta.as<uint8_t>(),
-                            g_ws.res.as<UnitResult>(), d_energy, d_assign, st),
+        CK(launch_backtrack(du, n, dm, ds, p, ws.cand_idx.as<int32_t>(), ws.beta.as<uint8_t>(),
+                            ws.res.as<UnitResult>(), d_energy, d_assign, st),
            "backtrack kernel");
         begin = end;
     }
@@ -460,9 +500,10 @@ struct Segment {
     int64_t j0, j1;
 };
 
-hgm_status run_batch(const hgm_model *const *models, int nm, const hgm_scene *const *scenes, int ns,
+hgm_status run_batch(Exec &ex, const hgm_model *const *models, int nm, const hgm_scene *const *scenes, int ns,
                      const hgm_params *hp, cudaStream_t st, float *energy, int32_t *assign)
 {
+    Workspace &ws = *ex.ws;
     hgm_status rc = check_params(hp);
     if (rc) return rc;
     Plan pl;
@@ -486,19 +527,19 @@ hgm_status run_batch(const hgm_model *const *models, int nm, const hgm_scene *co
         tmin_all = std::min(tmin_all, models[m]->t_sorted.front());
         tmax_all = std::max(tmax_all, models[m]->t_sorted.back());
     }
-    CK(g_ws.modelcat.ensure((size_t)R * F * sizeof(float)), "workspace (models)");
+    CK(ws.modelcat.ensure((size_t)R * F * sizeof(float)), "workspace (models)");
     for (int m = 0; m < nm; ++m)
-        CK(cudaMemcpyAsync(g_ws.modelcat.as<float>() + (size_t)urow[m] * F, models[m]->d.f,
+        CK(cudaMemcpyAsync(ws.modelcat.as<float>() + (size_t)urow[m] * F, models[m]->d.f,
                            (size_t)models[m]->d.M * F * sizeof(float), cudaMemcpyDeviceToDevice, st),
            "gather model descriptors");
     std::vector<ModelRec> mrec(nm);
     for (int m = 0; m < nm; ++m)
         mrec[m] = ModelRec{models[m]->d.xy, models[m]->d.t, models[m]->d.perm, models[m]->d.M, urow[m],
                            models[m]->d.f, models[m]->d.geo};
-    CK(g_ws.mrec.ensure(nm * sizeof(ModelRec)), "workspace");
-    CK(cudaMemcpyAsync(g_ws.mrec.p, mrec.data(), nm * sizeof(ModelRec), cudaMemcpyHostToDevice, st), "upload");
-    CK(g_ws.status.ensure(sizeof(int)), "workspace");
-    CK(cudaMemsetAsync(g_ws.status.p, 0, sizeof(int), st), "memset");
+    CK(ws.mrec.ensure(nm * sizeof(ModelRec)), "workspace");
+    if ((rc = h2d(ex, ws.mrec.p, mrec.data(), nm * sizeof(ModelRec), st))) return rc;
+    CK(ws.status.ensure(sizeof(int)), "workspace");
+    CK(cudaMemsetAsync(ws.status.p, 0, sizeof(int), st), "memset");
 
     // proposal network: first-layer projections of the model points (the scene points' per segment)
     const hgm_prop *prop = hp->prune;
@@ -510,20 +551,20 @@ hgm_status run_batch(const hgm_model *const *models, int nm, const hgm_scene *co
         if (prop->L.F != Fu) return fail(HGM_EINVAL, "proposal network built for F = %d, descriptors have F = %d",
                                          prop->L.F, Fu);
         const float *th = prop->theta;
-        CK(g_ws.P.ensure((size_t)R * kPropHidden * sizeof(float)), "workspace (projections)");
-        CK(launch_rowdot_plain(g_ws.modelcat.as<float>(), R, F, th + prop->L.o_W1, kPropHidden, prop->L.dp, Fu,
-                               th + prop->L.o_b1, g_ws.P.as<float>(), kPropHidden, g_ws.status.as<int>(), st),
+        CK(ws.P.ensure((size_t)R * kPropHidden * sizeof(float)), "workspace (projections)");
+        CK(launch_rowdot_plain(ws.modelcat.as<float>(), R, F, th + prop->L.o_W1, kPropHidden, prop->L.dp, Fu,
+                               th + prop->L.o_b1, ws.P.as<float>(), kPropHidden, ws.status.as<int>(), st),
            "projection kernel");
         // position terms of the model points folded into P (the scene points' into Q)
-        CK(g_ws.modelxy.ensure((size_t)R * 2 * sizeof(float)), "workspace (models)");
+        CK(ws.modelxy.ensure((size_t)R * 2 * sizeof(float)), "workspace (models)");
         for (int m = 0; m < nm; ++m)
-            CK(cudaMemcpyAsync(g_ws.modelxy.as<float>() + (size_t)urow[m] * 2, models[m]->d.xy,
+            CK(cudaMemcpyAsync(ws.modelxy.as<float>() + (size_t)urow[m] * 2, models[m]->d.xy,
                                (size_t)models[m]->d.M * 2 * sizeof(float), cudaMemcpyDeviceToDevice, st),
                "gather model positions");
-        CK(launch_prop_fold_xy(g_ws.P.as<float>(), R, g_ws.modelxy.as<float>(), th + prop->L.o_W1 + 2 * Fu,
+        CK(launch_prop_fold_xy(ws.P.as<float>(), R, ws.modelxy.as<float>(), th + prop->L.o_W1 + 2 * Fu,
                                prop->L.dp, -1.0f, st),
            "projection kernel");
-        pi.P = g_ws.P.as<float>();
+        pi.P = ws.P.as<float>();
         pi.W2 = th + prop->L.o_W2;
         pi.b2 = th + prop->L.o_b2;
         pi.w3 = th + prop->L.o_w3;
@@ -535,13 +576,15 @@ hgm_status run_batch(const hgm_model *const *models, int nm, const hgm_scene *co
         pi.rescore = hp->precision == 1 ? 1 : 0;
         p.rescore = 0;   // the kept candidates are re-scored by the pruning kernel instead
         if (!g_ws.fb_total.p) {
+            if (ex.mode == Exec::kCapture) return fail(HGM_ECUDA, "plan: fallback counter missing");
             CK(g_ws.fb_total.ensure(sizeof(unsigned long long)), "workspace");
             CK(cudaMemsetAsync(g_ws.fb_total.p, 0, sizeof(unsigned long long), st), "memset");
         }
     }
+    ex.tensor = pruning || hp->precision == 1;
     if (hp->precision == 1) {
-        CK(g_ws.mnorm.ensure((size_t)R * sizeof(float)), "workspace (norms)");
-        CK(launch_sqnorm_bf16(g_ws.modelcat.as<float>(), R, F, F, g_ws.mnorm.as<float>(), st), "norm kernel");
+        CK(ws.mnorm.ensure((size_t)R * sizeof(float)), "workspace (norms)");
+        CK(launch_sqnorm_bf16(ws.modelcat.as<float>(), R, F, F, ws.mnorm.as<float>(), st), "norm kernel");
     }
 
     // outputs: device pointers are written in place, host ones through staging
@@ -552,24 +595,27 @@ hgm_status run_batch(const hgm_model *const *models, int nm, const hgm_scene *co
     if (energy) {
         if (e_dev) d_energy = energy;
         else {
-            CK(g_ws.out_e.ensure((size_t)n_out * sizeof(float)), "workspace (energy)");
-            d_energy = g_ws.out_e.as<float>();
+            CK(ws.out_e.ensure((size_t)n_out * sizeof(float)), "workspace (energy)");
+            d_energy = ws.out_e.as<float>();
         }
     }
     if (assign) {
         if (a_dev) d_assign = assign;
         else {
-            CK(g_ws.out_a.ensure((size_t)n_assign * sizeof(int32_t)), "workspace (assign)");
-            d_assign = g_ws.out_a.as<int32_t>();
+            CK(ws.out_a.ensure((size_t)n_assign * sizeof(int32_t)), "workspace (assign)");
+            d_assign = ws.out_a.as<int32_t>();
         }
     }
 
     // budgets: unary table (+ projections) per segment group, and candidate lists + argmin tables per chunk
-    size_t free_b = 0, total_b = 0;
-    CK(cudaMemGetInfo(&free_b, &total_b), "cudaMemGetInfo");
-    const size_t budget = g_budget_override ? g_budget_override
-                                            : std::max<size_t>((size_t)256 << 20,
-                                                               std::min<size_t>((size_t)24 << 30, free_b / 3));
+    size_t budget = ex.budget;
+    if (ex.mode != Exec::kCapture) {
+        size_t free_b = 0, total_b = 0;
+        CK(cudaMemGetInfo(&free_b, &total_b), "cudaMemGetInfo");
+        budget = g_budget_override ? g_budget_override
+                                   : std::max<size_t>((size_t)256 << 20, std::min<size_t>((size_t)24 << 30, free_b / 3));
+        ex.budget = budget;
+    }
     const int64_t per_point = (int64_t)R * 4 + (pruning ? (int64_t)kPropHidden * 4 : 0);
     const int64_t max_points = std::max<int64_t>(1, (int64_t)budget / per_point);
 
@@ -612,26 +658,25 @@ hgm_status run_batch(const hgm_model *const *models, int nm, const hgm_scene *co
             ++gend;
         }
         const int ng = (int)(gend - gbegin);
-        CK(g_ws.U.ensure((size_t)R * gpoints * sizeof(float)), "workspace (unary table)");
-        if (pruning) CK(g_ws.Q.ensure((size_t)gpoints * kPropHidden * sizeof(float)), "workspace (projections)");
+        CK(ws.U.ensure((size_t)R * gpoints * sizeof(float)), "workspace (unary table)");
+        if (pruning) CK(ws.Q.ensure((size_t)gpoints * kPropHidden * sizeof(float)), "workspace (projections)");
         std::vector<SceneRec> srec((size_t)ng);
         int64_t off = 0, smax = 0;
         for (int g = 0; g < ng; ++g) {
             const Segment &sg = segs[gbegin + g];
             const SceneDev &d = scenes[sg.s]->d;
             const int64_t pts = sg.j1 - sg.j0, pitch = round_up4((int)std::max<int64_t>(pts, 1));
-            SceneRec r{d.xy, d.t, d.frame_start, d.perm, g_ws.U.as<float>() + (size_t)R * off, pitch, d.S, d.n_frames,
+            SceneRec r{d.xy, d.t, d.frame_start, d.perm, ws.U.as<float>() + (size_t)R * off, pitch, d.S, d.n_frames,
                        d.f};
             r.ucol0 = sg.j0;
-            if (pruning) r.pq = g_ws.Q.as<float>() + (size_t)off * kPropHidden;
+            if (pruning) r.pq = ws.Q.as<float>() + (size_t)off * kPropHidden;
             srec[(size_t)g] = r;
             off += pitch;
             smax = std::max(smax, pts);
         }
-        CK(g_ws.srec.ensure((size_t)ng * sizeof(SceneRec)), "workspace");
-        CK(cudaMemcpyAsync(g_ws.srec.p, srec.data(), (size_t)ng * sizeof(SceneRec), cudaMemcpyHostToDevice, st),
-           "upload");
-        if (hp->precision == 1) CK(g_ws.snorm.ensure((size_t)std::max<int64_t>(smax, 1) * sizeof(float)), "workspace");
+        CK(ws.srec.ensure((size_t)ng * sizeof(SceneRec)), "workspace");
+        if ((rc = h2d(ex, ws.srec.p, srec.data(), (size_t)ng * sizeof(SceneRec), st))) return rc;
+        if (hp->precision == 1) CK(ws.snorm.ensure((size_t)std::max<int64_t>(smax, 1) * sizeof(float)), "workspace");
         for (int g = 0; g < ng; ++g) {
             const Segment &sg = segs[gbegin + g];
             const SceneDev &d = scenes[sg.s]->d;
@@ -639,20 +684,20 @@ hgm_status run_batch(const hgm_model *const *models, int nm, const hgm_scene *co
             const int pts = (int)(sg.j1 - sg.j0);
             float *U = const_cast<float *>(srec[(size_t)g].U);
             if (hp->precision == 1) {
-                CK(launch_sqnorm_bf16(segf, pts, F, F, g_ws.snorm.as<float>(), st), "norm kernel");
-                CK(launch_unary_bf16(g_ws.modelcat.as<float>(), R, segf, pts, F, F, g_ws.mnorm.as<float>(),
-                                     g_ws.snorm.as<float>(), p.lambda1, U, srec[(size_t)g].upitch,
-                                     g_ws.status.as<int>(), st),
+                CK(launch_sqnorm_bf16(segf, pts, F, F, ws.snorm.as<float>(), st), "norm kernel");
+                CK(launch_unary_bf16(ws.modelcat.as<float>(), R, segf, pts, F, F, ws.mnorm.as<float>(),
+                                     ws.snorm.as<float>(), p.lambda1, U, srec[(size_t)g].upitch,
+                                     ws.status.as<int>(), st),
                    "BF16 unary kernel");
             } else {
-                CK(launch_unary(g_ws.modelcat.as<float>(), R, segf, pts, F, p.lambda1, U, (int)srec[(size_t)g].upitch,
+                CK(launch_unary(ws.modelcat.as<float>(), R, segf, pts, F, p.lambda1, U, (int)srec[(size_t)g].upitch,
                                 st),
                    "unary kernel");
             }
             if (pruning) {
                 const float *th = prop->theta;
                 CK(launch_rowdot_plain(segf, pts, F, th + prop->L.o_W1 + Fu, kPropHidden, prop->L.dp, Fu, nullptr,
-                                       const_cast<float *>(srec[(size_t)g].pq), kPropHidden, g_ws.status.as<int>(),
+                                       const_cast<float *>(srec[(size_t)g].pq), kPropHidden, ws.status.as<int>(),
                                        st),
                    "projection kernel");
                 CK(launch_prop_fold_xy(const_cast<float *>(srec[(size_t)g].pq), pts,
@@ -699,7 +744,7 @@ hgm_status run_batch(const hgm_model *const *models, int nm, const hgm_scene *co
                     all[(size_t)w++] = u;
                 }
             }
-        rc = run_units(models, all, max_M, K, keep, pruning, p, pi, st, d_energy, d_assign, budget);
+        rc = run_units(ex, models, all, max_M, K, keep, pruning, p, pi, st, d_energy, d_assign, budget);
         if (rc) return rc;
         gbegin = gend;
     }
@@ -708,8 +753,16 @@ hgm_status run_batch(const hgm_model *const *models, int nm, const hgm_scene *co
     if (assign && !a_dev)
         CK(cudaMemcpyAsync(assign, d_assign, (size_t)n_assign * sizeof(int32_t), cudaMemcpyDeviceToHost, st),
            "assign D2H");
-    if ((energy && !e_dev) || (assign && !a_dev)) CK(cudaStreamSynchronize(st), "synchronise outputs");
-    else CK(cudaGetLastError(), "launch");
+    if (ex.mode == Exec::kCapture) return HGM_OK;
+    // host outputs, or a tensor-core kernel whose bounded waits report through the status flag: wait here
+    if ((energy && !e_dev) || (assign && !a_dev) || ex.tensor) {
+        int status = 0;
+        if (ex.tensor) CK(cudaMemcpyAsync(&status, ws.status.p, sizeof(int), cudaMemcpyDeviceToHost, st), "status");
+        CK(cudaStreamSynchronize(st), "synchronise outputs");
+        if (status) return fail(HGM_ETIMEOUT, "a bounded tensor-core wait gave up");
+    } else {
+        CK(cudaGetLastError(), "launch");
+    }
     return HGM_OK;
 }
 
@@ -795,6 +848,29 @@ void hgm_default_params(hgm_params *p)
 }
 
 const char *hgm_last_error(void) { return g_err.c_str(); }
+
+// ---- plans: a batch laid out once and replayed as a CUDA graph ---------------------------------------------
+struct hgm_plan {
+    uint32_t magic;
+    Workspace ws;
+    std::vector<std::pair<void *, size_t>> pinned;   // host sources of the recorded uploads
+    cudaStream_t cap = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    int64_t pruned_units = 0;
+    bool tensor = false;
+};
+
+namespace {
+void free_plan(hgm_plan *pl)
+{
+    if (pl->exec) cudaGraphExecDestroy(pl->exec);
+    if (pl->graph) cudaGraphDestroy(pl->graph);
+    if (pl->cap) cudaStreamDestroy(pl->cap);
+    for (auto &h : pl->pinned) cudaFreeHost(h.first);
+    pl->pinned.clear();
+}
+}  // namespace
 
 hgm_status hgm_create_model(const float *xy, const int32_t *t, const float *desc, int32_t M, int32_t F, void *stream,
                             hgm_model **out)
@@ -936,6 +1012,12 @@ void hgm_destroy(void *handle)
         free_scene(s);
         s->magic = kDeadMagic;
         delete s;
+    } else if (magic == kPlanMagic) {
+        hgm_plan *pl = static_cast<hgm_plan *>(handle);
+        cudaDeviceSynchronize();
+        free_plan(pl);
+        pl->magic = kDeadMagic;
+        delete pl;
     } else if (magic == kPropMagic) {
         hgm_prop *p = static_cast<hgm_prop *>(handle);
         cudaDeviceSynchronize();
@@ -992,7 +1074,10 @@ hgm_status hgm_match(const hgm_model *model, const hgm_scene *scene, const hgm_p
     if (n_offsets) *n_offsets = n;
     if (first_offset) *first_offset = f;
     if (!energy && !assign) return HGM_OK;
-    return run_batch(&model, 1, &scene, 1, params, (cudaStream_t)stream, energy, assign);
+    Exec ex;
+    hgm_status rc2 = run_batch(ex, &model, 1, &scene, 1, params, (cudaStream_t)stream, energy, assign);
+    g_pruned_units += ex.pruned_units;
+    return rc2;
 }
 
 hgm_status hgm_match_batch(const hgm_model *const *models, int32_t n_models, const hgm_scene *const *scenes,
@@ -1002,7 +1087,10 @@ hgm_status hgm_match_batch(const hgm_model *const *models, int32_t n_models, con
     g_err.clear();
     if (n_models < 0 || n_scenes < 0 || (n_models && !models) || (n_scenes && !scenes))
         return fail(HGM_EINVAL, "bad model/scene arrays");
-    return run_batch(models, n_models, scenes, n_scenes, params, (cudaStream_t)stream, energy, assign);
+    Exec ex;
+    hgm_status rc = run_batch(ex, models, n_models, scenes, n_scenes, params, (cudaStream_t)stream, energy, assign);
+    g_pruned_units += ex.pruned_units;
+    return rc;
 }
 
 hgm_status hgm_model_order(const hgm_model *model, int32_t *perm)
@@ -1207,7 +1295,8 @@ hgm_status hgm_autotune(const hgm_model *const *models, int32_t n_models, const 
         float vbest = 3.0e38f;
         for (int rep = 0; rep < 3; ++rep) {          // first repetition is a warm-up
             CK(cudaEventRecord(a, st), "event");
-            rc = run_batch(models, n_models, scenes, n_scenes, &ps, st, nullptr, nullptr);
+            Exec ex;
+            rc = run_batch(ex, models, n_models, scenes, n_scenes, &ps, st, nullptr, nullptr);
             if (rc) { set_recurse_variant(keep); cudaEventDestroy(a); cudaEventDestroy(b); return rc; }
             CK(cudaEventRecord(b, st), "event");
             CK(cudaEventSynchronize(b), "event");
@@ -1230,6 +1319,89 @@ hgm_status hgm_profile_enable(int32_t on)
     std::lock_guard<std::mutex> lk(g_prof_mu);
     g_prof_on = on == 1;
     g_count_mode = on == 2;
+    return HGM_OK;
+}
+
+hgm_status hgm_plan_create(const hgm_model *const *models, int32_t n_models, const hgm_scene *const *scenes,
+                           int32_t n_scenes, const hgm_params *params, float *energy, int32_t *assign, void *stream,
+                           hgm_plan **out)
+{
+    std::lock_guard<std::mutex> lk(g_mu);
+    g_err.clear();
+    if (!out) return fail(HGM_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (n_models < 1 || n_scenes < 1 || !models || !scenes) return fail(HGM_EINVAL, "bad model/scene arrays");
+    if ((energy && !is_device_ptr(energy)) || (assign && !is_device_ptr(assign)))
+        return fail(HGM_EINVAL, "plan outputs must be device pointers");
+    hgm_status rc = check_params(params);
+    if (rc) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    hgm_plan *pl = new hgm_plan();
+    pl->magic = kPlanMagic;
+    auto bail = [&](hgm_status r) {
+        g_capturing = false;
+        free_plan(pl);
+        delete pl;
+        return r;
+    };
+    // sizing pass: runs the batch once on the plan's workspace (growing it) and keeps the host uploads
+    Exec ex;
+    ex.mode = Exec::kSizing;
+    ex.ws = &pl->ws;
+    ex.pinned = &pl->pinned;
+    if ((rc = run_batch(ex, models, n_models, scenes, n_scenes, params, st, energy, assign))) return bail(rc);
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return bail(cuda_fail(e, "plan sizing pass"));
+    pl->pruned_units = ex.pruned_units;
+    pl->tensor = ex.tensor;
+    g_pruned_units += ex.pruned_units;   // the sizing pass ran the batch
+    // recorded pass, on a private stream (the legacy stream cannot be captured)
+    if ((e = cudaStreamCreateWithFlags(&pl->cap, cudaStreamNonBlocking)) != cudaSuccess)
+        return bail(cuda_fail(e, "plan stream"));
+    Exec rec;
+    rec.mode = Exec::kCapture;
+    rec.ws = &pl->ws;
+    rec.pinned = &pl->pinned;
+    rec.budget = ex.budget;
+    if ((e = cudaStreamBeginCapture(pl->cap, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
+        return bail(cuda_fail(e, "begin capture"));
+    g_capturing = true;
+    rc = run_batch(rec, models, n_models, scenes, n_scenes, params, pl->cap, energy, assign);
+    g_capturing = false;
+    cudaGraph_t g = nullptr;
+    e = cudaStreamEndCapture(pl->cap, &g);
+    pl->graph = g;
+    if (rc) return bail(rc);
+    if (e != cudaSuccess) return bail(cuda_fail(e, "end capture"));
+    if (rec.pin_next != pl->pinned.size()) return bail(fail(HGM_ECUDA, "plan: recorded pass skipped uploads"));
+    if ((e = cudaGraphInstantiate(&pl->exec, pl->graph, 0)) != cudaSuccess)
+        return bail(cuda_fail(e, "graph instantiate"));
+    *out = pl;
+    return HGM_OK;
+}
+
+hgm_status hgm_plan_run(hgm_plan *plan, void *stream)
+{
+    std::lock_guard<std::mutex> lk(g_mu);
+    g_err.clear();
+    if (!plan || plan->magic != kPlanMagic) return fail(HGM_EINVAL, "invalid plan");
+    cudaStream_t st = (cudaStream_t)stream;
+    if (plan->tensor) CK(cudaMemsetAsync(plan->ws.status.p, 0, sizeof(int), st), "memset");
+    CK(cudaGraphLaunch(plan->exec, st), "graph launch");
+    g_pruned_units += plan->pruned_units;
+    return HGM_OK;
+}
+
+hgm_status hgm_plan_check(hgm_plan *plan, void *stream)
+{
+    std::lock_guard<std::mutex> lk(g_mu);
+    g_err.clear();
+    if (!plan || plan->magic != kPlanMagic) return fail(HGM_EINVAL, "invalid plan");
+    cudaStream_t st = (cudaStream_t)stream;
+    int status = 0;
+    if (plan->tensor) CK(cudaMemcpyAsync(&status, plan->ws.status.p, sizeof(int), cudaMemcpyDeviceToHost, st), "status");
+    CK(cudaStreamSynchronize(st), "synchronise");
+    if (status) return fail(HGM_ETIMEOUT, "a bounded tensor-core wait gave up");
     return HGM_OK;
 }
 

@@ -168,6 +168,7 @@ void prof_end(int kernel, cudaStream_t st);
 
 constexpr uint32_t kModelMagic = 0x4d4f444cu;   // "MODL"
 constexpr uint32_t kSceneMagic = 0x53434e45u;   // "SCNE"
+constexpr uint32_t kPlanMagic = 0x504c414eu;    // "PLAN"
 
 }  // namespace hgm
 

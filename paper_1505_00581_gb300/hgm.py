@@ -62,6 +62,9 @@ SIGNATURES = {
     "hgm_set_recurse_variant": (_i32, [_i32]),
     "hgm_get_recurse_variant": (_i32, []),
     "hgm_set_workspace_budget": (_i32, [_i64]),
+    "hgm_plan_create": (_i32, [_vp, _i32, _vp, _i32, _vp, _vp, _vp, _vp, _vp]),
+    "hgm_plan_run": (_i32, [_vp, _vp]),
+    "hgm_plan_check": (_i32, [_vp, _vp]),
     "hgm_prop_scores": (_i32, [_vp, _vp, _vp, _vp, _i32, _i32, _vp, _vp]),
     "hgm_model_order": (_i32, [_vp, _p32]),
     "hgm_scene_order": (_i32, [_vp, _p32]),
@@ -122,8 +125,9 @@ def default_params(**over) -> Params:
 
 
 def _stream(stream=None) -> int:
+    """cudaStream_t handle: an int, a torch.cuda.Stream (its cuda_stream), or None for torch's current stream."""
     if stream is not None:
-        return int(stream)
+        return int(getattr(stream, "cuda_stream", stream))
     try:
         import torch
         if torch.cuda.is_available() and torch.cuda.is_initialized():
@@ -363,6 +367,39 @@ def autotune(models: Sequence[Model], scenes: Sequence[Scene], params: Params, s
         except OSError:
             pass
     return int(best.value), times
+
+
+class Plan:
+    """hgm_plan: a batch laid out once and replayed as a CUDA graph. energy / assign: device tensors in the
+    batch_layout order (kept alive by the plan)."""
+
+    def __init__(self, models, scenes, params: Params, energy=None, assign=None, stream=None):
+        self.lib = load()
+        mh = (ctypes.c_void_p * len(models))(*[m.handle for m in models])
+        sh = (ctypes.c_void_p * len(scenes))(*[s.handle for s in scenes])
+        (pe, ke), (pa, ka) = _ptr(energy), _ptr(assign)
+        self._keep = (models, scenes, params, ke, ka)
+        h = ctypes.c_void_p()
+        _check(self.lib.hgm_plan_create(mh, len(models), sh, len(scenes), ctypes.byref(params), pe, pa,
+                                        _stream(stream), ctypes.byref(h)))
+        self.handle = h
+
+    def run(self, stream=None):
+        _check(self.lib.hgm_plan_run(self.handle, _stream(stream)))
+
+    def check(self, stream=None):
+        _check(self.lib.hgm_plan_check(self.handle, _stream(stream)))
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self.lib.hgm_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def set_workspace_budget(nbytes: int):
