@@ -47,6 +47,21 @@ def dist_env():
     return world, rank, local
 
 
+def max_over_ranks(x: float, dist=None, device="cpu") -> float:
+    """The largest value of x over the ranks (the job's wall time is the slowest rank's)."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank: float, world: int, seconds: float) -> float:
+    """Whole-job throughput: the units all ranks processed over the slowest rank's time."""
+    return units_per_rank * world / seconds
+
+
 def workload(name: str, seed_shift: int):
     from paper_1505_00581_gb300 import synth
     if name == "batched_exact":
@@ -202,7 +217,7 @@ def _time_form(torch, hgm, models, scenes, p, energy, assign, steps, warmup, str
     return sum(a.elapsed_time(b) for a, b in zip(starts, ends)) / steps, hgm.profile_read()
 
 
-def run_pruned(args, torch, hgm, wl, models, scenes, energy, assign, es, as_, dev, stream, world):
+def run_pruned(args, torch, hgm, wl, models, scenes, energy, assign, es, as_, dev, stream, world, dist=None):
     """The pruned + BF16 form on the same workload: BF16 tensor-core unary table, the proposal network
     keeps 8 of the 64 candidates per list, recursion on the short lists, exact fallback for infeasible
     units. Quality is measured against this run's exact results (energy/assign hold them)."""
@@ -224,9 +239,10 @@ def run_pruned(args, torch, hgm, wl, models, scenes, energy, assign, es, as_, de
     torch.cuda.profiler.start()
     ms, prof = _time_form(torch, hgm, models, scenes, p, e2, a2, args.steps, args.warmup, stream, flush)
     torch.cuda.profiler.stop()
+    ms = max_over_ranks(ms, dist, dev)
     n_pruned, n_fb = hgm.prune_counters(reset=True)
-    g_ms = None if args.no_graph else _time_plan(torch, hgm, models, scenes, p, e2, a2, args.steps, args.warmup,
-                                                  stream, flush)
+    g_ms = None if args.no_graph else max_over_ranks(
+        _time_plan(torch, hgm, models, scenes, p, e2, a2, args.steps, args.warmup, stream, flush), dist, dev)
     hgm.prune_counters(reset=True)
     blocks = []
     for mi, m in enumerate(wl.models):
@@ -243,15 +259,16 @@ def run_pruned(args, torch, hgm, wl, models, scenes, energy, assign, es, as_, de
     e8 = torch.empty(int(es8[-1]), dtype=torch.float32, device=dev)
     a8 = torch.empty(int(as8[-1]), dtype=torch.int32, device=dev)
     ms8, _ = _time_form(torch, hgm, models, scenes, pb, e8, a8, max(1, args.steps // 2), 1, stream, flush)
+    ms8 = max_over_ranks(ms8, dist, dev)
     base_q = prop_train.compare(e_ref, a_ref, e8.cpu().numpy(), a8.cpu().numpy(), blocks, erows, masks)
-    frames = wl.total_frames * world
-    return {"value": frames / (ms / 1e3), "unit": "frames/s", "ms_per_step": ms,
+    return {"value": job_rate(wl.total_frames, world, ms / 1e3), "unit": "frames/s", "ms_per_step": ms,
             "kernel_ms_per_step": {k: v[0] / args.steps for k, v in prof.items()},
-            "graph": None if g_ms is None else {"value": frames / (g_ms / 1e3), "unit": "frames/s", "ms_per_step": g_ms},
+            "graph": None if g_ms is None else {"value": job_rate(wl.total_frames, world, g_ms / 1e3), "unit": "frames/s",
+                                                "ms_per_step": g_ms},
             "keep": 8, "K": wl.K, "precision": "BF16 unary + FP32 re-score of kept candidates",
             "fallback_units_per_step": n_fb / max(1, args.steps + args.warmup),
             "units_per_step": n_pruned / max(1, args.steps + args.warmup), **quality,
-            "top8_by_unary_baseline": {"value": frames / (ms8 / 1e3), "unit": "frames/s", **base_q},
+            "top8_by_unary_baseline": {"value": job_rate(wl.total_frames, world, ms8 / 1e3), "unit": "frames/s", **base_q},
             "training": {k: v for k, v in info.items() if k != "loss"}, "final_loss": (info.get("loss") or [[0, None]])[-1][1],
             "train_s": train_s}
 
@@ -349,13 +366,10 @@ def main():
     hgm.profile_enable(False)
     ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends))
     prof = hgm.profile_read()
-    t_local = torch.tensor([ms], dtype=torch.float64, device=dev)
-    if dist:
-        dist.all_reduce(t_local, op=dist.ReduceOp.MAX)
-    ms_max = float(t_local.item())
+    ms_max = max_over_ranks(ms, dist, dev)
     ms_step = ms_max / args.steps
     frames_all = wl.total_frames * world
-    value = frames_all / (ms_step / 1e3)
+    value = job_rate(wl.total_frames, world, ms_step / 1e3)
     fin = torch.isfinite(energy).sum().item()
 
     # end to end: host arrays -> handles -> batch -> host outputs, copies inside the timed region
@@ -381,15 +395,16 @@ def main():
                 h.close()
             if k > 0:
                 e2e_times.append(t1 - t0)
-        e2e_sec = float(np.mean(e2e_times))
-        e2e = {"value": frames_all / e2e_sec if world == 1 else wl.total_frames * world / e2e_sec,
+        e2e_sec = max_over_ranks(float(np.mean(e2e_times)), dist, dev)
+        e2e = {"value": job_rate(wl.total_frames, world, e2e_sec),
                "unit": "frames/s", "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
 
     # the same exact batch replayed as a CUDA graph (hgm_plan)
     graph = None
     if not args.no_graph:
-        g_ms = _time_plan(torch, hgm, models, scenes, p, energy, assign, args.steps, args.warmup, stream, flush)
-        graph = {"value": frames_all / (g_ms / 1e3), "unit": "frames/s", "ms_per_step": g_ms,
+        g_ms = max_over_ranks(_time_plan(torch, hgm, models, scenes, p, energy, assign, args.steps, args.warmup,
+                                         stream, flush), dist, dev)
+        graph = {"value": job_rate(wl.total_frames, world, g_ms / 1e3), "unit": "frames/s", "ms_per_step": g_ms,
                  "form": "plain exact FP32, one graph launch per step"}
 
     pk, pk_kind = peaks()
@@ -425,7 +440,7 @@ def main():
 
     pruned = None
     if not args.no_pruned:
-        pruned = run_pruned(args, torch, hgm, wl, models, scenes, energy, assign, es, as_, dev, stream, world)
+        pruned = run_pruned(args, torch, hgm, wl, models, scenes, energy, assign, es, as_, dev, stream, world, dist)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "frames/s", "n_gpus": world, "steps": args.steps,
