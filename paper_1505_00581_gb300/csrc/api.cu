@@ -573,8 +573,8 @@ hgm_status run_batch(Exec &ex, const hgm_model *const *models, int nm, const hgm
         pi.dp = prop->L.dp;
         pi.inv_window = 1.0f / (float)std::max(hp->window, 1);
         pi.keep = keep;
-        pi.rescore = hp->precision == 1 ? 1 : 0;
-        p.rescore = 0;   // the kept candidates are re-scored by the pruning kernel instead
+        pi.rescore = hp->precision == 1 ? 1 : 0;   // the kept candidates are re-scored by the pruning pass
+        // (the selection still re-scores the 8 smallest of every full list: the fallback solves those)
         if (!g_ws.fb_total.p) {
             if (ex.mode == Exec::kCapture) return fail(HGM_ECUDA, "plan: fallback counter missing");
             CK(g_ws.fb_total.ensure(sizeof(unsigned long long)), "workspace");

@@ -205,6 +205,30 @@ def precision_long(seed: int = 2, n_models: int = 50, n_frames: int = 30000, M_r
     return Workload(f"precision_long_{n_models}x1x{n_frames}_K64", models, [sc], K=64, window=3)
 
 
+def combined(seed: int = 3, n_models: int = 100, n_scenes: int = 16, M_range=(16, 256),
+             frames_range=(10_000, 100_000), lam: float = 80.0, implant_frac: float = 0.05,
+             frame=(640.0, 480.0)) -> Workload:
+    """The full combined workload: models of M in 16..256 points vs scenes of 10k-100k frames at 640x480 with
+    Poisson(80) points per frame; implants of random models cover about implant_frac of the offsets (each
+    implant is seen by the 2w+1 offsets around it); K=64, w=3. Scaled-down instances (fewer models and
+    scenes, shorter scenes) keep the same shape."""
+    rng = np.random.default_rng(seed)
+    models = [make_model(rng, int(rng.integers(M_range[0], M_range[1] + 1))) for _ in range(n_models)]
+    pool = np.concatenate([m.centres for m in models])
+    scenes = []
+    w = 3
+    for _ in range(n_scenes):
+        nf = int(rng.integers(frames_range[0], frames_range[1] + 1))
+        n_imp = max(1, int(round(implant_frac * nf / (2 * w + 1))))
+        imp = []
+        for _ in range(n_imp):
+            m = int(rng.integers(0, n_models))
+            span = int(models[m].t.max())
+            imp.append((m, int(rng.integers(0, max(1, nf - span)))))
+        scenes.append(make_scene(rng, nf, frame, ("poisson", lam), pool, models, imp))
+    return Workload(f"combined_{n_models}x{n_scenes}_K64", models, scenes, K=64, window=w)
+
+
 def tiny_case(seed: int, M: int = 5, n_frames: int = 12, per_frame: int = 3, K: int = 5, window: int = 1,
               F: int = 8, T: int = 10, frame=(20.0, 20.0)) -> Workload:
     """Very small random instance for brute-force enumeration."""
