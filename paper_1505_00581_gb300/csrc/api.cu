@@ -464,6 +464,11 @@ hgm_status run_units(Exec &ex, const hgm_model *const *models, std::vector<Unit>
             const int64_t scratch = recurse_fused_scratch(K, max_M);
             if (scratch < 0) return fail(HGM_ECUDA, "device query failed");
             CK(ws.beta_fb.ensure((size_t)scratch), "workspace (fallback)");
+            if (pi.rescore)   // precision mode: the fallback solves full lists, their costs in FP32
+                CK(launch_rescore_units(ws.fb_units.as<Unit>(), n, ws.fb_count.as<int>(), dm, ds, p,
+                                        ws.cand_idx.as<int32_t>(), ws.cand_cnt.as<int32_t>(), ws.cand_u.as<float>(),
+                                        st),
+                   "re-score kernel (fallback)");
             CK(launch_recurse_fused(ws.fb_units.as<Unit>(), n, ws.fb_count.as<int>(), dm, ds, p,
                                     ws.cand_idx.as<int32_t>(), ws.cand_u.as<float>(), ws.cand_cnt.as<int32_t>(),
                                     ws.beta_fb.as<uint8_t>(), max_M, d_energy, d_assign, ws.counter.as<int>(), st),
@@ -573,8 +578,8 @@ hgm_status run_batch(Exec &ex, const hgm_model *const *models, int nm, const hgm
         pi.dp = prop->L.dp;
         pi.inv_window = 1.0f / (float)std::max(hp->window, 1);
         pi.keep = keep;
-        pi.rescore = hp->precision == 1 ? 1 : 0;   // the kept candidates are re-scored by the pruning pass
-        // (the selection still re-scores the 8 smallest of every full list: the fallback solves those)
+        pi.rescore = hp->precision == 1 ? 1 : 0;   // the kept candidates are re-scored by the pruning pass,
+        p.rescore = 0;                              // the fallback units' full lists by the fallback pass
         if (!g_ws.fb_total.p) {
             if (ex.mode == Exec::kCapture) return fail(HGM_ECUDA, "plan: fallback counter missing");
             CK(g_ws.fb_total.ensure(sizeof(unsigned long long)), "workspace");

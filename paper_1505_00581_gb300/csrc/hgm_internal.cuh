@@ -114,6 +114,10 @@ cudaError_t launch_prop_prune(const Unit *units, int64_t n_units, const ModelRec
                               const int32_t *cand_cnt, float *scores, int32_t *out_idx, float *out_u,
                               int32_t *out_cnt, int *status, cudaStream_t st);
 cudaError_t launch_derive_units(const Unit *in, int64_t n, int K, int keep, Unit *out, cudaStream_t st);
+// Precision mode: FP32 unary cost of every candidate of the fallback units' full lists (count on the device).
+cudaError_t launch_rescore_units(const Unit *units, int64_t n_max, const int *n_dev, const ModelRec *models,
+                                 const SceneRec *scenes, Params p, const int32_t *cand_idx, const int32_t *cand_cnt,
+                                 float *cand_u, cudaStream_t st);
 cudaError_t launch_collect_infeasible(const UnitResult *res, const Unit *units, int64_t n, Unit *list, int *count,
                                       unsigned long long *total, cudaStream_t st);
 

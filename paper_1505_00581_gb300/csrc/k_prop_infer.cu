@@ -308,6 +308,32 @@ __global__ void __launch_bounds__(256) prop_rescore_kernel(const Unit *__restric
     }
 }
 
+// Precision mode, fallback units: every candidate of their full lists gets its FP32 unary cost (the same
+// value as the FP32 table). Unit count read on the device; one CTA per unit at a time.
+__global__ void __launch_bounds__(256) rescore_units_kernel(const Unit *__restrict__ units, int64_t n_max,
+                                                            const int *__restrict__ n_dev,
+                                                            const ModelRec *__restrict__ models,
+                                                            const SceneRec *__restrict__ scenes, Params p,
+                                                            const int32_t *__restrict__ cand_idx,
+                                                            const int32_t *__restrict__ cand_cnt,
+                                                            float *__restrict__ cand_u)
+{
+    const int64_t n = min((int64_t)*n_dev, n_max);
+    const int K = p.K;
+    for (int64_t u = blockIdx.x; u < n; u += gridDim.x) {
+        const Unit un = units[u];
+        const ModelRec md = models[un.model];
+        const SceneRec sc = scenes[un.scene];
+        const int64_t lbase = un.cand / K;
+        for (int e = threadIdx.x; e < md.M * K; e += blockDim.x) {
+            const int li = e / K, c = e - li * K;
+            if (c >= cand_cnt[lbase + li]) continue;
+            const int64_t o = un.cand + e;
+            cand_u[o] = exact_u(md.f + (int64_t)li * p.F, sc.f + (int64_t)cand_idx[o] * p.F, p.F, p.lambda1);
+        }
+    }
+}
+
 // Units of the pruned pass: same problems, lists of `keep` candidates.
 __global__ void derive_units_kernel(const Unit *__restrict__ in, int64_t n, int K, int keep, Unit *__restrict__ out)
 {
@@ -388,6 +414,21 @@ cudaError_t launch_prop_prune(const Unit *units, int64_t n_units, const ModelRec
     }
     prof_end(kProfPrune, st);
     return e;
+}
+
+cudaError_t launch_rescore_units(const Unit *units, int64_t n_max, const int *n_dev, const ModelRec *models,
+                                 const SceneRec *scenes, Params p, const int32_t *cand_idx, const int32_t *cand_cnt,
+                                 float *cand_u, cudaStream_t st)
+{
+    if (n_max <= 0) return cudaSuccess;
+    int dev = 0, sms = 0;
+    cudaError_t e;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    const int64_t grid = std::min<int64_t>(n_max, (int64_t)sms * 8);
+    rescore_units_kernel<<<(unsigned)grid, 256, 0, st>>>(units, n_max, n_dev, models, scenes, p, cand_idx, cand_cnt,
+                                                         cand_u);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_derive_units(const Unit *in, int64_t n, int K, int keep, Unit *out, cudaStream_t st)

@@ -63,8 +63,16 @@ __device__ __forceinline__ uint32_t lanemask_lt()
     return m;
 }
 
+// Kept entry k of b sits at a per-row rotation of its slot, so that the rows of different b -- whose
+// starts are multiples of 32 banks apart -- spread over the banks when several b are read or written
+// at the same position (phase 1 writes, the triple loop's reads).
 template <int KM>
-struct List {
+__device__ __forceinline__ int fb_at(int b, int k) { return b * KM + ((k + b) & (KM - 1)); }
+template <int KM>
+__device__ __forceinline__ int fs_at(int b, int k) { return b * KM + ((k + 4 * b) & (KM - 1)); }
+
+template <int KM>
+struct alignas(16) List {   // 16-byte aligned arrays: tiles read four consecutive entries at once
     float2 xy[KM];
     int32_t t[KM];
     float u[KM];
@@ -304,15 +312,16 @@ recurse_kernel(const Unit *__restrict__ units, int64_t n_units, const ModelRec *
                     pmk = lo32;
                 }
                 const int kept = __popcll(mk) + __popcll(pmk);
-                float *fbf = reinterpret_cast<float *>(sm.fb + b * KM);
+                float *fbf = reinterpret_cast<float *>(sm.fb);
                 for (unsigned long long m = mk; m; m &= m - 1) {
                     const int k = __ffsll((long long)m) - 1;
                     const int a = NP * k + h;
                     int pos = __popcll(mk & ((1ull << k) - 1));
                     if constexpr (NP == 2) pos += __popcll(pmk & ((h ? 2ull << k : 1ull << k) - 1));
-                    fbf[2 * pos] = arow[a];
-                    sm.fs[b * KM + pos] = (uint8_t)a;
-                    fbf[2 * pos + 1] = wrap_pi(__fadd_rn(A1, direction(pb, LA.xy[a])));   // p1 = A1 + theta(b->a)
+                    const int at = fb_at<KM>(b, pos);
+                    fbf[2 * at] = arow[a];
+                    sm.fs[fs_at<KM>(b, pos)] = (uint8_t)a;
+                    fbf[2 * at + 1] = wrap_pi(__fadd_rn(A1, direction(pb, LA.xy[a])));   // p1 = A1 + theta(b->a)
                 }
                 // tiles in decreasing kept count, then increasing b (the lanes of a warp then loop over
                 // similar numbers of a): b's first tile = sum of the tile counts of the b ranked before it
@@ -390,19 +399,27 @@ recurse_kernel(const Unit *__restrict__ units, int64_t n_units, const ModelRec *
                 const float2 pb = LB.xy[b];
                 const int tb = LB.t[b], ib = LB.idx[b];
                 float q1[CT], best[CT];
-                int arg[CT];
+                int arg[CT], tcq[CT];
 #pragma unroll
-                for (int k = 0; k < CT; ++k) {
-                    const int c = c0 + k;
-                    const bool ok = c < nc && LC.t[c] <= tb && LC.idx[c] != ib;
-                    q1[k] = ok ? direction(pb, LC.xy[c]) : kInf;   // theta(b->c)
-                    best[k] = kInf;
-                    arg[k] = kNoSlot;
+                for (int q4 = 0; q4 < CT; q4 += 4) {   // the tile's cells of list C, four at a time
+                    const int4 t4 = *reinterpret_cast<const int4 *>(&LC.t[c0 + q4]);
+                    const int4 i4 = *reinterpret_cast<const int4 *>(&LC.idx[c0 + q4]);
+                    const float4 xa = *reinterpret_cast<const float4 *>(&LC.xy[c0 + q4]);
+                    const float4 xb = *reinterpret_cast<const float4 *>(&LC.xy[c0 + q4 + 2]);
+                    const int tv[4] = {t4.x, t4.y, t4.z, t4.w}, iv[4] = {i4.x, i4.y, i4.z, i4.w};
+                    const float2 xv[4] = {make_float2(xa.x, xa.y), make_float2(xa.z, xa.w), make_float2(xb.x, xb.y),
+                                          make_float2(xb.z, xb.w)};
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        const int c = c0 + q4 + k;
+                        const bool ok = c < nc && tv[k] <= tb && iv[k] != ib;
+                        q1[q4 + k] = ok ? direction(pb, xv[k]) : kInf;   // theta(b->c)
+                        tcq[q4 + k] = tv[k];
+                        best[q4 + k] = kInf;
+                        arg[q4 + k] = kNoSlot;
+                    }
                 }
                 const int nf = sm.fn[b];
-
-                const float2 *fbb = sm.fb + b * KM;
-                const uint8_t *fsb = sm.fs + b * KM;
                 // cells in pairs: packed FP32x2 arithmetic, same roundings as triple_cost
                 static_assert(CT % 4 == 0, "tiles of a multiple of 4 cells");
                 unsigned long long q1p[CT / 2];
@@ -411,8 +428,8 @@ recurse_kernel(const Unit *__restrict__ units, int64_t n_units, const ModelRec *
                 const unsigned long long lamp = pk2(lam23, lam23);
 #pragma unroll 2
                 for (int k = 0; k < nf; ++k) {
-                    const float2 e = fbb[k];
-                    const int a = fsb[k];
+                    const float2 e = sm.fb[fb_at<KM>(b, k)];
+                    const int a = sm.fs[fs_at<KM>(b, k)];
                     if constexpr (kCount) n_eval += CT;
                     const float p2 = __fadd_rn(e.y, k2);
                     const unsigned long long bp = pk2(e.x, e.x), p1p = pk2(e.y, e.y), p2p = pk2(p2, p2);
@@ -434,7 +451,7 @@ recurse_kernel(const Unit *__restrict__ units, int64_t n_units, const ModelRec *
                         float al = kInf;
                         int bt = kNoSlot;
                         if (best[q] < kInf) {
-                            al = cell_alpha(best[q], lam2, dt_bc, tb, LC.t[c]);
+                            al = cell_alpha(best[q], lam2, dt_bc, tb, tcq[q]);
                             bt = arg[q];
                         }
                         sm.alpha[c * AS + b] = al;
