@@ -147,7 +147,7 @@ struct Workspace {
     Buffer modelcat, U, cand_idx, cand_u, cand_cnt, beta, units, res, mrec, srec, counter, out_e, out_a, evaluated;
     Buffer mnorm, snorm, status;
     Buffer stage, perm_stage, flag;   // inputs of hgm_create_model / hgm_create_scene
-    Buffer P, Q, modelxy, cand2_idx, cand2_u, cand2_cnt, units2, beta2, fb_units, fb_count, beta_fb, scores;
+    Buffer P, Q, Qb, modelxy, cand2_idx, cand2_u, cand2_cnt, units2, beta2, fb_units, fb_count, beta_fb, scores;
     Buffer fb_total;   // fallback units since the last hgm_prune_counters reset (device counter)
 };
 Workspace g_ws;
@@ -567,7 +567,7 @@ hgm_status run_batch(Exec &ex, const hgm_model *const *models, int nm, const hgm
                                (size_t)models[m]->d.M * 2 * sizeof(float), cudaMemcpyDeviceToDevice, st),
                "gather model positions");
         CK(launch_prop_fold_xy(ws.P.as<float>(), R, ws.modelxy.as<float>(), th + prop->L.o_W1 + 2 * Fu,
-                               prop->L.dp, -1.0f, st),
+                               prop->L.dp, -1.0f, nullptr, st),
            "projection kernel");
         pi.P = ws.P.as<float>();
         pi.W2 = th + prop->L.o_W2;
@@ -621,7 +621,7 @@ hgm_status run_batch(Exec &ex, const hgm_model *const *models, int nm, const hgm
                                    : std::max<size_t>((size_t)256 << 20, std::min<size_t>((size_t)24 << 30, free_b / 3));
         ex.budget = budget;
     }
-    const int64_t per_point = (int64_t)R * 4 + (pruning ? (int64_t)kPropHidden * 4 : 0);
+    const int64_t per_point = (int64_t)R * 4 + (pruning ? (int64_t)kPropHidden * 6 : 0);
     const int64_t max_points = std::max<int64_t>(1, (int64_t)budget / per_point);
 
     // segments: per scene, runs of offsets whose reachable frames hold at most max_points points
@@ -664,7 +664,10 @@ hgm_status run_batch(Exec &ex, const hgm_model *const *models, int nm, const hgm
         }
         const int ng = (int)(gend - gbegin);
         CK(ws.U.ensure((size_t)R * gpoints * sizeof(float)), "workspace (unary table)");
-        if (pruning) CK(ws.Q.ensure((size_t)gpoints * kPropHidden * sizeof(float)), "workspace (projections)");
+        if (pruning) {
+            CK(ws.Q.ensure((size_t)gpoints * kPropHidden * sizeof(float)), "workspace (projections)");
+            CK(ws.Qb.ensure((size_t)gpoints * kPropHidden * sizeof(__nv_bfloat16)), "workspace (projections)");
+        }
         std::vector<SceneRec> srec((size_t)ng);
         int64_t off = 0, smax = 0;
         for (int g = 0; g < ng; ++g) {
@@ -674,7 +677,7 @@ hgm_status run_batch(Exec &ex, const hgm_model *const *models, int nm, const hgm
             SceneRec r{d.xy, d.t, d.frame_start, d.perm, ws.U.as<float>() + (size_t)R * off, pitch, d.S, d.n_frames,
                        d.f};
             r.ucol0 = sg.j0;
-            if (pruning) r.pq = ws.Q.as<float>() + (size_t)off * kPropHidden;
+            if (pruning) r.pq = ws.Qb.as<__nv_bfloat16>() + (size_t)off * kPropHidden;
             srec[(size_t)g] = r;
             off += pitch;
             smax = std::max(smax, pts);
@@ -701,13 +704,15 @@ hgm_status run_batch(Exec &ex, const hgm_model *const *models, int nm, const hgm
             }
             if (pruning) {
                 const float *th = prop->theta;
-                CK(launch_rowdot_plain(segf, pts, F, th + prop->L.o_W1 + Fu, kPropHidden, prop->L.dp, Fu, nullptr,
-                                       const_cast<float *>(srec[(size_t)g].pq), kPropHidden, ws.status.as<int>(),
-                                       st),
+                // FP32 projection of the segment's points (scratch), then position terms folded in and one
+                // rounding to the BF16 rows the scoring kernel gathers
+                float *qf = ws.Q.as<float>();
+                CK(launch_rowdot_plain(segf, pts, F, th + prop->L.o_W1 + Fu, kPropHidden, prop->L.dp, Fu, nullptr, qf,
+                                       kPropHidden, ws.status.as<int>(), st),
                    "projection kernel");
-                CK(launch_prop_fold_xy(const_cast<float *>(srec[(size_t)g].pq), pts,
-                                       reinterpret_cast<const float *>(d.xy) + (size_t)sg.j0 * 2,
-                                       th + prop->L.o_W1 + 2 * Fu, prop->L.dp, 1.0f, st),
+                CK(launch_prop_fold_xy(qf, pts, reinterpret_cast<const float *>(d.xy) + (size_t)sg.j0 * 2,
+                                       th + prop->L.o_W1 + 2 * Fu, prop->L.dp, 1.0f,
+                                       const_cast<__nv_bfloat16 *>(srec[(size_t)g].pq), st),
                    "projection kernel");
             }
         }
@@ -1206,18 +1211,19 @@ hgm_status hgm_prop_scores(const hgm_prop *prop, const hgm_model *model, const h
                            g_ws.P.as<float>(), kPropHidden, g_ws.status.as<int>(), st),
        "projection kernel");
     CK(launch_prop_fold_xy(g_ws.P.as<float>(), M, reinterpret_cast<const float *>(model->d.xy),
-                           th + prop->L.o_W1 + 2 * Fu, prop->L.dp, -1.0f, st),
+                           th + prop->L.o_W1 + 2 * Fu, prop->L.dp, -1.0f, nullptr, st),
        "projection kernel");
     CK(launch_rowdot_plain(scene->d.f, S, F, th + prop->L.o_W1 + Fu, kPropHidden, prop->L.dp, Fu, nullptr,
                            g_ws.Q.as<float>(), kPropHidden, g_ws.status.as<int>(), st),
        "projection kernel");
+    CK(g_ws.Qb.ensure((size_t)std::max(S, 1) * kPropHidden * sizeof(__nv_bfloat16)), "workspace (projections)");
     CK(launch_prop_fold_xy(g_ws.Q.as<float>(), S, reinterpret_cast<const float *>(scene->d.xy),
-                           th + prop->L.o_W1 + 2 * Fu, prop->L.dp, 1.0f, st),
+                           th + prop->L.o_W1 + 2 * Fu, prop->L.dp, 1.0f, g_ws.Qb.p, st),
        "projection kernel");
     const int64_t pitch = round_up4(std::max(S, 1));
     SceneRec sr{scene->d.xy, scene->d.t, scene->d.frame_start, scene->d.perm, g_ws.U.as<float>(), pitch, S,
                 scene->d.n_frames, scene->d.f};
-    sr.pq = g_ws.Q.as<float>();
+    sr.pq = g_ws.Qb.as<__nv_bfloat16>();
     CK(cudaMemcpyAsync(g_ws.srec.p, &sr, sizeof sr, cudaMemcpyHostToDevice, st), "upload");
     PropInfer pi{};
     pi.P = g_ws.P.as<float>();

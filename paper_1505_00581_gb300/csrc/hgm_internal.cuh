@@ -1,6 +1,7 @@
 // hgm_internal.cuh -- shared declarations of libhgm's host runtime and kernels.
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -57,7 +58,8 @@ struct SceneRec {
     int64_t upitch;      // row pitch of U in floats (>= S)
     int32_t S, n_frames;
     const float *f;      // sorted descriptors, row stride Params::F
-    const float *pq;     // proposal network: W1b f'_j per point of the block [.. x 128] (pruned mode only)
+    const __nv_bfloat16 *pq;   // proposal network: W1b f'_j + position terms per point of the block, BF16
+                               // [.. x 128] (pruned mode only)
     int64_t ucol0;       // first sorted scene point of the U / pq blocks (a segment of the scene)
 };
 
@@ -102,9 +104,10 @@ struct PropInfer {
 // Per-step model constants of the recursion: geo[i] = (A1, k2, dt_ab, dt_bc) for i >= 2 (zero for i < 2),
 // A1 = signed angle at i-1 (->i to ->i-2), k2 = wrap(A2 - A1 + pi) with A2 the angle at i (->i-1 to ->i-2).
 cudaError_t launch_model_geo(const float2 *xy, const int32_t *t, int M, float4 *geo, cudaStream_t st);
-// rows[r][h] += sign * (W1c[h][0] x_r + W1c[h][1] y_r) / 100 (the first layer's position terms), r < n.
+// rows[r][h] += sign * (W1c[h][0] x_r + W1c[h][1] y_r) / 100 (the first layer's position terms), r < n;
+// with out_bf16 non-null the sums go there as BF16 and rows is left unchanged.
 cudaError_t launch_prop_fold_xy(float *rows, int64_t n, const float *xy, const float *w1c, int dp, float sign,
-                                cudaStream_t st);
+                                void *out_bf16, cudaStream_t st);
 // The proposal network's logit of every candidate of every list (scores [n_lists x K], -inf for empty slots).
 cudaError_t launch_prop_score(const Unit *units, int64_t n_units, const ModelRec *models, const SceneRec *scenes,
                               Params p, const PropInfer &pi, const int32_t *cand_idx, const int32_t *cand_cnt,

@@ -20,6 +20,7 @@
 #include "hgm_internal.cuh"
 #include "prop.cuh"
 #include "tc05.cuh"
+#include "unary_common.cuh"
 
 namespace hgm {
 namespace {
@@ -35,25 +36,17 @@ struct Smem {
     unsigned char a[2][TM * H * 2];  // hidden layer 1 of two tiles, BF16, canonical K-major
     unsigned char w2[H * H * 2];     // W2 (rows = output units), BF16
     float part[2][2][TM];            // [buffer][column half][row]: half-sums of the last layer
-    float b2[H], w3[H], w1t[H];      // layer-2 bias, output weights, dt column of W1
+    float b2[H], w3[H];              // layer-2 bias and output weights
     float b3;
     uint64_t mbar[2];
     uint32_t tslot;
 };
 
-__device__ __forceinline__ float exact_u(const float *a, const float *b, int F, float lambda1)
-{
-    float s = 0.0f;
-    for (int k = 0; k < F; ++k) {
-        const float d = __fsub_rn(a[k], b[k]);
-        s = __fmaf_rn(d, d, s);
-    }
-    return __fmul_rn(lambda1, __fsqrt_rn(s));
-}
 
 // rows[r][h] += sign * (W1c[h][0] x_r + W1c[h][1] y_r) / 100: the position terms of the first layer.
+// With out_bf16, the sum is written there rounded to BF16 (rows left unchanged).
 __global__ void fold_xy_kernel(float *__restrict__ rows, int64_t n, const float2 *__restrict__ xy,
-                               const float *__restrict__ w1c, int dp, float sign)
+                               const float *__restrict__ w1c, int dp, float sign, __nv_bfloat16 *__restrict__ out_bf16)
 {
     const int64_t total = n * H;
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
@@ -61,12 +54,17 @@ __global__ void fold_xy_kernel(float *__restrict__ rows, int64_t n, const float2
         const int h = (int)(e % H);
         const float2 p = xy[r];
         const float t = fmaf(w1c[(int64_t)h * dp], p.x, w1c[(int64_t)h * dp + 1] * p.y);
-        rows[e] = fmaf(sign * 0.01f, t, rows[e]);
+        const float v = fmaf(sign * 0.01f, t, rows[e]);
+        if (out_bf16) out_bf16[e] = __float2bfloat16_rn(v);
+        else rows[e] = v;
     }
 }
 
 // Final logit of every candidate of every list: scores [n_lists x K] (-inf for empty slots).
-// 256 threads: row r = tid % 128 of the tile, half = tid / 128 owns hidden units [64 half, 64 half + 64).
+// 256 threads. Building a tile: warp w owns hidden units [32 (w%4), +32) of rows [64 (w/4), +64); lane l
+// takes row 8g + l/4 of each group g of 8 and the 8 units 32 (w%4) + 8 (l%4) .. +8, so a warp reads 8 BF16
+// Q rows as whole 32-byte sectors and writes 4 contiguous core matrices of the A tile. Epilogue: row
+// r = tid % 128, half = tid / 128 owns accumulator columns [64 half, 64 half + 64).
 __global__ void __launch_bounds__(256, 2) prop_score_kernel(const Unit *__restrict__ units, int64_t n_units,
                                                             const ModelRec *__restrict__ models,
                                                             const SceneRec *__restrict__ scenes, Params p,
@@ -82,6 +80,12 @@ __global__ void __launch_bounds__(256, 2) prop_score_kernel(const Unit *__restri
     const int K = p.K;
     const int lpt = TM >> kp_log2;                                  // lists per tile
     const int lsub = row >> kp_log2, slot = row & ((1 << kp_log2) - 1);
+    // build-phase roles
+    const int bh0 = 32 * (warp & 3) + 8 * (lane & 3);              // first of this lane's 8 hidden units
+    const int brow0 = 64 * (warp >> 2) + (lane >> 2);                // its row in group 0 (+8 per group)
+    float w1t[8];                                                    // W1c_t / w for those units
+#pragma unroll
+    for (int e = 0; e < 8; ++e) w1t[e] = pi.w1c[(int64_t)(bh0 + e) * pi.dp + 2] * pi.inv_window;
 
     if (warp == 0) tc05::tmem_alloc<2 * H>(&sm.tslot);
     for (int e = tid; e < H * (H / 8); e += 256) {          // W2 -> BF16, canonical layout
@@ -95,7 +99,6 @@ __global__ void __launch_bounds__(256, 2) prop_score_kernel(const Unit *__restri
     for (int h = tid; h < H; h += 256) {
         sm.b2[h] = pi.b2[h];
         sm.w3[h] = pi.w3[h];
-        sm.w1t[h] = pi.w1c[(int64_t)h * pi.dp + 2] * pi.inv_window;
     }
     if (tid == 0) {
         sm.b3 = pi.b3[0];
@@ -152,37 +155,61 @@ __global__ void __launch_bounds__(256, 2) prop_score_kernel(const Unit *__restri
         const int64_t lbase = un.cand / K;
         for (int i0 = 0; i0 < M; i0 += lpt) {
             const int buf = (int)(k & 1);
-            const int list = i0 + lsub;
-            const int n = list < M ? cand_cnt[lbase + list] : 0;
-            const bool valid = slot < n;
             unsigned char *arow = sm.a[buf];
-            if (valid) {
-                const int j = cand_idx[un.cand + (int64_t)list * K + slot];
-                const float4 *Q4 = reinterpret_cast<const float4 *>(sc.pq + (int64_t)(j - sc.ucol0) * H + h0);
-                const float4 *P4 = reinterpret_cast<const float4 *>(pi.P + (int64_t)(md.urow + list) * H + h0);
-                float4 q[16];
+            // gather: the 8 row groups' candidate indices first, then their frames and Q chunks
+            int jg[8];
+            bool vg[8];
 #pragma unroll
-                for (int c = 0; c < 16; ++c) q[c] = __ldg(Q4 + c);
-                const float dt = (float)(sc.t[j] - md.t[list] - un.offset);
-#pragma unroll
-                for (int c = 0; c < 16; c += 2) {
-                    const float4 pa = __ldg(P4 + c), pb = __ldg(P4 + c + 1);
-                    float v[8] = {pa.x + q[c].x,     pa.y + q[c].y,     pa.z + q[c].z,     pa.w + q[c].w,
-                                  pb.x + q[c + 1].x, pb.y + q[c + 1].y, pb.z + q[c + 1].z, pb.w + q[c + 1].w};
-                    __align__(16) __nv_bfloat162 hh[4];
-#pragma unroll
-                    for (int e = 0; e < 8; ++e) v[e] = fmaxf(fmaf(sm.w1t[h0 + 4 * c + e], dt, v[e]), 0.0f);
-#pragma unroll
-                    for (int e = 0; e < 4; ++e) hh[e] = __floats2bfloat162_rn(v[2 * e], v[2 * e + 1]);
-                    *reinterpret_cast<uint4 *>(arow + tc05::kmajor_offset(row, h0 + 4 * c, kLBO, kSBO)) =
-                        *reinterpret_cast<uint4 *>(hh);
-                }
-            } else {
-#pragma unroll
-                for (int c = 0; c < 64; c += 8)
-                    *reinterpret_cast<uint4 *>(arow + tc05::kmajor_offset(row, h0 + c, kLBO, kSBO)) =
-                        make_uint4(0, 0, 0, 0);
+            for (int g = 0; g < 8; ++g) {
+                const int r = brow0 + 8 * g, lst = i0 + (r >> kp_log2), sl = r & ((1 << kp_log2) - 1);
+                vg[g] = lst < M && sl < cand_cnt[lbase + (lst < M ? lst : 0)];
+                jg[g] = vg[g] ? cand_idx[un.cand + (int64_t)lst * K + sl] : 0;
             }
+            int tg[8];
+            uint4 qg[8];
+#pragma unroll
+            for (int g = 0; g < 8; ++g) {
+                if (vg[g]) {
+                    tg[g] = sc.t[jg[g]];
+                    qg[g] = __ldg(reinterpret_cast<const uint4 *>(sc.pq + (int64_t)(jg[g] - sc.ucol0) * H + bh0));
+                } else {
+                    tg[g] = 0;
+                    qg[g] = make_uint4(0, 0, 0, 0);
+                }
+            }
+            int plist = -1;
+            float pv[8];
+#pragma unroll
+            for (int g = 0; g < 8; ++g) {
+                const int r = brow0 + 8 * g, lst = i0 + (r >> kp_log2);
+                __align__(16) __nv_bfloat162 hh[4];
+                if (vg[g]) {
+                    if (lst != plist) {   // the row's list: this lane's 8 units of P (rows of a group share it)
+                        const float4 *P4 = reinterpret_cast<const float4 *>(pi.P + (int64_t)(md.urow + lst) * H + bh0);
+                        const float4 pa = __ldg(P4), pb = __ldg(P4 + 1);
+                        pv[0] = pa.x; pv[1] = pa.y; pv[2] = pa.z; pv[3] = pa.w;
+                        pv[4] = pb.x; pv[5] = pb.y; pv[6] = pb.z; pv[7] = pb.w;
+                        plist = lst;
+                    }
+                    const float dt = (float)(tg[g] - md.t[lst] - un.offset);
+                    const __nv_bfloat162 *q2 = reinterpret_cast<const __nv_bfloat162 *>(&qg[g]);
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        const float2 qf = __bfloat1622float2(q2[e]);
+                        const float x0 = fmaxf(fmaf(w1t[2 * e], dt, pv[2 * e] + qf.x), 0.0f);
+                        const float x1 = fmaxf(fmaf(w1t[2 * e + 1], dt, pv[2 * e + 1] + qf.y), 0.0f);
+                        hh[e] = __floats2bfloat162_rn(x0, x1);
+                    }
+                } else {
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) hh[e] = __floats2bfloat162_rn(0.0f, 0.0f);
+                }
+                *reinterpret_cast<uint4 *>(arow + tc05::kmajor_offset(r, bh0, kLBO, kSBO)) =
+                    *reinterpret_cast<uint4 *>(hh);
+            }
+            // this thread's epilogue row
+            const int list = i0 + lsub;
+            const bool valid = list < M && slot < cand_cnt[lbase + (list < M ? list : 0)];
             const int64_t o0 = (half == 0 && list < M && slot < K) ? (lbase + list) * K + slot : -1;
             tc05::fence_proxy_async_smem();
             tc05::fence_before_sync();
@@ -303,7 +330,7 @@ __global__ void __launch_bounds__(256) prop_rescore_kernel(const Unit *__restric
             if (c >= out_cnt[lbase + li]) continue;
             const int64_t o = (lbase + li) * keep + c;
             const int j = out_idx[o];
-            out_u[o] = exact_u(md.f + (int64_t)li * p.F, sc.f + (int64_t)j * p.F, p.F, p.lambda1);
+            out_u[o] = unary_fp32(md.f + (int64_t)li * p.F, sc.f + (int64_t)j * p.F, p.F, p.lambda1);
         }
     }
 }
@@ -329,7 +356,7 @@ __global__ void __launch_bounds__(256) rescore_units_kernel(const Unit *__restri
             const int li = e / K, c = e - li * K;
             if (c >= cand_cnt[lbase + li]) continue;
             const int64_t o = un.cand + e;
-            cand_u[o] = exact_u(md.f + (int64_t)li * p.F, sc.f + (int64_t)cand_idx[o] * p.F, p.F, p.lambda1);
+            cand_u[o] = unary_fp32(md.f + (int64_t)li * p.F, sc.f + (int64_t)cand_idx[o] * p.F, p.F, p.lambda1);
         }
     }
 }
@@ -363,11 +390,12 @@ __global__ void collect_infeasible_kernel(const UnitResult *__restrict__ res, co
 }  // namespace
 
 cudaError_t launch_prop_fold_xy(float *rows, int64_t n, const float *xy, const float *w1c, int dp, float sign,
-                                cudaStream_t st)
+                                void *out_bf16, cudaStream_t st)
 {
     if (n <= 0) return cudaSuccess;
     const int64_t blocks = std::min<int64_t>((n * H + 255) / 256, 8192);
-    fold_xy_kernel<<<(unsigned)blocks, 256, 0, st>>>(rows, n, reinterpret_cast<const float2 *>(xy), w1c, dp, sign);
+    fold_xy_kernel<<<(unsigned)blocks, 256, 0, st>>>(rows, n, reinterpret_cast<const float2 *>(xy), w1c, dp, sign,
+                                                     static_cast<__nv_bfloat16 *>(out_bf16));
     return cudaGetLastError();
 }
 

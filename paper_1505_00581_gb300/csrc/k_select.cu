@@ -13,6 +13,7 @@
 // the threshold plus the first equal ones in index order. Integer decisions
 // therefore depend only on the FP32 keys of kernel (a), bit for bit.
 #include "hgm_internal.cuh"
+#include "unary_common.cuh"
 
 namespace hgm {
 namespace {
@@ -146,14 +147,7 @@ __global__ void __launch_bounds__(kWarps * 32) select_kernel(const Unit *__restr
                     if (bs == lane + 32) kv[1] = __int_as_float(0x7f800000);
                 }
                 if (mine >= 0 && mine < kept) {
-                    const float *a = md.f + (int64_t)i * p.F;
-                    const float *b = sc.f + (int64_t)oidx[mine] * p.F;
-                    float s2 = 0.0f;
-                    for (int k = 0; k < p.F; ++k) {
-                        const float d = __fsub_rn(a[k], b[k]);
-                        s2 = __fmaf_rn(d, d, s2);
-                    }
-                    ou[mine] = __fmul_rn(p.lambda1, __fsqrt_rn(s2));
+                    ou[mine] = unary_fp32(md.f + (int64_t)i * p.F, sc.f + (int64_t)oidx[mine] * p.F, p.F, p.lambda1);
                 }
             }
         }

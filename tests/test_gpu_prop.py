@@ -225,15 +225,16 @@ def _pair_features(mod, sc, m, s, first, idx, cnt, window):
                   (sc.xy[j_c, 1].astype(np.float64) - mod.xy[i_c, 1]) / 100.0,
                   (sc.t[j_c].astype(np.float64) - mod.t[i_c] - o) / float(window)], axis=-1)
     X = np.concatenate([mod.f[i_c].astype(np.float64), sc.f[j_c].astype(np.float64), d], axis=-1)
-    return X[valid], valid
+    return X[valid], valid, mod.xy[i_c][valid].astype(np.float64), sc.xy[j_c][valid].astype(np.float64)
 
 
 @pytest.mark.parametrize("K,window,precision", [(64, 0, 0), (24, 3, 1)])
 def test_scoring_kernel_matches_fp64(env, K, window, precision):
     """The pruning pass's logits (first layer from the per-point projections with the position terms folded
     in, layer 2 on the tensor cores) against the FP64 network on the same candidates: to 2e-3 of the logit
-    range against the emulation that rounds the tensor-core operands to BF16 (the descriptors and W1a/W1b
-    in the projections, h1 and W2 in layer 2); within 5% of the spread against plain FP64. Empty slots are
+    range against the emulation that rounds to BF16 what the kernels round (the descriptors and W1a/W1b in
+    the projections, the scene projection Q once it holds the position terms, h1 and W2 in layer 2); within
+    5% of the spread against plain FP64. Empty slots are
     -inf. K = 64 with w = 0: lists of about 30 candidates (many empty slots); K = 24 with w = 3: full lists,
     four lists of 32 rows (8 of them empty) in each 128-row tile."""
     torch, hgm, _ = env
@@ -261,15 +262,19 @@ def test_scoring_kernel_matches_fp64(env, K, window, precision):
     hgm.prop_scores(prop, m, s, p, first, n, out)
     torch.cuda.synchronize()
     got = out.cpu().numpy()
-    X, valid = _pair_features(mod, sc, m, s, first, idx.cpu().numpy(), cnt.cpu().numpy(), max(window, 1))
+    X, valid, mxy, sxy = _pair_features(mod, sc, m, s, first, idx.cpu().numpy(), cnt.cpu().numpy(),
+                                        max(window, 1))
     assert valid.sum() > 1000 and (window > 0 or (~valid).sum() > 1000)
     assert np.all(got[~valid] == -np.inf)
     g = got[valid]
     assert np.all(np.isfinite(g))
     z64 = mlp.forward(ref, X)["z3"]
     W1 = ref["W1"]
-    z1 = _bf16(X[:, :F]) @ _bf16(W1[:, :F]).T + ref["b1"] + _bf16(X[:, F:2 * F]) @ _bf16(W1[:, F:2 * F]).T \
-        + X[:, 2 * F:] @ W1[:, 2 * F:].T
+    # P per model point (FP32 in the kernel), Q per scene point rounded once to BF16, both with the position
+    # terms folded in; the time term per candidate
+    Pm = _bf16(X[:, :F]) @ _bf16(W1[:, :F]).T + ref["b1"] - (mxy @ W1[:, 2 * F:2 * F + 2].T) / 100.0
+    Qs = _bf16(_bf16(X[:, F:2 * F]) @ _bf16(W1[:, F:2 * F]).T + (sxy @ W1[:, 2 * F:2 * F + 2].T) / 100.0)
+    z1 = Pm + Qs + X[:, 2 * F + 2:] @ W1[:, 2 * F + 2:].T
     z2 = _bf16(np.maximum(z1, 0.0)) @ _bf16(ref["W2"]).T + ref["b2"]
     z_emu = np.maximum(z2, 0.0) @ ref["w3"] + ref["b3"][0]
     assert np.max(np.abs(g - z_emu)) <= 2e-3 * max(1.0, np.max(np.abs(z_emu))), np.max(np.abs(g - z_emu))
