@@ -81,6 +81,8 @@ __global__ void __launch_bounds__(256, 2) prop_score_kernel(const Unit *__restri
     const int lpt = TM >> kp_log2;                                  // lists per tile
     const int lsub = row >> kp_log2, slot = row & ((1 << kp_log2) - 1);
     // build-phase roles
+    // a row's four 16-byte chunks sit on adjacent lanes (measured faster for the gathers than the
+    // bank-conflict-free order of the A-tile stores)
     const int bh0 = 32 * (warp & 3) + 8 * (lane & 3);              // first of this lane's 8 hidden units
     const int brow0 = 64 * (warp >> 2) + (lane >> 2);                // its row in group 0 (+8 per group)
     float w1t[8];                                                    // W1c_t / w for those units
@@ -372,18 +374,40 @@ __global__ void derive_units_kernel(const Unit *__restrict__ in, int64_t n, int 
     }
 }
 
-// Units whose pruned optimum is infeasible, appended to `list` (fallback to the full lists); `total`
-// accumulates their number across calls (read by hgm_prune_counters).
-__global__ void collect_infeasible_kernel(const UnitResult *__restrict__ res, const Unit *__restrict__ units,
-                                          int64_t n, Unit *__restrict__ list, int *__restrict__ count,
-                                          unsigned long long *__restrict__ total)
+// Units whose pruned optimum is infeasible, copied to `list` in their original (longest-first) order: the
+// fallback keeps the batch's load balance. One CTA of 1024 threads scans the flags in blocks of 1024.
+// `count` receives their number, `total` accumulates it across calls (read by hgm_prune_counters).
+__global__ void __launch_bounds__(1024) collect_infeasible_kernel(const UnitResult *__restrict__ res,
+                                                                  const Unit *__restrict__ units, int64_t n,
+                                                                  Unit *__restrict__ list, int *__restrict__ count,
+                                                                  unsigned long long *__restrict__ total)
 {
-    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
-        if (res[k].z1 < 0) {
-            const int at = atomicAdd(count, 1);
-            atomicAdd(total, 1ull);
-            list[at] = units[k];
+    __shared__ int wsum[32];
+    __shared__ int base;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid == 0) base = 0;
+    __syncthreads();
+    for (int64_t k0 = 0; k0 < n; k0 += 1024) {
+        const int64_t k = k0 + tid;
+        const bool f = k < n && res[k].z1 < 0;
+        const unsigned m = __ballot_sync(0xffffffffu, f);
+        if (lane == 0) wsum[warp] = __popc(m);
+        __syncthreads();
+        int before = 0, all = 0;
+        for (int w = 0; w < 32; ++w) {
+            const int c = wsum[w];
+            before += w < warp ? c : 0;
+            all += c;
         }
+        const int b0 = base;
+        if (f) list[b0 + before + __popc(m & ((1u << lane) - 1))] = units[k];
+        __syncthreads();
+        if (tid == 0) base = b0 + all;
+        __syncthreads();
+    }
+    if (tid == 0) {
+        *count = base;
+        atomicAdd(total, (unsigned long long)base);
     }
 }
 
@@ -470,8 +494,7 @@ cudaError_t launch_collect_infeasible(const UnitResult *res, const Unit *units, 
                                       unsigned long long *total, cudaStream_t st)
 {
     if (n <= 0) return cudaSuccess;
-    collect_infeasible_kernel<<<(unsigned)std::min<int64_t>((n + 255) / 256, 4096), 256, 0, st>>>(res, units, n, list,
-                                                                                                  count, total);
+    collect_infeasible_kernel<<<1, 1024, 0, st>>>(res, units, n, list, count, total);
     return cudaGetLastError();
 }
 

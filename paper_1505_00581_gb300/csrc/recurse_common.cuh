@@ -5,6 +5,7 @@
 // produce the same bits for the same inputs.
 #pragma once
 
+#include "f32x2.cuh"
 #include "fast_math.cuh"
 #include "hgm_internal.cuh"
 
@@ -52,37 +53,6 @@ __device__ __forceinline__ float triple_cost(float base, float p1, float p2, flo
     const float w1 = fminf(fabsf(d1), __fsub_rn(kTwoPi, fabsf(d1)));
     const float w2 = fminf(fabsf(d2), __fsub_rn(kTwoPi, fabsf(d2)));
     return __fmaf_rn(lam23, sqrt_fast(__fmaf_rn(w2, w2, __fmul_rn(w1, w1))), base);
-}
-
-// ---- packed FP32 pairs (sm_100-family add/sub/mul/fma .f32x2: per element the same IEEE
-// round-to-nearest operation as the scalar form, two lanes of work per instruction) ----------
-__device__ __forceinline__ unsigned long long pk2(float lo, float hi)
-{
-    unsigned long long r;
-    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
-    return r;
-}
-__device__ __forceinline__ void upk2(unsigned long long r, float &lo, float &hi)
-{
-    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(r));
-}
-__device__ __forceinline__ unsigned long long sub2(unsigned long long a, unsigned long long b)
-{
-    unsigned long long r;
-    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
-    return r;
-}
-__device__ __forceinline__ unsigned long long mul2(unsigned long long a, unsigned long long b)
-{
-    unsigned long long r;
-    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
-    return r;
-}
-__device__ __forceinline__ unsigned long long fma2(unsigned long long a, unsigned long long b, unsigned long long c)
-{
-    unsigned long long r;
-    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
-    return r;
 }
 
 // triple_cost for two cells (same a, b; c and c'): bit-identical to two triple_cost calls.
