@@ -89,7 +89,7 @@ struct Smem {
     // AS = NP (mod 32) and odd multiples are avoided: 65 for one thread per b, 66 for two
     static constexpr int AS = KM + NP;
     float alpha[KM * AS];                 // alpha_{i+1}(a,b) at b*AS + a (then base(a,b)); alpha_i(b,c) at c*AS + b
-    uint8_t fs[KM * KM];                  // slot a of each kept entry
+    uint8_t fs[KM * KM];                  // slot a of each kept entry, | 0x80 when a lies at b's position
     uint8_t fn[KM];                       // number of kept a per b
     uint8_t tile_b[KM * KM / 4];          // b of every tile of the step (tiles of >= 4 cells)
     uint16_t tbase[KM];                   // first tile of b
@@ -138,7 +138,7 @@ __device__ __forceinline__ void argmin_merge(float &v, int &k, float ov, int ok)
 // live in a per-CTA scratch block (beta + blockIdx.x * beta_cta, reused unit
 // after unit), and the CTA backtracks its own unit and writes the energy and
 // the assignment itself.
-template <int KM, int NT, int CT, int NP, bool kCount, bool kFused>
+template <int KM, int NT, int CT, int NP, int UR, bool kCount, bool kFused>
 __global__ void __launch_bounds__(NT, (KM > 32 ? 3 : 4))
 recurse_kernel(const Unit *__restrict__ units, int64_t n_units, const ModelRec *__restrict__ models,
                const SceneRec *__restrict__ scenes, Params p, const int32_t *__restrict__ cand_idx,
@@ -200,6 +200,9 @@ recurse_kernel(const Unit *__restrict__ units, int64_t n_units, const ModelRec *
             List<KM> &LC = sm.list[(i - 2) % 3];
             const float4 g = sm.geo[i & 1];
             const float A1 = g.x, k2 = g.y;
+            // p2 = p1 + k2 uses theta(a->b) = theta(b->a) + pi, which fails for a and b at the same position
+            // (both directions are atan2(0, 0) = 0, reading R1): such entries (flagged in fs) take k2c
+            const float k2c = wrap_pi(__fsub_rn(k2, kPi));
             const int dt_ab = __float_as_int(g.z), dt_bc = __float_as_int(g.w);
             const int na = LA.n, nb = LB.n, nc = LC.n;
 
@@ -307,10 +310,7 @@ recurse_kernel(const Unit *__restrict__ units, int64_t n_units, const ModelRec *
                     }
                 }
                 unsigned long long pmk = 0;
-                if constexpr (NP == 2) {
-                    const unsigned lo32 = __shfl_xor_sync(0xffffffffu, (unsigned)mk, 1);
-                    pmk = lo32;
-                }
+                if constexpr (NP == 2) pmk = __shfl_xor_sync(0xffffffffu, (unsigned)mk, 1);
                 const int kept = __popcll(mk) + __popcll(pmk);
                 float *fbf = reinterpret_cast<float *>(sm.fb);
                 for (unsigned long long m = mk; m; m &= m - 1) {
@@ -319,9 +319,10 @@ recurse_kernel(const Unit *__restrict__ units, int64_t n_units, const ModelRec *
                     int pos = __popcll(mk & ((1ull << k) - 1));
                     if constexpr (NP == 2) pos += __popcll(pmk & ((h ? 2ull << k : 1ull << k) - 1));
                     const int at = fb_at<KM>(b, pos);
+                    const float2 pa = LA.xy[a];
                     fbf[2 * at] = arow[a];
-                    sm.fs[fs_at<KM>(b, pos)] = (uint8_t)a;
-                    fbf[2 * at + 1] = wrap_pi(__fadd_rn(A1, direction(pb, LA.xy[a])));   // p1 = A1 + theta(b->a)
+                    sm.fs[fs_at<KM>(b, pos)] = (uint8_t)(a | (pa.x == pb.x && pa.y == pb.y ? 0x80 : 0));
+                    fbf[2 * at + 1] = wrap_pi(__fadd_rn(A1, direction(pb, pa)));   // p1 = A1 + theta(b->a)
                 }
                 // tiles in decreasing kept count, then increasing b (the lanes of a warp then loop over
                 // similar numbers of a): b's first tile = sum of the tile counts of the b ranked before it
@@ -426,12 +427,13 @@ recurse_kernel(const Unit *__restrict__ units, int64_t n_units, const ModelRec *
 #pragma unroll
                 for (int q = 0; q < CT / 2; ++q) q1p[q] = pk2(q1[2 * q], q1[2 * q + 1]);
                 const unsigned long long lamp = pk2(lam23, lam23);
-#pragma unroll 2
+#pragma unroll UR
                 for (int k = 0; k < nf; ++k) {
                     const float2 e = sm.fb[fb_at<KM>(b, k)];
-                    const int a = sm.fs[fs_at<KM>(b, k)];
+                    const int fa = sm.fs[fs_at<KM>(b, k)];
+                    const int a = fa & 0x7f;
                     if constexpr (kCount) n_eval += CT;
-                    const float p2 = __fadd_rn(e.y, k2);
+                    const float p2 = __fadd_rn(e.y, (fa & 0x80) ? k2c : k2);
                     const unsigned long long bp = pk2(e.x, e.x), p1p = pk2(e.y, e.y), p2p = pk2(p2, p2);
 #pragma unroll
                     for (int q4 = 0; q4 < CT; q4 += 4) {
@@ -516,7 +518,7 @@ struct FusedArgs {
     int32_t *assign = nullptr;
 };
 
-template <int KM, int NT, int CT, int NP, bool kCount, bool kFused>
+template <int KM, int NT, int CT, int NP, int UR, bool kCount, bool kFused>
 cudaError_t launch_recurse_t(const Unit *units, int64_t n_units, const ModelRec *models, const SceneRec *scenes,
                              Params p, const int32_t *cand_idx, const float *cand_u, const int32_t *cand_cnt,
                              uint8_t *beta, UnitResult *res, int *work_counter, unsigned long long *evaluated,
@@ -525,7 +527,7 @@ cudaError_t launch_recurse_t(const Unit *units, int64_t n_units, const ModelRec 
     // three CTAs of 256 threads per SM: 3 x (shared memory + 1 KB reserved) <= 228 KB
     static_assert(KM != 64 || NT != 256 || 3 * (sizeof(Smem<KM, NT, NP>) + 1024) <= 228 * 1024,
                   "recursion shared memory exceeds the three-CTA budget");
-    auto kern = recurse_kernel<KM, NT, CT, NP, kCount, kFused>;
+    auto kern = recurse_kernel<KM, NT, CT, NP, UR, kCount, kFused>;
     const size_t smem = sizeof(Smem<KM, NT, NP>);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -553,22 +555,22 @@ cudaError_t dispatch(int variant, const Unit *units, int64_t n_units, const Mode
                      UnitResult *res, int *work_counter, unsigned long long *evaluated, const FusedArgs &fa,
                      cudaStream_t st)
 {
-#define HGM_RECURSE(KM_, NT_, CT_, NP_)                                                                           \
-    return launch_recurse_t<KM_, NT_, CT_, NP_, kCount, kFused>(units, n_units, models, scenes, p, cand_idx,    \
-                                                                cand_u, cand_cnt, beta, res, work_counter,      \
-                                                                evaluated, fa, st)
+#define HGM_RECURSE(KM_, NT_, CT_, NP_, UR_)                                                                      \
+    return launch_recurse_t<KM_, NT_, CT_, NP_, UR_, kCount, kFused>(units, n_units, models, scenes, p, cand_idx,  \
+                                                                     cand_u, cand_cnt, beta, res, work_counter,   \
+                                                                     evaluated, fa, st)
     if (p.K <= 32) {
-        if (variant == 1) HGM_RECURSE(32, 128, 8, 2);
-        if (variant == 2) HGM_RECURSE(32, 128, 4, 1);
-        HGM_RECURSE(32, 128, 4, 2);
+        if (variant == 1) HGM_RECURSE(32, 128, 8, 2, 2);
+        if (variant == 2) HGM_RECURSE(32, 128, 4, 2, 4);
+        HGM_RECURSE(32, 128, 4, 2, 2);
     }
-    if (variant == 1) HGM_RECURSE(64, 256, 8, 2);
-    if (variant == 2) HGM_RECURSE(64, 256, 4, 1);
-    HGM_RECURSE(64, 256, 4, 2);
+    if (variant == 1) HGM_RECURSE(64, 256, 8, 2, 2);
+    if (variant == 2) HGM_RECURSE(64, 256, 4, 2, 4);
+    HGM_RECURSE(64, 256, 4, 2, 2);
 #undef HGM_RECURSE
 }
 
-int g_variant = 0;   // recursion variant: 0 = 4 c per tile, 1 = 8 c per tile, 2 = 4 c per tile and one list builder per b
+int g_variant = 0;   // recursion variant: 0 = 4 c per tile, 1 = 8 c per tile, 2 = 4 c per tile, triple loop unrolled by 4
 
 }  // namespace
 

@@ -82,6 +82,7 @@ __global__ void __launch_bounds__(kWarps * 32) recurse_small_kernel(
             const float A1 = signed_angle(mj, mi, mk);
             const float A2 = signed_angle(mi, mj, mk);
             const float k2 = wrap_pi(__fadd_rn(__fsub_rn(A2, A1), kPi));
+            const float k2c = wrap_pi(__fsub_rn(k2, kPi));   // a and b at the same position (reading R1)
             const int dt_ab = md.t[i] - md.t[i - 1], dt_bc = md.t[i - 1] - md.t[i - 2];
             for (int e = lane; e < CELLS; e += 32) {
                 const int a = e / KS, x = e % KS;
@@ -115,7 +116,8 @@ __global__ void __launch_bounds__(kWarps * 32) recurse_small_kernel(
                         if (ta < tb || sm.idx[sa][a] == ib) continue;
                         const float base = base_cost(sm.u[sa][a], lam2, dt_ab, ta, tb, sm.alpha[b * AS + a]);
                         const float p1 = wrap_pi(__fadd_rn(A1, sm.thab[a * KS + b]));
-                        const float p2 = __fadd_rn(p1, k2);
+                        const float2 pa = sm.xy[sa][a];
+                        const float p2 = __fadd_rn(p1, pa.x == pb.x && pa.y == pb.y ? k2c : k2);
                         const float v = triple_cost(base, p1, p2, q1, sm.thac[a * KS + c], lam23);
                         if (v < best) { best = v; arg = a; }
                     }

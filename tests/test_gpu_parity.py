@@ -478,3 +478,34 @@ def test_non_finite_descriptors_are_rejected(env, on_device):
     m, s = handles(hgm, mod, sc)
     first, e, a = hgm.match(m, s, hgm.default_params(K=wl.K, window=wl.window))
     assert np.isfinite(e).any()
+
+
+@pytest.mark.parametrize("K", [8, 64])
+def test_coincident_points_follow_the_atan2_reading(env, K):
+    """Points with identical positions (zero-length edges: atan2(0, 0) = 0, reading R1) -- clutter copies on
+    top of implanted points and a model with repeated positions -- give the oracle's energies on every
+    offset (K = 8: the short-list kernel; K = 64: the main kernel)."""
+    torch, hgm, oracle = env
+    rng = np.random.default_rng(31)
+    mod = synth.make_model(rng, 12, frame=(40.0, 30.0))
+    mod.xy[3] = mod.xy[1]
+    mod.xy[7] = mod.xy[6]
+    sc = synth.make_scene(rng, 40, (40.0, 30.0), 4, mod.centres, [mod], [(0, 9)], translate=False, xy_jitter=0.0,
+                          t_jitter=0.0)
+    imp = sc.implants[0].idx
+    extra_xy = sc.xy[imp[::2]].copy()                       # clutter exactly on implant points, same frames
+    extra_t = sc.t[imp[::2]].copy()
+    extra_f = sc.f[imp[::2]] + 0.5 * rng.standard_normal((len(imp[::2]), sc.F)).astype(np.float32)
+    sc = synth.Scene(np.concatenate([sc.xy, extra_xy]), np.concatenate([sc.t, extra_t]),
+                     np.concatenate([sc.f, extra_f]).astype(np.float32), None, sc.n_frames, sc.implants)
+    wl = synth.Workload("coincident", [mod], [sc], K=K, window=1)
+    m, s = handles(hgm, mod, sc, torch)
+    p = hgm.default_params(K=wl.K, window=wl.window)
+    first, e, a = hgm.match(m, s, p)
+    orc = oracle.Oracle.from_workload(wl)
+    for k in range(len(e)):
+        e64, z64, _ = orc.match(first + k)
+        assert np.isfinite(e64) == np.isfinite(e[k])
+        if np.isfinite(e64):
+            assert abs(e[k] - e64) <= 1e-5 * e64 + 1e-6, (k, e[k], e64)
+            assert np.array_equal(a[k], z64) or orc.energy(a[k]) <= e64 * (1 + 1e-5) + 1e-6
