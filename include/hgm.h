@@ -159,6 +159,21 @@ HGM_API hgm_status hgm_match_batch(const hgm_model *const *models, int32_t n_mod
                            int32_t n_scenes, const hgm_params *params, void *stream, float *energy,
                            int32_t *assign);
 
+/* The "independent chains" variant for models with several points per frame
+ * (Sec. 4, multiple points per frame, method 2; Table 4): the model's points
+ * are split into single-point chains -- chain k takes the point of
+ * within-frame rank k (ranked by the caller's index) of every model frame
+ * that has one -- each chain with at least 3 points is solved as its own
+ * model (Eqs. 10-13) over the whole model's offset range, and the matching
+ * distance at an offset is the mean of the chain energies (+inf where any
+ * chain is infeasible). energy [n_offsets], assign [n_offsets x M] (host or
+ * device, or NULL): each model point gets its chain's optimal scene point
+ * (-1 for points of chains shorter than 3). n_chains in 1..255; HGM_EINVAL
+ * if no chain has 3 points. Synchronous. */
+HGM_API hgm_status hgm_match_chains(const hgm_model *model, const hgm_scene *scene, const hgm_params *params,
+                                    int32_t n_chains, void *stream, int32_t *n_offsets, int32_t *first_offset,
+                                    float *energy, int32_t *assign);
+
 /* Completion: hgm_match and hgm_match_batch return once their work is queued
  * on `stream` when both outputs are device pointers and no tensor-core kernel
  * runs (precision 0, no pruning); with a host output, precision 1 or pruning

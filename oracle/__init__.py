@@ -3,4 +3,4 @@
 Importable only from tests/, __graft_entry__.smoke() and bench.py's CPU
 baseline / reference leg. The CUDA library never imports it.
 """
-from .oracle import Oracle, build  # noqa: F401
+from .oracle import ChainOracle, Oracle, build  # noqa: F401

@@ -245,3 +245,45 @@ class Oracle:
         if rc:
             raise ValueError("too many assignments for brute force")
         return float(e[0]), self._to_caller_z(z), int(nt[0])
+
+
+class ChainOracle:
+    """The "independent chains" variant (Sec. 4, multiple points per frame, method 2), FP64: the model's
+    points are grouped by frame; within a frame they are ranked by their index in the caller's arrays, and
+    chain k is the sequence of rank-k points in frame order. Every chain with at least 3 points is an
+    ordinary model for Oracle; the distance at offset o is the mean of the chains' optimal energies
+    (+inf if any chain is infeasible at o), and each model point takes its chain's optimal scene point
+    (-1 for points of chains shorter than 3)."""
+
+    def __init__(self, model_xy, model_t, model_f, scene_xy, scene_t, scene_f, n_frames: int, n_chains: int,
+                 **kw):
+        mt = np.asarray(model_t).astype(np.int64)
+        self.M = len(mt)
+        rank = np.zeros(self.M, np.int64)
+        for fr in np.unique(mt):
+            idx = np.nonzero(mt == fr)[0]            # caller indices of the frame, ascending
+            rank[idx] = np.arange(len(idx))
+        self.members = []
+        for k in range(int(n_chains)):
+            idx = np.nonzero(rank == k)[0]
+            idx = idx[np.argsort(mt[idx], kind="stable")]
+            if len(idx) >= 3:
+                self.members.append(idx)
+        if not self.members:
+            raise ValueError("no chain has 3 points")
+        mxy = np.asarray(model_xy)
+        mf = np.asarray(model_f)
+        self.chains = [Oracle(mxy[idx], mt[idx], mf[idx], scene_xy, scene_t, scene_f, n_frames, **kw)
+                       for idx in self.members]
+        self.first_offset = -int(mt.min())
+        self.n_offsets = max(0, int(n_frames) - int(mt.max() - mt.min()))
+
+    def match(self, o: int):
+        """(mean energy, caller-order assignment of all model points) at offset o."""
+        energies, z = [], np.full(self.M, -1, np.int32)
+        for idx, orc in zip(self.members, self.chains):
+            e, zc, _ = orc.match(o)
+            energies.append(e)
+            z[idx] = zc
+        e = float(np.mean(energies)) if all(np.isfinite(energies)) else float("inf")
+        return e, z

@@ -1090,6 +1090,204 @@ hgm_status hgm_match(const hgm_model *model, const hgm_scene *scene, const hgm_p
     return rc2;
 }
 
+// ---- the "independent chains" variant (Sec. 4, multiple points per frame, method 2) -------------------
+namespace hgm {
+namespace {
+
+__global__ void chain_gather_kernel(const float2 *__restrict__ xy, const int32_t *__restrict__ t,
+                                    const float *__restrict__ f, int Fp, const int32_t *__restrict__ ks, int n,
+                                    float2 *__restrict__ oxy, int32_t *__restrict__ ot, float *__restrict__ of)
+{
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < (int64_t)n * Fp;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int q = (int)(e / Fp), j = (int)(e - (int64_t)q * Fp);
+        const int k = ks[q];
+        of[e] = f[(int64_t)k * Fp + j];
+        if (j == 0) {
+            oxy[q] = xy[k];
+            ot[q] = t[k];
+        }
+    }
+}
+
+// energy[k] = mean of the chains' energies at offset k (+inf if any is infeasible); assignment rows
+// scattered to the model's caller indices (cmap: concatenated chain point -> caller index).
+__global__ void chain_combine_kernel(const float *__restrict__ ce, const int32_t *__restrict__ ca, int n_off,
+                                     int n_chains, const int32_t *__restrict__ cm, const int32_t *__restrict__ cmap,
+                                     int M, float *__restrict__ energy, int32_t *__restrict__ assign)
+{
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n_off; k += gridDim.x * blockDim.x) {
+        if (energy) {
+            float sum = 0.0f;
+            bool fin = true;
+            for (int c = 0; c < n_chains; ++c) {
+                const float v = ce[(int64_t)c * n_off + k];
+                fin = fin && v < __builtin_huge_valf();
+                sum = __fadd_rn(sum, v);
+            }
+            energy[k] = fin ? __fdiv_rn(sum, (float)n_chains) : __builtin_huge_valf();
+        }
+        if (assign) {
+            int32_t *row = assign + (int64_t)k * M;
+            for (int i = 0; i < M; ++i) row[i] = -1;
+            int64_t abase = 0, q0 = 0;
+            for (int c = 0; c < n_chains; ++c) {
+                const int mc = cm[c];
+                for (int q = 0; q < mc; ++q) row[cmap[q0 + q]] = ca[abase + (int64_t)k * mc + q];
+                abase += (int64_t)n_off * mc;
+                q0 += mc;
+            }
+        }
+    }
+}
+
+}  // namespace
+}  // namespace hgm
+
+hgm_status hgm_match_chains(const hgm_model *model, const hgm_scene *scene, const hgm_params *params,
+                            int32_t n_chains, void *stream, int32_t *n_offsets, int32_t *first_offset, float *energy,
+                            int32_t *assign)
+{
+    std::lock_guard<std::mutex> lk(g_mu);
+    g_err.clear();
+    hgm_status rc = check_params(params);
+    if (rc) return rc;
+    if (!valid_model(model) || !valid_scene(scene)) return fail(HGM_EINVAL, "invalid handle");
+    if (model->F_user != scene->F_user) return fail(HGM_EINVAL, "descriptor width differs between model and scene");
+    if (n_chains < 1 || n_chains > 255) return fail(HGM_EINVAL, "n_chains must be in 1..255 (got %d)", n_chains);
+    cudaStream_t st = (cudaStream_t)stream;
+    int32_t n, f;
+    pair_offsets(model, scene, params, &n, &f);
+    if (n_offsets) *n_offsets = n;
+    if (first_offset) *first_offset = f;
+    if ((!energy && !assign) || n == 0) return HGM_OK;
+    // chain c: the point of within-frame rank c (caller order) of every frame that has one
+    const int M = model->d.M;
+    std::vector<int32_t> rank((size_t)M);
+    for (int k = 0; k < M;) {
+        int e = k;
+        while (e < M && model->t_sorted[(size_t)e] == model->t_sorted[(size_t)k]) ++e;
+        std::vector<int32_t> ord;
+        for (int q = k; q < e; ++q) ord.push_back(q);
+        std::sort(ord.begin(), ord.end(), [&](int32_t x, int32_t y) { return model->perm[(size_t)x] < model->perm[(size_t)y]; });
+        for (size_t r = 0; r < ord.size(); ++r) rank[(size_t)ord[r]] = (int32_t)r;
+        k = e;
+    }
+    std::vector<std::vector<int32_t>> members;
+    for (int c = 0; c < n_chains; ++c) {
+        std::vector<int32_t> ks;
+        for (int k = 0; k < M; ++k)
+            if (rank[(size_t)k] == c) ks.push_back(k);
+        if (ks.size() >= 3) members.push_back(ks);
+    }
+    if (members.empty()) return fail(HGM_EINVAL, "no chain of the model has 3 points");
+    const int nc = (int)members.size();
+    // chain models: frame-sorted already (one point per frame), identity order
+    std::vector<hgm_model *> chains;
+    auto release = [&]() {
+        cudaStreamSynchronize(st);
+        for (hgm_model *cm : chains) {
+            free_model(cm);
+            delete cm;
+        }
+    };
+    std::vector<int32_t> cm_sizes, cmap;
+    const int Fp = model->d.F;
+    for (const auto &ks : members) {
+        hgm_model *cmdl = new hgm_model();
+        chains.push_back(cmdl);
+        const int mc = (int)ks.size();
+        cmdl->magic = kModelMagic;
+        cmdl->d = ModelDev{mc, Fp, nullptr, nullptr, nullptr, nullptr, nullptr};
+        cmdl->F_user = model->F_user;
+        std::vector<int32_t> ident((size_t)mc);
+        for (int q = 0; q < mc; ++q) {
+            ident[(size_t)q] = q;
+            cmdl->t_sorted.push_back(model->t_sorted[(size_t)ks[(size_t)q]]);
+            cmap.push_back(model->perm[(size_t)ks[(size_t)q]]);
+        }
+        cmdl->perm = ident;
+        cm_sizes.push_back(mc);
+        cudaError_t e = cudaSuccess;
+        int32_t *dks = nullptr;
+        if (e == cudaSuccess) e = cudaMalloc((void **)&cmdl->d.xy, (size_t)mc * sizeof(float2));
+        if (e == cudaSuccess) e = cudaMalloc((void **)&cmdl->d.t, (size_t)mc * sizeof(int32_t));
+        if (e == cudaSuccess) e = cudaMalloc((void **)&cmdl->d.f, (size_t)mc * Fp * sizeof(float));
+        if (e == cudaSuccess) e = cudaMalloc((void **)&cmdl->d.perm, (size_t)mc * sizeof(int32_t));
+        if (e == cudaSuccess) e = cudaMalloc((void **)&cmdl->d.geo, (size_t)mc * sizeof(float4));
+        if (e == cudaSuccess) e = cudaMalloc((void **)&dks, (size_t)mc * sizeof(int32_t));
+        if (e == cudaSuccess) e = cudaMemcpyAsync(dks, ks.data(), (size_t)mc * sizeof(int32_t), cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(cmdl->d.perm, ident.data(), (size_t)mc * sizeof(int32_t), cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess) {
+            chain_gather_kernel<<<(unsigned)std::min<int64_t>(((int64_t)mc * Fp + 255) / 256, 4096), 256, 0, st>>>(
+                model->d.xy, model->d.t, model->d.f, Fp, dks, mc, cmdl->d.xy, cmdl->d.t, cmdl->d.f);
+            e = cudaGetLastError();
+        }
+        if (e == cudaSuccess) e = launch_model_geo(cmdl->d.xy, cmdl->d.t, mc, cmdl->d.geo, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        cudaFree(dks);
+        if (e != cudaSuccess) {
+            release();
+            return cuda_fail(e, "chain models");
+        }
+    }
+    // every chain over the whole model's offsets (each chain's own range contains them)
+    hgm_params pc = *params;
+    pc.offset_lo = f;
+    pc.offset_hi = f + n - 1;
+    int64_t total_a = 0;
+    for (int mc : cm_sizes) total_a += (int64_t)n * mc;
+    float *ce = nullptr;
+    int32_t *ca = nullptr, *dcm = nullptr, *dmap = nullptr;
+    float *oe = nullptr;
+    int32_t *oa = nullptr;
+    const bool e_dev = energy && is_device_ptr(energy), a_dev = assign && is_device_ptr(assign);
+    cudaError_t e = cudaMalloc((void **)&ce, (size_t)nc * n * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc((void **)&ca, (size_t)total_a * sizeof(int32_t));
+    if (e == cudaSuccess) e = cudaMalloc((void **)&dcm, (size_t)nc * sizeof(int32_t));
+    if (e == cudaSuccess) e = cudaMalloc((void **)&dmap, cmap.size() * sizeof(int32_t));
+    if (e == cudaSuccess && energy && !e_dev) e = cudaMalloc((void **)&oe, (size_t)n * sizeof(float));
+    if (e == cudaSuccess && assign && !a_dev) e = cudaMalloc((void **)&oa, (size_t)n * M * sizeof(int32_t));
+    auto free_tmp = [&]() {
+        cudaStreamSynchronize(st);
+        cudaFree(ce);
+        cudaFree(ca);
+        cudaFree(dcm);
+        cudaFree(dmap);
+        cudaFree(oe);
+        cudaFree(oa);
+    };
+    if (e != cudaSuccess) {
+        free_tmp();
+        release();
+        return cuda_fail(e, "chain buffers");
+    }
+    Exec ex;
+    rc = run_batch(ex, const_cast<const hgm_model *const *>(chains.data()), nc, &scene, 1, &pc, st, ce, ca);
+    g_pruned_units += ex.pruned_units;
+    if (!rc) {
+        e = cudaMemcpyAsync(dcm, cm_sizes.data(), (size_t)nc * sizeof(int32_t), cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(dmap, cmap.data(), cmap.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st);
+        float *de = energy ? (e_dev ? energy : oe) : nullptr;
+        int32_t *da = assign ? (a_dev ? assign : oa) : nullptr;
+        if (e == cudaSuccess) {
+            chain_combine_kernel<<<(unsigned)std::min<int64_t>((n + 127) / 128, 4096), 128, 0, st>>>(
+                ce, ca, n, nc, dcm, dmap, M, de, da);
+            e = cudaGetLastError();
+        }
+        if (e == cudaSuccess && energy && !e_dev)
+            e = cudaMemcpyAsync(energy, oe, (size_t)n * sizeof(float), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess && assign && !a_dev)
+            e = cudaMemcpyAsync(assign, oa, (size_t)n * M * sizeof(int32_t), cudaMemcpyDeviceToHost, st);
+        if (e != cudaSuccess) rc = cuda_fail(e, "chain combine");
+    }
+    free_tmp();
+    release();
+    return rc;
+}
+
 hgm_status hgm_match_batch(const hgm_model *const *models, int32_t n_models, const hgm_scene *const *scenes,
                            int32_t n_scenes, const hgm_params *params, void *stream, float *energy, int32_t *assign)
 {

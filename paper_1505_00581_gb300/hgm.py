@@ -66,6 +66,7 @@ SIGNATURES = {
     "hgm_plan_run": (_i32, [_vp, _vp]),
     "hgm_plan_check": (_i32, [_vp, _vp]),
     "hgm_prop_scores": (_i32, [_vp, _vp, _vp, _vp, _i32, _i32, _vp, _vp]),
+    "hgm_match_chains": (_i32, [_vp, _vp, _PP, _i32, _vp, _p32, _p32, _vp, _vp]),
     "hgm_model_order": (_i32, [_vp, _p32]),
     "hgm_scene_order": (_i32, [_vp, _p32]),
     "hgm_unary": (_i32, [_vp, _vp, _f32, _vp, _vp]),
@@ -308,6 +309,21 @@ def match(model: Model, scene: Scene, params: Params, energy=None, assign=None, 
     nn, ff = ctypes.c_int32(), ctypes.c_int32()
     _check(lib.hgm_match(model.handle, scene.handle, ctypes.byref(params), _stream(stream), ctypes.byref(nn),
                          ctypes.byref(ff), pe, pa))
+    return first, ke if energy is not None else None, ka if assign is not None else None
+
+
+def match_chains(model: Model, scene: Scene, params: Params, n_chains: int, energy=None, assign=None, stream=None):
+    """hgm_match_chains: the mean energy of the model's single-point chains per offset and the union of their
+    assignments. Returns (first_offset, energy, assign) like match()."""
+    lib = load()
+    first, n = offsets(model, scene, params)
+    if energy is None and assign is None:
+        energy = np.zeros(n, np.float32)
+        assign = np.zeros((n, model.M), np.int32)
+    (pe, ke), (pa, ka) = _ptr(energy), _ptr(assign)
+    nn, ff = ctypes.c_int32(), ctypes.c_int32()
+    _check(lib.hgm_match_chains(model.handle, scene.handle, ctypes.byref(params), int(n_chains), _stream(stream),
+                                ctypes.byref(nn), ctypes.byref(ff), pe, pa))
     return first, ke if energy is not None else None, ka if assign is not None else None
 
 
