@@ -217,6 +217,39 @@ def _time_form(torch, hgm, models, scenes, p, energy, assign, steps, warmup, str
     return sum(a.elapsed_time(b) for a, b in zip(starts, ends)) / steps, hgm.profile_read()
 
 
+def run_chains(args, torch, hgm, wl, models, scenes, dev, stream, world, flush, dist=None, n_chains=3):
+    """The independent-chains variant (Sec. 4, method 2) on the same workload, whose models hold several
+    points per frame: every model split into its within-frame-rank chains, all chains of all models run
+    as one exact batch, the per-offset energy the mean over a model's chains."""
+    p = hgm.default_params(K=wl.K, window=wl.window, T=wl.T)
+    _, es, as_ = hgm.batch_layout(models, scenes, p)
+    e = torch.empty(int(es[-1]), dtype=torch.float32, device=dev)
+    a = torch.empty(int(as_[-1]), dtype=torch.int32, device=dev)
+    for _ in range(args.warmup):
+        hgm.match_chains_batch(models, scenes, p, n_chains, e, a)
+    torch.cuda.synchronize()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    for k in range(args.steps):
+        flush.zero_()
+        starts[k].record(stream)
+        hgm.match_chains_batch(models, scenes, p, n_chains, e, a)
+        ends[k].record(stream)
+    torch.cuda.synchronize()
+    ms = max_over_ranks(sum(x.elapsed_time(y) for x, y in zip(starts, ends)) / args.steps, dist, dev)
+    covered = total = n_chain_models = 0
+    for m in wl.models:
+        _, counts = np.unique(m.t, return_counts=True)
+        total += m.n
+        sizes = [int((counts > c).sum()) for c in range(n_chains)]
+        covered += sum(z for z in sizes if z >= 3)
+        n_chain_models += sum(1 for z in sizes if z >= 3)
+    fin = torch.isfinite(e).sum().item()
+    return {"value": job_rate(wl.total_frames, world, ms / 1e3), "unit": "frames/s", "ms_per_step": ms,
+            "n_chains": n_chains, "chain_models": n_chain_models, "model_points_covered": covered / max(total, 1),
+            "finite_offsets": int(fin), "form": "plain exact FP32 per chain, mean over chains"}
+
+
 def run_pruned(args, torch, hgm, wl, models, scenes, energy, assign, es, as_, dev, stream, world, dist=None):
     """The pruned + BF16 form on the same workload: BF16 tensor-core unary table, the proposal network
     keeps 8 of the 64 candidates per list, recursion on the short lists, exact fallback for infeasible
@@ -286,6 +319,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-graph", action="store_true", help="skip the CUDA-graph replay lines")
     ap.add_argument("--no-pruned", action="store_true", help="skip the pruned+BF16 form")
+    ap.add_argument("--no-chains", action="store_true", help="skip the independent-chains variant")
     ap.add_argument("--train-steps", type=int, default=2000)
     ap.add_argument("--checkpoint", default=None, help="load the proposal network from <path>.bin/.json")
     args = ap.parse_args()
@@ -438,6 +472,10 @@ def main():
                "sample": f"{n} seeded units of {total_units(wl)} ({t:.1f} s on {threads} threads), "
                          f"projected to the whole workload"}
 
+    chains = None
+    if not args.no_chains:
+        chains = run_chains(args, torch, hgm, wl, models, scenes, dev, stream, world, flush, dist)
+
     pruned = None
     if not args.no_pruned:
         pruned = run_pruned(args, torch, hgm, wl, models, scenes, energy, assign, es, as_, dev, stream, world, dist)
@@ -454,7 +492,8 @@ def main():
                            "recurse_variant": variant, "autotune_ms": variant_ms,
                            "parallelism": f"replicas x{world}"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "graph": graph, "gpu_launches": launches,
-                "clocks": clk_sum, "finite_offsets": int(fin), "pruned_bf16": pruned}
+                "clocks": clk_sum, "finite_offsets": int(fin), "pruned_bf16": pruned,
+                "chains": chains}
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()

@@ -164,15 +164,28 @@ HGM_API hgm_status hgm_match_batch(const hgm_model *const *models, int32_t n_mod
  * are split into single-point chains -- chain k takes the point of
  * within-frame rank k (ranked by the caller's index) of every model frame
  * that has one -- each chain with at least 3 points is solved as its own
- * model (Eqs. 10-13) over the whole model's offset range, and the matching
- * distance at an offset is the mean of the chain energies (+inf where any
- * chain is infeasible). energy [n_offsets], assign [n_offsets x M] (host or
- * device, or NULL): each model point gets its chain's optimal scene point
- * (-1 for points of chains shorter than 3). n_chains in 1..255; HGM_EINVAL
- * if no chain has 3 points. Synchronous. */
+ * model (Eqs. 10-13) over the whole model's offset range (the same offsets
+ * as hgm_match), and the matching distance at an offset is the mean of the
+ * chain energies, summed in chain order in FP32 (+inf where any chain is
+ * infeasible). energy [n_offsets], assign [n_offsets x M] (host or device,
+ * or NULL): each model point gets its chain's optimal scene point (-1 for
+ * points of chains shorter than 3, and for the whole row where a chain is
+ * infeasible). n_chains in 1..255; HGM_EINVAL if no chain of the model has
+ * 3 points. The split is kept on the model handle (rebuilt when n_chains
+ * changes; the first call for a model and n_chains synchronises the stream).
+ * Completion as for hgm_match. */
 HGM_API hgm_status hgm_match_chains(const hgm_model *model, const hgm_scene *scene, const hgm_params *params,
                                     int32_t n_chains, void *stream, int32_t *n_offsets, int32_t *first_offset,
                                     float *energy, int32_t *assign);
+
+/* hgm_match_chains for every (model, scene) pair of a batch in one pass: all
+ * chains of all models are run as one hgm_match_batch, then combined per pair.
+ * energy and assign use the layout of hgm_batch_layout for the same models,
+ * scenes and params. Completion as for hgm_match_batch. */
+HGM_API hgm_status hgm_match_chains_batch(const hgm_model *const *models, int32_t n_models,
+                                          const hgm_scene *const *scenes, int32_t n_scenes,
+                                          const hgm_params *params, int32_t n_chains, void *stream, float *energy,
+                                          int32_t *assign);
 
 /* Completion: hgm_match and hgm_match_batch return once their work is queued
  * on `stream` when both outputs are device pointers and no tensor-core kernel

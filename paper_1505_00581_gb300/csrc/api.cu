@@ -149,6 +149,7 @@ struct Workspace {
     Buffer stage, perm_stage, flag;   // inputs of hgm_create_model / hgm_create_scene
     Buffer P, Q, Qb, modelxy, cand2_idx, cand2_u, cand2_cnt, units2, beta2, fb_units, fb_count, beta_fb, scores;
     Buffer fb_total;   // fallback units since the last hgm_prune_counters reset (device counter)
+    Buffer chain_e, chain_a, chain_tab, chain_oe, chain_oa;   // independent-chains variant
 };
 Workspace g_ws;
 bool g_count_mode = false;   // hgm_profile_enable(2): batch runs use the accounting recursion variant
@@ -316,7 +317,7 @@ Params to_params(const hgm_params *p)
 // Offset range of a pair: o in [-t_1, F_s-1-t_M] intersected with [offset_lo, offset_hi].
 void pair_offsets(const hgm_model *m, const hgm_scene *s, const hgm_params *p, int32_t *n, int32_t *first)
 {
-    int64_t t1 = m->t_sorted.front(), tM = m->t_sorted.back();
+    int64_t t1 = m->span_t1, tM = m->span_tM;
     int64_t lo = -t1, hi = (int64_t)s->d.n_frames - 1 - tM;
     lo = std::max<int64_t>(lo, p->offset_lo);
     hi = std::min<int64_t>(hi, p->offset_hi);
@@ -334,6 +335,12 @@ hgm_status sort_points(const std::vector<int32_t> &t, std::vector<int32_t> &perm
 
 void free_model(hgm_model *m)
 {
+    for (hgm_model *c : m->chains) {
+        free_model(c);
+        delete c;
+    }
+    m->chains.clear();
+    m->chain_n = 0;
     cudaFree(m->d.xy);
     cudaFree(m->d.t);
     cudaFree(m->d.f);
@@ -919,6 +926,8 @@ hgm_status hgm_create_model(const float *xy, const int32_t *t, const float *desc
     m->F_user = F;
     m->t_sorted = stt;
     m->perm = perm;
+    m->span_t1 = stt.front();
+    m->span_tM = stt.back();
     if ((rc = upload(&m->d.xy, sxy, st)) || (rc = upload(&m->d.t, stt, st)) ||
         (rc = upload_sorted_rows(desc, M, F, Fp, perm, &m->d.f, "model", st)) ||
         (rc = upload(&m->d.perm, perm, st))) {
@@ -1110,35 +1119,227 @@ __global__ void chain_gather_kernel(const float2 *__restrict__ xy, const int32_t
     }
 }
 
-// energy[k] = mean of the chains' energies at offset k (+inf if any is infeasible); assignment rows
-// scattered to the model's caller indices (cmap: concatenated chain point -> caller index).
-__global__ void chain_combine_kernel(const float *__restrict__ ce, const int32_t *__restrict__ ca, int n_off,
-                                     int n_chains, const int32_t *__restrict__ cm, const int32_t *__restrict__ cmap,
-                                     int M, float *__restrict__ energy, int32_t *__restrict__ assign)
+// One (model, scene) pair of a chains batch: its outputs, and its chains' results in the chain batch.
+struct ChainPair {
+    int64_t e0, a0;      // first energy / assignment element of the pair in the caller's outputs
+    int32_t n, M;        // offsets of the pair, points of the model
+    int32_t nc, c0;      // chains of the model, first ChainRef of the pair
+    int32_t map0, pad;   // first chain_map entry of the model
+};
+struct ChainRef {
+    int64_t ce0, ca0;    // the chain's first energy / assignment element in the chain batch
+    int32_t mc, pad;     // points of the chain
+};
+
+// energy[k] = mean of the chains' energies at offset k, summed in chain order (+inf if any is infeasible);
+// assignment rows scattered to the model's caller indices (map: concatenated chain point -> caller index).
+__global__ void chain_combine_kernel(const ChainPair *__restrict__ pairs, int n_pairs,
+                                     const ChainRef *__restrict__ refs, const int32_t *__restrict__ map,
+                                     const float *__restrict__ ce, const int32_t *__restrict__ ca,
+                                     float *__restrict__ energy, int32_t *__restrict__ assign)
 {
-    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n_off; k += gridDim.x * blockDim.x) {
-        if (energy) {
-            float sum = 0.0f;
-            bool fin = true;
-            for (int c = 0; c < n_chains; ++c) {
-                const float v = ce[(int64_t)c * n_off + k];
-                fin = fin && v < __builtin_huge_valf();
-                sum = __fadd_rn(sum, v);
+    for (int q = blockIdx.y; q < n_pairs; q += gridDim.y) {
+        const ChainPair pr = pairs[q];
+        for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < pr.n; k += gridDim.x * blockDim.x) {
+            if (energy) {
+                float sum = 0.0f;
+                bool fin = true;
+                for (int c = 0; c < pr.nc; ++c) {
+                    const float v = ce[refs[pr.c0 + c].ce0 + k];
+                    fin = fin && v < __builtin_huge_valf();
+                    sum = __fadd_rn(sum, v);
+                }
+                energy[pr.e0 + k] = fin ? __fdiv_rn(sum, (float)pr.nc) : __builtin_huge_valf();
             }
-            energy[k] = fin ? __fdiv_rn(sum, (float)n_chains) : __builtin_huge_valf();
-        }
-        if (assign) {
-            int32_t *row = assign + (int64_t)k * M;
-            for (int i = 0; i < M; ++i) row[i] = -1;
-            int64_t abase = 0, q0 = 0;
-            for (int c = 0; c < n_chains; ++c) {
-                const int mc = cm[c];
-                for (int q = 0; q < mc; ++q) row[cmap[q0 + q]] = ca[abase + (int64_t)k * mc + q];
-                abase += (int64_t)n_off * mc;
-                q0 += mc;
+            if (assign) {
+                int32_t *row = assign + pr.a0 + (int64_t)k * pr.M;
+                for (int i = 0; i < pr.M; ++i) row[i] = -1;
+                int m0 = pr.map0;
+                for (int c = 0; c < pr.nc; ++c) {
+                    const ChainRef r = refs[pr.c0 + c];
+                    const int32_t *src = ca + r.ca0 + (int64_t)k * r.mc;
+                    for (int i = 0; i < r.mc; ++i) row[map[m0 + i]] = src[i];
+                    m0 += r.mc;
+                }
             }
         }
     }
+}
+
+// Splits model m into its chains (chain k: the point of within-frame rank k, ranked by caller index, of every
+// model frame that has one; chains with fewer than 3 points are dropped) and keeps them on the model.
+hgm_status build_chains(const hgm_model *m, int n_chains, int index, cudaStream_t st)
+{
+    if (m->chain_n == n_chains) return HGM_OK;
+    if (!m->chains.empty()) {
+        CK(cudaDeviceSynchronize(), "synchronise before replacing a chain split");
+        for (hgm_model *c : m->chains) {
+            free_model(c);
+            delete c;
+        }
+        m->chains.clear();
+        m->chain_map.clear();
+        m->chain_n = 0;
+    }
+    const int M = m->d.M;
+    std::vector<int32_t> rank((size_t)M);
+    for (int k = 0; k < M;) {
+        int e = k;
+        while (e < M && m->t_sorted[(size_t)e] == m->t_sorted[(size_t)k]) ++e;
+        std::vector<int32_t> ord;
+        for (int q = k; q < e; ++q) ord.push_back(q);
+        std::sort(ord.begin(), ord.end(), [&](int32_t x, int32_t y) { return m->perm[(size_t)x] < m->perm[(size_t)y]; });
+        for (size_t r = 0; r < ord.size(); ++r) rank[(size_t)ord[r]] = (int32_t)r;
+        k = e;
+    }
+    std::vector<std::vector<int32_t>> members;
+    for (int c = 0; c < n_chains; ++c) {
+        std::vector<int32_t> ks;
+        for (int k = 0; k < M; ++k)
+            if (rank[(size_t)k] == c) ks.push_back(k);
+        if (ks.size() >= 3) members.push_back(ks);
+    }
+    if (members.empty()) return fail(HGM_EINVAL, "models[%d]: no chain has 3 points", index);
+    const int Fp = m->d.F;
+    std::vector<hgm_model *> chains;
+    std::vector<int32_t> map;
+    cudaError_t e = cudaSuccess;
+    int32_t *dks = nullptr;
+    if (e == cudaSuccess) e = cudaMalloc((void **)&dks, (size_t)M * sizeof(int32_t));
+    for (const auto &ks : members) {
+        if (e != cudaSuccess) break;
+        hgm_model *cm = new hgm_model();
+        chains.push_back(cm);
+        const int mc = (int)ks.size();
+        cm->magic = kModelMagic;
+        cm->d = ModelDev{mc, Fp, nullptr, nullptr, nullptr, nullptr, nullptr};
+        cm->F_user = m->F_user;
+        std::vector<int32_t> ident((size_t)mc);
+        for (int q = 0; q < mc; ++q) {
+            ident[(size_t)q] = q;
+            cm->t_sorted.push_back(m->t_sorted[(size_t)ks[(size_t)q]]);
+            map.push_back(m->perm[(size_t)ks[(size_t)q]]);
+        }
+        cm->perm = ident;     // one point per frame, already in frame order
+        cm->span_t1 = m->span_t1;
+        cm->span_tM = m->span_tM;
+        if (e == cudaSuccess) e = cudaMalloc((void **)&cm->d.xy, (size_t)mc * sizeof(float2));
+        if (e == cudaSuccess) e = cudaMalloc((void **)&cm->d.t, (size_t)mc * sizeof(int32_t));
+        if (e == cudaSuccess) e = cudaMalloc((void **)&cm->d.f, (size_t)mc * Fp * sizeof(float));
+        if (e == cudaSuccess) e = cudaMalloc((void **)&cm->d.perm, (size_t)mc * sizeof(int32_t));
+        if (e == cudaSuccess) e = cudaMalloc((void **)&cm->d.geo, (size_t)mc * sizeof(float4));
+        if (e == cudaSuccess) e = cudaMemcpyAsync(dks, ks.data(), (size_t)mc * sizeof(int32_t), cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(cm->d.perm, ident.data(), (size_t)mc * sizeof(int32_t), cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess) {
+            chain_gather_kernel<<<(unsigned)std::min<int64_t>(((int64_t)mc * Fp + 255) / 256, 4096), 256, 0, st>>>(
+                m->d.xy, m->d.t, m->d.f, Fp, dks, mc, cm->d.xy, cm->d.t, cm->d.f);
+            e = cudaGetLastError();
+        }
+        if (e == cudaSuccess) e = launch_model_geo(cm->d.xy, cm->d.t, mc, cm->d.geo, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);   // dks and ident are reused / released
+    }
+    cudaFree(dks);
+    if (e != cudaSuccess) {
+        cudaStreamSynchronize(st);
+        for (hgm_model *c : chains) {
+            free_model(c);
+            delete c;
+        }
+        return cuda_fail(e, "chain models");
+    }
+    m->chains = chains;
+    m->chain_map = map;
+    m->chain_n = n_chains;
+    return HGM_OK;
+}
+
+hgm_status run_chains(const hgm_model *const *models, int nm, const hgm_scene *const *scenes, int ns,
+                      const hgm_params *params, int n_chains, cudaStream_t st, float *energy, int32_t *assign)
+{
+    hgm_status rc = check_params(params);
+    if (rc) return rc;
+    if (n_chains < 1 || n_chains > 255) return fail(HGM_EINVAL, "n_chains must be in 1..255 (got %d)", n_chains);
+    if (nm < 0 || ns < 0 || (nm && !models) || (ns && !scenes)) return fail(HGM_EINVAL, "bad model/scene arrays");
+    Plan pl;
+    if ((rc = build_plan(models, nm, scenes, ns, params, pl))) return rc;
+    if (pl.e_start.back() == 0 || (!energy && !assign)) return HGM_OK;
+    for (int m = 0; m < nm; ++m)
+        if ((rc = build_chains(models[m], n_chains, m, st))) return rc;
+    // the chain batch: every model's chains, in model order
+    std::vector<const hgm_model *> cms;
+    std::vector<int32_t> cbase((size_t)nm), map_start((size_t)nm);
+    std::vector<int32_t> map;
+    for (int m = 0; m < nm; ++m) {
+        cbase[(size_t)m] = (int32_t)cms.size();
+        map_start[(size_t)m] = (int32_t)map.size();
+        for (hgm_model *c : models[m]->chains) cms.push_back(c);
+        map.insert(map.end(), models[m]->chain_map.begin(), models[m]->chain_map.end());
+    }
+    const int NC = (int)cms.size();
+    Plan cpl;
+    if ((rc = build_plan(cms.data(), NC, scenes, ns, params, cpl))) return rc;
+    std::vector<ChainPair> pairs;
+    std::vector<ChainRef> refs;
+    for (int m = 0; m < nm; ++m)
+        for (int s = 0; s < ns; ++s) {
+            const size_t q = (size_t)m * ns + s;
+            const int32_t n = (int32_t)(pl.e_start[q + 1] - pl.e_start[q]);
+            if (n == 0) continue;
+            const int nc = (int)models[m]->chains.size();
+            pairs.push_back(ChainPair{pl.e_start[q], pl.a_start[q], n, models[m]->d.M, nc, (int32_t)refs.size(),
+                                      map_start[(size_t)m], 0});
+            for (int c = 0; c < nc; ++c) {
+                const size_t cq = (size_t)(cbase[(size_t)m] + c) * ns + s;
+                if (cpl.e_start[cq + 1] - cpl.e_start[cq] != n)
+                    return fail(HGM_ECUDA, "chain offset range differs from its model's");
+                refs.push_back(ChainRef{cpl.e_start[cq], cpl.a_start[cq], cms[(size_t)(cbase[(size_t)m] + c)]->d.M, 0});
+            }
+        }
+    Workspace &ws = g_ws;
+    const int64_t n_e = cpl.e_start.back(), n_a = cpl.a_start.back();
+    const size_t b_pairs = (pairs.size() * sizeof(ChainPair) + 255) & ~(size_t)255;
+    const size_t b_refs = (refs.size() * sizeof(ChainRef) + 255) & ~(size_t)255;
+    CK(ws.chain_e.ensure((size_t)n_e * sizeof(float)), "workspace (chains)");
+    CK(ws.chain_a.ensure((size_t)n_a * sizeof(int32_t)), "workspace (chains)");
+    CK(ws.chain_tab.ensure(b_pairs + b_refs + map.size() * sizeof(int32_t)), "workspace (chains)");
+    // chain results on the device (the chain batch fills every chain energy and assignment)
+    Exec ex;
+    rc = run_batch(ex, cms.data(), NC, scenes, ns, params, st, ws.chain_e.as<float>(), ws.chain_a.as<int32_t>());
+    g_pruned_units += ex.pruned_units;
+    if (rc) return rc;
+    char *tab = ws.chain_tab.as<char>();
+    if ((rc = h2d(ex, tab, pairs.data(), pairs.size() * sizeof(ChainPair), st)) ||
+        (rc = h2d(ex, tab + b_pairs, refs.data(), refs.size() * sizeof(ChainRef), st)) ||
+        (rc = h2d(ex, tab + b_pairs + b_refs, map.data(), map.size() * sizeof(int32_t), st)))
+        return rc;
+    const bool e_dev = energy && is_device_ptr(energy), a_dev = assign && is_device_ptr(assign);
+    const int64_t n_out = pl.e_start.back(), n_assign = pl.a_start.back();
+    float *de = energy;
+    int32_t *da = assign;
+    if (energy && !e_dev) {
+        CK(ws.chain_oe.ensure((size_t)n_out * sizeof(float)), "workspace (chains)");
+        de = ws.chain_oe.as<float>();
+    }
+    if (assign && !a_dev) {
+        CK(ws.chain_oa.ensure((size_t)n_assign * sizeof(int32_t)), "workspace (chains)");
+        da = ws.chain_oa.as<int32_t>();
+    }
+    int32_t max_n = 0;
+    for (const ChainPair &pr : pairs) max_n = std::max(max_n, pr.n);
+    const dim3 grid((unsigned)std::min<int64_t>((max_n + 127) / 128, 1024),
+                    (unsigned)std::min<size_t>(std::max<size_t>(pairs.size(), 1), 65535));
+    chain_combine_kernel<<<grid, 128, 0, st>>>(reinterpret_cast<const ChainPair *>(tab), (int)pairs.size(),
+                                               reinterpret_cast<const ChainRef *>(tab + b_pairs),
+                                               reinterpret_cast<const int32_t *>(tab + b_pairs + b_refs),
+                                               ws.chain_e.as<float>(), ws.chain_a.as<int32_t>(), de, da);
+    CK(cudaGetLastError(), "chain combine");
+    if (energy && !e_dev)
+        CK(cudaMemcpyAsync(energy, de, (size_t)n_out * sizeof(float), cudaMemcpyDeviceToHost, st), "copy energy");
+    if (assign && !a_dev)
+        CK(cudaMemcpyAsync(assign, da, (size_t)n_assign * sizeof(int32_t), cudaMemcpyDeviceToHost, st), "copy assign");
+    if ((energy && !e_dev) || (assign && !a_dev)) CK(cudaStreamSynchronize(st), "synchronise outputs");
+    return HGM_OK;
 }
 
 }  // namespace
@@ -1155,137 +1356,20 @@ hgm_status hgm_match_chains(const hgm_model *model, const hgm_scene *scene, cons
     if (!valid_model(model) || !valid_scene(scene)) return fail(HGM_EINVAL, "invalid handle");
     if (model->F_user != scene->F_user) return fail(HGM_EINVAL, "descriptor width differs between model and scene");
     if (n_chains < 1 || n_chains > 255) return fail(HGM_EINVAL, "n_chains must be in 1..255 (got %d)", n_chains);
-    cudaStream_t st = (cudaStream_t)stream;
     int32_t n, f;
     pair_offsets(model, scene, params, &n, &f);
     if (n_offsets) *n_offsets = n;
     if (first_offset) *first_offset = f;
-    if ((!energy && !assign) || n == 0) return HGM_OK;
-    // chain c: the point of within-frame rank c (caller order) of every frame that has one
-    const int M = model->d.M;
-    std::vector<int32_t> rank((size_t)M);
-    for (int k = 0; k < M;) {
-        int e = k;
-        while (e < M && model->t_sorted[(size_t)e] == model->t_sorted[(size_t)k]) ++e;
-        std::vector<int32_t> ord;
-        for (int q = k; q < e; ++q) ord.push_back(q);
-        std::sort(ord.begin(), ord.end(), [&](int32_t x, int32_t y) { return model->perm[(size_t)x] < model->perm[(size_t)y]; });
-        for (size_t r = 0; r < ord.size(); ++r) rank[(size_t)ord[r]] = (int32_t)r;
-        k = e;
-    }
-    std::vector<std::vector<int32_t>> members;
-    for (int c = 0; c < n_chains; ++c) {
-        std::vector<int32_t> ks;
-        for (int k = 0; k < M; ++k)
-            if (rank[(size_t)k] == c) ks.push_back(k);
-        if (ks.size() >= 3) members.push_back(ks);
-    }
-    if (members.empty()) return fail(HGM_EINVAL, "no chain of the model has 3 points");
-    const int nc = (int)members.size();
-    // chain models: frame-sorted already (one point per frame), identity order
-    std::vector<hgm_model *> chains;
-    auto release = [&]() {
-        cudaStreamSynchronize(st);
-        for (hgm_model *cm : chains) {
-            free_model(cm);
-            delete cm;
-        }
-    };
-    std::vector<int32_t> cm_sizes, cmap;
-    const int Fp = model->d.F;
-    for (const auto &ks : members) {
-        hgm_model *cmdl = new hgm_model();
-        chains.push_back(cmdl);
-        const int mc = (int)ks.size();
-        cmdl->magic = kModelMagic;
-        cmdl->d = ModelDev{mc, Fp, nullptr, nullptr, nullptr, nullptr, nullptr};
-        cmdl->F_user = model->F_user;
-        std::vector<int32_t> ident((size_t)mc);
-        for (int q = 0; q < mc; ++q) {
-            ident[(size_t)q] = q;
-            cmdl->t_sorted.push_back(model->t_sorted[(size_t)ks[(size_t)q]]);
-            cmap.push_back(model->perm[(size_t)ks[(size_t)q]]);
-        }
-        cmdl->perm = ident;
-        cm_sizes.push_back(mc);
-        cudaError_t e = cudaSuccess;
-        int32_t *dks = nullptr;
-        if (e == cudaSuccess) e = cudaMalloc((void **)&cmdl->d.xy, (size_t)mc * sizeof(float2));
-        if (e == cudaSuccess) e = cudaMalloc((void **)&cmdl->d.t, (size_t)mc * sizeof(int32_t));
-        if (e == cudaSuccess) e = cudaMalloc((void **)&cmdl->d.f, (size_t)mc * Fp * sizeof(float));
-        if (e == cudaSuccess) e = cudaMalloc((void **)&cmdl->d.perm, (size_t)mc * sizeof(int32_t));
-        if (e == cudaSuccess) e = cudaMalloc((void **)&cmdl->d.geo, (size_t)mc * sizeof(float4));
-        if (e == cudaSuccess) e = cudaMalloc((void **)&dks, (size_t)mc * sizeof(int32_t));
-        if (e == cudaSuccess) e = cudaMemcpyAsync(dks, ks.data(), (size_t)mc * sizeof(int32_t), cudaMemcpyHostToDevice, st);
-        if (e == cudaSuccess)
-            e = cudaMemcpyAsync(cmdl->d.perm, ident.data(), (size_t)mc * sizeof(int32_t), cudaMemcpyHostToDevice, st);
-        if (e == cudaSuccess) {
-            chain_gather_kernel<<<(unsigned)std::min<int64_t>(((int64_t)mc * Fp + 255) / 256, 4096), 256, 0, st>>>(
-                model->d.xy, model->d.t, model->d.f, Fp, dks, mc, cmdl->d.xy, cmdl->d.t, cmdl->d.f);
-            e = cudaGetLastError();
-        }
-        if (e == cudaSuccess) e = launch_model_geo(cmdl->d.xy, cmdl->d.t, mc, cmdl->d.geo, st);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-        cudaFree(dks);
-        if (e != cudaSuccess) {
-            release();
-            return cuda_fail(e, "chain models");
-        }
-    }
-    // every chain over the whole model's offsets (each chain's own range contains them)
-    hgm_params pc = *params;
-    pc.offset_lo = f;
-    pc.offset_hi = f + n - 1;
-    int64_t total_a = 0;
-    for (int mc : cm_sizes) total_a += (int64_t)n * mc;
-    float *ce = nullptr;
-    int32_t *ca = nullptr, *dcm = nullptr, *dmap = nullptr;
-    float *oe = nullptr;
-    int32_t *oa = nullptr;
-    const bool e_dev = energy && is_device_ptr(energy), a_dev = assign && is_device_ptr(assign);
-    cudaError_t e = cudaMalloc((void **)&ce, (size_t)nc * n * sizeof(float));
-    if (e == cudaSuccess) e = cudaMalloc((void **)&ca, (size_t)total_a * sizeof(int32_t));
-    if (e == cudaSuccess) e = cudaMalloc((void **)&dcm, (size_t)nc * sizeof(int32_t));
-    if (e == cudaSuccess) e = cudaMalloc((void **)&dmap, cmap.size() * sizeof(int32_t));
-    if (e == cudaSuccess && energy && !e_dev) e = cudaMalloc((void **)&oe, (size_t)n * sizeof(float));
-    if (e == cudaSuccess && assign && !a_dev) e = cudaMalloc((void **)&oa, (size_t)n * M * sizeof(int32_t));
-    auto free_tmp = [&]() {
-        cudaStreamSynchronize(st);
-        cudaFree(ce);
-        cudaFree(ca);
-        cudaFree(dcm);
-        cudaFree(dmap);
-        cudaFree(oe);
-        cudaFree(oa);
-    };
-    if (e != cudaSuccess) {
-        free_tmp();
-        release();
-        return cuda_fail(e, "chain buffers");
-    }
-    Exec ex;
-    rc = run_batch(ex, const_cast<const hgm_model *const *>(chains.data()), nc, &scene, 1, &pc, st, ce, ca);
-    g_pruned_units += ex.pruned_units;
-    if (!rc) {
-        e = cudaMemcpyAsync(dcm, cm_sizes.data(), (size_t)nc * sizeof(int32_t), cudaMemcpyHostToDevice, st);
-        if (e == cudaSuccess)
-            e = cudaMemcpyAsync(dmap, cmap.data(), cmap.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st);
-        float *de = energy ? (e_dev ? energy : oe) : nullptr;
-        int32_t *da = assign ? (a_dev ? assign : oa) : nullptr;
-        if (e == cudaSuccess) {
-            chain_combine_kernel<<<(unsigned)std::min<int64_t>((n + 127) / 128, 4096), 128, 0, st>>>(
-                ce, ca, n, nc, dcm, dmap, M, de, da);
-            e = cudaGetLastError();
-        }
-        if (e == cudaSuccess && energy && !e_dev)
-            e = cudaMemcpyAsync(energy, oe, (size_t)n * sizeof(float), cudaMemcpyDeviceToHost, st);
-        if (e == cudaSuccess && assign && !a_dev)
-            e = cudaMemcpyAsync(assign, oa, (size_t)n * M * sizeof(int32_t), cudaMemcpyDeviceToHost, st);
-        if (e != cudaSuccess) rc = cuda_fail(e, "chain combine");
-    }
-    free_tmp();
-    release();
-    return rc;
+    return run_chains(&model, 1, &scene, 1, params, n_chains, (cudaStream_t)stream, energy, assign);
+}
+
+hgm_status hgm_match_chains_batch(const hgm_model *const *models, int32_t n_models, const hgm_scene *const *scenes,
+                                  int32_t n_scenes, const hgm_params *params, int32_t n_chains, void *stream,
+                                  float *energy, int32_t *assign)
+{
+    std::lock_guard<std::mutex> lk(g_mu);
+    g_err.clear();
+    return run_chains(models, n_models, scenes, n_scenes, params, n_chains, (cudaStream_t)stream, energy, assign);
 }
 
 hgm_status hgm_match_batch(const hgm_model *const *models, int32_t n_models, const hgm_scene *const *scenes,

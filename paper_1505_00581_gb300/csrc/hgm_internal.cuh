@@ -186,6 +186,13 @@ struct hgm_model {
     int32_t F_user;
     std::vector<int32_t> t_sorted;   // host copy of sorted frames
     std::vector<int32_t> perm;       // host copy of the order
+    // frames that anchor the offset range o = -span_t1 .. F_s-1-span_tM: the model's own first and last
+    // frames, or for a chain of a multi-point model the whole model's (so that every chain shares its range)
+    int32_t span_t1 = 0, span_tM = 0;
+    // independent-chains split (built on first use for chain_n chains; released with the model)
+    mutable int32_t chain_n = 0;
+    mutable std::vector<hgm_model *> chains;        // the chains with >= 3 points, in chain order
+    mutable std::vector<int32_t> chain_map;         // concatenated chain points -> caller index in this model
 };
 
 struct hgm_scene {

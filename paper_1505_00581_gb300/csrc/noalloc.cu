@@ -115,7 +115,7 @@ extern "C" hgm_status hgm_match_noalloc(const hgm_model *model, const hgm_scene 
     cudaStream_t st = (cudaStream_t)stream;
 
     // offset range (same rule as hgm_offsets)
-    const int64_t t1 = model->t_sorted.front(), tM = model->t_sorted.back();
+    const int64_t t1 = model->span_t1, tM = model->span_tM;
     int64_t lo = std::max<int64_t>(-t1, params->offset_lo);
     int64_t hi = std::min<int64_t>((int64_t)scene->d.n_frames - 1 - tM, params->offset_hi);
     const int n_off = hi >= lo ? (int)(hi - lo + 1) : 0;

@@ -67,6 +67,8 @@ SIGNATURES = {
     "hgm_plan_check": (_i32, [_vp, _vp]),
     "hgm_prop_scores": (_i32, [_vp, _vp, _vp, _vp, _i32, _i32, _vp, _vp]),
     "hgm_match_chains": (_i32, [_vp, _vp, _PP, _i32, _vp, _p32, _p32, _vp, _vp]),
+    "hgm_match_chains_batch": (_i32, [ctypes.POINTER(_vp), _i32, ctypes.POINTER(_vp), _i32, _PP, _i32, _vp, _vp,
+                                      _vp]),
     "hgm_model_order": (_i32, [_vp, _p32]),
     "hgm_scene_order": (_i32, [_vp, _p32]),
     "hgm_unary": (_i32, [_vp, _vp, _f32, _vp, _vp]),
@@ -449,6 +451,18 @@ def match_batch(models: Sequence[Model], scenes: Sequence[Scene], params: Params
     sh = (ctypes.c_void_p * max(ns, 1))(*[s.handle for s in scenes])
     (pe, ke), (pa, ka) = _ptr(energy), _ptr(assign)
     _check(lib.hgm_match_batch(mh, nm, sh, ns, ctypes.byref(params), _stream(stream), pe, pa))
+    return ke, ka
+
+
+def match_chains_batch(models: Sequence[Model], scenes: Sequence[Scene], params: Params, n_chains: int,
+                       energy=None, assign=None, stream=None):
+    """match_chains for every (model, scene) pair in one pass; outputs in the batch_layout order."""
+    lib = load()
+    nm, ns = len(models), len(scenes)
+    mh = (ctypes.c_void_p * max(nm, 1))(*[m.handle for m in models])
+    sh = (ctypes.c_void_p * max(ns, 1))(*[s.handle for s in scenes])
+    (pe, ke), (pa, ka) = _ptr(energy), _ptr(assign)
+    _check(lib.hgm_match_chains_batch(mh, nm, sh, ns, ctypes.byref(params), int(n_chains), _stream(stream), pe, pa))
     return ke, ka
 
 

@@ -76,3 +76,46 @@ def test_chains_need_a_chain_of_three(env):
     with pytest.raises(hgm.HgmError) as err:
         hgm.match_chains(m2, s, p, 2)                     # two chains of 2 points
     assert err.value.status == hgm.HGM_EINVAL
+
+
+def test_chains_batch_matches_pairs_and_oracle(env):
+    """hgm_match_chains_batch over 3 models x 2 scenes: identical (bit for bit) to per-pair hgm_match_chains,
+    laid out as hgm_batch_layout, and on every offset within 1e-5 of the chain oracle; device outputs; the
+    split is rebuilt when n_chains changes."""
+    torch, hgm, oracle = env
+    dev = torch.device("cuda")
+    cases = [(11, 10, 2, 50, 5.0), (12, 8, np.array([1, 2, 3, 2, 3, 1, 2, 3]), 70, 6.0), (13, 12, 3, 40, 4.0)]
+    mods, scs = [], []
+    for seed, frames, per_frame, nf, clutter in cases:
+        mod, sc = _multi_point_case(seed, frames, per_frame, nf, clutter)
+        mods.append(mod)
+        scs.append(sc)
+    scs = scs[:2]
+    M = [hgm.Model(*(torch.from_numpy(a).to(dev) for a in (m.xy, m.t, m.f))) for m in mods]
+    S = [hgm.Scene(*(torch.from_numpy(a).to(dev) for a in (s.xy, s.t, s.f)), s.n_frames) for s in scs]
+    p = hgm.default_params(K=16, window=2)
+    first, es, as_ = hgm.batch_layout(M, S, p)
+    for n_chains in (3, 2, 3):
+        e = torch.empty(int(es[-1]), dtype=torch.float32, device=dev)
+        a = torch.empty(int(as_[-1]), dtype=torch.int32, device=dev)
+        hgm.match_chains_batch(M, S, p, n_chains, e, a)
+        torch.cuda.synchronize()
+        e, a = e.cpu().numpy(), a.cpu().numpy()
+        for mi, mod in enumerate(mods):
+            for si, sc in enumerate(scs):
+                q = mi * len(scs) + si
+                f1, e1, a1 = hgm.match_chains(M[mi], S[si], p, n_chains)
+                n = int(es[q + 1] - es[q])
+                assert f1 == first[q] and len(e1) == n
+                np.testing.assert_array_equal(e[es[q]:es[q + 1]], e1)
+                np.testing.assert_array_equal(a[as_[q]:as_[q + 1]].reshape(n, mod.n), a1)
+                if n_chains != 3:
+                    continue
+                co = oracle.ChainOracle(mod.xy, mod.t, mod.f, sc.xy, sc.t, sc.f, sc.n_frames, n_chains, K=16,
+                                        window=2, T=10, **LAM)
+                assert co.first_offset == f1 and co.n_offsets == n
+                for k in range(n):
+                    e64, _ = co.match(f1 + k)
+                    assert np.isfinite(e64) == np.isfinite(e1[k]), (q, k)
+                    if np.isfinite(e64):
+                        assert abs(e1[k] - e64) <= 1e-5 * e64 + 1e-6, (q, k, e1[k], e64)
