@@ -30,6 +30,28 @@ METRIC = "scene frames/sec matched (all models × offsets), plain exact vs prune
 OPS_PER_TRIPLE = 12          # FP32 lane ops per evaluated triple after hoisting
 SM_COUNT_FALLBACK = 152
 FP32_LANES_PER_SM = 128
+# DRAM bytes of one recursion launch, from an ncu capture (dram__bytes_read.sum + dram__bytes_write.sum) of
+# the batched_small case, with the sources of the kernel it captured and the capture's argmin-table bytes
+# sum n_offsets (M - 2) K^2. Both the tables written and the lists read grow in proportion to that sum,
+# so a full launch's traffic is scaled by it; a changed kernel source voids the figure.
+RECURSE_NCU = {"sources_sha256": "3e216ac0c0329b332808a70abbe245f55a0ebb901ad53bfcbbbbdfe06655acc8",
+               "bytes": 52_781_312 + 334_871_808, "beta_bytes": 393_031_680, "case": "batched_small",
+               "summary": "profiles/recurse_kernel_batched_exact.md"}
+RECURSE_SOURCES = ("k_recurse.cu", "recurse_common.cuh", "f32x2.cuh")
+
+
+def recurse_traffic(wl, chunks_per_step: int):
+    """DRAM bytes per recursion launch scaled from the committed capture, or None if the kernel changed."""
+    import hashlib
+    h = hashlib.sha256()
+    for f in RECURSE_SOURCES:
+        with open(os.path.join(ROOT, "paper_1505_00581_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    if h.hexdigest() != RECURSE_NCU["sources_sha256"]:
+        return None, None
+    beta = sum(wl.n_offsets(m, s) * (wl.models[m].n - 2) * wl.K * wl.K
+               for m in range(len(wl.models)) for s in range(len(wl.scenes)))
+    return RECURSE_NCU["bytes"] * beta / RECURSE_NCU["beta_bytes"] / chunks_per_step, beta / chunks_per_step
 
 
 def peaks():
@@ -313,8 +335,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="batched_exact")
-    ap.add_argument("--ref-units", type=int, default=48)
-    ap.add_argument("--cpu-units", type=int, default=48)
+    ap.add_argument("--ref-units", type=int, default=128)
+    ap.add_argument("--cpu-units", type=int, default=384)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-graph", action="store_true", help="skip the CUDA-graph replay lines")
@@ -451,8 +473,12 @@ def main():
     eval_per_launch = evaluated / chunks_per_step
     achieved = eval_per_launch * OPS_PER_TRIPLE / (rec_avg_ms / 1e3) / 1e12
     peak_ops = sm_count * FP32_LANES_PER_SM * float(pk.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
+    traffic, beta_bytes = recurse_traffic(wl, chunks_per_step)
     roofline = {"bound": "alu", "kernel": "recurse_kernel", "achieved": achieved, "peak": peak_ops,
-                "unit": "Tops/s (FP32 lane ops)", "frac": achieved / peak_ops, "traffic": None,
+                "unit": "Tops/s (FP32 lane ops)", "frac": achieved / peak_ops, "traffic": traffic,
+                "traffic_source": None if traffic is None else
+                f"ncu DRAM bytes of the {RECURSE_NCU['case']} capture ({RECURSE_NCU['summary']}), scaled by "
+                f"argmin-table bytes {beta_bytes:.4g} / {RECURSE_NCU['beta_bytes']:.4g}",
                 "peak_source": f"{sm_count} SMs x {FP32_LANES_PER_SM} FP32 lanes x sm_max_mhz of "
                                f"MEASURED_PEAKS.json ({pk_kind})",
                 "evaluated_triples_per_launch": eval_per_launch, "ops_per_triple": OPS_PER_TRIPLE,

@@ -8,7 +8,10 @@
  * second-order chain (Sec. 2.2, Eq. 9), its exact backward min-sum recursion
  * (Eq. 10) with initialisation (Eq. 11), argmin tables and backtracking
  * (Eq. 12) and the initial pair search (Eq. 13), under the causality and
- * temporal-closeness assumptions (Sec. 2.1, Eqs. 7-8).
+ * temporal-closeness assumptions (Sec. 2.1, Eqs. 7-8). Two candidate
+ * domains: per time offset with windowed, capped lists (the batched form),
+ * and the whole-block problem of the paper itself, where every scene node is
+ * a candidate of every model node (Sec. 2.2, Sec. 3).
  *
  * It is the parity reference for the CUDA library and shares no code with
  * it. Only the test-suite, the smoke check and the benchmark's CPU-baseline
@@ -226,36 +229,44 @@ int or_candidates(const or_ctx *c, int i, int o, int *idx, double *u)
     return keep;
 }
 
+/* Whole-block candidates (the paper's own formulation, Sec. 2.2 and Sec. 3:
+ * z_i ranges over every scene node, restricted only by the constraints of
+ * Eqs. 7-8): C_i = all S scene points in ascending index, for every i.
+ * Writes S indices to idx and the U of model point i to u; returns S. */
+int or_block_candidates(const or_ctx *c, int i, int *idx, double *u)
+{
+    for (int j = 0; j < c->S; ++j) { idx[j] = j; u[j] = or_unary(c, i, j); }
+    return c->S;
+}
+
 /* ---- exact recursion (Eqs. 10-13) ------------------------------------ */
 
-/* Solves one offset. Outputs the minimal energy (or +inf), the assignment
- * z[0..M-1] as sorted scene indices (-1 when infeasible), and optionally the
- * number of feasible (z_i, z_{i-1}, z_{i-2}) triples the recursion visits
- * (n_triples may be NULL). Returns 0 on success, -1 on allocation failure. */
-int or_match_offset(const or_ctx *c, int o, double *energy, int *z, int64_t *n_triples)
+/* Solves the chain problem over the given candidate lists: list i holds cnt[i]
+ * sorted scene indices at cand[i*Kc ..] with their U at cu[i*Kc ..]. Outputs
+ * the minimal energy (or +inf), the assignment z[0..M-1] as sorted scene
+ * indices (-1 when infeasible), and optionally the number of feasible
+ * (z_i, z_{i-1}, z_{i-2}) triples visited. Returns 0, or -1 on allocation
+ * failure. */
+static int solve_lists(const or_ctx *c, int Kc, const int *cand, const double *cu, const int *cnt,
+                       double *energy, int *z, int64_t *n_triples)
 {
-    const int M = c->M, K = c->K;
-    int *cand = (int *)malloc(sizeof(int) * (size_t)M * K);
-    double *cu = (double *)malloc(sizeof(double) * (size_t)M * K);
-    int *cnt = (int *)malloc(sizeof(int) * (size_t)M);
+    const int M = c->M, K = Kc;
     double *alpha_next = (double *)malloc(sizeof(double) * (size_t)K * K);
     double *alpha_cur = (double *)malloc(sizeof(double) * (size_t)K * K);
     int *beta = (int *)malloc(sizeof(int) * (size_t)M * K * K);
-    if (!cand || !cu || !cnt || !alpha_next || !alpha_cur || !beta) {
-        free(cand); free(cu); free(cnt); free(alpha_next); free(alpha_cur); free(beta);
+    if (!alpha_next || !alpha_cur || !beta) {
+        free(alpha_next); free(alpha_cur); free(beta);
         return -1;
     }
     int64_t triples = 0;
     int feasible = 1;
-    for (int i = 0; i < M; ++i) {
-        cnt[i] = or_candidates(c, i, o, cand + (size_t)i * K, cu + (size_t)i * K);
+    for (int i = 0; i < M; ++i)
         if (cnt[i] == 0) feasible = 0;
-    }
     for (int i = 0; i < M; ++i) z[i] = -1;
     *energy = INFINITY;
     if (feasible) {
         /* alpha_{M+1} == 0: alpha_next[ja*K + jb] holds alpha_{i+1}(z_i = slot ja, z_{i-1} = slot jb). */
-        for (int k = 0; k < K * K; ++k) alpha_next[k] = 0.0;
+        for (size_t k = 0; k < (size_t)K * K; ++k) alpha_next[k] = 0.0;
         for (int i = M - 1; i >= 2; --i) {          /* 0-based i is the paper's i+1 */
             const int *Ci = cand + (size_t)i * K, *Cb = cand + (size_t)(i - 1) * K, *Cc = cand + (size_t)(i - 2) * K;
             const double *Ui = cu + (size_t)i * K;
@@ -267,10 +278,10 @@ int or_match_offset(const or_ctx *c, int o, double *energy, int *z, int64_t *n_t
                         int a = Ci[ja], b = Cb[jb], cc = Cc[jc];
                         if (!or_feasible(c, a, b, cc)) continue;
                         ++triples;
-                        double v = Ui[ja] + or_triple(c, i, a, b, cc) + alpha_next[ja * K + jb];
+                        double v = Ui[ja] + or_triple(c, i, a, b, cc) + alpha_next[(size_t)ja * K + jb];
                         if (v < best) { best = v; arg = ja; }
                     }
-                    alpha_cur[jb * K + jc] = best;
+                    alpha_cur[(size_t)jb * K + jc] = best;
                     beta[((size_t)i * K + jb) * K + jc] = arg;
                 }
             }
@@ -281,13 +292,17 @@ int or_match_offset(const or_ctx *c, int o, double *energy, int *z, int64_t *n_t
         int b1 = -1, b2 = -1;
         for (int j1 = 0; j1 < cnt[0]; ++j1) {
             for (int j2 = 0; j2 < cnt[1]; ++j2) {
-                double v = cu[j1] + cu[K + j2] + alpha_next[j2 * K + j1];
+                double v = cu[j1] + cu[K + j2] + alpha_next[(size_t)j2 * K + j1];
                 if (v < best) { best = v; b1 = j1; b2 = j2; }
             }
         }
         if (b1 >= 0 && isfinite(best)) {
             /* Eq. 12: z_i = beta_i(z_{i-1}, z_{i-2}) */
             int *slot = (int *)malloc(sizeof(int) * (size_t)M);
+            if (!slot) {
+                free(alpha_next); free(alpha_cur); free(beta);
+                return -1;
+            }
             slot[0] = b1; slot[1] = b2;
             for (int i = 2; i < M; ++i) slot[i] = beta[((size_t)i * K + slot[i - 1]) * K + slot[i - 2]];
             for (int i = 0; i < M; ++i) z[i] = cand[(size_t)i * K + slot[i]];
@@ -296,8 +311,50 @@ int or_match_offset(const or_ctx *c, int o, double *energy, int *z, int64_t *n_t
         }
     }
     if (n_triples) *n_triples = triples;
-    free(cand); free(cu); free(cnt); free(alpha_next); free(alpha_cur); free(beta);
+    free(alpha_next); free(alpha_cur); free(beta);
     return 0;
+}
+
+/* Builds the lists of offset o (block != 0: the whole-block lists) with
+ * capacity *Kc; the caller frees cand, cu and cnt. */
+static int build_lists(const or_ctx *c, int block, int o, int **cand, double **cu, int **cnt, int *Kc)
+{
+    const int M = c->M, K = block ? (c->S > 0 ? c->S : 1) : c->K;
+    *Kc = K;
+    *cand = (int *)malloc(sizeof(int) * (size_t)M * K);
+    *cu = (double *)malloc(sizeof(double) * (size_t)M * K);
+    *cnt = (int *)malloc(sizeof(int) * (size_t)M);
+    if (!*cand || !*cu || !*cnt) {
+        free(*cand); free(*cu); free(*cnt);
+        return -1;
+    }
+    for (int i = 0; i < M; ++i)
+        (*cnt)[i] = block ? or_block_candidates(c, i, *cand + (size_t)i * K, *cu + (size_t)i * K)
+                          : or_candidates(c, i, o, *cand + (size_t)i * K, *cu + (size_t)i * K);
+    return 0;
+}
+
+/* Solves one offset (windowed, capped lists). See solve_lists for outputs. */
+int or_match_offset(const or_ctx *c, int o, double *energy, int *z, int64_t *n_triples)
+{
+    int *cand, *cnt, Kc;
+    double *cu;
+    if (build_lists(c, 0, o, &cand, &cu, &cnt, &Kc)) return -1;
+    int rc = solve_lists(c, Kc, cand, cu, cnt, energy, z, n_triples);
+    free(cand); free(cu); free(cnt);
+    return rc;
+}
+
+/* Solves the whole-block problem (every scene point a candidate of every
+ * model point, no offset). See solve_lists for outputs. */
+int or_match_block(const or_ctx *c, double *energy, int *z, int64_t *n_triples)
+{
+    int *cand, *cnt, Kc;
+    double *cu;
+    if (build_lists(c, 1, 0, &cand, &cu, &cnt, &Kc)) return -1;
+    int rc = solve_lists(c, Kc, cand, cu, cnt, energy, z, n_triples);
+    free(cand); free(cu); free(cnt);
+    return rc;
 }
 
 /* Runs or_match_offset over offsets[0..n-1]; energy[n], z[n*M]. */
@@ -317,20 +374,17 @@ int or_match_offsets(const or_ctx *c, const int *offsets, int n, double *energy,
  * assignments whose energy is within tol of the minimum. Intended for tiny
  * inputs only (product of list sizes up to ~1e6). Returns -1 if the product
  * exceeds max_assignments. */
-int or_bruteforce(const or_ctx *c, int o, double tol, int64_t max_assignments,
-                  double *energy, int *z, int64_t *n_ties)
+static int bruteforce_lists(const or_ctx *c, int block, int o, double tol, int64_t max_assignments,
+                            double *energy, int *z, int64_t *n_ties)
 {
-    const int M = c->M, K = c->K;
-    int *cand = (int *)malloc(sizeof(int) * (size_t)M * K);
-    double *cu = (double *)malloc(sizeof(double) * (size_t)M * K);
-    int *cnt = (int *)malloc(sizeof(int) * (size_t)M);
+    const int M = c->M;
+    int *cand, *cnt, K;
+    double *cu;
+    if (build_lists(c, block, o, &cand, &cu, &cnt, &K)) return -1;
     int *slot = (int *)calloc((size_t)M, sizeof(int));
     int *zz = (int *)malloc(sizeof(int) * (size_t)M);
     double prod = 1.0;
-    for (int i = 0; i < M; ++i) {
-        cnt[i] = or_candidates(c, i, o, cand + (size_t)i * K, cu + (size_t)i * K);
-        prod *= (double)cnt[i];
-    }
+    for (int i = 0; i < M; ++i) prod *= (double)cnt[i];
     for (int i = 0; i < M; ++i) z[i] = -1;
     *energy = INFINITY;
     *n_ties = 0;
@@ -365,4 +419,17 @@ int or_bruteforce(const or_ctx *c, int o, double tol, int64_t max_assignments,
     if (!isfinite(*energy)) for (int i = 0; i < M; ++i) z[i] = -1;
     free(cand); free(cu); free(cnt); free(slot); free(zz);
     return 0;
+}
+
+int or_bruteforce(const or_ctx *c, int o, double tol, int64_t max_assignments,
+                  double *energy, int *z, int64_t *n_ties)
+{
+    return bruteforce_lists(c, 0, o, tol, max_assignments, energy, z, n_ties);
+}
+
+/* Brute force of the whole-block problem (every scene point a candidate). */
+int or_bruteforce_block(const or_ctx *c, double tol, int64_t max_assignments,
+                        double *energy, int *z, int64_t *n_ties)
+{
+    return bruteforce_lists(c, 1, 0, tol, max_assignments, energy, z, n_ties);
 }

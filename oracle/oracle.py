@@ -78,6 +78,10 @@ def _load():
         lib.or_bruteforce.restype = ctypes.c_int
         lib.or_bruteforce.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_int64,
                                       dp, ip, lp]
+        lib.or_match_block.restype = ctypes.c_int
+        lib.or_match_block.argtypes = [ctypes.c_void_p, dp, ip, lp]
+        lib.or_bruteforce_block.restype = ctypes.c_int
+        lib.or_bruteforce_block.argtypes = [ctypes.c_void_p, ctypes.c_double, ctypes.c_int64, dp, ip, lp]
         _lib = lib
         return lib
 
@@ -242,6 +246,28 @@ class Oracle:
         z = np.zeros(self.M, np.int32)
         nt = np.zeros(1, np.int64)
         rc = self.lib.or_bruteforce(self.ctx, int(o), float(tol), int(max_assignments), _dp(e), _ip(z), _lp(nt))
+        if rc:
+            raise ValueError("too many assignments for brute force")
+        return float(e[0]), self._to_caller_z(z), int(nt[0])
+
+
+    # ---- the whole-block problem (Sec. 2.2 and Sec. 3: every scene node a candidate, no offsets) ----------
+    def match_block(self):
+        """(energy, caller-order assignment, feasible-triple count) of the whole-block problem: z_i ranges over
+        all S scene points, restricted only by causality, temporal closeness and distinctness (Eqs. 7-8)."""
+        e = np.zeros(1, np.float64)
+        z = np.zeros(self.M, np.int32)
+        nt = np.zeros(1, np.int64)
+        if self.lib.or_match_block(self.ctx, _dp(e), _ip(z), _lp(nt)):
+            raise MemoryError("oracle allocation failed")
+        return float(e[0]), self._to_caller_z(z), int(nt[0])
+
+    def bruteforce_block(self, tol: float = 1e-9, max_assignments: int = 2_000_000):
+        """(min energy, caller-order first minimiser, near-ties) of the whole-block problem by enumeration."""
+        e = np.zeros(1, np.float64)
+        z = np.zeros(self.M, np.int32)
+        nt = np.zeros(1, np.int64)
+        rc = self.lib.or_bruteforce_block(self.ctx, float(tol), int(max_assignments), _dp(e), _ip(z), _lp(nt))
         if rc:
             raise ValueError("too many assignments for brute force")
         return float(e[0]), self._to_caller_z(z), int(nt[0])

@@ -146,6 +146,30 @@ def _stats(e_ref, a_ref, e, a, M_rows, sel=None):
     return hits / max(pts, 1), match / max(units, 1), units
 
 
+def pair_stats(e_ref, a_ref, e, a, M_rows, e_rows):
+    """Quality at the level recognition uses: per (model, scene) pair the matching distance is the
+    minimum energy over offsets. Over the pairs with a finite exact minimum: how often the pruned
+    minimum sits at the same offset, the point recall of the pruned assignment at the exact best offset,
+    and the mean relative gap of the pruned minimum."""
+    n = same = pts = hits = 0
+    gaps = []
+    for q, (start, nu, M) in enumerate(M_rows):
+        es = e_rows[q]
+        er, ep = e_ref[es:es + nu], e[es:es + nu]
+        if nu == 0 or not np.isfinite(er).any():
+            continue
+        k = int(np.argmin(er))
+        n += 1
+        same += int(np.isfinite(ep).any() and int(np.argmin(ep)) == k)
+        R = a_ref[start + k * M:start + (k + 1) * M]
+        A = a[start + k * M:start + (k + 1) * M]
+        pts += M
+        hits += int((A == R).sum())
+        gaps.append((float(np.min(ep)) - float(er[k])) / max(float(er[k]), 1e-12))
+    return {"pairs": n, "best_offset_match": same / max(n, 1), "point_recall_at_best": hits / max(pts, 1),
+            "mean_rel_gap": float(np.mean(gaps)) if gaps else 0.0}
+
+
 def compare(e_ref, a_ref, e, a, M_rows, e_rows=None, implant_mask=None):
     """Recall / unit match / energy gap of (e, a) against the exact (e_ref, a_ref).
     a, a_ref: flat assignment arrays; M_rows: (assign start, n_units, M) per (model, scene) pair;
@@ -158,6 +182,8 @@ def compare(e_ref, a_ref, e, a, M_rows, e_rows=None, implant_mask=None):
            "mean_rel_gap": float(np.mean(gaps)) if gaps.size else 0.0,
            "mean_abs_rel_gap": float(np.mean(np.abs(gaps))) if gaps.size else 0.0,
            "feasible_mismatch": int(np.sum(np.isfinite(e_ref) != np.isfinite(e)))}
+    if e_rows is not None:
+        out["pairs"] = pair_stats(e_ref, a_ref, e, a, M_rows, e_rows)
     if implant_mask is not None and e_rows is not None:
         for name, pick in (("implant", implant_mask), ("clutter", [~m for m in implant_mask])):
             r, u, nu = _stats(e_ref, a_ref, e, a, M_rows, pick)
