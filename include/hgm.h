@@ -187,6 +187,29 @@ HGM_API hgm_status hgm_match_chains_batch(const hgm_model *const *models, int32_
                                           const hgm_params *params, int32_t n_chains, void *stream, float *energy,
                                           int32_t *assign);
 
+/* The whole-block problem: the paper's own formulation (Sec. 2.2 and Sec. 3),
+ * with no time offsets and no candidate windows. Every scene point is a
+ * candidate of every model point; only the constraints of Eqs. 7-8 (reading
+ * R3: t'(z_{i-2}) <= t'(z_{i-1}) <= t'(z_i), t'(z_i) - t'(z_{i-2}) < T,
+ * distinct points) restrict the chain. The recursion (Eqs. 10-13) runs over
+ * the band of the trellis these constraints leave (Sec. 3.3), its loop bounds
+ * taken from the minnode table (Sec. 3.5). One result per (model, scene)
+ * pair, pair q = m * n_scenes + s:
+ *  energy [n_models x n_scenes] (host or device, or NULL): the minimum of
+ *      Eq. 9, +inf if no chain is feasible;
+ *  assign (host or device, or NULL): for pair q, M_m entries starting at
+ *      sum of M over the earlier pairs; the caller scene index of each caller
+ *      model point, -1 where infeasible.
+ * params: lambda1..3 and T are used (T <= 0: no closeness limit); window, K
+ * and the offset range are ignored. HGM_EUNSUPPORTED for precision 1 or
+ * pruning, or if more than 65535 scene points lie within T frames of one
+ * frame (the argmin tables hold 16-bit offsets); HGM_ENOMEM if the argmin
+ * tables, (M-2) x cells x 2 bytes per pair, do not fit. Completion as for
+ * hgm_match_batch (asynchronous with device outputs). */
+HGM_API hgm_status hgm_match_block(const hgm_model *const *models, int32_t n_models, const hgm_scene *const *scenes,
+                                   int32_t n_scenes, const hgm_params *params, void *stream, float *energy,
+                                   int32_t *assign);
+
 /* Completion: hgm_match and hgm_match_batch return once their work is queued
  * on `stream` when both outputs are device pointers and no tensor-core kernel
  * runs (precision 0, no pruning); with a host output, precision 1 or pruning

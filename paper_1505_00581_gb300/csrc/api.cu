@@ -150,6 +150,7 @@ struct Workspace {
     Buffer P, Q, Qb, modelxy, cand2_idx, cand2_u, cand2_cnt, units2, beta2, fb_units, fb_count, beta_fb, scores;
     Buffer fb_total;   // fallback units since the last hgm_prune_counters reset (device counter)
     Buffer chain_e, chain_a, chain_tab, chain_oe, chain_oa;   // independent-chains variant
+    Buffer blk_tab, blk_cellb, blk_dir, blk_model, blk_U, blk_beta, blk_scratch, blk_rec, blk_oe, blk_oa;   // whole block
 };
 Workspace g_ws;
 bool g_count_mode = false;   // hgm_profile_enable(2): batch runs use the accounting recursion variant
@@ -1370,6 +1371,179 @@ hgm_status hgm_match_chains_batch(const hgm_model *const *models, int32_t n_mode
     std::lock_guard<std::mutex> lk(g_mu);
     g_err.clear();
     return run_chains(models, n_models, scenes, n_scenes, params, n_chains, (cudaStream_t)stream, energy, assign);
+}
+
+// ---- the whole-block problem (Sec. 2.2, Sec. 3: every scene point a candidate of every model point) --------
+hgm_status hgm_match_block(const hgm_model *const *models, int32_t n_models, const hgm_scene *const *scenes,
+                           int32_t n_scenes, const hgm_params *params, void *stream, float *energy, int32_t *assign)
+{
+    std::lock_guard<std::mutex> lk(g_mu);
+    g_err.clear();
+    hgm_status rc = check_params(params);
+    if (rc) return rc;
+    if (params->precision != 0 || params->prune)
+        return fail(HGM_EUNSUPPORTED, "the whole-block problem runs in plain FP32 only (precision 0, no pruning)");
+    if (n_models < 0 || n_scenes < 0 || (n_models && !models) || (n_scenes && !scenes))
+        return fail(HGM_EINVAL, "bad model/scene arrays");
+    const int nm = n_models, ns = n_scenes;
+    if (nm == 0 || ns == 0 || (!energy && !assign)) return HGM_OK;
+    int F = -1;
+    for (int m = 0; m < nm; ++m) {
+        if (!valid_model(models[m])) return fail(HGM_EINVAL, "models[%d] is not a model handle", m);
+        if (F < 0) F = models[m]->F_user;
+        if (models[m]->F_user != F) return fail(HGM_EINVAL, "descriptor widths differ across models");
+    }
+    for (int s = 0; s < ns; ++s) {
+        if (!valid_scene(scenes[s])) return fail(HGM_EINVAL, "scenes[%d] is not a scene handle", s);
+        if (scenes[s]->F_user != F) return fail(HGM_EINVAL, "descriptor width differs between model and scene");
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    const int T = params->T;
+    // band tables per scene (host, from the minnode table): lo(b), cs(b)
+    std::vector<int64_t> lo_off((size_t)ns), cs_off((size_t)ns), cell_off((size_t)ns), cells((size_t)ns);
+    std::vector<int32_t> lo_all;
+    std::vector<int64_t> cs_all;
+    int64_t total_cells = 0, max_cells = 0;
+    for (int s = 0; s < ns; ++s) {
+        const hgm_scene *sc = scenes[s];
+        const std::vector<int32_t> &fs = sc->fs_host;
+        const int S = sc->d.S, nf = sc->d.n_frames;
+        lo_off[(size_t)s] = (int64_t)lo_all.size();
+        cs_off[(size_t)s] = (int64_t)cs_all.size();
+        int64_t c = 0;
+        for (int f = 0; f < nf; ++f) {
+            const int lo = T > 0 ? fs[(size_t)std::max(0, f - T + 1)] : 0;
+            const int reach = (T > 0 ? fs[(size_t)std::min(nf, f + T)] : S) - fs[(size_t)f];
+            if (reach > 0xffff)
+                return fail(HGM_EUNSUPPORTED, "scenes[%d]: %d points within T frames of frame %d (at most 65535)", s,
+                            reach, f);
+            for (int b = fs[(size_t)f]; b < fs[(size_t)f + 1]; ++b) {
+                lo_all.push_back(lo);
+                cs_all.push_back(c);
+                c += fs[(size_t)f + 1] - lo;
+            }
+        }
+        cs_all.push_back(c);
+        (void)S;
+        cells[(size_t)s] = c;
+        cell_off[(size_t)s] = total_cells;
+        total_cells += c;
+        max_cells = std::max(max_cells, c);
+    }
+    // units and outputs: pair q = m * n_scenes + s, assignment rows of M_m in pair order
+    std::vector<BlockUnit> units;
+    int64_t beta_total = 0, a_total = 0;
+    int R = 0;
+    std::vector<int> urow((size_t)nm);
+    for (int m = 0; m < nm; ++m) {
+        urow[(size_t)m] = R;
+        R += models[m]->d.M;
+    }
+    for (int m = 0; m < nm; ++m)
+        for (int s = 0; s < ns; ++s) {
+            units.push_back(BlockUnit{m, s, beta_total, (int64_t)m * ns + s, a_total});
+            beta_total += (int64_t)(models[m]->d.M - 2) * cells[(size_t)s];
+            a_total += models[m]->d.M;
+        }
+    size_t free_b = 0, total_b = 0;
+    CK(cudaMemGetInfo(&free_b, &total_b), "cudaMemGetInfo");
+    if ((double)beta_total * 2 > 0.6 * (double)free_b)
+        return fail(HGM_ENOMEM, "whole-block argmin tables need %lld bytes", (long long)(beta_total * 2));
+    Workspace &ws = g_ws;
+    const int Fp = models[0]->d.F;
+    int64_t S_total = 0;
+    std::vector<int64_t> u_off((size_t)ns);
+    for (int s = 0; s < ns; ++s) {
+        u_off[(size_t)s] = S_total * R;
+        S_total += scenes[s]->d.S;
+    }
+    CK(ws.blk_tab.ensure(lo_all.size() * sizeof(int32_t) + cs_all.size() * sizeof(int64_t) + 64), "workspace (block)");
+    CK(ws.blk_cellb.ensure((size_t)std::max<int64_t>(total_cells, 1) * sizeof(int32_t)), "workspace (block)");
+    CK(ws.blk_dir.ensure((size_t)std::max<int64_t>(total_cells, 1) * 2 * sizeof(float)), "workspace (block)");
+    CK(ws.blk_model.ensure((size_t)R * Fp * sizeof(float)), "workspace (block)");
+    CK(ws.blk_U.ensure((size_t)std::max<int64_t>(S_total * R, 1) * sizeof(float)), "workspace (block)");
+    CK(ws.blk_beta.ensure((size_t)std::max<int64_t>(beta_total, 1) * sizeof(uint16_t)), "workspace (block)");
+    const size_t b_units = (units.size() * sizeof(BlockUnit) + 255) & ~(size_t)255;
+    const size_t b_m = ((size_t)nm * sizeof(ModelRec) + 255) & ~(size_t)255;
+    const size_t b_s = ((size_t)ns * sizeof(SceneRec) + 255) & ~(size_t)255;
+    const size_t b_g = ((size_t)ns * sizeof(BlockGeo) + 255) & ~(size_t)255;
+    CK(ws.blk_rec.ensure(b_units + b_m + b_s + b_g), "workspace (block)");
+    int32_t *d_lo = ws.blk_tab.as<int32_t>();
+    const size_t lo_bytes = (lo_all.size() * sizeof(int32_t) + 7) & ~(size_t)7;
+    int64_t *d_cs = reinterpret_cast<int64_t *>(ws.blk_tab.as<char>() + lo_bytes);
+    Exec ex;
+    if ((rc = h2d(ex, d_lo, lo_all.data(), lo_all.size() * sizeof(int32_t), st)) ||
+        (rc = h2d(ex, d_cs, cs_all.data(), cs_all.size() * sizeof(int64_t), st)))
+        return rc;
+    std::vector<BlockGeo> geos((size_t)ns);
+    std::vector<SceneRec> srec((size_t)ns);
+    float *dirf_all = ws.blk_dir.as<float>(), *dirb_all = dirf_all + total_cells;
+    for (int s = 0; s < ns; ++s) {
+        const hgm_scene *sc = scenes[s];
+        const int32_t *lo = d_lo + lo_off[(size_t)s];
+        const int64_t *cs = d_cs + cs_off[(size_t)s];
+        int32_t *cellb = ws.blk_cellb.as<int32_t>() + cell_off[(size_t)s];
+        float *dirf = dirf_all + cell_off[(size_t)s], *dirb = dirb_all + cell_off[(size_t)s];
+        CK(launch_block_geo(sc->d.xy, sc->d.S, lo, cs, cells[(size_t)s], cellb, dirf, dirb, st), "block geometry");
+        geos[(size_t)s] = BlockGeo{lo, cs, cellb, dirf, dirb, cells[(size_t)s]};
+        float *U = ws.blk_U.as<float>() + u_off[(size_t)s];
+        srec[(size_t)s] = SceneRec{sc->d.xy, sc->d.t, sc->d.frame_start, sc->d.perm, U, (int64_t)sc->d.S, sc->d.S,
+                                   sc->d.n_frames, sc->d.f, nullptr, 0};
+    }
+    std::vector<ModelRec> mrec((size_t)nm);
+    for (int m = 0; m < nm; ++m) {
+        const hgm_model *md = models[m];
+        CK(cudaMemcpyAsync(ws.blk_model.as<float>() + (size_t)urow[(size_t)m] * Fp, md->d.f,
+                           (size_t)md->d.M * Fp * sizeof(float), cudaMemcpyDeviceToDevice, st),
+           "gather model descriptors");
+        mrec[(size_t)m] = ModelRec{md->d.xy, md->d.t, md->d.perm, md->d.M, urow[(size_t)m], md->d.f, md->d.geo};
+    }
+    for (int s = 0; s < ns; ++s)
+        if (scenes[s]->d.S > 0)
+            CK(launch_unary(ws.blk_model.as<float>(), R, scenes[s]->d.f, scenes[s]->d.S, Fp, params->lambda1,
+                            ws.blk_U.as<float>() + u_off[(size_t)s], scenes[s]->d.S, st),
+               "unary kernel");
+    char *rec = ws.blk_rec.as<char>();
+    if ((rc = h2d(ex, rec, units.data(), units.size() * sizeof(BlockUnit), st)) ||
+        (rc = h2d(ex, rec + b_units, mrec.data(), mrec.size() * sizeof(ModelRec), st)) ||
+        (rc = h2d(ex, rec + b_units + b_m, srec.data(), srec.size() * sizeof(SceneRec), st)) ||
+        (rc = h2d(ex, rec + b_units + b_m + b_s, geos.data(), geos.size() * sizeof(BlockGeo), st)))
+        return rc;
+    const bool e_dev = energy && is_device_ptr(energy), a_dev = assign && is_device_ptr(assign);
+    float *de = energy;
+    int32_t *da = assign;
+    if (!energy || !e_dev) {
+        CK(ws.blk_oe.ensure(units.size() * sizeof(float)), "workspace (block)");
+        de = ws.blk_oe.as<float>();
+    }
+    if (!assign || !a_dev) {
+        CK(ws.blk_oa.ensure((size_t)a_total * sizeof(int32_t)), "workspace (block)");
+        da = ws.blk_oa.as<int32_t>();
+    }
+    Params p = to_params(params);
+    p.F = Fp;
+    float *scratch = nullptr;
+    int grid_global = 0;
+    if (max_cells > block_smem_cells()) {
+        int dev = 0, sms = 0;
+        CK(cudaGetDevice(&dev), "device");
+        CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "device");
+        grid_global = (int)std::min<int64_t>((int64_t)units.size(), (int64_t)sms * 2);
+        CK(ws.blk_scratch.ensure((size_t)grid_global * 2 * max_cells * sizeof(float)), "workspace (block)");
+        scratch = ws.blk_scratch.as<float>();
+    }
+    CK(launch_block_recurse(reinterpret_cast<const BlockUnit *>(rec), (int)units.size(),
+                            reinterpret_cast<const ModelRec *>(rec + b_units),
+                            reinterpret_cast<const SceneRec *>(rec + b_units + b_m),
+                            reinterpret_cast<const BlockGeo *>(rec + b_units + b_m + b_s), p, max_cells,
+                            ws.blk_beta.as<uint16_t>(), scratch, grid_global, de, da, st),
+       "block recursion kernel");
+    if (energy && !e_dev)
+        CK(cudaMemcpyAsync(energy, de, units.size() * sizeof(float), cudaMemcpyDeviceToHost, st), "copy energy");
+    if (assign && !a_dev)
+        CK(cudaMemcpyAsync(assign, da, (size_t)a_total * sizeof(int32_t), cudaMemcpyDeviceToHost, st), "copy assign");
+    if ((energy && !e_dev) || (assign && !a_dev)) CK(cudaStreamSynchronize(st), "synchronise outputs");
+    return HGM_OK;
 }
 
 hgm_status hgm_match_batch(const hgm_model *const *models, int32_t n_models, const hgm_scene *const *scenes,

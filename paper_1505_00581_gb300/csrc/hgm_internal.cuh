@@ -170,6 +170,29 @@ cudaError_t launch_count(const Unit *units, int64_t n_units, const ModelRec *mod
                          cudaStream_t st);
 
 // Profiling hooks (api.cu).
+// k_block.cu: the whole-block problem (every scene point a candidate, no offsets).
+struct BlockGeo {            // band tables of one scene (see k_block.cu)
+    const int32_t *lo;       // [S] first point of b's band
+    const int64_t *cs;       // [S+1] first cell of b's band
+    const int32_t *cellb;    // [cells] owner b of each cell
+    const float *dirf;       // [cells] theta(b->c)
+    const float *dirb;       // [cells] theta(c->b)
+    int64_t cells;
+};
+struct BlockUnit {
+    int32_t model, scene;
+    int64_t beta;            // first argmin entry (uint16) of this unit: (M-2) x cells
+    int64_t out_e, out_a;    // energy index, first assignment element
+};
+cudaError_t launch_block_geo(const float2 *xy, int S, const int32_t *lo, const int64_t *cs, int64_t cells,
+                             int32_t *cellb, float *dirf, float *dirb, cudaStream_t st);
+int64_t block_smem_cells();   // largest band table (cells) whose two copies fit one CTA's shared memory
+// scratch == nullptr: tables in shared memory (max_cells <= block_smem_cells()); else per-CTA global scratch
+// of 2 x max_cells floats for grid_global CTAs.
+cudaError_t launch_block_recurse(const BlockUnit *units, int n_units, const ModelRec *models, const SceneRec *scenes,
+                                 const BlockGeo *geos, Params p, int64_t max_cells, uint16_t *beta, float *scratch,
+                                 int grid_global, float *energy, int32_t *assign, cudaStream_t st);
+
 void prof_begin(int kernel, cudaStream_t st);
 void prof_end(int kernel, cudaStream_t st);
 

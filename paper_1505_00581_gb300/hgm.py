@@ -67,6 +67,7 @@ SIGNATURES = {
     "hgm_plan_check": (_i32, [_vp, _vp]),
     "hgm_prop_scores": (_i32, [_vp, _vp, _vp, _vp, _i32, _i32, _vp, _vp]),
     "hgm_match_chains": (_i32, [_vp, _vp, _PP, _i32, _vp, _p32, _p32, _vp, _vp]),
+    "hgm_match_block": (_i32, [ctypes.POINTER(_vp), _i32, ctypes.POINTER(_vp), _i32, _PP, _vp, _vp, _vp]),
     "hgm_match_chains_batch": (_i32, [ctypes.POINTER(_vp), _i32, ctypes.POINTER(_vp), _i32, _PP, _i32, _vp, _vp,
                                       _vp]),
     "hgm_model_order": (_i32, [_vp, _p32]),
@@ -451,6 +452,29 @@ def match_batch(models: Sequence[Model], scenes: Sequence[Scene], params: Params
     sh = (ctypes.c_void_p * max(ns, 1))(*[s.handle for s in scenes])
     (pe, ke), (pa, ka) = _ptr(energy), _ptr(assign)
     _check(lib.hgm_match_batch(mh, nm, sh, ns, ctypes.byref(params), _stream(stream), pe, pa))
+    return ke, ka
+
+
+def block_layout(models: Sequence[Model], n_scenes: int):
+    """First assignment element of every (model, scene) pair of match_block (pair q = m * n_scenes + s)."""
+    sizes = np.repeat(np.array([m.M for m in models], np.int64), n_scenes)
+    return np.concatenate([[0], np.cumsum(sizes)])
+
+
+def match_block(models: Sequence[Model], scenes: Sequence[Scene], params: Params, energy=None, assign=None,
+                stream=None):
+    """The whole-block problem (every scene point a candidate, no offsets): one energy per (model, scene) pair
+    and the pairs' assignments laid out as block_layout. None outputs are returned as numpy arrays."""
+    lib = load()
+    nm, ns = len(models), len(scenes)
+    starts = block_layout(models, ns)
+    if energy is None and assign is None:
+        energy = np.zeros(nm * ns, np.float32)
+        assign = np.zeros(int(starts[-1]), np.int32)
+    mh = (ctypes.c_void_p * max(nm, 1))(*[m.handle for m in models])
+    sh = (ctypes.c_void_p * max(ns, 1))(*[s.handle for s in scenes])
+    (pe, ke), (pa, ka) = _ptr(energy), _ptr(assign)
+    _check(lib.hgm_match_block(mh, nm, sh, ns, ctypes.byref(params), _stream(stream), pe, pa))
     return ke, ka
 
 

@@ -229,6 +229,34 @@ def combined(seed: int = 3, n_models: int = 100, n_scenes: int = 16, M_range=(16
     return Workload(f"combined_{n_models}x{n_scenes}_K64", models, scenes, K=64, window=w)
 
 
+def paper_model(rng: np.random.Generator, M: int = 30, F: int = 162, frame: Tuple[float, float] = (160.0, 120.0),
+                n_clusters: int = 8, noise: float = 0.3) -> PointSet:
+    """A model shaped like the paper's: one point per frame over M consecutive frames (Sec. 4: models of
+    20-30 frames after saliency selection), descriptors as make_model."""
+    centres = rng.standard_normal((n_clusters, F))
+    t = np.arange(M)
+    xy = rng.uniform((0.0, 0.0), frame, size=(M, 2))
+    f = centres[rng.integers(0, n_clusters, size=M)] + noise * rng.standard_normal((M, F))
+    return PointSet(xy.astype(np.float32), t.astype(np.int32), f.astype(np.float32), centres)
+
+
+def paper_blocks(seed: int = 4, n_models: int = 50, M: int = 30, n_blocks: int = 4, block_frames: int = 60,
+                 lam: float = 1.0, implant_frac: float = 0.5, frame=(160.0, 120.0)) -> Workload:
+    """The paper's real-time scenario (Sec. 4, Table 2): 50 models of 30 one-per-frame points against scene
+    blocks of 60 frames with about one point per frame (Poisson(lam) clutter), matched as whole blocks;
+    about implant_frac of the blocks hold a jittered copy of a random model at a random offset."""
+    rng = np.random.default_rng(seed)
+    models = [paper_model(rng, M) for _ in range(n_models)]
+    pool = np.concatenate([m.centres for m in models])
+    scenes = []
+    for _ in range(n_blocks):
+        imps = []
+        if rng.random() < implant_frac:
+            imps = [(int(rng.integers(n_models)), int(rng.integers(0, block_frames - M + 1)))]
+        scenes.append(make_scene(rng, block_frames, frame, ("poisson", lam), pool, models, imps))
+    return Workload(f"paper_blocks_{n_models}x{n_blocks}_M{M}_F{block_frames}", models, scenes, K=64, window=3)
+
+
 def tiny_case(seed: int, M: int = 5, n_frames: int = 12, per_frame: int = 3, K: int = 5, window: int = 1,
               F: int = 8, T: int = 10, frame=(20.0, 20.0)) -> Workload:
     """Very small random instance for brute-force enumeration."""
