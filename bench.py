@@ -272,6 +272,63 @@ def run_chains(args, torch, hgm, wl, models, scenes, dev, stream, world, flush, 
             "finite_offsets": int(fin), "form": "plain exact FP32 per chain, mean over chains"}
 
 
+def run_blocks(args, torch, hgm, dev, stream, flush):
+    """The paper's own formulation (every scene point a candidate, no offsets) in its two scenarios (Sec. 4,
+    Table 2): 50 models of 30 points streamed over a one-minute scene as 60-frame blocks every 30 frames
+    (latency per block, end to end from host points to host results), and 50 models against a 723-frame
+    scene of ~754 points matched whole."""
+    from paper_1505_00581_gb300 import synth
+    ws = synth.paper_stream()
+    p = hgm.default_params(T=ws.T, lambda1=ws.lambda1, lambda2=ws.lambda2, lambda3=ws.lambda3)
+    models = [hgm.Model(*(torch.from_numpy(a).to(dev) for a in (m.xy, m.t, m.f))) for m in ws.models]
+    sc = ws.scenes[0]
+    blocks = [b[1:4] for b in hgm.stream_blocks(sc.xy, sc.t, sc.f, sc.n_frames, 60, 30)]
+    st = hgm.Stream(models, p, 60, stream=stream)
+    e = np.zeros(len(models), np.float32)
+    a = np.zeros(int(st.starts[-1]), np.int32)
+    for k in range(max(3, args.warmup)):
+        st.match(*blocks[k % len(blocks)], energy=e, assign=a, stream=stream)
+    lat = []
+    for rep in range(max(1, min(args.steps, 3))):
+        for b in blocks:
+            t0 = time.perf_counter()
+            st.match(*b, energy=e, assign=a, stream=stream)
+            lat.append(time.perf_counter() - t0)
+    lat_ms = np.array(lat) * 1e3
+    per_pass = float(lat_ms.sum()) / max(1, min(args.steps, 3))
+    h2d = sum(x.nbytes for b in blocks for x in b) / len(blocks)
+    streaming = {"workload": ws.name, "blocks": len(blocks), "block_frames": 60, "hop_frames": 30,
+                 "points_per_block": float(np.mean([len(b[1]) for b in blocks])), "models": len(models),
+                 "latency_ms": {"median": float(np.median(lat_ms)), "p90": float(np.percentile(lat_ms, 90)),
+                                "max": float(lat_ms.max())},
+                 "value": sc.n_frames / (per_pass / 1e3), "unit": "scene frames/s (overlapping blocks, e2e)",
+                 "ms_per_frame": per_pass / sc.n_frames, "h2d_bytes_per_block": int(h2d),
+                 "d2h_bytes_per_block": int(e.nbytes + a.nbytes)}
+    st.close()
+    # Table 2's whole-scene case, device outputs, CUDA events
+    ww = synth.paper_whole()
+    wm = [hgm.Model(*(torch.from_numpy(a_).to(dev) for a_ in (m.xy, m.t, m.f))) for m in ww.models]
+    s0 = ww.scenes[0]
+    wsc = [hgm.Scene(*(torch.from_numpy(a_).to(dev) for a_ in (s0.xy, s0.t, s0.f)), s0.n_frames)]
+    ed = torch.empty(len(wm), dtype=torch.float32, device=dev)
+    ad = torch.empty(int(hgm.block_layout(wm, 1)[-1]), dtype=torch.int32, device=dev)
+    for _ in range(args.warmup):
+        hgm.match_block(wm, wsc, p, ed, ad, stream=stream)
+    torch.cuda.synchronize()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    for x, y in evs:
+        flush.zero_()
+        x.record(stream)
+        hgm.match_block(wm, wsc, p, ed, ad, stream=stream)
+        y.record(stream)
+    torch.cuda.synchronize()
+    ms = sum(x.elapsed_time(y) for x, y in evs) / len(evs)
+    whole = {"workload": ww.name, "scene_points": s0.n, "scene_frames": s0.n_frames, "models": len(wm),
+             "ms": ms, "value": s0.n_frames / (ms / 1e3), "unit": "scene frames/s (all models, whole scene)",
+             "finite": int(torch.isfinite(ed).sum().item())}
+    return {"streaming": streaming, "whole_scene": whole}
+
+
 def run_pruned(args, torch, hgm, wl, models, scenes, energy, assign, es, as_, dev, stream, world, dist=None):
     """The pruned + BF16 form on the same workload: BF16 tensor-core unary table, the proposal network
     keeps 8 of the 64 candidates per list, recursion on the short lists, exact fallback for infeasible
@@ -342,6 +399,7 @@ def main():
     ap.add_argument("--no-graph", action="store_true", help="skip the CUDA-graph replay lines")
     ap.add_argument("--no-pruned", action="store_true", help="skip the pruned+BF16 form")
     ap.add_argument("--no-chains", action="store_true", help="skip the independent-chains variant")
+    ap.add_argument("--no-blocks", action="store_true", help="skip the whole-block and streaming forms")
     ap.add_argument("--train-steps", type=int, default=2000)
     ap.add_argument("--checkpoint", default=None, help="load the proposal network from <path>.bin/.json")
     args = ap.parse_args()
@@ -502,6 +560,10 @@ def main():
     if not args.no_chains:
         chains = run_chains(args, torch, hgm, wl, models, scenes, dev, stream, world, flush, dist)
 
+    blocks = None
+    if not args.no_blocks:
+        blocks = run_blocks(args, torch, hgm, dev, stream, flush)
+
     pruned = None
     if not args.no_pruned:
         pruned = run_pruned(args, torch, hgm, wl, models, scenes, energy, assign, es, as_, dev, stream, world, dist)
@@ -519,7 +581,7 @@ def main():
                            "parallelism": f"replicas x{world}"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "graph": graph, "gpu_launches": launches,
                 "clocks": clk_sum, "finite_offsets": int(fin), "pruned_bf16": pruned,
-                "chains": chains}
+                "chains": chains, "whole_block": blocks}
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()

@@ -61,6 +61,7 @@ typedef struct hgm_model hgm_model;
 typedef struct hgm_scene hgm_scene;
 typedef struct hgm_prop hgm_prop;
 typedef struct hgm_plan hgm_plan;
+typedef struct hgm_stream hgm_stream;
 
 typedef enum {
     HGM_OK = 0,
@@ -112,7 +113,7 @@ HGM_API hgm_status hgm_create_model(const float *xy, const int32_t *t, const flo
 HGM_API hgm_status hgm_create_scene(const float *xy, const int32_t *t, const float *desc, int32_t S, int32_t F,
                             int32_t n_frames, void *stream, hgm_scene **out);
 
-/* Releases a model, scene, proposal-network or plan handle and its device
+/* Releases a model, scene, proposal-network, plan or stream handle and its device
  * memory. NULL is a no-op.
  * Work on the handle must be complete (or ordered before on the stream the
  * handle was used on) -- the call synchronises the device first. */
@@ -209,6 +210,29 @@ HGM_API hgm_status hgm_match_chains_batch(const hgm_model *const *models, int32_
 HGM_API hgm_status hgm_match_block(const hgm_model *const *models, int32_t n_models, const hgm_scene *const *scenes,
                                    int32_t n_scenes, const hgm_params *params, void *stream, float *energy,
                                    int32_t *assign);
+
+/* Streaming blocks (Sec. 4: for continuous video the scene is cut into
+ * blocks of about 60 frames, each matched whole against every model as it
+ * arrives). A stream keeps the models' rows, the band and argmin tables and
+ * a pinned staging buffer between blocks, so a block costs one upload, six
+ * kernel launches and the read-back of its results, with no device
+ * allocation once the buffers have grown to the largest block seen.
+ * hgm_stream_create: models (handles; they must outlive the stream), params
+ * as for hgm_match_block, block_frames >= 1 (frames of one block).
+ * Release with hgm_destroy. */
+HGM_API hgm_status hgm_stream_create(const hgm_model *const *models, int32_t n_models, const hgm_params *params,
+                                     int32_t block_frames, void *stream, hgm_stream **out);
+
+/* Matches one block: n points (xy n x 2, t n with frames in [0, block_frames)
+ * relative to the block's first frame, desc n x F; host or device) against
+ * every model as hgm_match_block does for one scene. energy [n_models] and
+ * assign [sum of M] (host or device, or NULL) follow hgm_match_block's
+ * layout; assignments are indices into this call's point arrays. With host
+ * outputs the call returns when the results are there (HGM_EINVAL if a
+ * descriptor was non-finite); with device outputs it is asynchronous. Blocks
+ * that overlap (e.g. 60 frames every 30) are separate calls. */
+HGM_API hgm_status hgm_stream_match(hgm_stream *s, const float *xy, const int32_t *t, const float *desc, int32_t n,
+                                    void *stream, float *energy, int32_t *assign);
 
 /* Completion: hgm_match and hgm_match_batch return once their work is queued
  * on `stream` when both outputs are device pointers and no tensor-core kernel

@@ -150,9 +150,46 @@ struct Workspace {
     Buffer P, Q, Qb, modelxy, cand2_idx, cand2_u, cand2_cnt, units2, beta2, fb_units, fb_count, beta_fb, scores;
     Buffer fb_total;   // fallback units since the last hgm_prune_counters reset (device counter)
     Buffer chain_e, chain_a, chain_tab, chain_oe, chain_oa;   // independent-chains variant
-    Buffer blk_tab, blk_cellb, blk_dir, blk_model, blk_U, blk_beta, blk_scratch, blk_rec, blk_oe, blk_oa;   // whole block
+};
+
+// Buffers of the whole-block form: band tables, model rows, unary table, argmin tables, records, outputs.
+struct BlockBufs {
+    Buffer tab, cellb, dir, model, mrec, U, beta, scratch, rec, oe, oa;
+    int R = 0;                  // model rows gathered into `model` (prep_block_models)
+    std::vector<int> urow;
 };
 Workspace g_ws;
+BlockBufs g_blk;
+}  // namespace
+}  // namespace hgm
+
+// A stream of scene blocks matched against fixed models (hgm_stream_*).
+struct hgm_stream {
+    uint32_t magic;
+    std::vector<const hgm_model *> models;
+    hgm_params params;
+    int32_t block_frames, F_user, Fp;
+    hgm::BlockBufs bb;
+    hgm::Buffer sc_buf, raw;           // the block's sorted points (xy | t | perm | minnode), raw descriptors
+    hgm::Buffer f;                     // sorted, padded descriptors
+    hgm::Buffer flag;
+    void *pinned = nullptr;       // host staging of the uploads
+    size_t pinned_bytes = 0;
+    hgm_scene view;               // the current block as a scene (device arrays owned by this object)
+};
+
+namespace hgm {
+namespace {
+constexpr uint32_t kStreamMagic = 0x5354524du;   // "STRM"
+
+bool valid_stream(const hgm_stream *s) { return s && s->magic == kStreamMagic; }
+
+void free_stream(hgm_stream *s)
+{
+    if (s->pinned) cudaFreeHost(s->pinned);
+    s->pinned = nullptr;
+}
+
 bool g_count_mode = false;   // hgm_profile_enable(2): batch runs use the accounting recursion variant
 size_t g_budget_override = 0;   // hgm_set_workspace_budget: bytes for the unary table and for a chunk (0 = auto)
 int64_t g_pruned_units = 0;
@@ -1038,6 +1075,12 @@ void hgm_destroy(void *handle)
         free_plan(pl);
         pl->magic = kDeadMagic;
         delete pl;
+    } else if (magic == kStreamMagic) {
+        hgm_stream *sm = static_cast<hgm_stream *>(handle);
+        cudaDeviceSynchronize();
+        free_stream(sm);
+        sm->magic = kDeadMagic;
+        delete sm;
     } else if (magic == kPropMagic) {
         hgm_prop *p = static_cast<hgm_prop *>(handle);
         cudaDeviceSynchronize();
@@ -1374,30 +1417,47 @@ hgm_status hgm_match_chains_batch(const hgm_model *const *models, int32_t n_mode
 }
 
 // ---- the whole-block problem (Sec. 2.2, Sec. 3: every scene point a candidate of every model point) --------
-hgm_status hgm_match_block(const hgm_model *const *models, int32_t n_models, const hgm_scene *const *scenes,
-                           int32_t n_scenes, const hgm_params *params, void *stream, float *energy, int32_t *assign)
+namespace {
+
+hgm_status check_block_models(const hgm_model *const *models, int nm, int *F)
 {
-    std::lock_guard<std::mutex> lk(g_mu);
-    g_err.clear();
-    hgm_status rc = check_params(params);
-    if (rc) return rc;
-    if (params->precision != 0 || params->prune)
-        return fail(HGM_EUNSUPPORTED, "the whole-block problem runs in plain FP32 only (precision 0, no pruning)");
-    if (n_models < 0 || n_scenes < 0 || (n_models && !models) || (n_scenes && !scenes))
-        return fail(HGM_EINVAL, "bad model/scene arrays");
-    const int nm = n_models, ns = n_scenes;
-    if (nm == 0 || ns == 0 || (!energy && !assign)) return HGM_OK;
-    int F = -1;
+    *F = -1;
     for (int m = 0; m < nm; ++m) {
         if (!valid_model(models[m])) return fail(HGM_EINVAL, "models[%d] is not a model handle", m);
-        if (F < 0) F = models[m]->F_user;
-        if (models[m]->F_user != F) return fail(HGM_EINVAL, "descriptor widths differ across models");
+        if (*F < 0) *F = models[m]->F_user;
+        if (models[m]->F_user != *F) return fail(HGM_EINVAL, "descriptor widths differ across models");
     }
-    for (int s = 0; s < ns; ++s) {
-        if (!valid_scene(scenes[s])) return fail(HGM_EINVAL, "scenes[%d] is not a scene handle", s);
-        if (scenes[s]->F_user != F) return fail(HGM_EINVAL, "descriptor width differs between model and scene");
+    return HGM_OK;
+}
+
+// Gathers the models' sorted descriptors into one row block and uploads their records.
+hgm_status prep_block_models(BlockBufs &bb, const hgm_model *const *models, int nm, cudaStream_t st)
+{
+    bb.R = 0;
+    bb.urow.assign((size_t)nm, 0);
+    for (int m = 0; m < nm; ++m) {
+        bb.urow[(size_t)m] = bb.R;
+        bb.R += models[m]->d.M;
     }
-    cudaStream_t st = (cudaStream_t)stream;
+    const int Fp = nm ? models[0]->d.F : 0;
+    CK(bb.model.ensure((size_t)std::max(bb.R, 1) * std::max(Fp, 1) * sizeof(float)), "workspace (block)");
+    CK(bb.mrec.ensure((size_t)std::max(nm, 1) * sizeof(ModelRec)), "workspace (block)");
+    std::vector<ModelRec> mrec((size_t)nm);
+    for (int m = 0; m < nm; ++m) {
+        const hgm_model *md = models[m];
+        CK(cudaMemcpyAsync(bb.model.as<float>() + (size_t)bb.urow[(size_t)m] * Fp, md->d.f,
+                           (size_t)md->d.M * Fp * sizeof(float), cudaMemcpyDeviceToDevice, st),
+           "gather model descriptors");
+        mrec[(size_t)m] = ModelRec{md->d.xy, md->d.t, md->d.perm, md->d.M, bb.urow[(size_t)m], md->d.f, md->d.geo};
+    }
+    Exec ex;
+    return h2d(ex, bb.mrec.p, mrec.data(), mrec.size() * sizeof(ModelRec), st);
+}
+
+// The whole-block problem for every (model, scene) pair; the models were prepared by prep_block_models.
+hgm_status run_block(BlockBufs &bb, const hgm_model *const *models, int nm, const hgm_scene *const *scenes, int ns,
+                     const hgm_params *params, cudaStream_t st, float *energy, int32_t *assign)
+{
     const int T = params->T;
     // band tables per scene (host, from the minnode table): lo(b), cs(b)
     std::vector<int64_t> lo_off((size_t)ns), cs_off((size_t)ns), cell_off((size_t)ns), cells((size_t)ns);
@@ -1424,7 +1484,6 @@ hgm_status hgm_match_block(const hgm_model *const *models, int32_t n_models, con
             }
         }
         cs_all.push_back(c);
-        (void)S;
         cells[(size_t)s] = c;
         cell_off[(size_t)s] = total_cells;
         total_cells += c;
@@ -1433,23 +1492,20 @@ hgm_status hgm_match_block(const hgm_model *const *models, int32_t n_models, con
     // units and outputs: pair q = m * n_scenes + s, assignment rows of M_m in pair order
     std::vector<BlockUnit> units;
     int64_t beta_total = 0, a_total = 0;
-    int R = 0;
-    std::vector<int> urow((size_t)nm);
-    for (int m = 0; m < nm; ++m) {
-        urow[(size_t)m] = R;
-        R += models[m]->d.M;
-    }
     for (int m = 0; m < nm; ++m)
         for (int s = 0; s < ns; ++s) {
             units.push_back(BlockUnit{m, s, beta_total, (int64_t)m * ns + s, a_total});
             beta_total += (int64_t)(models[m]->d.M - 2) * cells[(size_t)s];
             a_total += models[m]->d.M;
         }
-    size_t free_b = 0, total_b = 0;
-    CK(cudaMemGetInfo(&free_b, &total_b), "cudaMemGetInfo");
-    if ((double)beta_total * 2 > 0.6 * (double)free_b)
-        return fail(HGM_ENOMEM, "whole-block argmin tables need %lld bytes", (long long)(beta_total * 2));
-    Workspace &ws = g_ws;
+    const size_t beta_bytes = (size_t)std::max<int64_t>(beta_total, 1) * sizeof(uint16_t);
+    if (beta_bytes > bb.beta.bytes) {
+        size_t free_b = 0, total_b = 0;
+        CK(cudaMemGetInfo(&free_b, &total_b), "cudaMemGetInfo");
+        if ((double)beta_bytes > 0.6 * (double)(free_b + bb.beta.bytes))
+            return fail(HGM_ENOMEM, "whole-block argmin tables need %zu bytes", beta_bytes);
+    }
+    const int R = bb.R;
     const int Fp = models[0]->d.F;
     int64_t S_total = 0;
     std::vector<int64_t> u_off((size_t)ns);
@@ -1457,92 +1513,231 @@ hgm_status hgm_match_block(const hgm_model *const *models, int32_t n_models, con
         u_off[(size_t)s] = S_total * R;
         S_total += scenes[s]->d.S;
     }
-    CK(ws.blk_tab.ensure(lo_all.size() * sizeof(int32_t) + cs_all.size() * sizeof(int64_t) + 64), "workspace (block)");
-    CK(ws.blk_cellb.ensure((size_t)std::max<int64_t>(total_cells, 1) * sizeof(int32_t)), "workspace (block)");
-    CK(ws.blk_dir.ensure((size_t)std::max<int64_t>(total_cells, 1) * 2 * sizeof(float)), "workspace (block)");
-    CK(ws.blk_model.ensure((size_t)R * Fp * sizeof(float)), "workspace (block)");
-    CK(ws.blk_U.ensure((size_t)std::max<int64_t>(S_total * R, 1) * sizeof(float)), "workspace (block)");
-    CK(ws.blk_beta.ensure((size_t)std::max<int64_t>(beta_total, 1) * sizeof(uint16_t)), "workspace (block)");
+    const size_t lo_bytes = (lo_all.size() * sizeof(int32_t) + 7) & ~(size_t)7;
+    CK(bb.tab.ensure(lo_bytes + cs_all.size() * sizeof(int64_t)), "workspace (block)");
+    CK(bb.cellb.ensure((size_t)std::max<int64_t>(total_cells, 1) * sizeof(int32_t)), "workspace (block)");
+    CK(bb.dir.ensure((size_t)std::max<int64_t>(total_cells, 1) * 2 * sizeof(float)), "workspace (block)");
+    CK(bb.U.ensure((size_t)std::max<int64_t>(S_total * R, 1) * sizeof(float)), "workspace (block)");
+    CK(bb.beta.ensure(beta_bytes), "workspace (block)");
     const size_t b_units = (units.size() * sizeof(BlockUnit) + 255) & ~(size_t)255;
-    const size_t b_m = ((size_t)nm * sizeof(ModelRec) + 255) & ~(size_t)255;
     const size_t b_s = ((size_t)ns * sizeof(SceneRec) + 255) & ~(size_t)255;
     const size_t b_g = ((size_t)ns * sizeof(BlockGeo) + 255) & ~(size_t)255;
-    CK(ws.blk_rec.ensure(b_units + b_m + b_s + b_g), "workspace (block)");
-    int32_t *d_lo = ws.blk_tab.as<int32_t>();
-    const size_t lo_bytes = (lo_all.size() * sizeof(int32_t) + 7) & ~(size_t)7;
-    int64_t *d_cs = reinterpret_cast<int64_t *>(ws.blk_tab.as<char>() + lo_bytes);
+    CK(bb.rec.ensure(b_units + b_s + b_g), "workspace (block)");
+    int32_t *d_lo = bb.tab.as<int32_t>();
+    int64_t *d_cs = reinterpret_cast<int64_t *>(bb.tab.as<char>() + lo_bytes);
     Exec ex;
+    hgm_status rc;
     if ((rc = h2d(ex, d_lo, lo_all.data(), lo_all.size() * sizeof(int32_t), st)) ||
         (rc = h2d(ex, d_cs, cs_all.data(), cs_all.size() * sizeof(int64_t), st)))
         return rc;
     std::vector<BlockGeo> geos((size_t)ns);
     std::vector<SceneRec> srec((size_t)ns);
-    float *dirf_all = ws.blk_dir.as<float>(), *dirb_all = dirf_all + total_cells;
+    float *dirf_all = bb.dir.as<float>(), *dirb_all = dirf_all + total_cells;
     for (int s = 0; s < ns; ++s) {
         const hgm_scene *sc = scenes[s];
         const int32_t *lo = d_lo + lo_off[(size_t)s];
         const int64_t *cs = d_cs + cs_off[(size_t)s];
-        int32_t *cellb = ws.blk_cellb.as<int32_t>() + cell_off[(size_t)s];
+        int32_t *cellb = bb.cellb.as<int32_t>() + cell_off[(size_t)s];
         float *dirf = dirf_all + cell_off[(size_t)s], *dirb = dirb_all + cell_off[(size_t)s];
         CK(launch_block_geo(sc->d.xy, sc->d.S, lo, cs, cells[(size_t)s], cellb, dirf, dirb, st), "block geometry");
         geos[(size_t)s] = BlockGeo{lo, cs, cellb, dirf, dirb, cells[(size_t)s]};
-        float *U = ws.blk_U.as<float>() + u_off[(size_t)s];
+        float *U = bb.U.as<float>() + u_off[(size_t)s];
         srec[(size_t)s] = SceneRec{sc->d.xy, sc->d.t, sc->d.frame_start, sc->d.perm, U, (int64_t)sc->d.S, sc->d.S,
                                    sc->d.n_frames, sc->d.f, nullptr, 0};
-    }
-    std::vector<ModelRec> mrec((size_t)nm);
-    for (int m = 0; m < nm; ++m) {
-        const hgm_model *md = models[m];
-        CK(cudaMemcpyAsync(ws.blk_model.as<float>() + (size_t)urow[(size_t)m] * Fp, md->d.f,
-                           (size_t)md->d.M * Fp * sizeof(float), cudaMemcpyDeviceToDevice, st),
-           "gather model descriptors");
-        mrec[(size_t)m] = ModelRec{md->d.xy, md->d.t, md->d.perm, md->d.M, urow[(size_t)m], md->d.f, md->d.geo};
-    }
-    for (int s = 0; s < ns; ++s)
-        if (scenes[s]->d.S > 0)
-            CK(launch_unary(ws.blk_model.as<float>(), R, scenes[s]->d.f, scenes[s]->d.S, Fp, params->lambda1,
-                            ws.blk_U.as<float>() + u_off[(size_t)s], scenes[s]->d.S, st),
+        if (sc->d.S > 0)
+            CK(launch_unary(bb.model.as<float>(), R, sc->d.f, sc->d.S, Fp, params->lambda1, U, sc->d.S, st),
                "unary kernel");
-    char *rec = ws.blk_rec.as<char>();
+    }
+    char *rec = bb.rec.as<char>();
     if ((rc = h2d(ex, rec, units.data(), units.size() * sizeof(BlockUnit), st)) ||
-        (rc = h2d(ex, rec + b_units, mrec.data(), mrec.size() * sizeof(ModelRec), st)) ||
-        (rc = h2d(ex, rec + b_units + b_m, srec.data(), srec.size() * sizeof(SceneRec), st)) ||
-        (rc = h2d(ex, rec + b_units + b_m + b_s, geos.data(), geos.size() * sizeof(BlockGeo), st)))
+        (rc = h2d(ex, rec + b_units, srec.data(), srec.size() * sizeof(SceneRec), st)) ||
+        (rc = h2d(ex, rec + b_units + b_s, geos.data(), geos.size() * sizeof(BlockGeo), st)))
         return rc;
     const bool e_dev = energy && is_device_ptr(energy), a_dev = assign && is_device_ptr(assign);
     float *de = energy;
     int32_t *da = assign;
     if (!energy || !e_dev) {
-        CK(ws.blk_oe.ensure(units.size() * sizeof(float)), "workspace (block)");
-        de = ws.blk_oe.as<float>();
+        CK(bb.oe.ensure(units.size() * sizeof(float)), "workspace (block)");
+        de = bb.oe.as<float>();
     }
     if (!assign || !a_dev) {
-        CK(ws.blk_oa.ensure((size_t)a_total * sizeof(int32_t)), "workspace (block)");
-        da = ws.blk_oa.as<int32_t>();
+        CK(bb.oa.ensure((size_t)a_total * sizeof(int32_t)), "workspace (block)");
+        da = bb.oa.as<int32_t>();
     }
     Params p = to_params(params);
     p.F = Fp;
     float *scratch = nullptr;
     int grid_global = 0;
-    if (max_cells > block_smem_cells()) {
+    static int64_t smem_cells = -1;
+    if (smem_cells < 0) smem_cells = block_smem_cells();
+    if (max_cells > smem_cells) {
         int dev = 0, sms = 0;
         CK(cudaGetDevice(&dev), "device");
         CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "device");
         grid_global = (int)std::min<int64_t>((int64_t)units.size(), (int64_t)sms * 2);
-        CK(ws.blk_scratch.ensure((size_t)grid_global * 2 * max_cells * sizeof(float)), "workspace (block)");
-        scratch = ws.blk_scratch.as<float>();
+        CK(bb.scratch.ensure((size_t)grid_global * 2 * max_cells * sizeof(float)), "workspace (block)");
+        scratch = bb.scratch.as<float>();
     }
-    CK(launch_block_recurse(reinterpret_cast<const BlockUnit *>(rec), (int)units.size(),
-                            reinterpret_cast<const ModelRec *>(rec + b_units),
-                            reinterpret_cast<const SceneRec *>(rec + b_units + b_m),
-                            reinterpret_cast<const BlockGeo *>(rec + b_units + b_m + b_s), p, max_cells,
-                            ws.blk_beta.as<uint16_t>(), scratch, grid_global, de, da, st),
+    CK(launch_block_recurse(reinterpret_cast<const BlockUnit *>(rec), (int)units.size(), bb.mrec.as<ModelRec>(),
+                            reinterpret_cast<const SceneRec *>(rec + b_units),
+                            reinterpret_cast<const BlockGeo *>(rec + b_units + b_s), p, max_cells,
+                            bb.beta.as<uint16_t>(), scratch, grid_global, de, da, st),
        "block recursion kernel");
     if (energy && !e_dev)
         CK(cudaMemcpyAsync(energy, de, units.size() * sizeof(float), cudaMemcpyDeviceToHost, st), "copy energy");
     if (assign && !a_dev)
         CK(cudaMemcpyAsync(assign, da, (size_t)a_total * sizeof(int32_t), cudaMemcpyDeviceToHost, st), "copy assign");
     if ((energy && !e_dev) || (assign && !a_dev)) CK(cudaStreamSynchronize(st), "synchronise outputs");
+    return HGM_OK;
+}
+
+}  // namespace
+
+hgm_status hgm_match_block(const hgm_model *const *models, int32_t n_models, const hgm_scene *const *scenes,
+                           int32_t n_scenes, const hgm_params *params, void *stream, float *energy, int32_t *assign)
+{
+    std::lock_guard<std::mutex> lk(g_mu);
+    g_err.clear();
+    hgm_status rc = check_params(params);
+    if (rc) return rc;
+    if (params->precision != 0 || params->prune)
+        return fail(HGM_EUNSUPPORTED, "the whole-block problem runs in plain FP32 only (precision 0, no pruning)");
+    if (n_models < 0 || n_scenes < 0 || (n_models && !models) || (n_scenes && !scenes))
+        return fail(HGM_EINVAL, "bad model/scene arrays");
+    if (n_models == 0 || n_scenes == 0 || (!energy && !assign)) return HGM_OK;
+    int F;
+    if ((rc = check_block_models(models, n_models, &F))) return rc;
+    for (int s = 0; s < n_scenes; ++s) {
+        if (!valid_scene(scenes[s])) return fail(HGM_EINVAL, "scenes[%d] is not a scene handle", s);
+        if (scenes[s]->F_user != F) return fail(HGM_EINVAL, "descriptor width differs between model and scene");
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    if ((rc = prep_block_models(g_blk, models, n_models, st))) return rc;
+    return run_block(g_blk, models, n_models, scenes, n_scenes, params, st, energy, assign);
+}
+
+// ---- streaming blocks (Sec. 4: the scene cut into blocks of ~60 frames, matched as they arrive) ----------
+hgm_status hgm_stream_create(const hgm_model *const *models, int32_t n_models, const hgm_params *params,
+                             int32_t block_frames, void *stream, hgm_stream **out)
+{
+    std::lock_guard<std::mutex> lk(g_mu);
+    g_err.clear();
+    if (!out) return fail(HGM_EINVAL, "out is NULL");
+    *out = nullptr;
+    hgm_status rc = check_params(params);
+    if (rc) return rc;
+    if (params->precision != 0 || params->prune)
+        return fail(HGM_EUNSUPPORTED, "the whole-block problem runs in plain FP32 only (precision 0, no pruning)");
+    if (n_models < 1 || !models) return fail(HGM_EINVAL, "need at least one model");
+    if (block_frames < 1) return fail(HGM_EINVAL, "block_frames must be >= 1 (got %d)", block_frames);
+    int F;
+    if ((rc = check_block_models(models, n_models, &F))) return rc;
+    hgm_stream *s = new hgm_stream();
+    s->magic = kStreamMagic;
+    s->models.assign(models, models + n_models);
+    s->params = *params;
+    s->block_frames = block_frames;
+    s->F_user = F;
+    s->Fp = models[0]->d.F;
+    s->view.magic = kSceneMagic;
+    s->view.F_user = F;
+    cudaStream_t st = (cudaStream_t)stream;
+    rc = prep_block_models(s->bb, s->models.data(), n_models, st);
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (!rc && e != cudaSuccess) rc = cuda_fail(e, "stream create");
+    if (rc) {
+        free_stream(s);
+        s->magic = kDeadMagic;
+        delete s;
+        return rc;
+    }
+    *out = s;
+    return HGM_OK;
+}
+
+hgm_status hgm_stream_match(hgm_stream *s, const float *xy, const int32_t *t, const float *desc, int32_t n,
+                            void *stream, float *energy, int32_t *assign)
+{
+    std::lock_guard<std::mutex> lk(g_mu);
+    g_err.clear();
+    if (!valid_stream(s)) return fail(HGM_EINVAL, "not a stream handle");
+    if (n < 0) return fail(HGM_EINVAL, "n must be >= 0");
+    if (n > 0 && (!xy || !t || !desc)) return fail(HGM_EINVAL, "NULL input array");
+    cudaStream_t st = (cudaStream_t)stream;
+    const int B = s->block_frames, F = s->F_user, Fp = s->Fp;
+    std::vector<float> hxy;
+    std::vector<int32_t> ht;
+    hgm_status rc;
+    if ((rc = fetch(xy, (size_t)n * 2, hxy, st)) || (rc = fetch(t, (size_t)n, ht, st))) return rc;
+    for (int32_t v : ht)
+        if (v < 0 || v >= B) return fail(HGM_EINVAL, "block frame %d outside [0, %d)", v, B);
+    for (float v : hxy)
+        if (!std::isfinite(v)) return fail(HGM_EINVAL, "non-finite scene coordinate");
+    // stable counting sort by frame; the block's points, permutation and minnode table in one upload
+    std::vector<int32_t> fs((size_t)B + 1, 0);
+    for (int32_t v : ht) fs[(size_t)v + 1]++;
+    for (int f = 0; f < B; ++f) fs[(size_t)f + 1] += fs[(size_t)f];
+    std::vector<int32_t> perm((size_t)n);
+    {
+        std::vector<int32_t> w(fs.begin(), fs.end() - 1);
+        for (int32_t k = 0; k < n; ++k) perm[(size_t)w[(size_t)ht[(size_t)k]]++] = k;
+    }
+    const size_t o_xy = 0, o_t = o_xy + (((size_t)n * 8 + 15) & ~(size_t)15);
+    const size_t o_perm = o_t + (((size_t)n * 4 + 15) & ~(size_t)15);
+    const size_t o_fs = o_perm + (((size_t)n * 4 + 15) & ~(size_t)15);
+    const size_t o_raw = o_fs + (((size_t)(B + 1) * 4 + 15) & ~(size_t)15);
+    const bool desc_dev = n > 0 && is_device_ptr(desc);
+    const size_t total = o_raw + (desc_dev ? 0 : (size_t)n * F * sizeof(float));
+    if (total > s->pinned_bytes) {
+        CK(cudaStreamSynchronize(st), "synchronise before growing the staging buffer");
+        if (s->pinned) cudaFreeHost(s->pinned);
+        s->pinned = nullptr;
+        s->pinned_bytes = 0;
+        CK(cudaMallocHost(&s->pinned, total * 2), "pinned staging");
+        s->pinned_bytes = total * 2;
+    } else {
+        CK(cudaStreamSynchronize(st), "synchronise the staging buffer");   // the previous block's upload
+    }
+    char *h = static_cast<char *>(s->pinned);
+    float2 *sxy = reinterpret_cast<float2 *>(h + o_xy);
+    int32_t *stt = reinterpret_cast<int32_t *>(h + o_t);
+    for (int32_t k = 0; k < n; ++k) {
+        const int32_t q = perm[(size_t)k];
+        sxy[k] = make_float2(hxy[(size_t)q * 2], hxy[(size_t)q * 2 + 1]);
+        stt[k] = ht[(size_t)q];
+    }
+    std::memcpy(h + o_perm, perm.data(), (size_t)n * 4);
+    std::memcpy(h + o_fs, fs.data(), (size_t)(B + 1) * 4);
+    if (!desc_dev && n > 0) std::memcpy(h + o_raw, desc, (size_t)n * F * sizeof(float));
+    CK(s->sc_buf.ensure(total), "stream buffers");
+    CK(s->f.ensure((size_t)std::max(n, 1) * Fp * sizeof(float)), "stream buffers");
+    CK(s->flag.ensure(sizeof(int)), "stream buffers");
+    CK(cudaMemcpyAsync(s->sc_buf.p, h, total, cudaMemcpyHostToDevice, st), "upload block");
+    char *d = s->sc_buf.as<char>();
+    CK(cudaMemsetAsync(s->flag.p, 0, sizeof(int), st), "memset");
+    if (n > 0) {
+        const float *dsrc = desc_dev ? desc : reinterpret_cast<const float *>(d + o_raw);
+        const int64_t blocks = std::min<int64_t>(((int64_t)n * Fp + 255) / 256, 65536);
+        gather_rows_kernel<<<(unsigned)blocks, 256, 0, st>>>(dsrc, F, reinterpret_cast<const int32_t *>(d + o_perm), n,
+                                                             Fp, s->f.as<float>(), s->flag.as<int>());
+        CK(cudaGetLastError(), "gather kernel");
+    }
+    hgm_scene &v = s->view;
+    v.d = SceneDev{n, Fp, B, reinterpret_cast<float2 *>(d + o_xy), reinterpret_cast<int32_t *>(d + o_t),
+                   s->f.as<float>(), reinterpret_cast<int32_t *>(d + o_fs), reinterpret_cast<int32_t *>(d + o_perm)};
+    v.perm = perm;
+    v.fs_host = fs;
+    const hgm_scene *sv = &v;
+    std::vector<const hgm_model *> &ms = s->models;
+    const bool host_out = (energy && !is_device_ptr(energy)) || (assign && !is_device_ptr(assign));
+    rc = run_block(s->bb, ms.data(), (int)ms.size(), &sv, 1, &s->params, st, energy, assign);
+    if (rc) return rc;
+    int bad = 0;
+    if (host_out) {
+        CK(cudaMemcpyAsync(&bad, s->flag.p, sizeof(int), cudaMemcpyDeviceToHost, st), "flag");
+        CK(cudaStreamSynchronize(st), "synchronise");
+        if (bad) return fail(HGM_EINVAL, "non-finite block descriptor (outputs are not valid)");
+    }
     return HGM_OK;
 }
 

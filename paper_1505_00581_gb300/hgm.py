@@ -67,6 +67,8 @@ SIGNATURES = {
     "hgm_plan_check": (_i32, [_vp, _vp]),
     "hgm_prop_scores": (_i32, [_vp, _vp, _vp, _vp, _i32, _i32, _vp, _vp]),
     "hgm_match_chains": (_i32, [_vp, _vp, _PP, _i32, _vp, _p32, _p32, _vp, _vp]),
+    "hgm_stream_create": (_i32, [ctypes.POINTER(_vp), _i32, _PP, _i32, _vp, ctypes.POINTER(_vp)]),
+    "hgm_stream_match": (_i32, [_vp, _vp, _vp, _vp, _i32, _vp, _vp, _vp]),
     "hgm_match_block": (_i32, [ctypes.POINTER(_vp), _i32, ctypes.POINTER(_vp), _i32, _PP, _vp, _vp, _vp]),
     "hgm_match_chains_batch": (_i32, [ctypes.POINTER(_vp), _i32, ctypes.POINTER(_vp), _i32, _PP, _i32, _vp, _vp,
                                       _vp]),
@@ -476,6 +478,57 @@ def match_block(models: Sequence[Model], scenes: Sequence[Scene], params: Params
     (pe, ke), (pa, ka) = _ptr(energy), _ptr(assign)
     _check(lib.hgm_match_block(mh, nm, sh, ns, ctypes.byref(params), _stream(stream), pe, pa))
     return ke, ka
+
+
+class Stream:
+    """hgm_stream_*: blocks of block_frames frames matched whole against fixed models as they arrive."""
+
+    def __init__(self, models: Sequence[Model], params: Params, block_frames: int, stream=None):
+        self.lib = load()
+        self.models = list(models)     # the handles must outlive the stream
+        self.params = params
+        self.block_frames = int(block_frames)
+        self.starts = block_layout(self.models, 1)
+        mh = (ctypes.c_void_p * len(self.models))(*[m.handle for m in self.models])
+        h = ctypes.c_void_p()
+        _check(self.lib.hgm_stream_create(mh, len(self.models), ctypes.byref(params), self.block_frames,
+                                          _stream(stream), ctypes.byref(h)))
+        self.handle = h
+
+    def match(self, xy, t, f, energy=None, assign=None, stream=None):
+        """One block: frames t in [0, block_frames). Returns (energy [n_models], assign [sum M])."""
+        if energy is None and assign is None:
+            energy = np.zeros(len(self.models), np.float32)
+            assign = np.zeros(int(self.starts[-1]), np.int32)
+        xy, t, f = _as(xy, np.float32), _as(t, np.int32), _as(f, np.float32)
+        n = int(t.shape[0])
+        (pxy, kxy), (pt, kt), (pf, kf) = _ptr(xy), _ptr(t), _ptr(f)
+        (pe, ke), (pa, ka) = _ptr(energy), _ptr(assign)
+        _check(self.lib.hgm_stream_match(self.handle, pxy, pt, pf, n, _stream(stream), pe, pa))
+        return ke, ka
+
+    def close(self):
+        if getattr(self, "handle", None) and self.handle.value:
+            self.lib.hgm_destroy(self.handle)
+            self.handle = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def stream_blocks(xy, t, f, n_frames: int, block_frames: int = 60, hop: int = 30):
+    """Cuts a scene into blocks of block_frames frames starting every hop frames (the last block ends at the
+    scene's end). Yields (first_frame, xy, t - first_frame, f, caller indices) per block."""
+    t = np.asarray(t)
+    starts = list(range(0, max(1, n_frames - block_frames + 1), hop))
+    if starts[-1] + block_frames < n_frames:
+        starts.append(n_frames - block_frames)
+    for s0 in starts:
+        idx = np.nonzero((t >= s0) & (t < s0 + block_frames))[0]
+        yield s0, xy[idx], (t[idx] - s0).astype(np.int32), f[idx], idx
 
 
 def match_chains_batch(models: Sequence[Model], scenes: Sequence[Scene], params: Params, n_chains: int,

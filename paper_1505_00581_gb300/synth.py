@@ -257,6 +257,30 @@ def paper_blocks(seed: int = 4, n_models: int = 50, M: int = 30, n_blocks: int =
     return Workload(f"paper_blocks_{n_models}x{n_blocks}_M{M}_F{block_frames}", models, scenes, K=64, window=3)
 
 
+def paper_stream(seed: int = 5, n_models: int = 50, M: int = 30, n_frames: int = 1800, lam: float = 1.0,
+                 implant_every: int = 120, frame=(160.0, 120.0)) -> Workload:
+    """The paper's continuous-video scenario (Sec. 4): 50 one-per-frame models of 30 points and one long scene
+    of about one point per frame (a minute at 30 frames/s), with a jittered copy of a random model every
+    implant_every frames; streamed as 60-frame blocks."""
+    rng = np.random.default_rng(seed)
+    models = [paper_model(rng, M) for _ in range(n_models)]
+    pool = np.concatenate([m.centres for m in models])
+    imps = [(int(rng.integers(n_models)), int(o)) for o in range(15, n_frames - M, implant_every)]
+    sc = make_scene(rng, n_frames, frame, ("poisson", lam), pool, models, imps)
+    return Workload(f"paper_stream_{n_models}x1_M{M}_F{n_frames}", models, [sc], K=64, window=3)
+
+
+def paper_whole(seed: int = 6, n_models: int = 50, M: int = 30, n_frames: int = 723, nodes: int = 754,
+                frame=(160.0, 120.0)) -> Workload:
+    """Table 2's scene: a 723-frame video with about 754 interest points (one implant), matched whole."""
+    rng = np.random.default_rng(seed)
+    models = [paper_model(rng, M) for _ in range(n_models)]
+    pool = np.concatenate([m.centres for m in models])
+    sc = make_scene(rng, n_frames, frame, ("poisson", (nodes - M) / n_frames), pool, models,
+                    [(int(rng.integers(n_models)), n_frames // 2)])
+    return Workload(f"paper_whole_{n_models}x1_M{M}_F{n_frames}", models, [sc], K=64, window=3)
+
+
 def tiny_case(seed: int, M: int = 5, n_frames: int = 12, per_frame: int = 3, K: int = 5, window: int = 1,
               F: int = 8, T: int = 10, frame=(20.0, 20.0)) -> Workload:
     """Very small random instance for brute-force enumeration."""

@@ -1,0 +1,88 @@
+"""Streaming blocks on the GPU (hgm_stream_*): a scene cut into 60-frame blocks every 30 frames, each block
+matched whole against every model, against the FP64 oracle's whole-block solve of the same block, and
+bit for bit against hgm_match_block on a scene handle of that block."""
+import numpy as np
+import pytest
+
+from paper_1505_00581_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+LAM = dict(lambda1=0.6, lambda2=0.2, lambda3=5.0)
+
+
+@pytest.fixture(scope="module")
+def env():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    from paper_1505_00581_gb300 import build, hgm
+    build.build()
+    hgm.load()
+    import oracle
+    oracle.build()
+    return torch, hgm, oracle
+
+
+def _long_scene(seed, n_models=3, n_frames=240, lam=1.2):
+    rng = np.random.default_rng(seed)
+    models = [synth.paper_model(rng, 30) for _ in range(n_models)]
+    pool = np.concatenate([m.centres for m in models])
+    imps = [(k % n_models, int(o)) for k, o in enumerate(range(10, n_frames - 30, 70))]
+    sc = synth.make_scene(rng, n_frames, (160.0, 120.0), ("poisson", lam), pool, models, imps)
+    return models, sc
+
+
+def test_stream_blocks_match_oracle_and_block_call(env):
+    torch, hgm, oracle = env
+    mods, sc = _long_scene(5)
+    M = [hgm.Model(m.xy, m.t, m.f) for m in mods]
+    p = hgm.default_params()
+    st = hgm.Stream(M, p, 60)
+    n_blocks = finite = 0
+    for s0, bxy, bt, bf, idx in hgm.stream_blocks(sc.xy, sc.t, sc.f, sc.n_frames, 60, 30):
+        e, a = st.match(bxy, bt, bf)
+        # the same block as a scene handle through hgm_match_block: identical bits
+        S = hgm.Scene(bxy, bt, bf, 60)
+        e2, a2 = hgm.match_block(M, [S], p)
+        np.testing.assert_array_equal(e, e2)
+        np.testing.assert_array_equal(a, a2)
+        for mi, mod in enumerate(mods):
+            orc = oracle.Oracle(mod.xy, mod.t, mod.f, bxy, bt, bf, 60, K=8, window=1, T=10, **LAM)
+            e64, z64, _ = orc.match_block()
+            z = a[st.starts[mi]:st.starts[mi + 1]]
+            assert np.isfinite(e64) == np.isfinite(e[mi])
+            if np.isfinite(e64):
+                finite += 1
+                assert abs(e[mi] - e64) <= 1e-5 * e64 + 1e-6, (s0, mi, e[mi], e64)
+                if not np.array_equal(z, z64):
+                    assert orc.energy(z) <= e64 * (1 + 1e-5) + 1e-6
+        n_blocks += 1
+    assert n_blocks == 7 and finite >= 10
+
+
+def test_stream_growth_device_inputs_and_errors(env):
+    torch, hgm, oracle = env
+    mods, _ = _long_scene(6, n_models=2)
+    M = [hgm.Model(m.xy, m.t, m.f) for m in mods]
+    p = hgm.default_params()
+    st = hgm.Stream(M, p, 60)
+    rng = np.random.default_rng(3)
+    pool = np.concatenate([m.centres for m in mods])
+    dev = torch.device("cuda")
+    for lam in (0.5, 6.0, 1.0):      # the second block grows every buffer; the third reuses them
+        sc = synth.make_scene(rng, 60, (160.0, 120.0), ("poisson", lam), pool, mods, [(0, 12)])
+        e, a = st.match(sc.xy, sc.t, sc.f)
+        ed = torch.empty(2, dtype=torch.float32, device=dev)
+        ad = torch.empty(int(st.starts[-1]), dtype=torch.int32, device=dev)
+        st.match(*(torch.from_numpy(x).to(dev) for x in (sc.xy, sc.t, sc.f)), energy=ed, assign=ad)
+        torch.cuda.synchronize()
+        np.testing.assert_array_equal(e, ed.cpu().numpy())
+        np.testing.assert_array_equal(a, ad.cpu().numpy())
+        orc = oracle.Oracle(mods[0].xy, mods[0].t, mods[0].f, sc.xy, sc.t, sc.f, 60, K=8, window=1, T=10, **LAM)
+        e64, _, _ = orc.match_block()
+        assert abs(e[0] - e64) <= 1e-5 * e64 + 1e-6
+    bad_t = np.full(4, 60, np.int32)
+    with pytest.raises(hgm.HgmError) as err:
+        st.match(np.zeros((4, 2), np.float32), bad_t, np.zeros((4, mods[0].F), np.float32))
+    assert err.value.status == hgm.HGM_EINVAL
+    st.close()
