@@ -365,6 +365,22 @@ def run_pruned(args, torch, hgm, wl, models, scenes, energy, assign, es, as_, de
     masks = prop_train.implant_masks(wl, first_, es_)
     erows = [int(es_[q]) for q in range(len(blocks))]
     quality = prop_train.compare(e_ref, a_ref, e2.cpu().numpy(), a2.cpu().numpy(), blocks, erows, masks)
+    # the pruned form with the refinement (keep 12 of 64, then per pair the 32 offsets of lowest pruned
+    # energy solved unpruned): the operating point whose per-pair distances match the unpruned ones
+    pr = hgm.default_params(K=wl.K, window=wl.window, T=wl.T, precision=1, prune=prop, keep=12, refine=32)
+    hgm.refine_counter(reset=True)
+    msr, _ = _time_form(torch, hgm, models, scenes, pr, e2, a2, args.steps, args.warmup, stream, flush)
+    msr = max_over_ranks(msr, dist, dev)
+    n_ref = hgm.refine_counter(reset=True) / max(1, args.steps + args.warmup)
+    refined_q = prop_train.compare(e_ref, a_ref, e2.cpu().numpy(), a2.cpu().numpy(), blocks, erows, masks)
+    refined = {"value": job_rate(wl.total_frames, world, msr / 1e3), "unit": "frames/s", "ms_per_step": msr,
+               "keep": 12, "refine": 32, "refined_units_per_step": n_ref, **refined_q}
+    # the BF16 distance form alone (no pruning): tensor-core unary table, 8 smallest re-scored in FP32
+    pu = hgm.default_params(K=wl.K, window=wl.window, T=wl.T, precision=1)
+    msu, _ = _time_form(torch, hgm, models, scenes, pu, e2, a2, max(1, args.steps // 2), 1, stream, flush)
+    msu = max_over_ranks(msu, dist, dev)
+    bf16_q = prop_train.compare(e_ref, a_ref, e2.cpu().numpy(), a2.cpu().numpy(), blocks, erows, masks)
+    bf16 = {"value": job_rate(wl.total_frames, world, msu / 1e3), "unit": "frames/s", "ms_per_step": msu, **bf16_q}
     # the same pruning without the network: the 8 smallest unary costs (K = 8 window cap), BF16 + re-score
     pb = hgm.default_params(K=8, window=wl.window, T=wl.T, precision=1)
     first8, es8, as8 = hgm.batch_layout(models, scenes, pb)
@@ -380,6 +396,7 @@ def run_pruned(args, torch, hgm, wl, models, scenes, energy, assign, es, as_, de
             "keep": 8, "K": wl.K, "precision": "BF16 unary + FP32 re-score of kept candidates",
             "fallback_units_per_step": n_fb / max(1, args.steps + args.warmup),
             "units_per_step": n_pruned / max(1, args.steps + args.warmup), **quality,
+            "refined": refined, "bf16_unpruned": bf16,
             "top8_by_unary_baseline": {"value": job_rate(wl.total_frames, world, ms8 / 1e3), "unit": "frames/s", **base_q},
             "training": {k: v for k, v in info.items() if k != "loss"}, "final_loss": (info.get("loss") or [[0, None]])[-1][1],
             "train_s": train_s}

@@ -92,9 +92,13 @@ typedef struct {
                                       candidates of every list (ties: lower slot) before the recursion; units
                                       whose pruned optimum is infeasible are re-solved on the full lists. */
     int32_t keep;       /* candidates kept per list when pruning, 1..K (default 8) */
+    int32_t refine;     /* with pruning: per (model, scene) pair, the `refine` offsets of lowest pruned
+                           energy are solved again without pruning (same precision mode), so a pair's
+                           minimum over offsets is the unpruned one whenever its offset is among them.
+                           0 (default) = off; 0..65535. Not available in plans (HGM_EUNSUPPORTED). */
 } hgm_params;
 
-/* Fills *p with the defaults above (prune = NULL, keep = 8). */
+/* Fills *p with the defaults above (prune = NULL, keep = 8, refine = 0). */
 HGM_API void hgm_default_params(hgm_params *p);
 
 /* Creates a model from M points (host or device pointers; copied). The chain
@@ -419,6 +423,8 @@ HGM_API hgm_status hgm_profile_evaluated(int64_t *evaluated, int32_t reset);
 /* Units solved on the pruned lists and units re-solved on the full lists
  * (fallback) by batch calls with pruning, since the last reset. */
 HGM_API hgm_status hgm_prune_counters(int64_t *pruned_units, int64_t *fallback_units, int32_t reset);
+/* Units solved again by the refinement (hgm_params.refine) since the last reset. */
+HGM_API hgm_status hgm_refine_counter(int64_t *refined_units, int32_t reset);
 HGM_API hgm_status hgm_profile_read(double *ms, int64_t *launches, int32_t n_kernels);
 HGM_API hgm_status hgm_profile_reset(void);
 

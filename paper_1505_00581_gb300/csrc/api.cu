@@ -150,6 +150,7 @@ struct Workspace {
     Buffer P, Q, Qb, modelxy, cand2_idx, cand2_u, cand2_cnt, units2, beta2, fb_units, fb_count, beta_fb, scores;
     Buffer fb_total;   // fallback units since the last hgm_prune_counters reset (device counter)
     Buffer chain_e, chain_a, chain_tab, chain_oe, chain_oa;   // independent-chains variant
+    Buffer rf_e, rf_a;        // refinement of the pruned form: device outputs when the caller's are on the host
 };
 
 // Buffers of the whole-block form: band tables, model rows, unary table, argmin tables, records, outputs.
@@ -193,6 +194,7 @@ void free_stream(hgm_stream *s)
 bool g_count_mode = false;   // hgm_profile_enable(2): batch runs use the accounting recursion variant
 size_t g_budget_override = 0;   // hgm_set_workspace_budget: bytes for the unary table and for a chunk (0 = auto)
 int64_t g_pruned_units = 0;
+int64_t g_refined_units = 0;   // units solved again by the refinement of the pruned form
 
 // How run_batch issues its work: on the shared workspace (ordinary calls), or for a plan on the plan's own
 // workspace, first as a sizing pass (grows the workspace, keeps a pinned copy of every host upload) and then
@@ -205,6 +207,8 @@ struct Exec {
     size_t pin_next = 0;
     int64_t pruned_units = 0;                             // units of the pruned pass issued
     bool tensor = false;                                  // a tensor-core kernel ran (status flag is live)
+    const std::vector<uint8_t> *select = nullptr;         // if set: only the units whose energy index is marked
+    int64_t refined_units = 0;                            // units solved again by the refinement
 };
 
 hgm_status h2d(Exec &ex, void *dst, const void *src, size_t bytes, cudaStream_t st)
@@ -335,6 +339,8 @@ hgm_status check_params(const hgm_params *p)
     if (p->prune) {
         if (p->prune->magic != kPropMagic) return fail(HGM_EINVAL, "prune is not a proposal-network handle");
         if (p->keep < 1 || p->keep > p->K) return fail(HGM_EINVAL, "keep must be in 1..K (got %d)", p->keep);
+        if (p->refine < 0 || p->refine > 65535)
+            return fail(HGM_EINVAL, "refine must be in 0..65535 (got %d)", p->refine);
     }
     return HGM_OK;
 }
@@ -676,9 +682,14 @@ hgm_status run_batch(Exec &ex, const hgm_model *const *models, int nm, const hgm
         for (int m = 0; m < nm; ++m) {
             const size_t q = (size_t)m * ns + s;
             const int64_t n = pl.e_start[q + 1] - pl.e_start[q];
-            if (n > 0) {
-                o_lo = std::min<int64_t>(o_lo, pl.first[q]);
-                o_hi = std::max<int64_t>(o_hi, (int64_t)pl.first[q] + n - 1);
+            for (int64_t k = 0; k < n; ++k) {
+                if (ex.select && !(*ex.select)[(size_t)(pl.e_start[q] + k)]) continue;
+                o_lo = std::min<int64_t>(o_lo, pl.first[q] + k);
+                o_hi = std::max<int64_t>(o_hi, pl.first[q] + k);
+                if (!ex.select) {
+                    o_hi = std::max<int64_t>(o_hi, (int64_t)pl.first[q] + n - 1);
+                    break;
+                }
             }
         }
         if (o_lo > o_hi) continue;
@@ -776,7 +787,15 @@ hgm_status run_batch(Exec &ex, const hgm_model *const *models, int nm, const hgm
             for (int g = 0; g < ng; ++g) {
                 int64_t lo, hi;
                 span(m, g, lo, hi);
-                if (hi > lo) { bucket[(size_t)(max_M - models[m]->d.M)] += hi - lo; n_units += hi - lo; }
+                if (hi <= lo) continue;
+                int64_t cnt = hi - lo;
+                if (ex.select) {
+                    const size_t q = (size_t)m * ns + segs[gbegin + g].s;
+                    cnt = 0;
+                    for (int64_t o = lo; o < hi; ++o) cnt += (*ex.select)[(size_t)(pl.e_start[q] + (o - pl.first[q]))];
+                }
+                bucket[(size_t)(max_M - models[m]->d.M)] += cnt;
+                n_units += cnt;
             }
         std::vector<int64_t> pos(bucket.size() + 1, 0);
         for (size_t k = 0; k < bucket.size(); ++k) pos[k + 1] = pos[k] + bucket[k];
@@ -790,6 +809,7 @@ hgm_status run_batch(Exec &ex, const hgm_model *const *models, int nm, const hgm
                 const int M = models[m]->d.M;
                 int64_t &w = pos[(size_t)(max_M - M)];
                 for (int64_t o = lo; o < hi; ++o) {
+                    if (ex.select && !(*ex.select)[(size_t)(pl.e_start[q] + (o - pl.first[q]))]) continue;
                     Unit u{};
                     u.model = m;
                     u.scene = g;
@@ -818,6 +838,67 @@ hgm_status run_batch(Exec &ex, const hgm_model *const *models, int nm, const hgm
     } else {
         CK(cudaGetLastError(), "launch");
     }
+    return HGM_OK;
+}
+
+// run_batch, followed, for the pruned form with params->refine > 0, by the refinement: per (model, scene)
+// pair the `refine` offsets of lowest pruned energy (finite; ties to the lower offset) are solved again
+// without pruning, in the same precision mode, over the pruned results.
+hgm_status run_matching(Exec &ex, const hgm_model *const *models, int nm, const hgm_scene *const *scenes, int ns,
+                        const hgm_params *hp, cudaStream_t st, float *energy, int32_t *assign)
+{
+    if (!hp || !hp->prune || hp->refine <= 0 || (!energy && !assign))
+        return run_batch(ex, models, nm, scenes, ns, hp, st, energy, assign);
+    hgm_status rc = check_params(hp);
+    if (rc) return rc;
+    Plan pl;
+    if ((rc = build_plan(models, nm, scenes, ns, hp, pl))) return rc;
+    const int64_t n_out = pl.e_start.back(), n_assign = pl.a_start.back();
+    if (n_out == 0) return HGM_OK;
+    const bool e_dev = energy && is_device_ptr(energy), a_dev = assign && is_device_ptr(assign);
+    float *de = energy;
+    int32_t *da = assign;
+    if (!e_dev) {
+        CK(g_ws.rf_e.ensure((size_t)n_out * sizeof(float)), "workspace (refinement)");
+        de = g_ws.rf_e.as<float>();
+    }
+    if (assign && !a_dev) {
+        CK(g_ws.rf_a.ensure((size_t)n_assign * sizeof(int32_t)), "workspace (refinement)");
+        da = g_ws.rf_a.as<int32_t>();
+    }
+    if ((rc = run_batch(ex, models, nm, scenes, ns, hp, st, de, da))) return rc;
+    std::vector<float> eh((size_t)n_out);
+    CK(cudaMemcpyAsync(eh.data(), de, (size_t)n_out * sizeof(float), cudaMemcpyDeviceToHost, st), "energy D2H");
+    CK(cudaStreamSynchronize(st), "synchronise");
+    std::vector<uint8_t> sel((size_t)n_out, 0);
+    std::vector<int64_t> idx;
+    int64_t n_sel = 0;
+    for (size_t q = 0; q + 1 < pl.e_start.size(); ++q) {
+        idx.clear();
+        for (int64_t k = pl.e_start[q]; k < pl.e_start[q + 1]; ++k)
+            if (eh[(size_t)k] < INFINITY) idx.push_back(k);
+        const size_t r = std::min<size_t>((size_t)hp->refine, idx.size());
+        std::partial_sort(idx.begin(), idx.begin() + (std::ptrdiff_t)r, idx.end(), [&](int64_t x, int64_t y) {
+            return eh[(size_t)x] < eh[(size_t)y] || (eh[(size_t)x] == eh[(size_t)y] && x < y);
+        });
+        for (size_t k = 0; k < r; ++k) sel[(size_t)idx[k]] = 1;
+        n_sel += (int64_t)r;
+    }
+    if (n_sel > 0) {
+        hgm_params pe = *hp;
+        pe.prune = nullptr;
+        pe.refine = 0;
+        Exec ex2;
+        ex2.select = &sel;
+        if ((rc = run_batch(ex2, models, nm, scenes, ns, &pe, st, de, da))) return rc;
+        ex.tensor = ex.tensor || ex2.tensor;
+    }
+    ex.refined_units += n_sel;
+    if (energy && !e_dev)
+        CK(cudaMemcpyAsync(energy, de, (size_t)n_out * sizeof(float), cudaMemcpyDeviceToHost, st), "energy D2H");
+    if (assign && !a_dev)
+        CK(cudaMemcpyAsync(assign, da, (size_t)n_assign * sizeof(int32_t), cudaMemcpyDeviceToHost, st), "assign D2H");
+    CK(cudaStreamSynchronize(st), "synchronise outputs");
     return HGM_OK;
 }
 
@@ -900,6 +981,7 @@ void hgm_default_params(hgm_params *p)
     p->offset_hi = INT32_MAX;
     p->prune = nullptr;
     p->keep = 8;
+    p->refine = 0;
 }
 
 const char *hgm_last_error(void) { return g_err.c_str(); }
@@ -1138,8 +1220,9 @@ hgm_status hgm_match(const hgm_model *model, const hgm_scene *scene, const hgm_p
     if (first_offset) *first_offset = f;
     if (!energy && !assign) return HGM_OK;
     Exec ex;
-    hgm_status rc2 = run_batch(ex, &model, 1, &scene, 1, params, (cudaStream_t)stream, energy, assign);
+    hgm_status rc2 = run_matching(ex, &model, 1, &scene, 1, params, (cudaStream_t)stream, energy, assign);
     g_pruned_units += ex.pruned_units;
+    g_refined_units += ex.refined_units;
     return rc2;
 }
 
@@ -1749,8 +1832,10 @@ hgm_status hgm_match_batch(const hgm_model *const *models, int32_t n_models, con
     if (n_models < 0 || n_scenes < 0 || (n_models && !models) || (n_scenes && !scenes))
         return fail(HGM_EINVAL, "bad model/scene arrays");
     Exec ex;
-    hgm_status rc = run_batch(ex, models, n_models, scenes, n_scenes, params, (cudaStream_t)stream, energy, assign);
+    hgm_status rc = run_matching(ex, models, n_models, scenes, n_scenes, params, (cudaStream_t)stream, energy,
+                                 assign);
     g_pruned_units += ex.pruned_units;
+    g_refined_units += ex.refined_units;
     return rc;
 }
 
@@ -1997,6 +2082,8 @@ hgm_status hgm_plan_create(const hgm_model *const *models, int32_t n_models, con
         return fail(HGM_EINVAL, "plan outputs must be device pointers");
     hgm_status rc = check_params(params);
     if (rc) return rc;
+    if (params->prune && params->refine > 0)
+        return fail(HGM_EUNSUPPORTED, "plans do not run the refinement (it reads the pruned energies on the host)");
     cudaStream_t st = (cudaStream_t)stream;
     hgm_plan *pl = new hgm_plan();
     pl->magic = kPlanMagic;
@@ -2073,6 +2160,14 @@ hgm_status hgm_set_workspace_budget(int64_t bytes)
     g_err.clear();
     if (bytes < 0) return fail(HGM_EINVAL, "budget must be >= 0");
     g_budget_override = (size_t)bytes;
+    return HGM_OK;
+}
+
+hgm_status hgm_refine_counter(int64_t *refined_units, int32_t reset)
+{
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (refined_units) *refined_units = g_refined_units;
+    if (reset) g_refined_units = 0;
     return HGM_OK;
 }
 

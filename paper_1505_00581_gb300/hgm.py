@@ -36,7 +36,7 @@ class Params(ctypes.Structure):
     _fields_ = [("lambda1", ctypes.c_float), ("lambda2", ctypes.c_float), ("lambda3", ctypes.c_float),
                 ("T", ctypes.c_int32), ("window", ctypes.c_int32), ("K", ctypes.c_int32),
                 ("precision", ctypes.c_int32), ("offset_lo", ctypes.c_int32), ("offset_hi", ctypes.c_int32),
-                ("prune", ctypes.c_void_p), ("keep", ctypes.c_int32)]
+                ("prune", ctypes.c_void_p), ("keep", ctypes.c_int32), ("refine", ctypes.c_int32)]
 
 
 _PP = ctypes.POINTER(Params)
@@ -84,6 +84,7 @@ SIGNATURES = {
     "hgm_profile_read": (_i32, [_pd, _p64, _i32]),
     "hgm_profile_evaluated": (_i32, [_p64, _i32]),
     "hgm_prune_counters": (_i32, [_p64, _p64, _i32]),
+    "hgm_refine_counter": (_i32, [_p64, _i32]),
     "hgm_profile_reset": (_i32, []),
 }
 
@@ -602,6 +603,12 @@ def prune_counters(reset: bool = False):
     a, b = ctypes.c_int64(), ctypes.c_int64()
     _check(load().hgm_prune_counters(ctypes.byref(a), ctypes.byref(b), 1 if reset else 0))
     return int(a.value), int(b.value)
+
+
+def refine_counter(reset: bool = False) -> int:
+    v = ctypes.c_int64()
+    _check(load().hgm_refine_counter(ctypes.byref(v), 1 if reset else 0))
+    return int(v.value)
 
 
 def profile_evaluated(reset: bool = False) -> int:
