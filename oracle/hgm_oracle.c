@@ -41,7 +41,13 @@
  *     uses the FP64 U.
  *  R6 ties: the argmin over z_i keeps the lowest candidate slot; the initial
  *     pair keeps the lexicographically lowest (slot of z_1, then of z_2).
- *  No dummy assignment (W^d of Eq. 2) is used.
+ *  R5 dummy assignment (Eq. 2), off unless or_ctx_set_dummy gives W^d >= 0:
+ *     every list gets one extra slot eps (after the real candidates, so ties
+ *     prefer a real point) with U(eps) = W^d (times lambda1, as every U here).
+ *     A term that involves eps vanishes: Delta(i,j) is 0 if z_i or z_j is eps,
+ *     D^g is 0 if any point of the triangle is eps. A triple holding eps is
+ *     feasible iff its real points, in chain order, are distinct, ordered in
+ *     time and span less than T frames. eps is the scene index OR_EPS (-2).
  *
  * Scene and model arrays given to this file are already stably sorted by
  * frame (the Python wrapper does that); indices below are sorted indices.
@@ -60,7 +66,10 @@ typedef struct {
     double lambda1, lambda2, lambda3;
     int T, window, K;
     int *frame_start;                            /* minnode table, nframes+1 */
+    double wd;                                   /* dummy cost W^d; < 0: no dummy assignment */
 } or_ctx;
+
+#define OR_EPS (-2)
 
 /* ---- construction ---------------------------------------------------- */
 
@@ -76,6 +85,7 @@ or_ctx *or_ctx_create(int M, const double *mx, const double *my, const int *mt, 
     c->sx = sx; c->sy = sy; c->st = st; c->sf = sf;
     c->lambda1 = lambda1; c->lambda2 = lambda2; c->lambda3 = lambda3;
     c->T = T; c->window = window; c->K = K;
+    c->wd = -1.0;
     /* minnode(f) (Sec. 3.4): first sorted scene index whose frame is >= f. */
     c->frame_start = (int *)malloc(sizeof(int) * (size_t)(nframes + 1));
     if (!c->frame_start) { free(c); return NULL; }
@@ -85,6 +95,12 @@ or_ctx *or_ctx_create(int M, const double *mx, const double *my, const int *mt, 
         c->frame_start[f] = n;
     }
     return c;
+}
+
+/* Enables the dummy assignment with cost W^d (wd >= 0) or disables it (wd < 0). */
+void or_ctx_set_dummy(or_ctx *c, double wd)
+{
+    c->wd = wd;
 }
 
 void or_ctx_destroy(or_ctx *c)
@@ -137,15 +153,23 @@ static double angle_at(double vx, double vy, double px, double py, double qx, do
     return wrap_angle(direction(vx, vy, qx, qy) - direction(vx, vy, px, py));
 }
 
-/* Delta of Eq. 5 for model pair (i,j) assigned to scene pair (zi,zj). */
+/* U of model point i assigned to z (Eq. 2 with both branches, lambda1 absorbed). */
+static double unary_z(const or_ctx *c, int i, int z)
+{
+    return z == OR_EPS ? c->lambda1 * c->wd : or_unary(c, i, z);
+}
+
+/* Delta of Eq. 5 for model pair (i,j) assigned to scene pair (zi,zj); 0 if either is eps. */
 static double delta_t(const or_ctx *c, int i, int j, int zi, int zj)
 {
+    if (zi == OR_EPS || zj == OR_EPS) return 0.0;
     return fabs((double)(c->mt[i] - c->mt[j]) - (double)(c->st[zi] - c->st[zj]));
 }
 
 /* D^g of Eq. 6 for model triangle (i, i-1, i-2) and scene triangle (a,b,c). */
 double or_geo(const or_ctx *c, int i, int a, int b, int cc)
 {
+    if (a == OR_EPS || b == OR_EPS || cc == OR_EPS) return 0.0;
     /* first row: angle at the middle vertex j = i-1 of triangle (i,j,k) */
     double am1 = angle_at(c->mx[i - 1], c->my[i - 1], c->mx[i], c->my[i], c->mx[i - 2], c->my[i - 2]);
     double as1 = angle_at(c->sx[b], c->sy[b], c->sx[a], c->sy[a], c->sx[cc], c->sy[cc]);
@@ -167,6 +191,20 @@ double or_triple(const or_ctx *c, int i, int a, int b, int cc)
 /* Causality (Eq. 7), closeness (Eq. 8) and distinctness, reading R3. */
 int or_feasible(const or_ctx *c, int a, int b, int cc)
 {
+    if (a == OR_EPS || b == OR_EPS || cc == OR_EPS) {
+        /* the real points of the triple, newest first (chain order a, b, c) */
+        int p[3], n = 0;
+        if (a != OR_EPS) p[n++] = a;
+        if (b != OR_EPS) p[n++] = b;
+        if (cc != OR_EPS) p[n++] = cc;
+        for (int k = 0; k + 1 < n; ++k)
+            for (int l = k + 1; l < n; ++l)
+                if (p[k] == p[l]) return 0;
+        for (int k = 0; k + 1 < n; ++k)
+            if (!(c->st[p[k + 1]] <= c->st[p[k]])) return 0;
+        if (n >= 2 && c->T > 0 && !(c->st[p[0]] - c->st[p[n - 1]] < c->T)) return 0;
+        return 1;
+    }
     if (a == b || b == cc || a == cc) return 0;
     if (!(c->st[cc] <= c->st[b] && c->st[b] <= c->st[a])) return 0;
     if (c->T > 0 && !(c->st[a] - c->st[cc] < c->T)) return 0;
@@ -178,7 +216,7 @@ int or_feasible(const or_ctx *c, int a, int b, int cc)
 double or_energy(const or_ctx *c, const int *z)
 {
     double e = 0.0;
-    for (int i = 0; i < c->M; ++i) e += or_unary(c, i, z[i]);
+    for (int i = 0; i < c->M; ++i) e += unary_z(c, i, z[i]);
     for (int i = 2; i < c->M; ++i) {
         if (!or_feasible(c, z[i], z[i - 1], z[i - 2])) return INFINITY;
         e += or_triple(c, i, z[i], z[i - 1], z[i - 2]);
@@ -319,7 +357,8 @@ static int solve_lists(const or_ctx *c, int Kc, const int *cand, const double *c
  * capacity *Kc; the caller frees cand, cu and cnt. */
 static int build_lists(const or_ctx *c, int block, int o, int **cand, double **cu, int **cnt, int *Kc)
 {
-    const int M = c->M, K = block ? (c->S > 0 ? c->S : 1) : c->K;
+    const int dummy = c->wd >= 0.0;
+    const int M = c->M, K = (block ? (c->S > 0 ? c->S : 1) : c->K) + dummy;
     *Kc = K;
     *cand = (int *)malloc(sizeof(int) * (size_t)M * K);
     *cu = (double *)malloc(sizeof(double) * (size_t)M * K);
@@ -328,9 +367,16 @@ static int build_lists(const or_ctx *c, int block, int o, int **cand, double **c
         free(*cand); free(*cu); free(*cnt);
         return -1;
     }
-    for (int i = 0; i < M; ++i)
-        (*cnt)[i] = block ? or_block_candidates(c, i, *cand + (size_t)i * K, *cu + (size_t)i * K)
-                          : or_candidates(c, i, o, *cand + (size_t)i * K, *cu + (size_t)i * K);
+    for (int i = 0; i < M; ++i) {
+        int n = block ? or_block_candidates(c, i, *cand + (size_t)i * K, *cu + (size_t)i * K)
+                      : or_candidates(c, i, o, *cand + (size_t)i * K, *cu + (size_t)i * K);
+        if (dummy) {   /* eps after the real candidates (R5) */
+            (*cand)[(size_t)i * K + n] = OR_EPS;
+            (*cu)[(size_t)i * K + n] = unary_z(c, i, OR_EPS);
+            ++n;
+        }
+        (*cnt)[i] = n;
+    }
     return 0;
 }
 

@@ -57,6 +57,7 @@ def _load():
                                       ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
                                       ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_int]
         lib.or_ctx_destroy.argtypes = [ctypes.c_void_p]
+        lib.or_ctx_set_dummy.argtypes = [ctypes.c_void_p, ctypes.c_double]
         lib.or_unary.restype = ctypes.c_double
         lib.or_unary.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int]
         lib.or_rank_key.restype = ctypes.c_float
@@ -109,7 +110,7 @@ class Oracle:
 
     def __init__(self, model_xy, model_t, model_f, scene_xy, scene_t, scene_f, n_frames: int,
                  K: int, window: int, lambda1: float = 0.6, lambda2: float = 0.2, lambda3: float = 5.0,
-                 T: int = 10):
+                 T: int = 10, dummy_cost: Optional[float] = None):
         self.lib = _load()
         mt = np.asarray(model_t).astype(np.int64)
         st = np.asarray(scene_t).astype(np.int64)
@@ -135,6 +136,10 @@ class Oracle:
                                           self.F, self.n_frames, *self.lambdas, self.T, self.window, self.K)
         if not self.ctx:
             raise MemoryError("oracle context allocation failed")
+        # the dummy assignment of Eq. 2 (reading R5): an extra candidate eps per list, cost W^d
+        self.dummy_cost = dummy_cost
+        if dummy_cost is not None:
+            self.lib.or_ctx_set_dummy(self.ctx, float(dummy_cost))
 
     @classmethod
     def from_workload(cls, wl, m: int = 0, s: int = 0, **over):
@@ -162,24 +167,27 @@ class Oracle:
         return np.arange(self.first_offset, self.first_offset + self.n_offsets, dtype=np.int64)
 
     # ---- per-term access (sorted indices) ---------------------------------
+    EPS = -2   # the dummy assignment in assignment arrays
+
     def _to_sorted_z(self, z_caller):
-        """Caller-order assignment -> sorted-order scene indices in chain order."""
-        inv = np.empty(self.S, np.int64)
+        """Caller-order assignment -> sorted-order scene indices in chain order (eps stays -2)."""
+        inv = np.empty(max(self.S, 1), np.int64)
         inv[self.sperm] = np.arange(self.S)
         z = np.asarray(z_caller, dtype=np.int64)[self.mperm]
-        return np.where(z >= 0, inv[np.maximum(z, 0)], -1).astype(np.int32)
+        return np.where(z >= 0, inv[np.maximum(z, 0)], np.where(z == self.EPS, self.EPS, -1)).astype(np.int32)
 
     def _to_caller_z(self, z_sorted):
         z_sorted = np.asarray(z_sorted, dtype=np.int64)
         out = np.full(self.M, -1, np.int64)
         ok = z_sorted >= 0
         out[self.mperm[ok]] = self.sperm[z_sorted[ok]]
+        out[self.mperm[z_sorted == self.EPS]] = self.EPS
         return out
 
     def energy(self, z_caller) -> float:
-        """E(z) (Eq. 9) of a caller-order assignment; +inf if infeasible."""
+        """E(z) (Eq. 9) of a caller-order assignment (-2 = the dummy eps); +inf if infeasible."""
         z = np.ascontiguousarray(self._to_sorted_z(z_caller))
-        if np.any(z < 0):
+        if np.any(z == -1) or (self.dummy_cost is None and np.any(z < 0)):
             return float("inf")
         return float(self.lib.or_energy(self.ctx, _ip(z)))
 
