@@ -329,6 +329,24 @@ def run_blocks(args, torch, hgm, dev, stream, flush):
     return {"streaming": streaming, "whole_scene": whole}
 
 
+def run_dummy(args, torch, hgm, wl, models, scenes, dev, stream, world, flush, dist=None, wd=8.0):
+    """The exact path with the dummy assignment of Eq. 2 (W^d = 8 descriptor-distance units: a model point
+    whose best candidate differs from it by more than about the distance between two descriptor clusters'
+    members is left unmatched) on the same workload."""
+    p = hgm.default_params(K=wl.K, window=wl.window, T=wl.T, dummy_cost=wd)
+    _, es, as_ = hgm.batch_layout(models, scenes, p)
+    e = torch.empty(int(es[-1]), dtype=torch.float32, device=dev)
+    a = torch.empty(int(as_[-1]), dtype=torch.int32, device=dev)
+    steps = max(1, min(args.steps, 3))
+    ms, prof = _time_form(torch, hgm, models, scenes, p, e, a, steps, 1, stream, flush)
+    ms = max_over_ranks(ms, dist, dev)
+    return {"value": job_rate(wl.total_frames, world, ms / 1e3), "unit": "frames/s", "ms_per_step": ms,
+            "dummy_cost": wd, "eps_fraction": float((a == -2).float().mean().item()),
+            "finite_offsets": int(torch.isfinite(e).sum().item()),
+            "kernel_ms_per_step": {k: v[0] / steps for k, v in prof.items()},
+            "form": "exact FP32 with an eps slot per list (own recursion kernel, sorted-base branch and bound)"}
+
+
 def run_pruned(args, torch, hgm, wl, models, scenes, energy, assign, es, as_, dev, stream, world, dist=None):
     """The pruned + BF16 form on the same workload: BF16 tensor-core unary table, the proposal network
     keeps 8 of the 64 candidates per list, recursion on the short lists, exact fallback for infeasible
@@ -417,6 +435,7 @@ def main():
     ap.add_argument("--no-pruned", action="store_true", help="skip the pruned+BF16 form")
     ap.add_argument("--no-chains", action="store_true", help="skip the independent-chains variant")
     ap.add_argument("--no-blocks", action="store_true", help="skip the whole-block and streaming forms")
+    ap.add_argument("--no-dummy", action="store_true", help="skip the dummy-assignment form")
     ap.add_argument("--train-steps", type=int, default=2000)
     ap.add_argument("--checkpoint", default=None, help="load the proposal network from <path>.bin/.json")
     args = ap.parse_args()
@@ -577,6 +596,10 @@ def main():
     if not args.no_chains:
         chains = run_chains(args, torch, hgm, wl, models, scenes, dev, stream, world, flush, dist)
 
+    dummy = None
+    if not args.no_dummy:
+        dummy = run_dummy(args, torch, hgm, wl, models, scenes, dev, stream, world, flush, dist)
+
     blocks = None
     if not args.no_blocks:
         blocks = run_blocks(args, torch, hgm, dev, stream, flush)
@@ -598,7 +621,7 @@ def main():
                            "parallelism": f"replicas x{world}"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "graph": graph, "gpu_launches": launches,
                 "clocks": clk_sum, "finite_offsets": int(fin), "pruned_bf16": pruned,
-                "chains": chains, "whole_block": blocks}
+                "chains": chains, "whole_block": blocks, "dummy": dummy}
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()

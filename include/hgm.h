@@ -96,6 +96,11 @@ typedef struct {
                            energy are solved again without pruning (same precision mode), so a pair's
                            minimum over offsets is the unpruned one whenever its offset is among them.
                            0 (default) = off; 0..65535. Not available in plans (HGM_EUNSUPPORTED). */
+    float dummy_cost;   /* W^d of Eq. 2: >= 0 adds the dummy assignment eps to every candidate list (model
+                           point not found; U(eps) = W^d, terms involving eps vanish, a triple holding
+                           eps must order its real points in time within T); eps is reported as -2 in
+                           assignments. < 0 (default -1) = off. HGM_EUNSUPPORTED with pruning and in the
+                           whole-block, streaming and no-allocation forms. */
 } hgm_params;
 
 /* Fills *p with the defaults above (prune = NULL, keep = 8, refine = 0). */

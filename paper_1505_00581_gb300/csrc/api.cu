@@ -151,6 +151,7 @@ struct Workspace {
     Buffer fb_total;   // fallback units since the last hgm_prune_counters reset (device counter)
     Buffer chain_e, chain_a, chain_tab, chain_oe, chain_oa;   // independent-chains variant
     Buffer rf_e, rf_a;        // refinement of the pruned form: device outputs when the caller's are on the host
+    Buffer beta_dummy;        // per-CTA argmin tables of the dummy-assignment recursion
 };
 
 // Buffers of the whole-block form: band tables, model rows, unary table, argmin tables, records, outputs.
@@ -336,6 +337,10 @@ hgm_status check_params(const hgm_params *p)
         return fail(HGM_EUNSUPPORTED, "precision %d not available (0 = FP32 exact, 1 = BF16 + FP32 re-score)",
                     p->precision);
     if (p->offset_lo > p->offset_hi) return fail(HGM_EINVAL, "offset_lo > offset_hi");
+    if (std::isnan(p->dummy_cost) || std::isinf(p->dummy_cost))
+        return fail(HGM_EINVAL, "dummy_cost must be finite (< 0 for none)");
+    if (p->dummy_cost >= 0 && p->prune)
+        return fail(HGM_EUNSUPPORTED, "the dummy assignment is not available with pruning");
     if (p->prune) {
         if (p->prune->magic != kPropMagic) return fail(HGM_EINVAL, "prune is not a proposal-network handle");
         if (p->keep < 1 || p->keep > p->K) return fail(HGM_EINVAL, "keep must be in 1..K (got %d)", p->keep);
@@ -355,6 +360,7 @@ Params to_params(const hgm_params *p)
     q.window = p->window;
     q.K = p->K;
     q.rescore = p->precision == 1 ? kRescore : 0;
+    q.dummy = p->dummy_cost >= 0 ? p->dummy_cost : -1.0f;
     return q;
 }
 
@@ -469,7 +475,7 @@ hgm_status run_units(Exec &ex, const hgm_model *const *models, std::vector<Unit>
         CK(ws.cand_idx.ensure((size_t)cand_e * sizeof(int32_t)), "workspace (candidates)");
         CK(ws.cand_u.ensure((size_t)cand_e * sizeof(float)), "workspace (candidates)");
         CK(ws.cand_cnt.ensure((size_t)(cand_e / K) * sizeof(int32_t)), "workspace (candidates)");
-        if (!pruning) CK(ws.beta.ensure((size_t)beta_b), "workspace (argmin tables)");
+        if (!pruning && p.dummy < 0) CK(ws.beta.ensure((size_t)beta_b), "workspace (argmin tables)");
         CK(ws.units.ensure((size_t)n * sizeof(Unit)), "workspace (units)");
         CK(ws.res.ensure((size_t)n * sizeof(UnitResult)), "workspace (results)");
         CK(ws.counter.ensure(sizeof(int)), "workspace");
@@ -525,6 +531,18 @@ hgm_status run_units(Exec &ex, const hgm_model *const *models, std::vector<Unit>
                                     ws.beta_fb.as<uint8_t>(), max_M, d_energy, d_assign, ws.counter.as<int>(), st),
                "recursion kernel (fallback)");
             ex.pruned_units += n;
+            begin = end;
+            continue;
+        }
+        if (p.dummy >= 0) {
+            // the dummy assignment: its own recursion kernel, which also backtracks
+            const int grid = dummy_grid();
+            if (grid <= 0) return fail(HGM_ECUDA, "device query failed");
+            CK(ws.beta_dummy.ensure((size_t)dummy_scratch_bytes(K, max_M, grid)), "workspace (argmin tables)");
+            CK(launch_recurse_dummy(du, n, dm, ds, p, p.dummy, ws.cand_idx.as<int32_t>(), ws.cand_u.as<float>(),
+                                    ws.cand_cnt.as<int32_t>(), ws.beta_dummy.as<uint8_t>(), max_M, grid, d_energy,
+                                    d_assign, st),
+               "recursion kernel (dummy)");
             begin = end;
             continue;
         }
@@ -982,6 +1000,7 @@ void hgm_default_params(hgm_params *p)
     p->prune = nullptr;
     p->keep = 8;
     p->refine = 0;
+    p->dummy_cost = -1.0f;
 }
 
 const char *hgm_last_error(void) { return g_err.c_str(); }
@@ -1683,8 +1702,9 @@ hgm_status hgm_match_block(const hgm_model *const *models, int32_t n_models, con
     g_err.clear();
     hgm_status rc = check_params(params);
     if (rc) return rc;
-    if (params->precision != 0 || params->prune)
-        return fail(HGM_EUNSUPPORTED, "the whole-block problem runs in plain FP32 only (precision 0, no pruning)");
+    if (params->precision != 0 || params->prune || params->dummy_cost >= 0)
+        return fail(HGM_EUNSUPPORTED,
+                    "the whole-block problem runs in plain FP32 only (precision 0, no pruning, no dummy)");
     if (n_models < 0 || n_scenes < 0 || (n_models && !models) || (n_scenes && !scenes))
         return fail(HGM_EINVAL, "bad model/scene arrays");
     if (n_models == 0 || n_scenes == 0 || (!energy && !assign)) return HGM_OK;
@@ -1709,8 +1729,9 @@ hgm_status hgm_stream_create(const hgm_model *const *models, int32_t n_models, c
     *out = nullptr;
     hgm_status rc = check_params(params);
     if (rc) return rc;
-    if (params->precision != 0 || params->prune)
-        return fail(HGM_EUNSUPPORTED, "the whole-block problem runs in plain FP32 only (precision 0, no pruning)");
+    if (params->precision != 0 || params->prune || params->dummy_cost >= 0)
+        return fail(HGM_EUNSUPPORTED,
+                    "the whole-block problem runs in plain FP32 only (precision 0, no pruning, no dummy)");
     if (n_models < 1 || !models) return fail(HGM_EINVAL, "need at least one model");
     if (block_frames < 1) return fail(HGM_EINVAL, "block_frames must be >= 1 (got %d)", block_frames);
     int F;

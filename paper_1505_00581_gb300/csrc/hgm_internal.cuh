@@ -84,6 +84,7 @@ struct Params {
     int32_t T, window, K;
     int32_t F = 0;       // descriptor row stride (padded width)
     int32_t rescore = 0; // 0, or: recompute the U of the `rescore` smallest candidates per list in FP32
+    float dummy = -1.0f; // W^d of the dummy assignment (k_dummy.cu), < 0: none
 };
 
 constexpr int kRescore = 8;   // candidates per list re-scored in FP32 by the BF16 precision mode
@@ -192,6 +193,14 @@ int64_t block_smem_cells();   // largest band table (cells) whose two copies fit
 cudaError_t launch_block_recurse(const BlockUnit *units, int n_units, const ModelRec *models, const SceneRec *scenes,
                                  const BlockGeo *geos, Params p, int64_t max_cells, uint16_t *beta, float *scratch,
                                  int grid_global, float *energy, int32_t *assign, cudaStream_t st);
+
+// k_dummy.cu: the recursion with the dummy assignment eps (fused backtrack; per-CTA argmin scratch).
+int dummy_grid();
+int64_t dummy_scratch_bytes(int K, int max_M, int grid);
+cudaError_t launch_recurse_dummy(const Unit *units, int64_t n_units, const ModelRec *models, const SceneRec *scenes,
+                                 Params p, float wd, const int32_t *cand_idx, const float *cand_u,
+                                 const int32_t *cand_cnt, uint8_t *scratch, int max_M, int grid, float *energy,
+                                 int32_t *assign, cudaStream_t st);
 
 void prof_begin(int kernel, cudaStream_t st);
 void prof_end(int kernel, cudaStream_t st);

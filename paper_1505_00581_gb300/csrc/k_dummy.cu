@@ -1,0 +1,308 @@
+// k_dummy.cu -- the recursion with the dummy assignment of Eq. 2 (reading R5).
+//
+// Every candidate list C_i(o) gets one more slot, eps, after its real candidates (slot K of a table of
+// L = K + 1 slots), with U(eps) = lambda1 W^d. A term that involves eps vanishes (Delta(i,j) if z_i or
+// z_j is eps; D^g if any point of the triangle is), and a triple holding eps is feasible iff its real
+// points, in chain order, are distinct, time-ordered and less than T frames apart. So the all-eps chain
+// is always feasible and every offset has a finite optimum.
+//
+// One persistent CTA per unit, all tables in shared memory (L x L floats each): alpha_{i+1} and alpha_i
+// (ping-pong), base(b, a) = U(a) + lambda2 Delta(a, b) + alpha_{i+1}(a, b) (eps rules applied), and the
+// per-step directions P1(b, a) = A1 + theta(b->a), P2(b, a) = A2 + theta(a->b), R(a, c) = theta(a->c).
+// Threads stride over the cells (b, c), c fastest, so a warp shares b (broadcast reads of base, P1, P2)
+// and reads consecutive R(a, c). The argmin slots go to a per-CTA global scratch, (M-2) x L x L bytes,
+// and the CTA backtracks its own unit (Eq. 12); eps is reported as -2 in the assignment.
+#include "hgm_internal.cuh"
+#include "recurse_common.cuh"
+
+namespace hgm {
+namespace {
+
+constexpr int kDummyThreads = 256;
+constexpr int kL = kMaxK + 1;          // table side: up to 64 real slots + eps
+constexpr int kTab = kL * kL;
+
+struct DummySmem {
+    float alpha[2][kTab];
+    float base[kTab];                  // [b][a]
+    float p1[kTab], p2[kTab];          // [b][a]
+    float r[kTab];                     // [a][c]
+    float2 xy[3][kL];                  // lists i (a), i-1 (b), i-2 (c)
+    int t[3][kL], id[3][kL];
+    float u[3][kL];
+    uint8_t srt[kL][kMaxK];            // per row b: the real a by increasing base(b, a) (ties: lower slot)
+    int cnt[3];
+};
+static_assert(2 * (sizeof(DummySmem) + 1024 + 128) <= 228 * 1024, "two CTAs per SM");
+
+// (key, slot) order: smaller key first, then lower slot
+__device__ __forceinline__ bool key_less(float ka, int sa, float kb, int sb)
+{
+    return ka < kb || (ka == kb && sa < sb);
+}
+
+// Bitonic sort of 64 (key, slot) pairs held by a warp, two per lane (positions lane and lane + 32).
+__device__ __forceinline__ void warp_sort64(float &k0, int &s0, float &k1, int &s1, int lane)
+{
+#pragma unroll
+    for (int k = 2; k <= 64; k <<= 1) {
+#pragma unroll
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            if (j == 32) {   // positions lane and lane + 32 pair up inside the lane (k = 64: ascending)
+                if (key_less(k1, s1, k0, s0)) {
+                    const float tk = k0; const int ts = s0;
+                    k0 = k1; s0 = s1; k1 = tk; s1 = ts;
+                }
+            } else {
+#pragma unroll
+                for (int e = 0; e < 2; ++e) {
+                    float &kk = e ? k1 : k0;
+                    int &ss = e ? s1 : s0;
+                    const int i = lane + 32 * e;
+                    const float ok = __shfl_xor_sync(0xffffffffu, kk, j);
+                    const int os = __shfl_xor_sync(0xffffffffu, ss, j);
+                    const bool want_min = ((i & j) == 0) == ((i & k) == 0);
+                    const bool take = want_min ? key_less(ok, os, kk, ss) : key_less(kk, ss, ok, os);
+                    if (take) { kk = ok; ss = os; }
+                }
+            }
+        }
+    }
+}
+
+struct DummyBest {
+    float v;
+    int j1, j2;
+};
+
+__device__ __forceinline__ bool dummy_better(float v, int j1, int j2, const DummyBest &o)
+{
+    if (v != o.v) return v < o.v;
+    if (j1 != o.j1) return j1 < o.j1;
+    return j2 < o.j2;
+}
+
+__global__ void __launch_bounds__(kDummyThreads) dummy_recurse_kernel(
+    const Unit *__restrict__ units, int64_t n_units, const ModelRec *__restrict__ models,
+    const SceneRec *__restrict__ scenes, Params p, float wd, const int32_t *__restrict__ cand_idx,
+    const float *__restrict__ cand_u, const int32_t *__restrict__ cand_cnt, uint8_t *__restrict__ scratch,
+    int64_t scratch_per_cta, float *__restrict__ energy, int32_t *__restrict__ assign)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    DummySmem &sm = *reinterpret_cast<DummySmem *>(smem_raw);
+    __shared__ DummyBest red[kDummyThreads / 32];
+    const int K = p.K, L = K + 1, E = K;   // eps is slot K
+    const float lam2 = p.lambda2, lam23 = __fmul_rn(p.lambda2, p.lambda3);
+    const float ueps = __fmul_rn(p.lambda1, wd);
+    const float inf = __int_as_float(0x7f800000);
+    uint8_t *beta = scratch + (int64_t)blockIdx.x * scratch_per_cta;
+    for (int64_t u = blockIdx.x; u < n_units; u += gridDim.x) {
+        const Unit un = units[u];
+        const ModelRec md = models[un.model];
+        const SceneRec sc = scenes[un.scene];
+        const int M = md.M;
+        const int32_t *cidx = cand_idx + un.cand;
+        const float *cu = cand_u + un.cand;
+        const int32_t *ccnt = cand_cnt + un.cand / K;
+        int cur = 0;
+        for (int i = M - 1; i >= 2; --i) {
+            // lists of this step: slot s < cnt real, slot K eps
+            for (int e = threadIdx.x; e < 3 * L; e += blockDim.x) {
+                const int w = e / L, s = e - w * L, li = i - w;
+                const int n = ccnt[li];
+                if (s < n) {
+                    const int j = cidx[(int64_t)li * K + s];
+                    sm.xy[w][s] = sc.xy[j];
+                    sm.t[w][s] = sc.t[j];
+                    sm.id[w][s] = j;
+                    sm.u[w][s] = cu[(int64_t)li * K + s];
+                } else if (s == E) {
+                    sm.xy[w][s] = make_float2(0.f, 0.f);
+                    sm.t[w][s] = 0;
+                    sm.id[w][s] = -2;
+                    sm.u[w][s] = ueps;
+                }
+                if (s == 0) sm.cnt[w] = n;
+            }
+            __syncthreads();
+            const float2 mi = md.xy[i], mj = md.xy[i - 1], mk = md.xy[i - 2];
+            const float A1 = signed_angle(mj, mi, mk);   // at i-1, from ->i to ->i-2
+            const float A2 = signed_angle(mi, mj, mk);   // at i, from ->i-1 to ->i-2
+            const int dt1 = md.t[i] - md.t[i - 1], dt2 = md.t[i - 1] - md.t[i - 2];
+            const int na = sm.cnt[0], nb = sm.cnt[1], nc = sm.cnt[2];
+            const float *an = sm.alpha[cur];
+            const bool last = i == M - 1;
+            // base(b, a) and directions; rows/columns of empty slots are never read
+            for (int e = threadIdx.x; e < L * L; e += blockDim.x) {
+                const int b = e / L, a = e - b * L;
+                const bool ra = a < na, rb = b < nb;
+                if ((ra || a == E) && (rb || b == E)) {
+                    const float al = last ? 0.0f : an[a * L + b];   // alpha_{i+1}(z_i = a, z_{i-1} = b)
+                    float bs;
+                    if (ra && rb) bs = base_cost(sm.u[0][a], lam2, dt1, sm.t[0][a], sm.t[1][b], al);
+                    else bs = __fadd_rn(sm.u[0][a], al);
+                    sm.base[b * L + a] = bs;
+                    if (ra && rb) {
+                        sm.p1[b * L + a] = __fadd_rn(A1, direction(sm.xy[1][b], sm.xy[0][a]));
+                        sm.p2[b * L + a] = __fadd_rn(A2, direction(sm.xy[0][a], sm.xy[1][b]));
+                    }
+                }
+                const int a2 = b, c = a;   // R(a, c) over the same index space
+                if (a2 < na && c < nc) sm.r[a2 * L + c] = direction(sm.xy[0][a2], sm.xy[2][c]);
+            }
+            __syncthreads();
+            // branch and bound (exact): v(a, b, c) >= base(b, a). Each row's real a are sorted by base (a
+            // warp per row), so a cell walks them in that order and stops at the first base above its best.
+            {
+                const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+                for (int b = warp; b < L; b += kDummyThreads / 32) {
+                    if (!(b < nb || b == E)) continue;
+                    float k0 = lane < na ? sm.base[b * L + lane] : inf;
+                    float k1 = lane + 32 < na ? sm.base[b * L + lane + 32] : inf;
+                    int s0 = lane, s1 = lane + 32;
+                    warp_sort64(k0, s0, k1, s1, lane);
+                    sm.srt[b][lane] = (uint8_t)s0;
+                    sm.srt[b][lane + 32] = (uint8_t)s1;
+                }
+            }
+            __syncthreads();
+            float *ac = sm.alpha[cur ^ 1];
+            uint8_t *bt = beta + (int64_t)(i - 2) * L * L;
+            for (int e = threadIdx.x; e < L * L; e += blockDim.x) {
+                const int b = e / L, c = e - b * L;
+                const bool rb = b < nb, rc = c < nc;
+                if (!((rb || b == E) && (rc || c == E))) continue;
+                float best = inf;
+                int arg = 255;
+                const float *brow = sm.base + b * L;
+                if (rb && rc) {
+                    const int tb = sm.t[1][b], tc = sm.t[2][c], ib = sm.id[1][b], ic = sm.id[2][c];
+                    const bool bc_ok = ib != ic && tc <= tb && (p.T <= 0 || tb - tc < p.T);
+                    if (bc_ok) {
+                        const float q1 = direction(sm.xy[1][b], sm.xy[2][c]);
+                        best = brow[E];   // (eps, b, c): always feasible here, finite
+                        arg = E;
+                        auto eval = [&](int a) {
+                            const int ta = sm.t[0][a], ia = sm.id[0][a];
+                            if (ia == ib || ia == ic || ta < tb || (p.T > 0 && ta - tc >= p.T)) return;
+                            const float v = triple_cost(brow[a], sm.p1[b * L + a], sm.p2[b * L + a], q1,
+                                                        sm.r[a * L + c], lam23);
+                            if (v < best || (v == best && a < arg)) { best = v; arg = a; }
+                        };
+                        const uint8_t *order = sm.srt[b];
+                        for (int k = 0; k < na; ++k) {
+                            const int a = order[k];
+                            if (brow[a] > best) break;
+                            eval(a);
+                        }
+                    }
+                    if (best < inf) best = cell_alpha(best, lam2, dt2, tb, tc);
+                } else {
+                    // a triple holding eps costs base(b, a) alone: in sorted order the first feasible real
+                    // a is the smallest (lowest slot among equals); eps (the last slot) only if below it
+                    const uint8_t *order = sm.srt[b];
+                    const int tr = rc ? sm.t[2][c] : (rb ? sm.t[1][b] : 0);   // the other real point
+                    const int ir = rc ? sm.id[2][c] : (rb ? sm.id[1][b] : -3);
+                    const bool any = !rb && !rc;
+                    for (int k = 0; k < na; ++k) {
+                        const int a = order[k];
+                        const int ta = sm.t[0][a];
+                        if (!any && (sm.id[0][a] == ir || ta < tr || (p.T > 0 && ta - tr >= p.T))) continue;
+                        best = brow[a];
+                        arg = a;
+                        break;
+                    }
+                    if (brow[E] < best) { best = brow[E]; arg = E; }
+                }
+                ac[b * L + c] = best;
+                bt[b * L + c] = (uint8_t)arg;
+            }
+            cur ^= 1;
+            __syncthreads();
+        }
+        // Eq. 13 over (z_1 = j1, z_2 = j2) in C_1 + eps, C_2 + eps: U + U + alpha_3(j2, j1)
+        const float *a3 = sm.alpha[cur];
+        const int n0 = ccnt[0], n1 = ccnt[1];
+        DummyBest mine{inf, 0x7fffffff, 0x7fffffff};
+        for (int e = threadIdx.x; e < L * L; e += blockDim.x) {
+            const int j1 = e / L, j2 = e - j1 * L;
+            if (!((j1 < n0 || j1 == E) && (j2 < n1 || j2 == E))) continue;
+            const float u1 = j1 == E ? ueps : cu[j1], u2 = j2 == E ? ueps : cu[(int64_t)K + j2];
+            const float al = M == 2 ? 0.0f : a3[j2 * L + j1];
+            const float v = __fadd_rn(__fadd_rn(u1, u2), al);
+            if (v < inf && dummy_better(v, j1, j2, mine)) mine = DummyBest{v, j1, j2};
+        }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            DummyBest o{__shfl_xor_sync(0xffffffffu, mine.v, off), __shfl_xor_sync(0xffffffffu, mine.j1, off),
+                        __shfl_xor_sync(0xffffffffu, mine.j2, off)};
+            if (dummy_better(o.v, o.j1, o.j2, mine)) mine = o;
+        }
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mine;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            DummyBest best = red[0];
+            for (int w = 1; w < kDummyThreads / 32; ++w)
+                if (dummy_better(red[w].v, red[w].j1, red[w].j2, best)) best = red[w];
+            int32_t *row = assign + un.out_a;
+            if (best.v < inf) {
+                int s2 = best.j1, s1 = best.j2;   // slots of z_{i-2}, z_{i-1}
+                auto out = [&](int i, int s) {
+                    row[md.perm[i]] = s == E ? -2 : sc.perm[cidx[(int64_t)i * K + s]];
+                };
+                out(0, s2);
+                out(1, s1);
+                for (int i = 2; i < M; ++i) {
+                    const int sa = beta[(int64_t)(i - 2) * L * L + s1 * L + s2];
+                    out(i, sa);
+                    s2 = s1;
+                    s1 = sa;
+                }
+                energy[un.out_e] = best.v;
+            } else {
+                for (int i = 0; i < M; ++i) row[i] = -1;
+                energy[un.out_e] = inf;
+            }
+        }
+        __syncthreads();   // tables, lists and the reduction slots are reused by the next unit
+    }
+}
+
+}  // namespace
+
+int64_t dummy_scratch_bytes(int K, int max_M, int grid)
+{
+    const int64_t L = K + 1;
+    return (int64_t)grid * std::max(max_M - 2, 1) * L * L;
+}
+
+int dummy_grid()
+{
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) !=
+                                                  cudaSuccess)
+        return 0;
+    return sms * 2;
+}
+
+cudaError_t launch_recurse_dummy(const Unit *units, int64_t n_units, const ModelRec *models, const SceneRec *scenes,
+                                 Params p, float wd, const int32_t *cand_idx, const float *cand_u,
+                                 const int32_t *cand_cnt, uint8_t *scratch, int max_M, int grid, float *energy,
+                                 int32_t *assign, cudaStream_t st)
+{
+    if (n_units <= 0) return cudaSuccess;
+    if (p.K > kMaxK) return cudaErrorInvalidValue;
+    const size_t smem = sizeof(DummySmem);
+    cudaError_t e = cudaFuncSetAttribute(dummy_recurse_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const int64_t per_cta = (int64_t)std::max(max_M - 2, 1) * (p.K + 1) * (p.K + 1);
+    const int g = (int)std::min<int64_t>(n_units, grid);
+    prof_begin(kProfRecurse, st);
+    dummy_recurse_kernel<<<g, kDummyThreads, smem, st>>>(units, n_units, models, scenes, p, wd, cand_idx, cand_u,
+                                                         cand_cnt, scratch, per_cta, energy, assign);
+    e = cudaGetLastError();
+    prof_end(kProfRecurse, st);
+    return e;
+}
+
+}  // namespace hgm

@@ -36,7 +36,8 @@ class Params(ctypes.Structure):
     _fields_ = [("lambda1", ctypes.c_float), ("lambda2", ctypes.c_float), ("lambda3", ctypes.c_float),
                 ("T", ctypes.c_int32), ("window", ctypes.c_int32), ("K", ctypes.c_int32),
                 ("precision", ctypes.c_int32), ("offset_lo", ctypes.c_int32), ("offset_hi", ctypes.c_int32),
-                ("prune", ctypes.c_void_p), ("keep", ctypes.c_int32), ("refine", ctypes.c_int32)]
+                ("prune", ctypes.c_void_p), ("keep", ctypes.c_int32), ("refine", ctypes.c_int32),
+                ("dummy_cost", ctypes.c_float)]
 
 
 _PP = ctypes.POINTER(Params)

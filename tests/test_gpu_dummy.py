@@ -1,0 +1,109 @@
+"""The dummy assignment (Eq. 2, reading R5) on the GPU against the FP64 oracle with the same W^d: every
+offset's energy within 1e-5 relative, assignments (eps = -2) equal or of the same FP64 energy; offsets
+whose lists are empty become feasible; an expensive dummy reproduces the plain path."""
+import numpy as np
+import pytest
+
+from gpu_util import handles
+from paper_1505_00581_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+LAM = dict(lambda1=0.6, lambda2=0.2, lambda3=5.0)
+
+
+@pytest.fixture(scope="module")
+def env():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    from paper_1505_00581_gb300 import build, hgm
+    build.build()
+    hgm.load()
+    import oracle
+    oracle.build()
+    return torch, hgm, oracle
+
+
+def _check_pair(hgm, oracle, mod, sc, K, window, wd, precision=0, torch=None, T=10):
+    m, s = handles(hgm, mod, sc, torch)
+    p = hgm.default_params(K=K, window=window, T=T, dummy_cost=wd, precision=precision)
+    first, e, a = hgm.match(m, s, p)
+    orc = oracle.Oracle(mod.xy, mod.t, mod.f, sc.xy, sc.t, sc.f, sc.n_frames, K=K, window=window, T=T,
+                        dummy_cost=wd, **LAM)
+    assert first == orc.first_offset and len(e) == orc.n_offsets
+    n_eps = 0
+    for k in range(len(e)):
+        e64, z64, _ = orc.match(first + k)
+        assert np.isfinite(e64) and np.isfinite(e[k])
+        tol = 1e-5 * e64 + 1e-6 if precision == 0 else 2e-2 * e64 + 1e-4
+        assert abs(e[k] - e64) <= tol, (k, e[k], e64)
+        if precision == 0 and not np.array_equal(a[k], z64):
+            assert orc.energy(a[k]) <= e64 * (1 + 1e-5) + 1e-6, (k, orc.energy(a[k]), e64)
+        n_eps += int(np.sum(a[k] == -2))
+    return n_eps
+
+
+@pytest.mark.parametrize("wd", [0.5, 3.0, 8.0])
+def test_dummy_matches_oracle_single_pair(env, wd):
+    torch, hgm, oracle = env
+    wl = synth.single_match(0)
+    n_eps = _check_pair(hgm, oracle, wl.models[0], wl.scenes[0], 32, 2, wd, torch=torch)
+    if wd == 0.5:
+        assert n_eps > 0           # cheap dummies are taken
+
+
+def test_dummy_small_random_and_empty_windows(env):
+    """Sparse scenes (Poisson 0.7 points per frame, window 0): many lists are empty and only the
+    dummy makes those offsets feasible."""
+    torch, hgm, oracle = env
+    rng = np.random.default_rng(77)
+    for k in range(4):
+        mod = synth.make_model(rng, int(rng.integers(5, 12)), F=16, t_span=10)
+        sc = synth.make_scene(rng, 40, (60.0, 40.0), ("poisson", 0.7), mod.centres, [mod], [(0, 9)])
+        _check_pair(hgm, oracle, mod, sc, 8, 0, [0.2, 1.0, 2.5, 6.0][k], T=[10, 4, 10, 0][k])
+
+
+def test_dummy_precision_mode(env):
+    torch, hgm, oracle = env
+    wl = synth.single_match(0)
+    _check_pair(hgm, oracle, wl.models[0], wl.scenes[0], 32, 2, 3.0, precision=1, torch=torch)
+
+
+def test_expensive_dummy_is_the_plain_path(env):
+    torch, hgm, _ = env
+    wl = synth.batched_exact(seed=43, n_models=3, n_scenes=2, frames_range=(80, 120))
+    M = [hgm.Model(m.xy, m.t, m.f) for m in wl.models]
+    S = [hgm.Scene(s.xy, s.t, s.f, s.n_frames) for s in wl.scenes]
+    base = hgm.default_params(K=64, window=3)
+    first, es, as_ = hgm.batch_layout(M, S, base)
+    e0 = np.zeros(int(es[-1]), np.float32)
+    a0 = np.zeros(int(as_[-1]), np.int32)
+    hgm.match_batch(M, S, base, e0, a0)
+    e1 = np.zeros_like(e0)
+    a1 = np.zeros_like(a0)
+    hgm.match_batch(M, S, hgm.default_params(K=64, window=3, dummy_cost=1e5), e1, a1)
+    fin = np.isfinite(e0)
+    assert fin.sum() > 100
+    assert np.max(np.abs(e1[fin] - e0[fin]) / e0[fin]) <= 2e-6
+    assert np.all(e1[~fin] >= 1e5 * 0.6)
+    same = 0
+    for q in range(len(M) * len(S)):
+        Mq = wl.models[q // len(S)].n
+        for k in range(int(es[q + 1] - es[q])):
+            if fin[es[q] + k]:
+                ka = int(as_[q]) + k * Mq
+                same += np.array_equal(a0[ka:ka + Mq], a1[ka:ka + Mq])
+    assert same >= 0.99 * fin.sum()
+
+
+def test_dummy_rejected_with_pruning_and_blocks(env):
+    torch, hgm, _ = env
+    wl = synth.single_match(0)
+    m, s = handles(hgm, wl.models[0], wl.scenes[0])
+    prop = hgm.Proposal(162, seed=1)
+    with pytest.raises(hgm.HgmError) as err:
+        hgm.match(m, s, hgm.default_params(K=32, window=2, dummy_cost=1.0, prune=prop, keep=4))
+    assert err.value.status == hgm.HGM_EUNSUPPORTED
+    with pytest.raises(hgm.HgmError) as err:
+        hgm.match_block([m], [s], hgm.default_params(dummy_cost=1.0))
+    assert err.value.status == hgm.HGM_EUNSUPPORTED
