@@ -156,9 +156,18 @@ struct Workspace {
 
 // Buffers of the whole-block form: band tables, model rows, unary table, argmin tables, records, outputs.
 struct BlockBufs {
-    Buffer tab, cellb, dir, model, mrec, U, beta, scratch, rec, oe, oa;
+    Buffer tab, cellb, dir, model, mrec, U, beta, scratch, oe, oa;
     int R = 0;                  // model rows gathered into `model` (prep_block_models)
     std::vector<int> urow;
+    bool own_pinned = false;    // stream objects: upload the tables from a pinned staging buffer
+    void *pinned = nullptr;
+    size_t pinned_bytes = 0;
+    cudaEvent_t upload_done = nullptr;   // the last upload from `pinned` (it is rewritten after this)
+    ~BlockBufs()
+    {
+        if (pinned) cudaFreeHost(pinned);
+        if (upload_done) cudaEventDestroy(upload_done);
+    }
 };
 Workspace g_ws;
 BlockBufs g_blk;
@@ -175,6 +184,9 @@ struct hgm_stream {
     hgm::Buffer sc_buf, raw;           // the block's sorted points (xy | t | perm | minnode), raw descriptors
     hgm::Buffer f;                     // sorted, padded descriptors
     hgm::Buffer flag;
+    hgm::Buffer dev_e, dev_a;     // results before the read-back (host outputs)
+    void *pin_out = nullptr;      // pinned read-back of energies, assignments and the flag
+    size_t pin_out_bytes = 0;
     void *pinned = nullptr;       // host staging of the uploads
     size_t pinned_bytes = 0;
     hgm_scene view;               // the current block as a scene (device arrays owned by this object)
@@ -190,6 +202,8 @@ void free_stream(hgm_stream *s)
 {
     if (s->pinned) cudaFreeHost(s->pinned);
     s->pinned = nullptr;
+    if (s->pin_out) cudaFreeHost(s->pin_out);
+    s->pin_out = nullptr;
 }
 
 bool g_count_mode = false;   // hgm_profile_enable(2): batch runs use the accounting recursion variant
@@ -1615,46 +1629,69 @@ hgm_status run_block(BlockBufs &bb, const hgm_model *const *models, int nm, cons
         u_off[(size_t)s] = S_total * R;
         S_total += scenes[s]->d.S;
     }
-    const size_t lo_bytes = (lo_all.size() * sizeof(int32_t) + 7) & ~(size_t)7;
-    CK(bb.tab.ensure(lo_bytes + cs_all.size() * sizeof(int64_t)), "workspace (block)");
+    // one upload: [lo | cs | units | scene records | band records], each part 256-byte aligned
+    auto al256 = [](size_t v) { return (v + 255) & ~(size_t)255; };
+    const size_t o_cs = al256(lo_all.size() * sizeof(int32_t));
+    const size_t o_units = o_cs + al256(cs_all.size() * sizeof(int64_t));
+    const size_t o_srec = o_units + al256(units.size() * sizeof(BlockUnit));
+    const size_t o_geo = o_srec + al256((size_t)ns * sizeof(SceneRec));
+    const size_t tab_bytes = o_geo + al256((size_t)ns * sizeof(BlockGeo));
+    CK(bb.tab.ensure(tab_bytes), "workspace (block)");
     CK(bb.cellb.ensure((size_t)std::max<int64_t>(total_cells, 1) * sizeof(int32_t)), "workspace (block)");
     CK(bb.dir.ensure((size_t)std::max<int64_t>(total_cells, 1) * 2 * sizeof(float)), "workspace (block)");
     CK(bb.U.ensure((size_t)std::max<int64_t>(S_total * R, 1) * sizeof(float)), "workspace (block)");
     CK(bb.beta.ensure(beta_bytes), "workspace (block)");
-    const size_t b_units = (units.size() * sizeof(BlockUnit) + 255) & ~(size_t)255;
-    const size_t b_s = ((size_t)ns * sizeof(SceneRec) + 255) & ~(size_t)255;
-    const size_t b_g = ((size_t)ns * sizeof(BlockGeo) + 255) & ~(size_t)255;
-    CK(bb.rec.ensure(b_units + b_s + b_g), "workspace (block)");
-    int32_t *d_lo = bb.tab.as<int32_t>();
-    int64_t *d_cs = reinterpret_cast<int64_t *>(bb.tab.as<char>() + lo_bytes);
-    Exec ex;
-    hgm_status rc;
-    if ((rc = h2d(ex, d_lo, lo_all.data(), lo_all.size() * sizeof(int32_t), st)) ||
-        (rc = h2d(ex, d_cs, cs_all.data(), cs_all.size() * sizeof(int64_t), st)))
-        return rc;
+    char *dtab = bb.tab.as<char>();
+    const int32_t *d_lo = reinterpret_cast<const int32_t *>(dtab);
+    const int64_t *d_cs = reinterpret_cast<const int64_t *>(dtab + o_cs);
     std::vector<BlockGeo> geos((size_t)ns);
     std::vector<SceneRec> srec((size_t)ns);
     float *dirf_all = bb.dir.as<float>(), *dirb_all = dirf_all + total_cells;
     for (int s = 0; s < ns; ++s) {
         const hgm_scene *sc = scenes[s];
-        const int32_t *lo = d_lo + lo_off[(size_t)s];
-        const int64_t *cs = d_cs + cs_off[(size_t)s];
-        int32_t *cellb = bb.cellb.as<int32_t>() + cell_off[(size_t)s];
-        float *dirf = dirf_all + cell_off[(size_t)s], *dirb = dirb_all + cell_off[(size_t)s];
-        CK(launch_block_geo(sc->d.xy, sc->d.S, lo, cs, cells[(size_t)s], cellb, dirf, dirb, st), "block geometry");
-        geos[(size_t)s] = BlockGeo{lo, cs, cellb, dirf, dirb, cells[(size_t)s]};
-        float *U = bb.U.as<float>() + u_off[(size_t)s];
-        srec[(size_t)s] = SceneRec{sc->d.xy, sc->d.t, sc->d.frame_start, sc->d.perm, U, (int64_t)sc->d.S, sc->d.S,
-                                   sc->d.n_frames, sc->d.f, nullptr, 0};
+        geos[(size_t)s] = BlockGeo{d_lo + lo_off[(size_t)s], d_cs + cs_off[(size_t)s],
+                                   bb.cellb.as<int32_t>() + cell_off[(size_t)s], dirf_all + cell_off[(size_t)s],
+                                   dirb_all + cell_off[(size_t)s], cells[(size_t)s]};
+        srec[(size_t)s] = SceneRec{sc->d.xy, sc->d.t, sc->d.frame_start, sc->d.perm, bb.U.as<float>() + u_off[(size_t)s],
+                                   (int64_t)sc->d.S, sc->d.S, sc->d.n_frames, sc->d.f, nullptr, 0};
+    }
+    char *h = nullptr;
+    std::vector<char> blob;
+    if (bb.own_pinned) {
+        if (!bb.upload_done) CK(cudaEventCreateWithFlags(&bb.upload_done, cudaEventDisableTiming), "event");
+        CK(cudaEventSynchronize(bb.upload_done), "wait for the previous upload");
+        if (bb.pinned_bytes < tab_bytes) {
+            if (bb.pinned) cudaFreeHost(bb.pinned);
+            bb.pinned = nullptr;
+            bb.pinned_bytes = 0;
+            CK(cudaMallocHost(&bb.pinned, 2 * tab_bytes), "pinned staging");
+            bb.pinned_bytes = 2 * tab_bytes;
+        }
+        h = static_cast<char *>(bb.pinned);
+    } else {
+        blob.resize(tab_bytes);
+        h = blob.data();
+    }
+    std::memcpy(h, lo_all.data(), lo_all.size() * sizeof(int32_t));
+    std::memcpy(h + o_cs, cs_all.data(), cs_all.size() * sizeof(int64_t));
+    std::memcpy(h + o_units, units.data(), units.size() * sizeof(BlockUnit));
+    std::memcpy(h + o_srec, srec.data(), srec.size() * sizeof(SceneRec));
+    std::memcpy(h + o_geo, geos.data(), geos.size() * sizeof(BlockGeo));
+    CK(cudaMemcpyAsync(dtab, h, tab_bytes, cudaMemcpyHostToDevice, st), "upload block tables");
+    if (bb.own_pinned) CK(cudaEventRecord(bb.upload_done, st), "event");
+    for (int s = 0; s < ns; ++s) {
+        const hgm_scene *sc = scenes[s];
+        const BlockGeo &g = geos[(size_t)s];
+        CK(launch_block_geo(sc->d.xy, sc->d.S, g.lo, g.cs, g.cells, const_cast<int32_t *>(g.cellb),
+                            const_cast<float *>(g.dirf), const_cast<float *>(g.dirb), st),
+           "block geometry");
         if (sc->d.S > 0)
-            CK(launch_unary(bb.model.as<float>(), R, sc->d.f, sc->d.S, Fp, params->lambda1, U, sc->d.S, st),
+            CK(launch_unary(bb.model.as<float>(), R, sc->d.f, sc->d.S, Fp, params->lambda1,
+                            const_cast<float *>(srec[(size_t)s].U), sc->d.S, st),
                "unary kernel");
     }
-    char *rec = bb.rec.as<char>();
-    if ((rc = h2d(ex, rec, units.data(), units.size() * sizeof(BlockUnit), st)) ||
-        (rc = h2d(ex, rec + b_units, srec.data(), srec.size() * sizeof(SceneRec), st)) ||
-        (rc = h2d(ex, rec + b_units + b_s, geos.data(), geos.size() * sizeof(BlockGeo), st)))
-        return rc;
+    char *rec = dtab + o_units;
+    const size_t b_units = o_srec - o_units, b_s = o_geo - o_srec;
     const bool e_dev = energy && is_device_ptr(energy), a_dev = assign && is_device_ptr(assign);
     float *de = energy;
     int32_t *da = assign;
@@ -1745,6 +1782,7 @@ hgm_status hgm_stream_create(const hgm_model *const *models, int32_t n_models, c
     s->Fp = models[0]->d.F;
     s->view.magic = kSceneMagic;
     s->view.F_user = F;
+    s->bb.own_pinned = true;
     cudaStream_t st = (cudaStream_t)stream;
     rc = prep_block_models(s->bb, s->models.data(), n_models, st);
     cudaError_t e = cudaStreamSynchronize(st);
@@ -1833,14 +1871,42 @@ hgm_status hgm_stream_match(hgm_stream *s, const float *xy, const int32_t *t, co
     v.fs_host = fs;
     const hgm_scene *sv = &v;
     std::vector<const hgm_model *> &ms = s->models;
-    const bool host_out = (energy && !is_device_ptr(energy)) || (assign && !is_device_ptr(assign));
-    rc = run_block(s->bb, ms.data(), (int)ms.size(), &sv, 1, &s->params, st, energy, assign);
+    const bool e_host = energy && !is_device_ptr(energy), a_host = assign && !is_device_ptr(assign);
+    if (!e_host && !a_host) return run_block(s->bb, ms.data(), (int)ms.size(), &sv, 1, &s->params, st, energy, assign);
+    // host outputs: results into device buffers, then one read-back of energies, assignments and the
+    // descriptor flag through pinned memory and a single wait
+    const size_t nm = ms.size();
+    size_t a_total = 0;
+    for (const hgm_model *m : ms) a_total += (size_t)m->d.M;
+    CK(s->dev_e.ensure(nm * sizeof(float)), "stream buffers");
+    CK(s->dev_a.ensure(std::max<size_t>(a_total, 1) * sizeof(int32_t)), "stream buffers");
+    rc = run_block(s->bb, ms.data(), (int)nm, &sv, 1, &s->params, st, s->dev_e.as<float>(), s->dev_a.as<int32_t>());
     if (rc) return rc;
+    const size_t o_a = (nm * sizeof(float) + 15) & ~(size_t)15;
+    const size_t o_f = o_a + ((a_total * sizeof(int32_t) + 15) & ~(size_t)15);
+    if (o_f + 16 > s->pin_out_bytes) {
+        if (s->pin_out) cudaFreeHost(s->pin_out);
+        s->pin_out = nullptr;
+        s->pin_out_bytes = 0;
+        CK(cudaMallocHost(&s->pin_out, o_f + 16), "pinned staging");
+        s->pin_out_bytes = o_f + 16;
+    }
+    char *ho = static_cast<char *>(s->pin_out);
+    CK(cudaMemcpyAsync(ho, s->dev_e.p, nm * sizeof(float), cudaMemcpyDeviceToHost, st), "copy energy");
+    CK(cudaMemcpyAsync(ho + o_a, s->dev_a.p, a_total * sizeof(int32_t), cudaMemcpyDeviceToHost, st), "copy assign");
+    CK(cudaMemcpyAsync(ho + o_f, s->flag.p, sizeof(int), cudaMemcpyDeviceToHost, st), "flag");
+    CK(cudaStreamSynchronize(st), "synchronise");
     int bad = 0;
-    if (host_out) {
-        CK(cudaMemcpyAsync(&bad, s->flag.p, sizeof(int), cudaMemcpyDeviceToHost, st), "flag");
-        CK(cudaStreamSynchronize(st), "synchronise");
-        if (bad) return fail(HGM_EINVAL, "non-finite block descriptor (outputs are not valid)");
+    std::memcpy(&bad, ho + o_f, sizeof(int));
+    if (bad) return fail(HGM_EINVAL, "non-finite block descriptor (outputs are not valid)");
+    if (energy) {
+        if (e_host) std::memcpy(energy, ho, nm * sizeof(float));
+        else CK(cudaMemcpyAsync(energy, s->dev_e.p, nm * sizeof(float), cudaMemcpyDeviceToDevice, st), "copy energy");
+    }
+    if (assign) {
+        if (a_host) std::memcpy(assign, ho + o_a, a_total * sizeof(int32_t));
+        else CK(cudaMemcpyAsync(assign, s->dev_a.p, a_total * sizeof(int32_t), cudaMemcpyDeviceToDevice, st),
+                "copy assign");
     }
     return HGM_OK;
 }

@@ -19,7 +19,8 @@
 namespace hgm {
 namespace {
 
-constexpr int kBlockThreads = 256;
+constexpr int kBlockThreads = 256;       // many units: several CTAs per SM
+constexpr int kBlockThreadsWide = 1024;  // fewer units than SMs: one wide CTA per unit (latency-bound steps)
 
 __global__ void block_cells_kernel(const int64_t *__restrict__ cs, int S, int32_t *__restrict__ cellb)
 {
@@ -52,14 +53,14 @@ __device__ __forceinline__ bool init_better(float v, int c, int b, const InitBes
     return b < o.b;
 }
 
-template <bool kSmem>
-__global__ void __launch_bounds__(kBlockThreads) block_recurse_kernel(
+template <bool kSmem, int NT>
+__global__ void __launch_bounds__(NT) block_recurse_kernel(
     const BlockUnit *__restrict__ units, int n_units, const ModelRec *__restrict__ models,
     const SceneRec *__restrict__ scenes, const BlockGeo *__restrict__ geos, Params p, uint16_t *__restrict__ beta,
     float *__restrict__ scratch, int64_t scratch_cells, float *__restrict__ energy, int32_t *__restrict__ assign)
 {
     extern __shared__ float sm[];
-    __shared__ InitBest red[kBlockThreads / 32];
+    __shared__ InitBest red[NT / 32];
     const float lam2 = p.lambda2, lam23 = __fmul_rn(p.lambda2, p.lambda3);
     const float inf = __int_as_float(0x7f800000);
     for (int u = blockIdx.x; u < n_units; u += gridDim.x) {
@@ -135,7 +136,7 @@ __global__ void __launch_bounds__(kBlockThreads) block_recurse_kernel(
         __syncthreads();
         if (threadIdx.x == 0) {
             InitBest best = red[0];
-            for (int w = 1; w < kBlockThreads / 32; ++w)
+            for (int w = 1; w < NT / 32; ++w)
                 if (init_better(red[w].v, red[w].c, red[w].b, best)) best = red[w];
             int32_t *row = assign + un.out_a;
             if (best.v < inf) {
@@ -180,7 +181,7 @@ int64_t block_smem_cells()
     if (cudaGetDevice(&dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
         return 0;
-    const int64_t avail = (int64_t)optin - (int64_t)sizeof(InitBest) * (kBlockThreads / 32) - 1024;
+    const int64_t avail = (int64_t)optin - (int64_t)sizeof(InitBest) * (kBlockThreadsWide / 32) - 1024;
     return avail > 0 ? avail / (2 * (int64_t)sizeof(float)) : 0;
 }
 
@@ -194,18 +195,22 @@ cudaError_t launch_block_recurse(const BlockUnit *units, int n_units, const Mode
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return e;
     prof_begin(kProfRecurse, st);
+    const bool wide = n_units < sms;
     if (scratch == nullptr) {
         const size_t smem = (size_t)max_cells * 2 * sizeof(float);
-        e = cudaFuncSetAttribute(block_recurse_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        auto kern = wide ? block_recurse_kernel<true, kBlockThreadsWide> : block_recurse_kernel<true, kBlockThreads>;
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e == cudaSuccess) {
             const int grid = std::min(n_units, sms * 8);
-            block_recurse_kernel<true><<<grid, kBlockThreads, smem, st>>>(units, n_units, models, scenes, geos, p, beta,
-                                                                          nullptr, 0, energy, assign);
+            kern<<<grid, wide ? kBlockThreadsWide : kBlockThreads, smem, st>>>(units, n_units, models, scenes, geos, p,
+                                                                                beta, nullptr, 0, energy, assign);
             e = cudaGetLastError();
         }
     } else {
-        block_recurse_kernel<false><<<grid_global, kBlockThreads, 0, st>>>(units, n_units, models, scenes, geos, p,
-                                                                           beta, scratch, max_cells, energy, assign);
+        auto kern = wide ? block_recurse_kernel<false, kBlockThreadsWide> : block_recurse_kernel<false, kBlockThreads>;
+        kern<<<grid_global, wide ? kBlockThreadsWide : kBlockThreads, 0, st>>>(units, n_units, models, scenes, geos, p,
+                                                                                beta, scratch, max_cells, energy,
+                                                                                assign);
         e = cudaGetLastError();
     }
     prof_end(kProfRecurse, st);
