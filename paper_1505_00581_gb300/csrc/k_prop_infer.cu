@@ -21,6 +21,7 @@
 #include "prop.cuh"
 #include "tc05.cuh"
 #include "unary_common.cuh"
+#include "f32x2.cuh"
 
 namespace hgm {
 namespace {
@@ -131,13 +132,24 @@ __global__ void __launch_bounds__(256, 2) prop_score_kernel(const Unit *__restri
             parity ^= 1u << b;
             pending &= ~(1u << b);
             tc05::fence_after_sync();
+            // columns in pairs (packed FP32x2 add and FMA): even and odd columns accumulate separately
+            unsigned long long acc2 = pk2(0.0f, 0.0f);
 #pragma unroll
             for (int c0 = 0; c0 < 64; c0 += 32) {
                 float v[32];
                 tc05::tmem_ld32(tlane + (uint32_t)(H * b + c0), v);
 #pragma unroll
-                for (int q = 0; q < 32; ++q) acc = fmaf(fmaxf(v[q] + sm.b2[h0 + c0 + q], 0.0f), sm.w3[h0 + c0 + q], acc);
+                for (int q = 0; q < 32; q += 2) {
+                    const float2 b2 = *reinterpret_cast<const float2 *>(&sm.b2[h0 + c0 + q]);
+                    const float2 w3 = *reinterpret_cast<const float2 *>(&sm.w3[h0 + c0 + q]);
+                    float z0, z1;
+                    upk2(add2(pk2(v[q], v[q + 1]), pk2(b2.x, b2.y)), z0, z1);
+                    acc2 = fma2(pk2(fmaxf(z0, 0.0f), fmaxf(z1, 0.0f)), pk2(w3.x, w3.y), acc2);
+                }
             }
+            float a0, a1;
+            upk2(acc2, a0, a1);
+            acc = a0 + a1;
         } else {
             bad = true;
             if (lane == 0) atomicExch(status, 1);
@@ -196,11 +208,13 @@ __global__ void __launch_bounds__(256, 2) prop_score_kernel(const Unit *__restri
                     const float dt = (float)(tg[g] - md.t[lst] - un.offset);
                     const __nv_bfloat162 *q2 = reinterpret_cast<const __nv_bfloat162 *>(&qg[g]);
 #pragma unroll
-                    for (int e = 0; e < 4; ++e) {
+                    for (int e = 0; e < 4; ++e) {   // two hidden units per packed FP32x2 add and FMA
                         const float2 qf = __bfloat1622float2(q2[e]);
-                        const float x0 = fmaxf(fmaf(w1t[2 * e], dt, pv[2 * e] + qf.x), 0.0f);
-                        const float x1 = fmaxf(fmaf(w1t[2 * e + 1], dt, pv[2 * e + 1] + qf.y), 0.0f);
-                        hh[e] = __floats2bfloat162_rn(x0, x1);
+                        float x0, x1;
+                        upk2(fma2(pk2(w1t[2 * e], w1t[2 * e + 1]), pk2(dt, dt),
+                                  add2(pk2(pv[2 * e], pv[2 * e + 1]), pk2(qf.x, qf.y))),
+                             x0, x1);
+                        hh[e] = __floats2bfloat162_rn(fmaxf(x0, 0.0f), fmaxf(x1, 0.0f));
                     }
                 } else {
 #pragma unroll
