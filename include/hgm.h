@@ -401,6 +401,12 @@ HGM_API hgm_status hgm_count_triples(const hgm_model *model, const hgm_scene *sc
  * hook, so that the function's error bound can be checked against FP64. */
 HGM_API hgm_status hgm_atan2_f32(const float *y, const float *x, int64_t n, void *stream, float *out);
 
+/* Test hook for the bounded waits of the tensor-core kernels: one warp waits,
+ * with the same bounded mbarrier poll, on a barrier that nothing completes,
+ * gives up after `polls` polls (1..2^20) and sets *status (device int32) to 1;
+ * the context stays usable. Asynchronous on `stream`. */
+HGM_API hgm_status hgm_debug_timeout(uint32_t polls, void *stream, int32_t *status);
+
 /* C = bf16(A) * bf16(B)^T, FP32 accumulation on the 5th-generation tensor cores
  * (tcgen05.mma, accumulator in tensor memory): A [M x K], B [N x K], C [M x N],
  * row-major FP32 device arrays; K a multiple of 16 in 16..256. A test hook

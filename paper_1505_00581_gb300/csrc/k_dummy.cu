@@ -142,13 +142,16 @@ __global__ void __launch_bounds__(kDummyThreads) dummy_recurse_kernel(
                     if (ra && rb) bs = base_cost(sm.u[0][a], lam2, dt1, sm.t[0][a], sm.t[1][b], al);
                     else bs = __fadd_rn(sm.u[0][a], al);
                     sm.base[b * L + a] = bs;
-                    if (ra && rb) {
+                    // directions only where a triple can use them: a after b (else every (a, b, c) with real
+                    // points is infeasible and the cell loop skips a before reading them)
+                    if (ra && rb && sm.t[0][a] >= sm.t[1][b]) {
                         sm.p1[b * L + a] = __fadd_rn(A1, direction(sm.xy[1][b], sm.xy[0][a]));
                         sm.p2[b * L + a] = __fadd_rn(A2, direction(sm.xy[0][a], sm.xy[1][b]));
                     }
                 }
-                const int a2 = b, c = a;   // R(a, c) over the same index space
-                if (a2 < na && c < nc) sm.r[a2 * L + c] = direction(sm.xy[0][a2], sm.xy[2][c]);
+                const int a2 = b, c = a;   // R(a, c) over the same index space, where (a, c) can be feasible
+                if (a2 < na && c < nc && sm.t[2][c] <= sm.t[0][a2] && !(p.T > 0 && sm.t[0][a2] - sm.t[2][c] >= p.T))
+                    sm.r[a2 * L + c] = direction(sm.xy[0][a2], sm.xy[2][c]);
             }
             __syncthreads();
             // branch and bound (exact): v(a, b, c) >= base(b, a). Each row's real a are sorted by base (a

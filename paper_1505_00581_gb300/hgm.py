@@ -80,6 +80,7 @@ SIGNATURES = {
     "hgm_candidates": (_i32, [_vp, _vp, _PP, _i32, _i32, _vp, _vp, _vp]),
     "hgm_count_triples": (_i32, [_vp, _vp, _PP, _i32, _i32, _vp, _vp]),
     "hgm_atan2_f32": (_i32, [_vp, _vp, _i64, _vp, _vp]),
+    "hgm_debug_timeout": (_i32, [ctypes.c_uint32, _vp, _vp]),
     "hgm_gemm_bf16": (_i32, [_vp, _vp, _i32, _i32, _i32, _vp, _vp, _vp]),
     "hgm_profile_enable": (_i32, [_i32]),
     "hgm_profile_read": (_i32, [_pd, _p64, _i32]),
@@ -577,6 +578,13 @@ def count_triples(model: Model, scene: Scene, params: Params, first: int, n: int
     _check(load().hgm_count_triples(model.handle, scene.handle, ctypes.byref(params), int(first), int(n),
                                     _stream(stream), po))
     return ko
+
+
+def debug_timeout(polls: int, status, stream=None):
+    """hgm_debug_timeout: a bounded wait that runs out; status (device int32 tensor) becomes 1."""
+    (ps, ks) = _ptr(status)
+    _check(load().hgm_debug_timeout(int(polls), _stream(stream), ps))
+    return ks
 
 
 def atan2_f32(y, x, out, stream=None):
