@@ -149,8 +149,9 @@ class Clocks:
                 "samples": len(sm)}
 
 
-def oracle_sample(wl, n_units: int, seed: int, threads: int):
-    """Times the FP64 oracle on a seeded sample of units; returns (seconds, units)."""
+def oracle_sample(wl, n_units: int, seed: int, threads: int, results: list = None):
+    """Times the FP64 oracle on a seeded sample of units; returns (seconds, units). With `results`, appends
+    (model, scene, offset, energy, caller-order assignment) per unit."""
     from concurrent.futures import ThreadPoolExecutor
 
     from oracle import Oracle
@@ -167,8 +168,14 @@ def oracle_sample(wl, n_units: int, seed: int, threads: int):
         jobs.append((orc, orc.first_offset + int(rng.integers(orc.n_offsets))))
     t0 = time.perf_counter()
     with ThreadPoolExecutor(max_workers=threads) as ex:
-        list(ex.map(lambda j: j[0].match(j[1]), jobs))
-    return time.perf_counter() - t0, n_units
+        out = list(ex.map(lambda j: j[0].match(j[1]), jobs))
+    dt = time.perf_counter() - t0
+    if results is not None:
+        keys = {id(o): k for k, o in orcs.items()}
+        for (orc, o), (e, z, _) in zip(jobs, out):
+            m, s_ = keys[id(orc)]
+            results.append((m, s_, o, e, z))
+    return dt, n_units
 
 
 def total_units(wl):
@@ -371,6 +378,16 @@ def run_pruned(args, torch, hgm, wl, models, scenes, energy, assign, es, as_, de
     torch.cuda.profiler.stop()
     ms = max_over_ranks(ms, dist, dev)
     n_pruned, n_fb = hgm.prune_counters(reset=True)
+    pk, pk_kind = peaks()
+    cands = sum(wl.n_offsets(mi, si) * wl.models[mi].n for mi in range(len(wl.models))
+                for si in range(len(wl.scenes))) * wl.K
+    prune_ms = prof["prune"][0] / args.steps
+    sc_tflops = cands * 2.0 * 128 * 128 / (prune_ms / 1e3) / 1e12
+    scoring_roofline = {"kernel": "prop_score_kernel (+ keep, re-score)", "bound": "tensor",
+                        "achieved": sc_tflops, "peak": pk.get("bf16_tflops", 1900.0), "unit": "TFLOP/s",
+                        "frac": sc_tflops / pk.get("bf16_tflops", 1900.0),
+                        "work": f"{cands} candidate slots x 2 x 128 x 128 (layer 2 on the tensor cores)",
+                        "peak_source": f"bf16_tflops of MEASURED_PEAKS.json ({pk_kind})"}
     g_ms = None if args.no_graph else max_over_ranks(
         _time_plan(torch, hgm, models, scenes, p, e2, a2, args.steps, args.warmup, stream, flush), dist, dev)
     hgm.prune_counters(reset=True)
@@ -414,7 +431,7 @@ def run_pruned(args, torch, hgm, wl, models, scenes, energy, assign, es, as_, de
             "keep": 8, "K": wl.K, "precision": "BF16 unary + FP32 re-score of kept candidates",
             "fallback_units_per_step": n_fb / max(1, args.steps + args.warmup),
             "units_per_step": n_pruned / max(1, args.steps + args.warmup), **quality,
-            "refined": refined, "bf16_unpruned": bf16,
+            "refined": refined, "bf16_unpruned": bf16, "scoring_roofline": scoring_roofline,
             "top8_by_unary_baseline": {"value": job_rate(wl.total_frames, world, ms8 / 1e3), "unit": "frames/s", **base_q},
             "training": {k: v for k, v in info.items() if k != "loss"}, "final_loss": (info.get("loss") or [[0, None]])[-1][1],
             "train_s": train_s}
@@ -580,17 +597,47 @@ def main():
                 "feasible_triples_per_s": triples / chunks_per_step / (rec_avg_ms / 1e3),
                 "avg_launch_ms": rec_avg_ms,
                 "kernel_ms_per_step": {k: v[0] / args.steps for k, v in prof.items()}}
+    # the other kernels of the step against their own bounds
+    F_pad = (wl.models[0].F + 3) // 4 * 4
+    R_rows = sum(m.n for m in wl.models)
+    pairs_u = R_rows * sum(sc_.n for sc_ in wl.scenes)
+    un_ms = prof["unary"][0] / args.steps
+    sel_ms = prof["select"][0] / args.steps
+    lists = sum(wl.n_offsets(mi, si) * wl.models[mi].n for mi in range(len(wl.models)) for si in range(len(wl.scenes)))
+    roofline["other_kernels"] = {
+        "unary_kernel": {"bound": "alu", "achieved": pairs_u * 2 * F_pad / (un_ms / 1e3) / 1e12, "peak": peak_ops,
+                         "unit": "Tops/s (FP32 lane ops)",
+                         "frac": pairs_u * 2 * F_pad / (un_ms / 1e3) / 1e12 / peak_ops,
+                         "work": f"{pairs_u:.4g} (model point, scene point) pairs x 2 x {F_pad} ops"},
+        "select_kernel": {"bound": "latency", "lists_per_s": lists / (sel_ms / 1e3), "ms_per_step": sel_ms,
+                          "work": f"{lists} candidate lists (4 radix passes over each window)"}}
     launches = sum(v[1] for v in prof.values())
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         threads = os.cpu_count() or 1
         n_s = max(threads, args.cpu_units)
-        t, n = oracle_sample(wl, n_s, 11, threads)
+        sampled = []
+        t, n = oracle_sample(wl, n_s, 11, threads, sampled)
         sec_all = t / n * total_units(wl)
+        # the same units from the timed GPU run, against their FP64 energies and assignments
+        e_h, a_h = energy.cpu().numpy(), assign.cpu().numpy()
+        errs, same = [], 0
+        for m_, s_, o, e64, z64 in sampled:
+            q = m_ * len(wl.scenes) + s_
+            k = o - int(first[q])
+            eg = float(e_h[int(es[q]) + k])
+            Mq = wl.models[m_].n
+            zg = a_h[int(as_[q]) + k * Mq:int(as_[q]) + (k + 1) * Mq]
+            if np.isfinite(e64):
+                errs.append(abs(eg - e64) / max(abs(e64), 1e-30))
+            same += int(np.array_equal(zg, z64) or (not np.isfinite(e64) and not np.isfinite(eg)))
         cpu = {"value": wl.total_frames / sec_all, "unit": "frames/s", "cores": threads, "kind": "oracle",
                "sample": f"{n} seeded units of {total_units(wl)} ({t:.1f} s on {threads} threads), "
-                         f"projected to the whole workload"}
+                         f"projected to the whole workload",
+               "fp64_check": {"units": n, "finite": len(errs), "max_rel_err": max(errs) if errs else None,
+                              "mean_rel_err": float(np.mean(errs)) if errs else None,
+                              "assignment_equal": same / max(n, 1)}}
 
     chains = None
     if not args.no_chains:
