@@ -18,6 +18,8 @@
 #include <numeric>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "hgm_internal.cuh"
 #include "prop.cuh"
 
@@ -299,8 +301,13 @@ hgm_status upload_sorted_rows(const float *src, int64_t n, int F, int Fp, const 
 }  // namespace
 
 // Profiling hooks used by the kernel launchers.
+// NVTX ranges (host-side launch spans) of the pipeline stages, for timeline tools
+static const char *const kStageNames[kProfCount] = {"hgm: unary", "hgm: select", "hgm: recursion",
+                                                    "hgm: backtrack", "hgm: pruning"};
+
 void prof_begin(int kernel, cudaStream_t st)
 {
+    nvtxRangePushA(kStageNames[kernel]);
     if (!g_prof_on || g_capturing) return;
     std::lock_guard<std::mutex> lk(g_prof_mu);
     ProfRec r{kernel, prof_event(), prof_event()};
@@ -312,6 +319,7 @@ void prof_begin(int kernel, cudaStream_t st)
 
 void prof_end(int kernel, cudaStream_t st)
 {
+    nvtxRangePop();
     if (!g_prof_on || g_capturing) return;
     std::lock_guard<std::mutex> lk(g_prof_mu);
     if (!g_prof_is_open[kernel]) return;

@@ -77,3 +77,30 @@ def test_params_validation(lib):
         assert rc == code, over
     p = hgm.default_params()
     assert lib.hgm_offsets(None, None, ctypes.byref(p), ctypes.byref(n), ctypes.byref(f)) == hgm.HGM_EINVAL
+
+
+def test_validation_of_the_wider_forms(lib):
+    """Argument checks of the chains, whole-block, streaming, dummy and refinement options answer on the
+    host, before any device work."""
+    from paper_1505_00581_gb300 import hgm
+    p = hgm.default_params(dummy_cost=float("nan"))
+    n, f = ctypes.c_int32(), ctypes.c_int32()
+    assert lib.hgm_offsets(None, None, ctypes.byref(p), ctypes.byref(n), ctypes.byref(f)) == hgm.HGM_EINVAL
+    assert b"dummy_cost" in lib.hgm_last_error()
+    nil = (ctypes.c_void_p * 1)(None)
+    for over in (dict(precision=1), dict(dummy_cost=1.0)):
+        p = hgm.default_params(**over)
+        assert lib.hgm_match_block(nil, 1, nil, 1, ctypes.byref(p), None, None, None) == hgm.HGM_EUNSUPPORTED
+        h = ctypes.c_void_p()
+        assert lib.hgm_stream_create(nil, 1, ctypes.byref(p), 60, None, ctypes.byref(h)) == hgm.HGM_EUNSUPPORTED
+        assert not h.value
+    p = hgm.default_params()
+    h = ctypes.c_void_p()
+    assert lib.hgm_stream_create(nil, 1, ctypes.byref(p), 0, None, ctypes.byref(h)) == hgm.HGM_EINVAL
+    e = np.zeros(4, np.float32)
+    assert lib.hgm_match_chains(None, None, ctypes.byref(p), 3, None, None, None, e.ctypes.data, None) == hgm.HGM_EINVAL
+    assert lib.hgm_match_chains_batch(nil, 1, nil, 1, ctypes.byref(p), 0, None, e.ctypes.data, None) == hgm.HGM_EINVAL
+    assert lib.hgm_debug_timeout(0, None, None) == hgm.HGM_EINVAL
+    junk = (ctypes.c_uint32 * 4)(1, 2, 3, 4)
+    assert lib.hgm_stream_match(ctypes.cast(junk, ctypes.c_void_p), None, None, None, 0, None, None, None) \
+        == hgm.HGM_EINVAL
