@@ -128,3 +128,17 @@ def test_plan_rejects_host_outputs(env):
     with pytest.raises(hgm.HgmError) as err:
         hgm.Plan(ms, ss, p, np.zeros(int(es[-1]), np.float32), None)
     assert err.value.status == hgm.HGM_EINVAL
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_plan_dummy_assignment_equals_match_batch(env, precision):
+    """The dummy-assignment recursion recorded in a graph: replays equal the direct call bit for bit."""
+    torch, hgm = env
+    wl = _small_workload(seed=17)
+    ms, ss = _batch(torch, hgm, wl)
+    p = hgm.default_params(K=64, window=3, dummy_cost=4.0, precision=precision)
+    e0, a0 = _direct(torch, hgm, ms, ss, p)
+    assert np.all(np.isfinite(e0)) and np.any(a0 == -2)
+    for e, a in _plan_runs(torch, hgm, ms, ss, p):
+        np.testing.assert_array_equal(e, e0)
+        np.testing.assert_array_equal(a, a0)
