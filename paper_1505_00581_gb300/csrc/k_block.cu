@@ -54,7 +54,7 @@ __device__ __forceinline__ bool init_better(float v, int c, int b, const InitBes
 }
 
 template <bool kSmem, int NT>
-__global__ void __launch_bounds__(NT) block_recurse_kernel(
+__global__ void __launch_bounds__(NT, 1) block_recurse_kernel(
     const BlockUnit *__restrict__ units, int n_units, const ModelRec *__restrict__ models,
     const SceneRec *__restrict__ scenes, const BlockGeo *__restrict__ geos, Params p, uint16_t *__restrict__ beta,
     float *__restrict__ scratch, int64_t scratch_cells, float *__restrict__ energy, int32_t *__restrict__ assign)

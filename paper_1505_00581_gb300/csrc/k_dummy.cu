@@ -9,8 +9,8 @@
 // One persistent CTA per unit, all tables in shared memory (L x L floats each): alpha_{i+1} and alpha_i
 // (ping-pong), base(b, a) = U(a) + lambda2 Delta(a, b) + alpha_{i+1}(a, b) (eps rules applied), and the
 // per-step directions P1(b, a) = A1 + theta(b->a), P2(b, a) = A2 + theta(a->b), R(a, c) = theta(a->c).
-// Threads stride over the cells (b, c), c fastest, so a warp shares b (broadcast reads of base, P1, P2)
-// and reads consecutive R(a, c). The argmin slots go to a per-CTA global scratch, (M-2) x L x L bytes,
+// Threads take groups of four consecutive c of one b (c fastest, so a warp shares b: broadcast reads of
+// base, P1, P2) and walk b's row of base in increasing order until no open cell of the group can improve. The argmin slots go to a per-CTA global scratch, (M-2) x L x L bytes,
 // and the CTA backtracks its own unit (Eq. 12); eps is reported as -2 in the assignment.
 #include "hgm_internal.cuh"
 #include "recurse_common.cuh"
@@ -82,7 +82,7 @@ __device__ __forceinline__ bool dummy_better(float v, int j1, int j2, const Dumm
     return j2 < o.j2;
 }
 
-__global__ void __launch_bounds__(kDummyThreads) dummy_recurse_kernel(
+__global__ void __launch_bounds__(kDummyThreads, 2) dummy_recurse_kernel(
     const Unit *__restrict__ units, int64_t n_units, const ModelRec *__restrict__ models,
     const SceneRec *__restrict__ scenes, Params p, float wd, const int32_t *__restrict__ cand_idx,
     const float *__restrict__ cand_u, const int32_t *__restrict__ cand_cnt, uint8_t *__restrict__ scratch,
@@ -171,52 +171,77 @@ __global__ void __launch_bounds__(kDummyThreads) dummy_recurse_kernel(
             __syncthreads();
             float *ac = sm.alpha[cur ^ 1];
             uint8_t *bt = beta + (int64_t)(i - 2) * L * L;
-            for (int e = threadIdx.x; e < L * L; e += blockDim.x) {
-                const int b = e / L, c = e - b * L;
+            // real cells (b, c) in groups of four consecutive c: one walk of b's base-sorted row serves the
+            // group, and stops at the first base above every open cell's best (exact: v >= base)
+            const int G = (nc + 3) >> 2;
+            for (int e = threadIdx.x; e < nb * G; e += blockDim.x) {
+                const int b = e / G, c0 = 4 * (e - b * G);
+                const int tb = sm.t[1][b], ib = sm.id[1][b];
+                const float *brow = sm.base + b * L;
+                float best[4], q1[4];
+                int arg[4], tcq[4], icq[4];
+                bool open[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const int c = c0 + q;
+                    const bool inc = c < nc;
+                    tcq[q] = inc ? sm.t[2][c] : 0;
+                    icq[q] = inc ? sm.id[2][c] : -3;
+                    open[q] = inc && icq[q] != ib && tcq[q] <= tb && (p.T <= 0 || tb - tcq[q] < p.T);
+                    q1[q] = open[q] ? direction(sm.xy[1][b], sm.xy[2][c]) : 0.0f;
+                    best[q] = open[q] ? brow[E] : inf;   // (eps, b, c) is feasible with every open cell
+                    arg[q] = open[q] ? E : 255;
+                }
+                const uint8_t *order = sm.srt[b];
+                for (int k = 0; k < na; ++k) {
+                    const int a = order[k];
+                    const float ba = brow[a];
+                    float bmax = -inf;
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) bmax = fmaxf(bmax, open[q] ? best[q] : -inf);
+                    if (ba > bmax) break;
+                    const int ta = sm.t[0][a], ia = sm.id[0][a];
+                    if (ia == ib || ta < tb) continue;
+                    const float p1 = sm.p1[b * L + a], p2 = sm.p2[b * L + a];
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        if (!open[q] || ia == icq[q] || (p.T > 0 && ta - tcq[q] >= p.T)) continue;
+                        const float v = triple_cost(ba, p1, p2, q1[q], sm.r[a * L + c0 + q], lam23);
+                        if (v < best[q] || (v == best[q] && a < arg[q])) { best[q] = v; arg[q] = a; }
+                    }
+                }
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const int c = c0 + q;
+                    if (c < nc) {
+                        ac[b * L + c] = open[q] ? cell_alpha(best[q], lam2, dt2, tb, tcq[q]) : inf;
+                        bt[b * L + c] = (uint8_t)(open[q] ? arg[q] : 255);
+                    }
+                }
+            }
+            // cells holding eps (row b = eps over every c, column c = eps over the real b): a triple holding
+            // eps costs base(b, a) alone, so in sorted order the first feasible real a is the smallest
+            // (lowest slot among equals); eps (the last slot) only if below it
+            for (int e = threadIdx.x; e < nc + 1 + nb; e += blockDim.x) {
+                const int b = e <= nc ? E : e - (nc + 1);
+                const int c = e < nc ? e : E;
                 const bool rb = b < nb, rc = c < nc;
-                if (!((rb || b == E) && (rc || c == E))) continue;
+                const float *brow = sm.base + b * L;
+                const uint8_t *order = sm.srt[b];
+                const int tr = rc ? sm.t[2][c] : (rb ? sm.t[1][b] : 0);   // the other real point
+                const int ir = rc ? sm.id[2][c] : (rb ? sm.id[1][b] : -3);
+                const bool any = !rb && !rc;
                 float best = inf;
                 int arg = 255;
-                const float *brow = sm.base + b * L;
-                if (rb && rc) {
-                    const int tb = sm.t[1][b], tc = sm.t[2][c], ib = sm.id[1][b], ic = sm.id[2][c];
-                    const bool bc_ok = ib != ic && tc <= tb && (p.T <= 0 || tb - tc < p.T);
-                    if (bc_ok) {
-                        const float q1 = direction(sm.xy[1][b], sm.xy[2][c]);
-                        best = brow[E];   // (eps, b, c): always feasible here, finite
-                        arg = E;
-                        auto eval = [&](int a) {
-                            const int ta = sm.t[0][a], ia = sm.id[0][a];
-                            if (ia == ib || ia == ic || ta < tb || (p.T > 0 && ta - tc >= p.T)) return;
-                            const float v = triple_cost(brow[a], sm.p1[b * L + a], sm.p2[b * L + a], q1,
-                                                        sm.r[a * L + c], lam23);
-                            if (v < best || (v == best && a < arg)) { best = v; arg = a; }
-                        };
-                        const uint8_t *order = sm.srt[b];
-                        for (int k = 0; k < na; ++k) {
-                            const int a = order[k];
-                            if (brow[a] > best) break;
-                            eval(a);
-                        }
-                    }
-                    if (best < inf) best = cell_alpha(best, lam2, dt2, tb, tc);
-                } else {
-                    // a triple holding eps costs base(b, a) alone: in sorted order the first feasible real
-                    // a is the smallest (lowest slot among equals); eps (the last slot) only if below it
-                    const uint8_t *order = sm.srt[b];
-                    const int tr = rc ? sm.t[2][c] : (rb ? sm.t[1][b] : 0);   // the other real point
-                    const int ir = rc ? sm.id[2][c] : (rb ? sm.id[1][b] : -3);
-                    const bool any = !rb && !rc;
-                    for (int k = 0; k < na; ++k) {
-                        const int a = order[k];
-                        const int ta = sm.t[0][a];
-                        if (!any && (sm.id[0][a] == ir || ta < tr || (p.T > 0 && ta - tr >= p.T))) continue;
-                        best = brow[a];
-                        arg = a;
-                        break;
-                    }
-                    if (brow[E] < best) { best = brow[E]; arg = E; }
+                for (int k = 0; k < na; ++k) {
+                    const int a = order[k];
+                    const int ta = sm.t[0][a];
+                    if (!any && (sm.id[0][a] == ir || ta < tr || (p.T > 0 && ta - tr >= p.T))) continue;
+                    best = brow[a];
+                    arg = a;
+                    break;
                 }
+                if (brow[E] < best) { best = brow[E]; arg = E; }
                 ac[b * L + c] = best;
                 bt[b * L + c] = (uint8_t)arg;
             }
