@@ -19,6 +19,7 @@ namespace hgm {
 namespace {
 
 constexpr int kWarps = 8;
+constexpr int kKeyRegs = 8;   // windows of up to 32 x 8 = 256 keys are selected from registers
 
 __device__ __forceinline__ uint32_t lanemask_lt()
 {
@@ -27,7 +28,7 @@ __device__ __forceinline__ uint32_t lanemask_lt()
     return m;
 }
 
-__global__ void __launch_bounds__(kWarps * 32) select_kernel(const Unit *__restrict__ units, int64_t n_units,
+__global__ void __launch_bounds__(kWarps * 32, 3) select_kernel(const Unit *__restrict__ units, int64_t n_units,
                                                              const ModelRec *__restrict__ models,
                                                              const SceneRec *__restrict__ scenes, Params p,
                                                              int32_t *__restrict__ cand_idx,
@@ -62,15 +63,31 @@ __global__ void __launch_bounds__(kWarps * 32) select_kernel(const Unit *__restr
                     ou[e] = e < n ? key[e] : __int_as_float(0x7f800000);
                 }
             } else {
-                // radix select of the K-th smallest key (1-based rank kk)
+                // radix select of the K-th smallest key (1-based rank kk); windows of up to 256 keys are
+                // read once into registers (lane + 32 q), longer ones from memory in every pass
+                const bool inreg = n <= 32 * kKeyRegs;
+                uint32_t kb[kKeyRegs];
+#pragma unroll
+                for (int q = 0; q < kKeyRegs; ++q) {
+                    const int e = lane + 32 * q;
+                    kb[q] = inreg && e < n ? __float_as_uint(key[e]) : 0xffffffffu;
+                }
                 uint32_t prefix = 0, mask = 0;
                 int kk = K;
                 for (int shift = 24; shift >= 0; shift -= 8) {
                     for (int d = lane; d < 256; d += 32) hist[warp][d] = 0;
                     __syncwarp();
-                    for (int e = lane; e < n; e += 32) {
-                        uint32_t b = __float_as_uint(key[e]);
-                        if ((b & mask) == prefix) atomicAdd(&hist[warp][(b >> shift) & 255u], 1u);
+                    if (inreg) {
+#pragma unroll
+                        for (int q = 0; q < kKeyRegs; ++q) {
+                            const uint32_t b = kb[q];
+                            if (lane + 32 * q < n && (b & mask) == prefix) atomicAdd(&hist[warp][(b >> shift) & 255u], 1u);
+                        }
+                    } else {
+                        for (int e = lane; e < n; e += 32) {
+                            uint32_t b = __float_as_uint(key[e]);
+                            if ((b & mask) == prefix) atomicAdd(&hist[warp][(b >> shift) & 255u], 1u);
+                        }
                     }
                     __syncwarp();
                     uint32_t c[8];
@@ -109,7 +126,15 @@ __global__ void __launch_bounds__(kWarps * 32) select_kernel(const Unit *__restr
                 for (int c0 = 0; c0 < n; c0 += 32) {
                     int e = c0 + lane;
                     bool valid = e < n;
-                    float kv = valid ? key[e] : 0.0f;
+                    float kv = 0.0f;
+                    if (inreg) {
+#pragma unroll
+                        for (int q = 0; q < kKeyRegs; ++q)
+                            if (c0 == 32 * q) kv = __uint_as_float(kb[q]);
+                        kv = valid ? kv : 0.0f;
+                    } else {
+                        kv = valid ? key[e] : 0.0f;
+                    }
                     uint32_t b = __float_as_uint(kv);
                     bool lt = valid && b < tau;
                     bool eq = valid && b == tau;
