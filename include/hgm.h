@@ -29,7 +29,10 @@
  *    hgm_last_error() returns a message (thread-local, valid until the next
  *    call on the same thread).
  *  - "stream" is a cudaStream_t passed as void*; NULL is the legacy default
- *    stream. Device work is ordered on that stream.
+ *    stream. Device work is ordered on that stream. The library's shared
+ *    workspace is ordered across streams: each call's work waits for the
+ *    previous call's, whatever stream that was on (plans and stream objects
+ *    own their buffers; calls on one stream object must not overlap).
  *  - A pointer documented "host or device" may be either; the library asks
  *    the CUDA driver which. Host outputs make the call synchronous on the
  *    stream; device outputs leave it asynchronous.

@@ -173,6 +173,25 @@ struct BlockBufs {
 };
 Workspace g_ws;
 BlockBufs g_blk;
+
+// Calls on different streams share g_ws / g_blk: each call's work waits for the previous call's (on whatever
+// stream it ran), so a call with device outputs may return before its work finishes without racing the next.
+cudaEvent_t g_ws_event = nullptr;
+struct WsGuard {
+    cudaStream_t st;
+    explicit WsGuard(cudaStream_t s) : st(s)
+    {
+        if (g_ws_event) cudaStreamWaitEvent(st, g_ws_event, 0);
+    }
+    ~WsGuard()
+    {
+        if (!g_ws_event && cudaEventCreateWithFlags(&g_ws_event, cudaEventDisableTiming) != cudaSuccess) {
+            g_ws_event = nullptr;
+            return;
+        }
+        cudaEventRecord(g_ws_event, st);
+    }
+};
 }  // namespace
 }  // namespace hgm
 
@@ -1251,6 +1270,7 @@ hgm_status hgm_match(const hgm_model *model, const hgm_scene *scene, const hgm_p
 {
     std::lock_guard<std::mutex> lk(g_mu);
     g_err.clear();
+    WsGuard wsg((cudaStream_t)stream);
     hgm_status rc = check_params(params);
     if (rc) return rc;
     if (!valid_model(model) || !valid_scene(scene)) return fail(HGM_EINVAL, "invalid handle");
@@ -1519,6 +1539,7 @@ hgm_status hgm_match_chains(const hgm_model *model, const hgm_scene *scene, cons
 {
     std::lock_guard<std::mutex> lk(g_mu);
     g_err.clear();
+    WsGuard wsg((cudaStream_t)stream);
     hgm_status rc = check_params(params);
     if (rc) return rc;
     if (!valid_model(model) || !valid_scene(scene)) return fail(HGM_EINVAL, "invalid handle");
@@ -1537,6 +1558,7 @@ hgm_status hgm_match_chains_batch(const hgm_model *const *models, int32_t n_mode
 {
     std::lock_guard<std::mutex> lk(g_mu);
     g_err.clear();
+    WsGuard wsg((cudaStream_t)stream);
     return run_chains(models, n_models, scenes, n_scenes, params, n_chains, (cudaStream_t)stream, energy, assign);
 }
 
@@ -1745,6 +1767,7 @@ hgm_status hgm_match_block(const hgm_model *const *models, int32_t n_models, con
 {
     std::lock_guard<std::mutex> lk(g_mu);
     g_err.clear();
+    WsGuard wsg((cudaStream_t)stream);
     hgm_status rc = check_params(params);
     if (rc) return rc;
     if (params->precision != 0 || params->prune || params->dummy_cost >= 0)
@@ -1924,6 +1947,7 @@ hgm_status hgm_match_batch(const hgm_model *const *models, int32_t n_models, con
 {
     std::lock_guard<std::mutex> lk(g_mu);
     g_err.clear();
+    WsGuard wsg((cudaStream_t)stream);
     if (n_models < 0 || n_scenes < 0 || (n_models && !models) || (n_scenes && !scenes))
         return fail(HGM_EINVAL, "bad model/scene arrays");
     Exec ex;
@@ -1954,6 +1978,7 @@ hgm_status hgm_unary(const hgm_model *model, const hgm_scene *scene, float lambd
 {
     std::lock_guard<std::mutex> lk(g_mu);
     g_err.clear();
+    WsGuard wsg((cudaStream_t)stream);
     if (!valid_model(model) || !valid_scene(scene)) return fail(HGM_EINVAL, "invalid handle");
     if (model->F_user != scene->F_user) return fail(HGM_EINVAL, "descriptor width differs between model and scene");
     if (!U || !is_device_ptr(U)) return fail(HGM_EINVAL, "U must be a device pointer");
@@ -1968,6 +1993,7 @@ hgm_status hgm_unary_bf16(const hgm_model *model, const hgm_scene *scene, float 
 {
     std::lock_guard<std::mutex> lk(g_mu);
     g_err.clear();
+    WsGuard wsg((cudaStream_t)stream);
     if (!valid_model(model) || !valid_scene(scene)) return fail(HGM_EINVAL, "invalid handle");
     if (model->F_user != scene->F_user) return fail(HGM_EINVAL, "descriptor width differs between model and scene");
     if (!U || !is_device_ptr(U)) return fail(HGM_EINVAL, "U must be a device pointer");
@@ -1995,6 +2021,7 @@ hgm_status hgm_candidates(const hgm_model *model, const hgm_scene *scene, const 
 {
     std::lock_guard<std::mutex> lk(g_mu);
     g_err.clear();
+    WsGuard wsg((cudaStream_t)stream);
     if (!idx || !cnt || !is_device_ptr(idx) || !is_device_ptr(cnt)) return fail(HGM_EINVAL, "outputs must be device pointers");
     cudaStream_t st = (cudaStream_t)stream;
     Params p;
@@ -2014,6 +2041,7 @@ hgm_status hgm_prop_scores(const hgm_prop *prop, const hgm_model *model, const h
 {
     std::lock_guard<std::mutex> lk(g_mu);
     g_err.clear();
+    WsGuard wsg((cudaStream_t)stream);
     if (!prop || prop->magic != kPropMagic) return fail(HGM_EINVAL, "prop is not a proposal-network handle");
     if (!scores || !is_device_ptr(scores)) return fail(HGM_EINVAL, "scores must be a device pointer");
     if (params && params->K > 64) return fail(HGM_EUNSUPPORTED, "proposal scoring needs K <= 64");
@@ -2081,6 +2109,7 @@ hgm_status hgm_count_triples(const hgm_model *model, const hgm_scene *scene, con
 {
     std::lock_guard<std::mutex> lk(g_mu);
     g_err.clear();
+    WsGuard wsg((cudaStream_t)stream);
     if (!triples || !is_device_ptr(triples)) return fail(HGM_EINVAL, "triples must be a device pointer");
     cudaStream_t st = (cudaStream_t)stream;
     Params p;
@@ -2117,6 +2146,7 @@ hgm_status hgm_autotune(const hgm_model *const *models, int32_t n_models, const 
 {
     std::lock_guard<std::mutex> lk(g_mu);
     g_err.clear();
+    WsGuard wsg((cudaStream_t)stream);
     if (n_models < 1 || n_scenes < 1 || !models || !scenes || sample_offsets < 1)
         return fail(HGM_EINVAL, "bad autotune arguments");
     hgm_status rc = check_params(params);

@@ -142,3 +142,34 @@ def test_plan_dummy_assignment_equals_match_batch(env, precision):
     for e, a in _plan_runs(torch, hgm, ms, ss, p):
         np.testing.assert_array_equal(e, e0)
         np.testing.assert_array_equal(a, a0)
+
+
+def test_calls_on_two_streams_do_not_race(env):
+    """Two batches with device outputs issued back to back on different streams share the library's
+    workspace; the second waits for the first, so both equal their one-at-a-time results."""
+    torch, hgm = env
+    wl = _small_workload(seed=19)
+    ms, ss = _batch(torch, hgm, wl)
+    pa = hgm.default_params(K=64, window=3)
+    pb = hgm.default_params(K=24, window=2)
+    ea0, aa0 = _direct(torch, hgm, ms, ss, pa)
+    eb0, ab0 = _direct(torch, hgm, ms, ss, pb)
+    sa, sb = torch.cuda.Stream(), torch.cuda.Stream()
+    outs = []
+    for p_, st in ((pa, sa), (pb, sb)):
+        _, es, as_ = hgm.batch_layout(ms, ss, p_)
+        e = torch.empty(int(es[-1]), dtype=torch.float32, device="cuda")
+        a = torch.empty(int(as_[-1]), dtype=torch.int32, device="cuda")
+        outs.append((e, a))
+    for rep in range(3):
+        for (e, a), p_, st in zip(outs, (pa, pb), (sa, sb)):
+            e.fill_(-1.0)
+            a.fill_(-7)
+        torch.cuda.synchronize()
+        hgm.match_batch(ms, ss, pa, outs[0][0], outs[0][1], stream=sa)
+        hgm.match_batch(ms, ss, pb, outs[1][0], outs[1][1], stream=sb)
+        torch.cuda.synchronize()
+        np.testing.assert_array_equal(outs[0][0].cpu().numpy(), ea0)
+        np.testing.assert_array_equal(outs[0][1].cpu().numpy(), aa0)
+        np.testing.assert_array_equal(outs[1][0].cpu().numpy(), eb0)
+        np.testing.assert_array_equal(outs[1][1].cpu().numpy(), ab0)

@@ -86,3 +86,22 @@ def test_stream_growth_device_inputs_and_errors(env):
         st.match(np.zeros((4, 2), np.float32), bad_t, np.zeros((4, mods[0].F), np.float32))
     assert err.value.status == hgm.HGM_EINVAL
     st.close()
+
+
+def test_stream_empty_and_tiny_blocks(env):
+    """A block without points has no feasible chain (+inf, rows of -1); a block of two points cannot hold
+    a triangle either; the stream stays usable afterwards."""
+    torch, hgm, oracle = env
+    mods, sc = _long_scene(8, n_models=2, n_frames=60)
+    M = [hgm.Model(m.xy, m.t, m.f) for m in mods]
+    st = hgm.Stream(M, hgm.default_params(), 60)
+    F = mods[0].F
+    e, a = st.match(np.zeros((0, 2), np.float32), np.zeros(0, np.int32), np.zeros((0, F), np.float32))
+    assert np.all(np.isinf(e)) and np.all(a == -1)
+    e, a = st.match(sc.xy[:2], np.array([3, 5], np.int32), sc.f[:2])
+    assert np.all(np.isinf(e)) and np.all(a == -1)
+    e, a = st.match(sc.xy, sc.t, sc.f)
+    orc = oracle.Oracle(mods[0].xy, mods[0].t, mods[0].f, sc.xy, sc.t, sc.f, 60, K=8, window=1, T=10, **LAM)
+    e64, _, _ = orc.match_block()
+    assert np.isfinite(e64) and abs(e[0] - e64) <= 1e-5 * e64 + 1e-6
+    st.close()
