@@ -312,8 +312,13 @@ static int solve_lists(const or_ctx *c, int Kc, const int *cand, const double *c
                 for (int jc = 0; jc < cnt[i - 2]; ++jc) {
                     double best = INFINITY;
                     int arg = -1;
-                    for (int ja = 0; ja < cnt[i]; ++ja) {
-                        int a = Ci[ja], b = Cb[jb], cc = Cc[jc];
+                    const int b = Cb[jb], cc = Cc[jc];
+                    /* R3 between two real points b and c alone (distinct, t'(c) <= t'(b), t'(b) - t'(c) < T)
+                     * is implied by the feasibility of any (a, b, c): when it fails, no a is tried */
+                    const int bc_ok = b == OR_EPS || cc == OR_EPS ||
+                                      (b != cc && c->st[cc] <= c->st[b] && !(c->T > 0 && c->st[b] - c->st[cc] >= c->T));
+                    for (int ja = 0; bc_ok && ja < cnt[i]; ++ja) {
+                        int a = Ci[ja];
                         if (!or_feasible(c, a, b, cc)) continue;
                         ++triples;
                         double v = Ui[ja] + or_triple(c, i, a, b, cc) + alpha_next[(size_t)ja * K + jb];

@@ -105,3 +105,47 @@ def test_stream_empty_and_tiny_blocks(env):
     e64, _, _ = orc.match_block()
     assert np.isfinite(e64) and abs(e[0] - e64) <= 1e-5 * e64 + 1e-6
     st.close()
+
+
+def test_stream_full_size_sampled(env):
+    """The streaming workload of the benchmark at full size (50 models, a one-minute scene, 60-frame blocks
+    every 30 frames), in the benchmark's launch configuration; 12 seeded (block, model) results checked
+    against the oracle, and the whole-scene case of Table 2 on 6 seeded models."""
+    torch, hgm, oracle = env
+    ws = synth.paper_stream()
+    dev = torch.device("cuda")
+    M = [hgm.Model(*(torch.from_numpy(a).to(dev) for a in (m.xy, m.t, m.f))) for m in ws.models]
+    p = hgm.default_params()
+    st = hgm.Stream(M, p, 60)
+    sc = ws.scenes[0]
+    blocks = list(hgm.stream_blocks(sc.xy, sc.t, sc.f, sc.n_frames, 60, 30))
+    res = [st.match(bxy, bt, bf) for _, bxy, bt, bf, _ in blocks]
+    rng = np.random.default_rng(5)
+    for _ in range(12):
+        bi, mi = int(rng.integers(len(blocks))), int(rng.integers(len(M)))
+        _, bxy, bt, bf, _ = blocks[bi]
+        e, a = res[bi]
+        mod = ws.models[mi]
+        orc = oracle.Oracle(mod.xy, mod.t, mod.f, bxy, bt, bf, 60, K=8, window=1, T=10, **LAM)
+        e64, z64, _ = orc.match_block()
+        z = a[st.starts[mi]:st.starts[mi + 1]]
+        assert np.isfinite(e64) == np.isfinite(e[mi])
+        if np.isfinite(e64):
+            assert abs(e[mi] - e64) <= 1e-5 * e64 + 1e-6, (bi, mi, e[mi], e64)
+            if not np.array_equal(z, z64):
+                assert orc.energy(z) <= e64 * (1 + 1e-5) + 1e-6
+    st.close()
+    ww = synth.paper_whole()
+    s0 = ww.scenes[0]
+    WM = [hgm.Model(m.xy, m.t, m.f) for m in ww.models]
+    S = [hgm.Scene(s0.xy, s0.t, s0.f, s0.n_frames)]
+    e, a = hgm.match_block(WM, S, p)
+    starts = hgm.block_layout(WM, 1)
+    for mi in rng.choice(len(WM), 6, replace=False):
+        mod = ww.models[mi]
+        orc = oracle.Oracle(mod.xy, mod.t, mod.f, s0.xy, s0.t, s0.f, s0.n_frames, K=8, window=1, T=10, **LAM)
+        e64, z64, _ = orc.match_block()
+        assert np.isfinite(e64) and abs(e[mi] - e64) <= 1e-5 * e64 + 1e-6, (mi, e[mi], e64)
+        z = a[starts[mi]:starts[mi + 1]]
+        if not np.array_equal(z, z64):
+            assert orc.energy(z) <= e64 * (1 + 1e-5) + 1e-6
