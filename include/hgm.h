@@ -186,6 +186,8 @@ HGM_API hgm_status hgm_match_batch(const hgm_model *const *models, int32_t n_mod
  * infeasible). n_chains in 1..255; HGM_EINVAL if no chain of the model has
  * 3 points. The split is kept on the model handle (rebuilt when n_chains
  * changes; the first call for a model and n_chains synchronises the stream).
+ * params apply to every chain as in hgm_match_batch (precision, pruning and
+ * the dummy assignment included; the refinement is not applied).
  * Completion as for hgm_match. */
 HGM_API hgm_status hgm_match_chains(const hgm_model *model, const hgm_scene *scene, const hgm_params *params,
                                     int32_t n_chains, void *stream, int32_t *n_offsets, int32_t *first_offset,
