@@ -228,9 +228,21 @@ recurse_kernel(const Unit *__restrict__ units, int64_t n_units, const ModelRec *
                 float m1 = kInf, m2 = kInf, q1v = kInf, q2v = kInf;
                 int s1 = 1 << 20, s2 = 1 << 20;
                 const int t0c = nc > 0 ? LC.t[0] : 0;
+                // the a with t'(a) >= t'(b) form a suffix of list A (time order): the slots before it are never
+                // feasible with b and are neither evaluated nor read below (k0: first k that can reach it)
+                int k0 = 0;
+                if (inb) {
+                    int lo = 0, hi = na;
+                    while (lo < hi) {
+                        const int mid = (lo + hi) >> 1;
+                        if (LA.t[mid] < tb) lo = mid + 1;
+                        else hi = mid;
+                    }
+                    k0 = lo / NP;
+                }
                 if (inb) {
 #pragma unroll 4
-                    for (int k = 0; k < AH; ++k) {
+                    for (int k = k0; k < AH; ++k) {
                         const int a = NP * k + h;
                         // slots past the list hold t = 0x3fffffff, idx = -1, u = inf: never feasible with b
                         const int ta = LA.t[a];
@@ -304,7 +316,7 @@ recurse_kernel(const Unit *__restrict__ units, int64_t n_units, const ModelRec *
                 unsigned long long mk = 0;
                 if (live) {
 #pragma unroll 8
-                    for (int k = 0; k < AH; ++k) {
+                    for (int k = k0; k < AH; ++k) {
                         const float bs = arow[NP * k + h];   // +inf for a past the list
                         if (bs < kInf && bs <= thr) mk |= 1ull << k;
                     }
@@ -356,17 +368,27 @@ recurse_kernel(const Unit *__restrict__ units, int64_t n_units, const ModelRec *
                     pf_u = cu[(int64_t)(i - 3) * K + pfi];
                 }
                 if (tid == P1 && i >= 3) sm.geo[(i - 1) & 1] = md.geo[i - 1];
-                for (int e = tid - P1; e < na * KM; e += NT - P1) {
-                    const int a = e / KM, c = e % KM;
-                    float r = kInf;
+                {
+                    // two threads per c, interleaved a. A kept a of a cell (b, c) has t'(a) >= t'(b) >= t'(c), so
+                    // only the rows from the first a with t'(a) >= t'(c) are read; entries of c past the list
+                    // belong to cells whose theta(b->c) is +inf, so their value is never used either
+                    const int q = tid - P1, c = q >> 1, h2 = q & 1;
                     if (c < nc) {
-                        const int ta = LA.t[a], tc = LC.t[c];
-                        // kept pairs have t'(c) <= t'(b) <= t'(a): entries with t'(c) > t'(a) are never read
-                        if (tc <= ta && !(T > 0 && ta - tc >= T) && LA.idx[a] != LC.idx[c]) {
-                            r = direction(LA.xy[a], LC.xy[c]);                   // theta(a->c)
+                        const int tc = LC.t[c], ic = LC.idx[c];
+                        const float2 pc = LC.xy[c];
+                        int lo = 0, hi = na;
+                        while (lo < hi) {
+                            const int mid = (lo + hi) >> 1;
+                            if (LA.t[mid] < tc) lo = mid + 1;
+                            else hi = mid;
+                        }
+                        for (int a = lo + h2; a < na; a += 2) {
+                            const int ta = LA.t[a];
+                            float r = kInf;
+                            if (!(T > 0 && ta - tc >= T) && LA.idx[a] != ic) r = direction(LA.xy[a], pc);   // theta(a->c)
+                            sm.r[a * RS + c] = r;
                         }
                     }
-                    sm.r[a * RS + c] = r;
                 }
                 pf_ok = pf && pfi < pf_n;
                 if (pf_ok) {
