@@ -36,11 +36,11 @@
 // triple loop, in increasing slot order with a strict '<', so the lowest slot
 // still wins exact ties -- the result is bit-identical to the full minimisation.
 //
-// Work split per step (two CTA barriers): phase 1, NP threads per b (adjacent
+// Work split per step (three CTA barriers): phase 1, NP threads per b (adjacent
 // lanes, interleaved a) build the kept lists with pairwise shuffles only, while
-// the other warps compute the theta(a->c) table; the list builders then meet on
-// a named barrier and warp 0 orders the b by decreasing kept count and lays out
-// the tile table; phase 3, tiles of one b and CT consecutive c with
+// the other warps compute the theta(a->c) table; then every thread takes part in
+// ordering the b by decreasing kept count and laying out the tile table; phase
+// 3, tiles of one b and CT consecutive c with
 // t'(c) <= t'(b) are flattened across the CTA's threads in that order (similar
 // loop lengths within a warp), each thread looping over the kept a of its b.
 // The per-step model constants come from a table built at model creation, and
@@ -346,20 +346,6 @@ recurse_kernel(const Unit *__restrict__ units, int64_t n_units, const ModelRec *
                     sm.tcount[b] = (uint8_t)nt_b;
                     sm.pw[b] = (key << 5) | nt_b;
                 }
-                asm volatile("bar.sync 1, %0;" ::"r"(P1) : "memory");
-                int before = 0, total = 0;
-                for (int b2 = h; b2 < KM; b2 += NP) {
-                    const int w = sm.pw[b2];
-                    total += w & 31;
-                    if ((w >> 5) > key) before += w & 31;
-                }
-                if constexpr (NP == 2) {
-                    before += __shfl_xor_sync(0xffffffffu, before, 1);
-                    total += __shfl_xor_sync(0xffffffffu, total, 1);
-                }
-                if (h == 0) sm.tbase[b] = (uint16_t)before;
-                for (int t = h; t < nt_b; t += NP) sm.tile_b[before + t] = (uint8_t)b;
-                if (tid == 0) sm.ntile = total;
             } else {
                 // ---- phase 2 (concurrent): theta(a->c) for every a and the c with t'(c) <= t'(a)
                 if (pf) {
@@ -398,6 +384,29 @@ recurse_kernel(const Unit *__restrict__ units, int64_t n_units, const ModelRec *
             }
             __syncthreads();
 
+            // tile layout, by every thread (NT / KM per b): b's first tile = the tile count of the b ranked
+            // before it (decreasing kept count, then increasing b)
+            {
+                constexpr int RP = NT / KM;
+                static_assert(RP >= 1 && RP <= 32 && (RP & (RP - 1)) == 0, "threads per b in the ranking");
+                const int b = tid / RP, part = tid % RP;
+                const int wb = sm.pw[b], key = wb >> 5, nt_b = wb & 31;
+                int before = 0, total = 0;
+                for (int b2 = part; b2 < KM; b2 += RP) {
+                    const int w = sm.pw[b2];
+                    total += w & 31;
+                    if ((w >> 5) > key) before += w & 31;
+                }
+#pragma unroll
+                for (int off = 1; off < RP; off <<= 1) {
+                    before += __shfl_xor_sync(0xffffffffu, before, off);
+                    total += __shfl_xor_sync(0xffffffffu, total, off);
+                }
+                if (part == 0) sm.tbase[b] = (uint16_t)before;
+                for (int t = part; t < nt_b; t += RP) sm.tile_b[before + t] = (uint8_t)b;
+                if (tid == 0) sm.ntile = total;
+            }
+
             // list A is not read from here on: its buffer receives list C of the next step
             if (pf) {
                 LA.idx[pfi] = pf_ok ? pf_j : -1;
@@ -412,6 +421,8 @@ recurse_kernel(const Unit *__restrict__ units, int64_t n_units, const ModelRec *
                 LA.t[pfi] = 0x3fffffff;
                 LA.u[pfi] = kInf;
             }
+
+            __syncthreads();   // the tile layout is complete
 
             // ---- phase 3: tiles (b, CT consecutive c)
             const int ntile = sm.ntile;
