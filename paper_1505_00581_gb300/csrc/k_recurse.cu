@@ -223,11 +223,9 @@ recurse_kernel(const Unit *__restrict__ units, int64_t n_units, const ModelRec *
                 int tb = 0, ib = -1;
                 if (inb) { pb = LB.xy[b]; tb = LB.t[b]; ib = LB.idx[b]; }
                 float *arow = sm.alpha + b * AS;
-                // smallest and second-smallest base (value, slot) over all feasible a, and the two smallest
-                // values over the a also feasible with the earliest c (t'(a) - t'(C_0) < T)
-                float m1 = kInf, m2 = kInf, q1v = kInf, q2v = kInf;
+                // smallest and second-smallest base (value, slot) over all feasible a
+                float m1 = kInf, m2 = kInf;
                 int s1 = 1 << 20, s2 = 1 << 20;
-                const int t0c = nc > 0 ? LC.t[0] : 0;
                 // the a with t'(a) >= t'(b) form a suffix of list A (time order): the slots before it are never
                 // feasible with b and are neither evaluated nor read below (k0: first k that can reach it)
                 int k0 = 0;
@@ -252,17 +250,12 @@ recurse_kernel(const Unit *__restrict__ units, int64_t n_units, const ModelRec *
                         arow[a] = bs;   // base(a,b) replaces alpha_{i+1}(a,b): read once, by this thread
                         if (bs < m1) { m2 = m1; s2 = s1; m1 = bs; s1 = a; }
                         else if (bs < m2) { m2 = bs; s2 = a; }
-                        if (!(T > 0 && ta - t0c >= T)) {
-                            if (bs < q1v) { q2v = q1v; q1v = bs; }
-                            else if (bs < q2v) q2v = bs;
-                        }
                     }
                 }
                 if constexpr (NP == 2) {
                     // merge the pair's (value, slot) top-2 lists; ties go to the lower slot
                     const float om1 = __shfl_xor_sync(0xffffffffu, m1, 1), om2 = __shfl_xor_sync(0xffffffffu, m2, 1);
                     const int os1 = __shfl_xor_sync(0xffffffffu, s1, 1), os2 = __shfl_xor_sync(0xffffffffu, s2, 1);
-                    const float oq1 = __shfl_xor_sync(0xffffffffu, q1v, 1), oq2 = __shfl_xor_sync(0xffffffffu, q2v, 1);
                     if (om1 < m1 || (om1 == m1 && os1 < s1)) {
                         if (m1 < om2 || (m1 == om2 && s1 < os2)) { m2 = m1; s2 = s1; }
                         else { m2 = om2; s2 = os2; }
@@ -270,8 +263,6 @@ recurse_kernel(const Unit *__restrict__ units, int64_t n_units, const ModelRec *
                     } else if (om1 < m2 || (om1 == m2 && os1 < s2)) {
                         m2 = om1; s2 = os1;
                     }
-                    q2v = fminf(fmaxf(q1v, oq1), fminf(q2v, oq2));
-                    q1v = fminf(q1v, oq1);
                 }
                 const float bv = m1;
                 // c with t'(c) <= t'(b) form a prefix of C (time order): its length by binary search
@@ -286,9 +277,9 @@ recurse_kernel(const Unit *__restrict__ units, int64_t n_units, const ModelRec *
                     ccount = lo;
                 }
                 const bool live = inb && bv < kInf && ccount > 0;
-                // cells (b,c) where the witness s1 is infeasible: their best base is at most the second
-                // smallest over the a feasible with c -- exactly m2 when the runner-up s2 is feasible with
-                // c, else at most q2v (the a feasible with C_0 are feasible with every later c)
+                // cells (b,c) where the witness s1 is infeasible: their best base is the second smallest over
+                // the a feasible with c -- exactly m2 when the runner-up s2 is feasible with c; otherwise
+                // (rare) every a is kept
                 bool anybad = false, loose = false;
                 if (live) {
                     const int tw = LA.t[s1], iw = LA.idx[s1];
@@ -308,10 +299,7 @@ recurse_kernel(const Unit *__restrict__ units, int64_t n_units, const ModelRec *
                     loose |= __shfl_xor_sync(0xffffffffu, (int)loose, 1) != 0;
                 }
                 float thr = bv + gmax + 1e-6f * bv;
-                if (anybad) {
-                    const float bb = loose ? q2v : m2;
-                    thr = bb < kInf ? fmaxf(thr, bb + gmax + 1e-6f * bb) : kInf;
-                }
+                if (anybad) thr = !loose && m2 < kInf ? fmaxf(thr, m2 + gmax + 1e-6f * m2) : kInf;
                 // keep base <= thr, compacted in increasing a: positions from the pair's kept masks
                 unsigned long long mk = 0;
                 if (live) {
