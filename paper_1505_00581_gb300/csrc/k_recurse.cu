@@ -285,10 +285,10 @@ recurse_kernel(const Unit *__restrict__ units, int64_t n_units, const ModelRec *
                     const int tw = LA.t[s1], iw = LA.idx[s1];
                     const int t2 = s2 < KM ? LA.t[s2] : 0, i2 = s2 < KM ? LA.idx[s2] : -2;
 #pragma unroll 4
-                    for (int k = 0; k < AH; ++k) {
+                    for (int k = 0; NP * k + h < ccount; ++k) {
                         const int c = NP * k + h;
                         const int tc = LC.t[c], ic = LC.idx[c];
-                        if (c < ccount && ic != ib && ((T > 0 && tw - tc >= T) || iw == ic)) {
+                        if (ic != ib && ((T > 0 && tw - tc >= T) || iw == ic)) {
                             anybad = true;
                             if (!(m2 < kInf) || (T > 0 && t2 - tc >= T) || i2 == ic) loose = true;
                         }
