@@ -415,7 +415,11 @@ recurse_kernel(const Unit *__restrict__ units, int64_t n_units, const ModelRec *
             // ---- phase 3: tiles (b, CT consecutive c)
             const int ntile = sm.ntile;
             uint8_t *bstep = ubeta + (int64_t)(i - 2) * K * K;
-            for (int tile = tid; tile < ntile; tile += NT) {
+            // tiles in decreasing kept count, dealt to the threads back and forth (round r: thread t takes
+            // tile r NT + t for even r, r NT + NT - 1 - t for odd r) so that per-thread sums even out
+            for (int r0 = 0; r0 < ntile; r0 += NT) {
+                const int tile = r0 + (((r0 / NT) & 1) ? NT - 1 - tid : tid);
+                if (tile >= ntile) continue;
                 const int b = sm.tile_b[tile];
                 const int c0 = (tile - sm.tbase[b]) * CT;
                 const float2 pb = LB.xy[b];
