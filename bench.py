@@ -34,8 +34,8 @@ FP32_LANES_PER_SM = 128
 # the batched_small case, with the sources of the kernel it captured and the capture's argmin-table bytes
 # sum n_offsets (M - 2) K^2. Both the tables written and the lists read grow in proportion to that sum,
 # so a full launch's traffic is scaled by it; a changed kernel source voids the figure.
-RECURSE_NCU = {"sources_sha256": "f208118343544f45ad81ffe11a963a39f00a72f0661ebacf4b36b004694ce5f5",
-               "bytes": 52_860_160 + 334_314_240, "beta_bytes": 393_031_680, "case": "batched_small",
+RECURSE_NCU = {"sources_sha256": "142bae4331dc3a7b18edefa543aed14bbd5a624949445c5da4791af45f3afeb0",
+               "bytes": 52_798_720 + 333_985_024, "beta_bytes": 393_031_680, "case": "batched_small",
                "summary": "profiles/recurse_kernel_batched_exact.md"}
 RECURSE_SOURCES = ("k_recurse.cu", "recurse_common.cuh", "f32x2.cuh")
 
