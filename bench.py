@@ -5,7 +5,8 @@ selection, recursion, backtrack) with models and scenes resident in HBM and
 device outputs. Default workload: 10 models (M 16..64) x 8 scenes of
 300..1500 frames, Poisson(30) points/frame, K = 64, w = 3 (seeded synthetic).
 
-Prints ONE JSON line (rank 0). See the design doc for the roofline definitions.
+Prints ONE JSON line (rank 0); the roofline object names the dominant kernel, its
+algorithmic work per launch, the measured peak it is divided by and its DRAM traffic.
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 Under torchrun each rank matches its own copy of the workload (seed + rank,
 weak scaling, no collective on the data path).
@@ -27,7 +28,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "scene frames/sec matched (all models × offsets), plain exact vs pruned+BF16"
-OPS_PER_TRIPLE = 12          # FP32 lane ops per evaluated triple after hoisting
+OPS_PER_TRIPLE = 12          # FP32 lane ops per evaluated triple after hoisting the per-(a, b) and per-(b, c) terms
 SM_COUNT_FALLBACK = 152
 FP32_LANES_PER_SM = 128
 # DRAM bytes of one recursion launch, from an ncu capture (dram__bytes_read.sum + dram__bytes_write.sum) of

@@ -72,7 +72,7 @@ typedef enum {
     HGM_ENOMEM = 2,         /* device or host allocation failed */
     HGM_ECUDA = 3,          /* a CUDA runtime call failed (message has the CUDA error) */
     HGM_ETIMEOUT = 4,       /* a bounded device-side wait gave up */
-    HGM_EUNSUPPORTED = 5    /* valid request outside what this build implements (e.g. K > 64) */
+    HGM_EUNSUPPORTED = 5    /* valid request outside what this library implements (e.g. K > 64) */
 } hgm_status;
 
 /* Matching parameters. Defaults (hgm_default_params) are the paper's weights

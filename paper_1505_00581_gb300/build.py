@@ -2,7 +2,7 @@
 
 Output: paper_1505_00581_gb300/_build/libhgm.so (git-ignored). The CUDA runtime is
 linked statically so that the library loads on a machine without a GPU (the
-exported-symbol test) and finds no stray libcudart on the GPU machine.
+exported-symbol test) and finds no stray libcudart on the machine that runs it.
 """
 from __future__ import annotations
 

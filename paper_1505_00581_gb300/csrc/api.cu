@@ -373,7 +373,7 @@ hgm_status check_params(const hgm_params *p)
         return fail(HGM_EINVAL, "lambdas must be finite and >= 0");
     if (p->window < 0) return fail(HGM_EINVAL, "window must be >= 0");
     if (p->K < 1 || p->K > 255) return fail(HGM_EINVAL, "K must be in 1..255 (got %d)", p->K);
-    if (p->K > kMaxK) return fail(HGM_EUNSUPPORTED, "K > %d is not supported by this build", kMaxK);
+    if (p->K > kMaxK) return fail(HGM_EUNSUPPORTED, "K > %d is not supported by this library", kMaxK);
     if (p->precision != 0 && p->precision != 1)
         return fail(HGM_EUNSUPPORTED, "precision %d not available (0 = FP32 exact, 1 = BF16 + FP32 re-score)",
                     p->precision);

@@ -2,7 +2,7 @@
 //
 // Not part of the paper: a small MLP layered on the exact method that scores each
 // window candidate so that only the best `keep` enter the recursion (the pruned
-// form; the exact recursion stays its fallback and judge). Architecture:
+// form; the exact recursion stays its fallback and the yardstick of its recall and energy gap). Architecture:
 //   x = [f_i, f'_j, dx/100, dy/100, dt/w]  (d_in = 2F + 3)
 //   h1 = relu(W1 x + b1), h2 = relu(W2 h1 + b2)  (128 each),  z3 = w3.h2 + b3,  score = sigmoid(z3)
 // trained with binary cross-entropy on labels produced by the exact recursion.

@@ -106,7 +106,7 @@ extern "C" hgm_status hgm_match_noalloc(const hgm_model *model, const hgm_scene 
     if (model->F_user != scene->F_user)
         return set_error(HGM_EINVAL, "descriptor width differs between model and scene");
     if (params->K < 1 || params->K > 255) return set_error(HGM_EINVAL, "K must be in 1..255");
-    if (params->K > kMaxK) return set_error(HGM_EUNSUPPORTED, "K > 64 is not supported by this build");
+    if (params->K > kMaxK) return set_error(HGM_EUNSUPPORTED, "K > 64 is not supported by this library");
     if (params->window < 0 || params->precision != 0 || params->offset_lo > params->offset_hi ||
         params->dummy_cost >= 0 ||
         !(params->lambda1 >= 0 && params->lambda2 >= 0 && params->lambda3 >= 0))
