@@ -356,7 +356,7 @@ def run_dummy(args, torch, hgm, wl, models, scenes, dev, stream, world, flush, d
             "dummy_cost": wd, "eps_fraction": float((a == -2).float().mean().item()),
             "finite_offsets": int(torch.isfinite(e).sum().item()),
             "kernel_ms_per_step": {k: v[0] / steps for k, v in prof.items()},
-            "form": "exact FP32 with an eps slot per list (own recursion kernel, sorted-base branch and bound)"}
+            "form": "exact FP32 with an eps slot per list (own recursion kernel, kept-list branch and bound)"}
 
 
 def run_pruned(args, torch, hgm, wl, models, scenes, energy, assign, es, as_, dev, stream, world, dist=None):

@@ -9,9 +9,13 @@
 // One persistent CTA per unit, all tables in shared memory (L x L floats each): alpha_{i+1} and alpha_i
 // (ping-pong), base(b, a) = U(a) + lambda2 Delta(a, b) + alpha_{i+1}(a, b) (eps rules applied), and the
 // per-step directions P1(b, a) = A1 + theta(b->a), P2(b, a) = A2 + theta(a->b), R(a, c) = theta(a->c).
-// Threads take groups of four consecutive c of one b (c fastest, so a warp shares b: broadcast reads of
-// base, P1, P2) and walk b's row of base in increasing order until no open cell of the group can improve. The argmin slots go to a per-CTA global scratch, (M-2) x L x L bytes,
-// and the CTA backtracks its own unit (Eq. 12); eps is reported as -2 in the assignment.
+// Every open cell (b, c) has a best of at most thr(b): base(b, eps), since the triple (eps, b, c) is
+// feasible and costs that alone, and base(b, a1) + max D^g when the row's smallest base a1 is feasible with
+// every open c. A warp per row keeps the a with base <= thr(b) that may follow b and ranks them by
+// (base, slot). Threads take groups of four consecutive c of one b (c fastest, so a warp shares b:
+// broadcast reads of base, P1, P2) and walk b's kept a in that order until no open cell of the group can
+// improve. The argmin slots go to a per-CTA global scratch, (M-2) x L x L bytes, and the CTA backtracks
+// its own unit (Eq. 12); eps is reported as -2 in the assignment.
 #include "hgm_internal.cuh"
 #include "recurse_common.cuh"
 
@@ -21,6 +25,7 @@ namespace {
 constexpr int kDummyThreads = 256;
 constexpr int kL = kMaxK + 1;          // table side: up to 64 real slots + eps
 constexpr int kTab = kL * kL;
+constexpr float kGeoMax = 4.45f;       // > pi*sqrt(2) = 4.4429, bound of the FP32 D^g
 
 struct DummySmem {
     float alpha[2][kTab];
@@ -30,7 +35,8 @@ struct DummySmem {
     float2 xy[3][kL];                  // lists i (a), i-1 (b), i-2 (c)
     int t[3][kL], id[3][kL];
     float u[3][kL];
-    uint8_t srt[kL][kMaxK];            // per row b: the real a by increasing base(b, a) (ties: lower slot)
+    uint8_t srt[kL][kMaxK];            // per row b: the kept real a by increasing base(b, a) (ties: lower slot)
+    uint8_t kept[kL];                  // per row b: how many a srt[b] holds
     int cnt[3];
 };
 static_assert(2 * (sizeof(DummySmem) + 1024 + 128) <= 228 * 1024, "two CTAs per SM");
@@ -39,35 +45,6 @@ static_assert(2 * (sizeof(DummySmem) + 1024 + 128) <= 228 * 1024, "two CTAs per 
 __device__ __forceinline__ bool key_less(float ka, int sa, float kb, int sb)
 {
     return ka < kb || (ka == kb && sa < sb);
-}
-
-// Bitonic sort of 64 (key, slot) pairs held by a warp, two per lane (positions lane and lane + 32).
-__device__ __forceinline__ void warp_sort64(float &k0, int &s0, float &k1, int &s1, int lane)
-{
-#pragma unroll
-    for (int k = 2; k <= 64; k <<= 1) {
-#pragma unroll
-        for (int j = k >> 1; j > 0; j >>= 1) {
-            if (j == 32) {   // positions lane and lane + 32 pair up inside the lane (k = 64: ascending)
-                if (key_less(k1, s1, k0, s0)) {
-                    const float tk = k0; const int ts = s0;
-                    k0 = k1; s0 = s1; k1 = tk; s1 = ts;
-                }
-            } else {
-#pragma unroll
-                for (int e = 0; e < 2; ++e) {
-                    float &kk = e ? k1 : k0;
-                    int &ss = e ? s1 : s0;
-                    const int i = lane + 32 * e;
-                    const float ok = __shfl_xor_sync(0xffffffffu, kk, j);
-                    const int os = __shfl_xor_sync(0xffffffffu, ss, j);
-                    const bool want_min = ((i & j) == 0) == ((i & k) == 0);
-                    const bool take = want_min ? key_less(ok, os, kk, ss) : key_less(kk, ss, ok, os);
-                    if (take) { kk = ok; ss = os; }
-                }
-            }
-        }
-    }
 }
 
 struct DummyBest {
@@ -94,6 +71,7 @@ __global__ void __launch_bounds__(kDummyThreads, 2) dummy_recurse_kernel(
     const int K = p.K, L = K + 1, E = K;   // eps is slot K
     const float lam2 = p.lambda2, lam23 = __fmul_rn(p.lambda2, p.lambda3);
     const float ueps = __fmul_rn(p.lambda1, wd);
+    const float gmax = lam23 * kGeoMax;
     const float inf = __int_as_float(0x7f800000);
     uint8_t *beta = scratch + (int64_t)blockIdx.x * scratch_per_cta;
     for (int64_t u = blockIdx.x; u < n_units; u += gridDim.x) {
@@ -154,18 +132,64 @@ __global__ void __launch_bounds__(kDummyThreads, 2) dummy_recurse_kernel(
                     sm.r[a2 * L + c] = direction(sm.xy[0][a2], sm.xy[2][c]);
             }
             __syncthreads();
-            // branch and bound (exact): v(a, b, c) >= base(b, a). Each row's real a are sorted by base (a
-            // warp per row), so a cell walks them in that order and stops at the first base above its best.
+            // branch and bound (exact): v(a, b, c) >= base(b, a), and no open cell of row b has a best above
+            // thr(b). A warp per row keeps the a with base <= thr(b) that may follow b (any real a after eps)
+            // and ranks them by (base, slot) by counting.
             {
+                const unsigned full = 0xffffffffu;
                 const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
                 for (int b = warp; b < L; b += kDummyThreads / 32) {
                     if (!(b < nb || b == E)) continue;
-                    float k0 = lane < na ? sm.base[b * L + lane] : inf;
-                    float k1 = lane + 32 < na ? sm.base[b * L + lane + 32] : inf;
-                    int s0 = lane, s1 = lane + 32;
-                    warp_sort64(k0, s0, k1, s1, lane);
-                    sm.srt[b][lane] = (uint8_t)s0;
-                    sm.srt[b][lane + 32] = (uint8_t)s1;
+                    const bool rb = b < nb;
+                    const float *brow = sm.base + b * L;
+                    const int tb = rb ? sm.t[1][b] : 0, ib = rb ? sm.id[1][b] : -3;
+                    float key[2];
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        const int a = lane + 32 * h;
+                        key[h] = a < na && (!rb || (sm.id[0][a] != ib && sm.t[0][a] >= tb)) ? brow[a] : inf;
+                    }
+                    float thr = brow[E];
+                    if (rb) {
+                        float m = key[0];
+                        int s = lane;
+                        if (key_less(key[1], lane + 32, m, s)) { m = key[1]; s = lane + 32; }
+#pragma unroll
+                        for (int off = 16; off > 0; off >>= 1) {
+                            const float om = __shfl_xor_sync(full, m, off);
+                            const int os = __shfl_xor_sync(full, s, off);
+                            if (key_less(om, os, m, s)) { m = om; s = os; }
+                        }
+                        if (m < inf) {
+                            // a1 = s must be feasible with every open c and with (b, eps)
+                            const int t1 = sm.t[0][s], i1 = sm.id[0][s];
+                            bool bad = lane == 0 && p.T > 0 && t1 - tb >= p.T;
+                            for (int c = lane; c < nc; c += 32) {
+                                const int tc = sm.t[2][c], ic = sm.id[2][c];
+                                const bool open = ic != ib && tc <= tb && (p.T <= 0 || tb - tc < p.T);
+                                if (open && (i1 == ic || (p.T > 0 && t1 - tc >= p.T))) bad = true;
+                            }
+                            if (!__any_sync(full, bad)) thr = fminf(thr, m + gmax + 1e-6f * fabsf(m));
+                        }
+                    }
+                    const bool k0 = key[0] < inf && key[0] <= thr, k1 = key[1] < inf && key[1] <= thr;
+                    const unsigned m0 = __ballot_sync(full, k0), m1 = __ballot_sync(full, k1);
+                    int r0 = 0, r1 = 0;
+                    for (unsigned mm = m0; mm; mm &= mm - 1) {
+                        const int l = __ffs(mm) - 1;
+                        const float kk = __shfl_sync(full, key[0], l);
+                        r0 += key_less(kk, l, key[0], lane);
+                        r1 += key_less(kk, l, key[1], lane + 32);
+                    }
+                    for (unsigned mm = m1; mm; mm &= mm - 1) {
+                        const int l = __ffs(mm) - 1;
+                        const float kk = __shfl_sync(full, key[1], l);
+                        r0 += key_less(kk, l + 32, key[0], lane);
+                        r1 += key_less(kk, l + 32, key[1], lane + 32);
+                    }
+                    if (k0) sm.srt[b][r0] = (uint8_t)lane;
+                    if (k1) sm.srt[b][r1] = (uint8_t)(lane + 32);
+                    if (lane == 0) sm.kept[b] = (uint8_t)(__popc(m0) + __popc(m1));
                 }
             }
             __syncthreads();
@@ -193,15 +217,15 @@ __global__ void __launch_bounds__(kDummyThreads, 2) dummy_recurse_kernel(
                     arg[q] = open[q] ? E : 255;
                 }
                 const uint8_t *order = sm.srt[b];
-                for (int k = 0; k < na; ++k) {
+                const int nk = sm.kept[b];
+                for (int k = 0; k < nk; ++k) {
                     const int a = order[k];
                     const float ba = brow[a];
                     float bmax = -inf;
 #pragma unroll
                     for (int q = 0; q < 4; ++q) bmax = fmaxf(bmax, open[q] ? best[q] : -inf);
                     if (ba > bmax) break;
-                    const int ta = sm.t[0][a], ia = sm.id[0][a];
-                    if (ia == ib || ta < tb) continue;
+                    const int ta = sm.t[0][a], ia = sm.id[0][a];   // kept: ia != ib, ta >= tb
                     const float p1 = sm.p1[b * L + a], p2 = sm.p2[b * L + a];
 #pragma unroll
                     for (int q = 0; q < 4; ++q) {
@@ -220,8 +244,10 @@ __global__ void __launch_bounds__(kDummyThreads, 2) dummy_recurse_kernel(
                 }
             }
             // cells holding eps (row b = eps over every c, column c = eps over the real b): a triple holding
-            // eps costs base(b, a) alone, so in sorted order the first feasible real a is the smallest
-            // (lowest slot among equals); eps (the last slot) only if below it
+            // eps costs base(b, a) alone, so in ranked order the first feasible kept a is the smallest (lowest
+            // slot among equals); eps (the last slot) only if below it. An a left out of row eps costs more
+            // than base(eps, eps); for a real b either the same holds or a1, the first kept, is feasible with
+            // (b, eps)
             for (int e = threadIdx.x; e < nc + 1 + nb; e += blockDim.x) {
                 const int b = e <= nc ? E : e - (nc + 1);
                 const int c = e < nc ? e : E;
@@ -233,7 +259,8 @@ __global__ void __launch_bounds__(kDummyThreads, 2) dummy_recurse_kernel(
                 const bool any = !rb && !rc;
                 float best = inf;
                 int arg = 255;
-                for (int k = 0; k < na; ++k) {
+                const int nk = sm.kept[b];
+                for (int k = 0; k < nk; ++k) {
                     const int a = order[k];
                     const int ta = sm.t[0][a];
                     if (!any && (sm.id[0][a] == ir || ta < tr || (p.T > 0 && ta - tr >= p.T))) continue;
