@@ -8,7 +8,8 @@
 //
 // One persistent CTA per unit, all tables in shared memory (L x L floats each): alpha_{i+1} and alpha_i
 // (ping-pong), base(b, a) = U(a) + lambda2 Delta(a, b) + alpha_{i+1}(a, b) (eps rules applied), and the
-// per-step directions P1(b, a) = A1 + theta(b->a), P2(b, a) = A2 + theta(a->b), R(a, c) = theta(a->c).
+// per-step directions P1(b, a) = A1 + theta(b->a), P2(b, a) = A2 + theta(a->b) (kept pairs only),
+// R(a, c) = theta(a->c).
 // Every open cell (b, c) has a best of at most thr(b): base(b, eps), since the triple (eps, b, c) is
 // feasible and costs that alone, and base(b, a1) + max D^g when the row's smallest base a1 is feasible with
 // every open c. A warp per row keeps the a with base <= thr(b) that may follow b and ranks them by
@@ -120,12 +121,6 @@ __global__ void __launch_bounds__(kDummyThreads, 2) dummy_recurse_kernel(
                     if (ra && rb) bs = base_cost(sm.u[0][a], lam2, dt1, sm.t[0][a], sm.t[1][b], al);
                     else bs = __fadd_rn(sm.u[0][a], al);
                     sm.base[b * L + a] = bs;
-                    // directions only where a triple can use them: a after b (else every (a, b, c) with real
-                    // points is infeasible and the cell loop skips a before reading them)
-                    if (ra && rb && sm.t[0][a] >= sm.t[1][b]) {
-                        sm.p1[b * L + a] = __fadd_rn(A1, direction(sm.xy[1][b], sm.xy[0][a]));
-                        sm.p2[b * L + a] = __fadd_rn(A2, direction(sm.xy[0][a], sm.xy[1][b]));
-                    }
                 }
                 const int a2 = b, c = a;   // R(a, c) over the same index space, where (a, c) can be feasible
                 if (a2 < na && c < nc && sm.t[2][c] <= sm.t[0][a2] && !(p.T > 0 && sm.t[0][a2] - sm.t[2][c] >= p.T))
@@ -190,6 +185,18 @@ __global__ void __launch_bounds__(kDummyThreads, 2) dummy_recurse_kernel(
                     if (k0) sm.srt[b][r0] = (uint8_t)lane;
                     if (k1) sm.srt[b][r1] = (uint8_t)(lane + 32);
                     if (lane == 0) sm.kept[b] = (uint8_t)(__popc(m0) + __popc(m1));
+                    // directions of the kept pairs of a real b, the only ones the cells read
+                    if (rb) {
+                        const float2 xb = sm.xy[1][b];
+#pragma unroll
+                        for (int h = 0; h < 2; ++h) {
+                            const int a = lane + 32 * h;
+                            if (h ? k1 : k0) {
+                                sm.p1[b * L + a] = __fadd_rn(A1, direction(xb, sm.xy[0][a]));
+                                sm.p2[b * L + a] = __fadd_rn(A2, direction(sm.xy[0][a], xb));
+                            }
+                        }
+                    }
                 }
             }
             __syncthreads();
