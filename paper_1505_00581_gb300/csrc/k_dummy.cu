@@ -26,13 +26,14 @@ namespace {
 constexpr int kDummyThreads = 256;
 constexpr int kL = kMaxK + 1;          // table side: up to 64 real slots + eps
 constexpr int kTab = kL * kL;
+constexpr int kRL = 68;                // row stride of R: four consecutive c of a row are one 16-byte load
 constexpr float kGeoMax = 4.45f;       // > pi*sqrt(2) = 4.4429, bound of the FP32 D^g
 
 struct DummySmem {
     float alpha[2][kTab];
     float base[kTab];                  // [b][a]
     float p1[kTab], p2[kTab];          // [b][a]
-    float r[kTab];                     // [a][c]
+    alignas(16) float r[kL * kRL];     // [a][c], row stride kRL
     float2 xy[3][kL];                  // lists i (a), i-1 (b), i-2 (c)
     int t[3][kL], id[3][kL];
     float u[3][kL];
@@ -124,7 +125,7 @@ __global__ void __launch_bounds__(kDummyThreads, 2) dummy_recurse_kernel(
                 }
                 const int a2 = b, c = a;   // R(a, c) over the same index space, where (a, c) can be feasible
                 if (a2 < na && c < nc && sm.t[2][c] <= sm.t[0][a2] && !(p.T > 0 && sm.t[0][a2] - sm.t[2][c] >= p.T))
-                    sm.r[a2 * L + c] = direction(sm.xy[0][a2], sm.xy[2][c]);
+                    sm.r[a2 * kRL + c] = direction(sm.xy[0][a2], sm.xy[2][c]);
             }
             __syncthreads();
             // branch and bound (exact): v(a, b, c) >= base(b, a), and no open cell of row b has a best above
@@ -223,6 +224,8 @@ __global__ void __launch_bounds__(kDummyThreads, 2) dummy_recurse_kernel(
                     best[q] = open[q] ? brow[E] : inf;   // (eps, b, c) is feasible with every open cell
                     arg[q] = open[q] ? E : 255;
                 }
+                const unsigned long long q1a = pk2(q1[0], q1[1]), q1b = pk2(q1[2], q1[3]);
+                const unsigned long long lamp = pk2(lam23, lam23);
                 const uint8_t *order = sm.srt[b];
                 const int nk = sm.kept[b];
                 for (int k = 0; k < nk; ++k) {
@@ -234,11 +237,16 @@ __global__ void __launch_bounds__(kDummyThreads, 2) dummy_recurse_kernel(
                     if (ba > bmax) break;
                     const int ta = sm.t[0][a], ia = sm.id[0][a];   // kept: ia != ib, ta >= tb
                     const float p1 = sm.p1[b * L + a], p2 = sm.p2[b * L + a];
+                    // R past the last c is never initialised: those lanes of v are discarded (open is false)
+                    const float4 r4 = *reinterpret_cast<const float4 *>(sm.r + a * kRL + c0);
+                    const unsigned long long bp = pk2(ba, ba), p1p = pk2(p1, p1), p2p = pk2(p2, p2);
+                    float v[4];
+                    triple_cost2(bp, p1p, p2p, q1a, pk2(r4.x, r4.y), lamp, v[0], v[1]);
+                    triple_cost2(bp, p1p, p2p, q1b, pk2(r4.z, r4.w), lamp, v[2], v[3]);
 #pragma unroll
                     for (int q = 0; q < 4; ++q) {
-                        if (!open[q] || ia == icq[q] || (p.T > 0 && ta - tcq[q] >= p.T)) continue;
-                        const float v = triple_cost(ba, p1, p2, q1[q], sm.r[a * L + c0 + q], lam23);
-                        if (v < best[q] || (v == best[q] && a < arg[q])) { best[q] = v; arg[q] = a; }
+                        const bool ok = open[q] && ia != icq[q] && !(p.T > 0 && ta - tcq[q] >= p.T);
+                        if (ok && (v[q] < best[q] || (v[q] == best[q] && a < arg[q]))) { best[q] = v[q]; arg[q] = a; }
                     }
                 }
 #pragma unroll

@@ -1,10 +1,12 @@
 """The dummy assignment (Eq. 2, reading R5) on the GPU against the FP64 oracle with the same W^d: every
 offset's energy within 1e-5 relative, assignments (eps = -2) equal or of the same FP64 energy; offsets
 whose lists are empty become feasible; an expensive dummy reproduces the plain path."""
+from concurrent.futures import ThreadPoolExecutor
+
 import numpy as np
 import pytest
 
-from gpu_util import handles
+from gpu_util import check_offset, handles
 from paper_1505_00581_gb300 import synth
 
 pytestmark = pytest.mark.gpu
@@ -107,3 +109,53 @@ def test_dummy_rejected_with_pruning_and_blocks(env):
     with pytest.raises(hgm.HgmError) as err:
         hgm.match_block([m], [s], hgm.default_params(dummy_cost=1.0))
     assert err.value.status == hgm.HGM_EUNSUPPORTED
+
+
+def test_full_batched_workload_sampled(env):
+    """The 10-model x 8-scene workload at full size with W^d = 8, in the benchmark's launch configuration
+    (one batch call, device outputs): every offset finite, and a seeded sample of units plus the implants'
+    own offsets against the oracle with the same W^d."""
+    torch, hgm, oracle = env
+    wl = synth.batched_exact()
+    wd = 8.0
+    ms = [hgm.Model(*(torch.from_numpy(a).cuda() for a in (mod.xy, mod.t, mod.f))) for mod in wl.models]
+    ss = [hgm.Scene(*(torch.from_numpy(a).cuda() for a in (sc.xy, sc.t, sc.f)), sc.n_frames) for sc in wl.scenes]
+    p = hgm.default_params(K=wl.K, window=wl.window, T=wl.T, dummy_cost=wd)
+    first, es, as_ = hgm.batch_layout(ms, ss, p)
+    e = torch.empty(int(es[-1]), dtype=torch.float32, device="cuda")
+    a = torch.empty(int(as_[-1]), dtype=torch.int32, device="cuda")
+    hgm.match_batch(ms, ss, p, e, a)
+    torch.cuda.synchronize()
+    e, a = e.cpu().numpy(), a.cpu().numpy()
+    assert np.all(np.isfinite(e))
+    assert np.all((a >= 0) | (a == -2))
+    rng = np.random.default_rng(2025)
+    samples = []
+    for _ in range(32):
+        mi = int(rng.integers(len(wl.models)))
+        si = int(rng.integers(len(wl.scenes)))
+        q = mi * len(wl.scenes) + si
+        samples.append((mi, si, q, int(rng.integers(int(es[q + 1] - es[q])))))
+    for si, sc in enumerate(wl.scenes):
+        for imp in sc.implants:
+            q = imp.model * len(wl.scenes) + si
+            k = imp.offset - int(first[q])
+            if 0 <= k < es[q + 1] - es[q]:
+                samples.append((imp.model, si, q, k))
+    oracles = {}
+    for mi, si, q, k in samples:
+        if (mi, si) not in oracles:
+            oracles[(mi, si)] = oracle.Oracle.from_workload(wl, mi, si, dummy_cost=wd)
+
+    def run(sample):
+        mi, si, q, k = sample
+        M = wl.models[mi].n
+        orc = oracles[(mi, si)]
+        e_or, z_or, _ = orc.match(int(first[q]) + k)
+        row = a[as_[q] + k * M: as_[q] + (k + 1) * M]
+        return check_offset(orc, int(first[q]) + k, e[es[q] + k], row, e_or=e_or, z_or=z_or)
+
+    with ThreadPoolExecutor(max_workers=16) as ex:
+        results = list(ex.map(run, samples))
+    for (ok, tie, why), smp in zip(results, samples):
+        assert ok, (smp, why)
