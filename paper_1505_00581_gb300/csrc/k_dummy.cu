@@ -186,16 +186,16 @@ __global__ void __launch_bounds__(kDummyThreads, 2) dummy_recurse_kernel(
                     if (k0) sm.srt[b][r0] = (uint8_t)lane;
                     if (k1) sm.srt[b][r1] = (uint8_t)(lane + 32);
                     if (lane == 0) sm.kept[b] = (uint8_t)(__popc(m0) + __popc(m1));
-                    // directions of the kept pairs of a real b, the only ones the cells read
+                    // directions of the kept pairs of a real b, the only ones the cells read: lane r takes the
+                    // kept a of rank r
                     if (rb) {
+                        __syncwarp();
+                        const int nk = __popc(m0) + __popc(m1);
                         const float2 xb = sm.xy[1][b];
-#pragma unroll
-                        for (int h = 0; h < 2; ++h) {
-                            const int a = lane + 32 * h;
-                            if (h ? k1 : k0) {
-                                sm.p1[b * L + a] = __fadd_rn(A1, direction(xb, sm.xy[0][a]));
-                                sm.p2[b * L + a] = __fadd_rn(A2, direction(sm.xy[0][a], xb));
-                            }
+                        for (int r = lane; r < nk; r += 32) {
+                            const int a = sm.srt[b][r];
+                            sm.p1[b * L + a] = __fadd_rn(A1, direction(xb, sm.xy[0][a]));
+                            sm.p2[b * L + a] = __fadd_rn(A2, direction(sm.xy[0][a], xb));
                         }
                     }
                 }
