@@ -71,6 +71,9 @@ __global__ void __launch_bounds__(kDummyThreads, 2) dummy_recurse_kernel(
     DummySmem &sm = *reinterpret_cast<DummySmem *>(smem_raw);
     __shared__ DummyBest red[kDummyThreads / 32];
     const int K = p.K, L = K + 1, E = K;   // eps is slot K
+    // e / L as one multiply-high: with m = ceil(2^32 / L), floor(e m / 2^32) = floor(e / L) for every
+    // e < 2^32 / L (the error e (m - 2^32 / L) / 2^32 stays below 1 / L); the flat loops index e < 3 L^2
+    const unsigned divL = 0xffffffffu / (unsigned)L + 1u;
     const float lam2 = p.lambda2, lam23 = __fmul_rn(p.lambda2, p.lambda3);
     const float ueps = __fmul_rn(p.lambda1, wd);
     const float gmax = lam23 * kGeoMax;
@@ -88,7 +91,7 @@ __global__ void __launch_bounds__(kDummyThreads, 2) dummy_recurse_kernel(
         for (int i = M - 1; i >= 2; --i) {
             // lists of this step: slot s < cnt real, slot K eps
             for (int e = threadIdx.x; e < 3 * L; e += blockDim.x) {
-                const int w = e / L, s = e - w * L, li = i - w;
+                const int w = (int)__umulhi((unsigned)e, divL), s = e - w * L, li = i - w;
                 const int n = ccnt[li];
                 if (s < n) {
                     const int j = cidx[(int64_t)li * K + s];
@@ -114,7 +117,7 @@ __global__ void __launch_bounds__(kDummyThreads, 2) dummy_recurse_kernel(
             const bool last = i == M - 1;
             // base(b, a) and directions; rows/columns of empty slots are never read
             for (int e = threadIdx.x; e < L * L; e += blockDim.x) {
-                const int b = e / L, a = e - b * L;
+                const int b = (int)__umulhi((unsigned)e, divL), a = e - b * L;
                 const bool ra = a < na, rb = b < nb;
                 if ((ra || a == E) && (rb || b == E)) {
                     const float al = last ? 0.0f : an[a * L + b];   // alpha_{i+1}(z_i = a, z_{i-1} = b)
@@ -295,7 +298,7 @@ __global__ void __launch_bounds__(kDummyThreads, 2) dummy_recurse_kernel(
         const int n0 = ccnt[0], n1 = ccnt[1];
         DummyBest mine{inf, 0x7fffffff, 0x7fffffff};
         for (int e = threadIdx.x; e < L * L; e += blockDim.x) {
-            const int j1 = e / L, j2 = e - j1 * L;
+            const int j1 = (int)__umulhi((unsigned)e, divL), j2 = e - j1 * L;
             if (!((j1 < n0 || j1 == E) && (j2 < n1 || j2 == E))) continue;
             const float u1 = j1 == E ? ueps : cu[j1], u2 = j2 == E ? ueps : cu[(int64_t)K + j2];
             const float al = M == 2 ? 0.0f : a3[j2 * L + j1];
