@@ -209,8 +209,9 @@ __global__ void __launch_bounds__(kDummyThreads, 2) dummy_recurse_kernel(
             // real cells (b, c) in groups of four consecutive c: one walk of b's base-sorted row serves the
             // group, and stops at the first base above every open cell's best (exact: v >= base)
             const int G = (nc + 3) >> 2;
+            const unsigned divG = 0xffffffffu / (unsigned)max(G, 2) + 1u;   // e / G as for e / L
             for (int e = threadIdx.x; e < nb * G; e += blockDim.x) {
-                const int b = e / G, c0 = 4 * (e - b * G);
+                const int b = G == 1 ? e : (int)__umulhi((unsigned)e, divG), c0 = 4 * (e - b * G);
                 const int tb = sm.t[1][b], ib = sm.id[1][b];
                 const float *brow = sm.base + b * L;
                 float best[4], q1[4];
