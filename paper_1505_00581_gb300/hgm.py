@@ -8,9 +8,8 @@ CUDA stream, and raises on a non-zero status. There is no CPU fallback: if
 from __future__ import annotations
 
 import ctypes
-import dataclasses
 import os
-from typing import Optional, Sequence
+from typing import Sequence
 
 import numpy as np
 

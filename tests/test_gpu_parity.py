@@ -4,14 +4,13 @@ Integer work (unary ranking key, candidate lists, triple counts) is compared
 bit for bit; energies within 1e-5 relative; assignments equal or a near-tie
 (see gpu_util). Inputs are the seeded synthetic workloads of synth.py.
 """
-import math
 from concurrent.futures import ThreadPoolExecutor
 
 import numpy as np
 import pytest
 
 from golden_io import read_examples
-from gpu_util import check_offset, energy_ok, handles
+from gpu_util import check_offset, handles
 from paper_1505_00581_gb300 import synth
 
 pytestmark = pytest.mark.gpu
