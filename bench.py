@@ -247,6 +247,31 @@ def _time_form(torch, hgm, models, scenes, p, energy, assign, steps, warmup, str
     return sum(a.elapsed_time(b) for a, b in zip(starts, ends)) / steps, hgm.profile_read()
 
 
+def alu_roofline(torch, hgm, run_once, prof, steps, kernel, note):
+    """Roofline of a form's recursion kernel, defined as for the main line: the triples its loops evaluate
+    (one untimed pass of the kernel's accounting variant) x OPS_PER_TRIPLE, over the kernel's average
+    launch time in the timed steps, against the FP32 lane peak."""
+    hgm.profile_evaluated(reset=True)
+    hgm.profile_enable(2)
+    run_once()
+    hgm.profile_enable(False)
+    evaluated = hgm.profile_evaluated(reset=True)
+    rec_ms, rec_n = prof["recurse"]
+    per_step = max(1, rec_n // steps)
+    avg_ms = rec_ms / max(rec_n, 1)
+    eval_launch = evaluated / per_step
+    pk, pk_kind = peaks()
+    sm_count = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count \
+        or SM_COUNT_FALLBACK
+    peak_ops = sm_count * FP32_LANES_PER_SM * float(pk.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
+    achieved = eval_launch * OPS_PER_TRIPLE / (avg_ms / 1e3) / 1e12
+    return {"bound": "alu", "kernel": kernel, "achieved": achieved, "peak": peak_ops,
+            "unit": "Tops/s (FP32 lane ops)", "frac": achieved / peak_ops, "traffic": None, "traffic_source": note,
+            "peak_source": f"{sm_count} SMs x {FP32_LANES_PER_SM} FP32 lanes x sm_max_mhz of MEASURED_PEAKS.json "
+                           f"({pk_kind})",
+            "evaluated_triples_per_launch": eval_launch, "ops_per_triple": OPS_PER_TRIPLE, "avg_launch_ms": avg_ms}
+
+
 def run_chains(args, torch, hgm, wl, models, scenes, dev, stream, world, flush, dist=None, n_chains=3):
     """The independent-chains variant (Sec. 4, method 2) on the same workload, whose models hold several
     points per frame: every model split into its within-frame-rank chains, all chains of all models run
@@ -260,13 +285,20 @@ def run_chains(args, torch, hgm, wl, models, scenes, dev, stream, world, flush, 
     torch.cuda.synchronize()
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    hgm.profile_reset()
+    hgm.profile_enable(True)
     for k in range(args.steps):
         flush.zero_()
         starts[k].record(stream)
         hgm.match_chains_batch(models, scenes, p, n_chains, e, a)
         ends[k].record(stream)
     torch.cuda.synchronize()
+    hgm.profile_enable(False)
+    prof = hgm.profile_read()
     ms = max_over_ranks(sum(x.elapsed_time(y) for x, y in zip(starts, ends)) / args.steps, dist, dev)
+    roofline = alu_roofline(torch, hgm, lambda: hgm.match_chains_batch(models, scenes, p, n_chains, e, a), prof,
+                            args.steps, "recurse_kernel",
+                            "the same kernel as the main line; its traffic there is per argmin-table byte")
     covered = total = n_chain_models = 0
     for m in wl.models:
         _, counts = np.unique(m.t, return_counts=True)
@@ -277,7 +309,8 @@ def run_chains(args, torch, hgm, wl, models, scenes, dev, stream, world, flush, 
     fin = torch.isfinite(e).sum().item()
     return {"value": job_rate(wl.total_frames, world, ms / 1e3), "unit": "frames/s", "ms_per_step": ms,
             "n_chains": n_chains, "chain_models": n_chain_models, "model_points_covered": covered / max(total, 1),
-            "finite_offsets": int(fin), "form": "plain exact FP32 per chain, mean over chains"}
+            "finite_offsets": int(fin), "kernel_ms_per_step": {k: v[0] / args.steps for k, v in prof.items()},
+            "roofline": roofline, "form": "plain exact FP32 per chain, mean over chains"}
 
 
 def run_blocks(args, torch, hgm, dev, stream, flush):
@@ -352,10 +385,15 @@ def run_dummy(args, torch, hgm, wl, models, scenes, dev, stream, world, flush, d
     ms, prof = _time_form(torch, hgm, models, scenes, p, e, a, steps, 1, stream, flush)
     torch.cuda.profiler.stop()
     ms = max_over_ranks(ms, dist, dev)
+    eps_fraction = float((a == -2).float().mean().item())
+    finite = int(torch.isfinite(e).sum().item())
+    roofline = alu_roofline(torch, hgm, lambda: hgm.match_batch(models, scenes, p, e, a), prof, steps,
+                            "dummy_recurse_kernel",
+                            "not captured at this size: profiles/dummy_recurse_kernel_batched_small.md has the "
+                            "DRAM bytes of the 1-scene case")
     return {"value": job_rate(wl.total_frames, world, ms / 1e3), "unit": "frames/s", "ms_per_step": ms,
-            "dummy_cost": wd, "eps_fraction": float((a == -2).float().mean().item()),
-            "finite_offsets": int(torch.isfinite(e).sum().item()),
-            "kernel_ms_per_step": {k: v[0] / steps for k, v in prof.items()},
+            "dummy_cost": wd, "eps_fraction": eps_fraction, "finite_offsets": finite,
+            "kernel_ms_per_step": {k: v[0] / steps for k, v in prof.items()}, "roofline": roofline,
             "form": "exact FP32 with an eps slot per list (own recursion kernel, kept-list branch and bound)"}
 
 

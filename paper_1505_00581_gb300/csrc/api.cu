@@ -580,9 +580,14 @@ hgm_status run_units(Exec &ex, const hgm_model *const *models, std::vector<Unit>
             const int grid = dummy_grid();
             if (grid <= 0) return fail(HGM_ECUDA, "device query failed");
             CK(ws.beta_dummy.ensure((size_t)dummy_scratch_bytes(K, max_M, grid)), "workspace (argmin tables)");
+            unsigned long long *ev = nullptr;
+            if (g_count_mode && ex.mode == Exec::kNormal) {
+                CK(ws.evaluated.ensure(sizeof(unsigned long long)), "workspace");
+                ev = ws.evaluated.as<unsigned long long>();
+            }
             CK(launch_recurse_dummy(du, n, dm, ds, p, p.dummy, ws.cand_idx.as<int32_t>(), ws.cand_u.as<float>(),
                                     ws.cand_cnt.as<int32_t>(), ws.beta_dummy.as<uint8_t>(), max_M, grid, d_energy,
-                                    d_assign, st),
+                                    d_assign, ev, st),
                "recursion kernel (dummy)");
             begin = end;
             continue;

@@ -195,12 +195,13 @@ cudaError_t launch_block_recurse(const BlockUnit *units, int n_units, const Mode
                                  int grid_global, float *energy, int32_t *assign, cudaStream_t st);
 
 // k_dummy.cu: the recursion with the dummy assignment eps (fused backtrack; per-CTA argmin scratch).
+// evaluated != NULL runs the accounting variant, which adds its evaluated triples to *evaluated.
 int dummy_grid();
 int64_t dummy_scratch_bytes(int K, int max_M, int grid);
 cudaError_t launch_recurse_dummy(const Unit *units, int64_t n_units, const ModelRec *models, const SceneRec *scenes,
                                  Params p, float wd, const int32_t *cand_idx, const float *cand_u,
                                  const int32_t *cand_cnt, uint8_t *scratch, int max_M, int grid, float *energy,
-                                 int32_t *assign, cudaStream_t st);
+                                 int32_t *assign, unsigned long long *evaluated, cudaStream_t st);
 
 void prof_begin(int kernel, cudaStream_t st);
 void prof_end(int kernel, cudaStream_t st);

@@ -61,11 +61,15 @@ __device__ __forceinline__ bool dummy_better(float v, int j1, int j2, const Dumm
     return j2 < o.j2;
 }
 
+// kCount = true builds the accounting variant: identical work, plus a count of the (a, open cell) triples
+// the walks evaluate, added to *evaluated (work accounting; not used on the timed path).
+template <bool kCount>
 __global__ void __launch_bounds__(kDummyThreads, 2) dummy_recurse_kernel(
     const Unit *__restrict__ units, int64_t n_units, const ModelRec *__restrict__ models,
     const SceneRec *__restrict__ scenes, Params p, float wd, const int32_t *__restrict__ cand_idx,
     const float *__restrict__ cand_u, const int32_t *__restrict__ cand_cnt, uint8_t *__restrict__ scratch,
-    int64_t scratch_per_cta, float *__restrict__ energy, int32_t *__restrict__ assign)
+    int64_t scratch_per_cta, float *__restrict__ energy, int32_t *__restrict__ assign,
+    unsigned long long *__restrict__ evaluated)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     DummySmem &sm = *reinterpret_cast<DummySmem *>(smem_raw);
@@ -79,6 +83,7 @@ __global__ void __launch_bounds__(kDummyThreads, 2) dummy_recurse_kernel(
     const float gmax = lam23 * kGeoMax;
     const float inf = __int_as_float(0x7f800000);
     uint8_t *beta = scratch + (int64_t)blockIdx.x * scratch_per_cta;
+    unsigned long long n_eval = 0;
     for (int64_t u = blockIdx.x; u < n_units; u += gridDim.x) {
         const Unit un = units[u];
         const ModelRec md = models[un.model];
@@ -228,6 +233,7 @@ __global__ void __launch_bounds__(kDummyThreads, 2) dummy_recurse_kernel(
                     best[q] = open[q] ? brow[E] : inf;   // (eps, b, c) is feasible with every open cell
                     arg[q] = open[q] ? E : 255;
                 }
+                const int nopen = (int)open[0] + (int)open[1] + (int)open[2] + (int)open[3];
                 const unsigned long long q1a = pk2(q1[0], q1[1]), q1b = pk2(q1[2], q1[3]);
                 const unsigned long long lamp = pk2(lam23, lam23);
                 const uint8_t *order = sm.srt[b];
@@ -239,6 +245,7 @@ __global__ void __launch_bounds__(kDummyThreads, 2) dummy_recurse_kernel(
 #pragma unroll
                     for (int q = 0; q < 4; ++q) bmax = fmaxf(bmax, open[q] ? best[q] : -inf);
                     if (ba > bmax) break;
+                    if constexpr (kCount) n_eval += nopen;
                     const int ta = sm.t[0][a], ia = sm.id[0][a];   // kept: ia != ib, ta >= tb
                     const float p1 = sm.p1[b * L + a], p2 = sm.p2[b * L + a];
                     // R past the last c is never initialised: those lanes of v are discarded (open is false)
@@ -340,6 +347,9 @@ __global__ void __launch_bounds__(kDummyThreads, 2) dummy_recurse_kernel(
         }
         __syncthreads();   // tables, lists and the reduction slots are reused by the next unit
     }
+    if constexpr (kCount) {
+        if (n_eval) atomicAdd(evaluated, n_eval);
+    }
 }
 
 }  // namespace
@@ -362,18 +372,19 @@ int dummy_grid()
 cudaError_t launch_recurse_dummy(const Unit *units, int64_t n_units, const ModelRec *models, const SceneRec *scenes,
                                  Params p, float wd, const int32_t *cand_idx, const float *cand_u,
                                  const int32_t *cand_cnt, uint8_t *scratch, int max_M, int grid, float *energy,
-                                 int32_t *assign, cudaStream_t st)
+                                 int32_t *assign, unsigned long long *evaluated, cudaStream_t st)
 {
     if (n_units <= 0) return cudaSuccess;
     if (p.K > kMaxK) return cudaErrorInvalidValue;
     const size_t smem = sizeof(DummySmem);
-    cudaError_t e = cudaFuncSetAttribute(dummy_recurse_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    auto kern = evaluated ? dummy_recurse_kernel<true> : dummy_recurse_kernel<false>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const int64_t per_cta = (int64_t)std::max(max_M - 2, 1) * (p.K + 1) * (p.K + 1);
     const int g = (int)std::min<int64_t>(n_units, grid);
     prof_begin(kProfRecurse, st);
-    dummy_recurse_kernel<<<g, kDummyThreads, smem, st>>>(units, n_units, models, scenes, p, wd, cand_idx, cand_u,
-                                                         cand_cnt, scratch, per_cta, energy, assign);
+    kern<<<g, kDummyThreads, smem, st>>>(units, n_units, models, scenes, p, wd, cand_idx, cand_u, cand_cnt, scratch,
+                                         per_cta, energy, assign, evaluated);
     e = cudaGetLastError();
     prof_end(kProfRecurse, st);
     return e;

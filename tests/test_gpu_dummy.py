@@ -159,3 +159,38 @@ def test_full_batched_workload_sampled(env):
         results = list(ex.map(run, samples))
     for (ok, tie, why), smp in zip(results, samples):
         assert ok, (smp, why)
+
+
+def test_accounting_variant_gives_identical_results(env):
+    """hgm_profile_enable(2) runs the dummy kernel's accounting variant: same energies and assignments bit
+    for bit, and a positive evaluation count no larger than the dense count of (a, b, c) over the real
+    candidates of every step (the walks evaluate real a against open real cells only)."""
+    torch, hgm, _ = env
+    wl = synth.batched_exact(seed=7, n_models=2, n_scenes=1, frames_range=(80, 80))
+    ms = [handles(hgm, mod, wl.scenes[0], torch)[0] for mod in wl.models]
+    ss = [handles(hgm, wl.models[0], sc, torch)[1] for sc in wl.scenes]
+    p = hgm.default_params(K=wl.K, window=wl.window, T=wl.T, dummy_cost=8.0)
+    first, es, as_ = hgm.batch_layout(ms, ss, p)
+    outs = []
+    for mode in (0, 2):
+        e = torch.empty(int(es[-1]), dtype=torch.float32, device="cuda")
+        a = torch.empty(int(as_[-1]), dtype=torch.int32, device="cuda")
+        hgm.profile_evaluated(reset=True)
+        hgm.profile_enable(mode)
+        try:
+            hgm.match_batch(ms, ss, p, e, a)
+        finally:
+            hgm.profile_enable(0)
+        torch.cuda.synchronize()
+        outs.append((e.cpu().numpy(), a.cpu().numpy(), hgm.profile_evaluated(reset=True)))
+    assert np.array_equal(outs[0][0], outs[1][0]) and np.array_equal(outs[0][1], outs[1][1])
+    assert outs[0][2] == 0
+    ev = outs[1][2]
+    dense = 0
+    for mi, mod in enumerate(wl.models):
+        idx = torch.empty((int(es[mi + 1] - es[mi]), mod.n, wl.K), dtype=torch.int32, device="cuda")
+        cnt = torch.empty((int(es[mi + 1] - es[mi]), mod.n), dtype=torch.int32, device="cuda")
+        hgm.candidates(ms[mi], ss[0], p, int(first[mi]), int(es[mi + 1] - es[mi]), idx, cnt)
+        c = cnt.cpu().numpy().astype(np.int64)
+        dense += int(np.sum(c[:, 2:] * c[:, 1:-1] * c[:, :-2]))
+    assert 0 < ev <= dense, (ev, dense)
