@@ -219,6 +219,7 @@ __global__ void __launch_bounds__(kDummyThreads, 2) dummy_recurse_kernel(
                 const int b = G == 1 ? e : (int)__umulhi((unsigned)e, divG), c0 = 4 * (e - b * G);
                 const int tb = sm.t[1][b], ib = sm.id[1][b];
                 const float *brow = sm.base + b * L;
+                const int nk = sm.kept[b];   // 0: every open cell of the group takes eps, no direction needed
                 float best[4], q1[4];
                 int arg[4], tcq[4], icq[4];
                 bool open[4];
@@ -229,7 +230,7 @@ __global__ void __launch_bounds__(kDummyThreads, 2) dummy_recurse_kernel(
                     tcq[q] = inc ? sm.t[2][c] : 0;
                     icq[q] = inc ? sm.id[2][c] : -3;
                     open[q] = inc && icq[q] != ib && tcq[q] <= tb && (p.T <= 0 || tb - tcq[q] < p.T);
-                    q1[q] = open[q] ? direction(sm.xy[1][b], sm.xy[2][c]) : 0.0f;
+                    q1[q] = open[q] && nk > 0 ? direction(sm.xy[1][b], sm.xy[2][c]) : 0.0f;
                     best[q] = open[q] ? brow[E] : inf;   // (eps, b, c) is feasible with every open cell
                     arg[q] = open[q] ? E : 255;
                 }
@@ -237,7 +238,6 @@ __global__ void __launch_bounds__(kDummyThreads, 2) dummy_recurse_kernel(
                 const unsigned long long q1a = pk2(q1[0], q1[1]), q1b = pk2(q1[2], q1[3]);
                 const unsigned long long lamp = pk2(lam23, lam23);
                 const uint8_t *order = sm.srt[b];
-                const int nk = sm.kept[b];
                 for (int k = 0; k < nk; ++k) {
                     const int a = order[k];
                     const float ba = brow[a];
