@@ -1,6 +1,8 @@
 """The "independent chains" variant on the GPU (hgm_match_chains) against the FP64 chain oracle: every
 offset's mean energy within 1e-5 relative, and each chain's part of the assignment an optimal chain of
 that chain's own problem."""
+from concurrent.futures import ThreadPoolExecutor
+
 import numpy as np
 import pytest
 
@@ -119,3 +121,79 @@ def test_chains_batch_matches_pairs_and_oracle(env):
                     assert np.isfinite(e64) == np.isfinite(e1[k]), (q, k)
                     if np.isfinite(e64):
                         assert abs(e1[k] - e64) <= 1e-5 * e64 + 1e-6, (q, k, e1[k], e64)
+
+
+def check_chain_offset(co, o, e_gpu, row):
+    """(ok, why) for one offset of the chains form: the mean energy within 1e-5 relative of the FP64 one,
+    each chain's part of the assignment of FP64 energy within 1e-5 of that chain's optimum, and the points
+    outside every chain -1. Each chain problem is solved once."""
+    energies = []
+    for idx, orc in zip(co.members, co.chains):
+        ec, _, _ = orc.match(o)
+        energies.append(ec)
+        if np.isfinite(ec) and not orc.energy(np.asarray(row)[idx]) <= ec * (1 + 1e-5) + 1e-6:
+            return False, f"chain {len(energies) - 1}: E64 {orc.energy(np.asarray(row)[idx])} vs {ec}"
+    e64 = float(np.mean(energies)) if all(np.isfinite(energies)) else float("inf")
+    if np.isfinite(e64) != np.isfinite(e_gpu):
+        return False, f"feasibility: {e_gpu} vs {e64}"
+    if np.isfinite(e64) and not abs(e_gpu - e64) <= 1e-5 * e64 + 1e-6:
+        return False, f"energy {e_gpu} vs {e64}"
+    outside = np.setdiff1d(np.arange(co.M), np.concatenate(co.members))
+    if not np.all(np.asarray(row)[outside] == -1):
+        return False, "a point outside every chain is assigned"
+    return True, ""
+
+
+def test_full_batched_workload_sampled(env):
+    """The chains form on the 10-model x 8-scene workload at full size, in the benchmark's launch
+    configuration (one hgm_match_chains_batch call, 3 chains, device outputs): a seeded sample of offsets
+    and the implants' own offsets against the chain oracle."""
+    torch, hgm, oracle = env
+    wl = synth.batched_exact()
+    n_chains = 3
+    ms = [hgm.Model(*(torch.from_numpy(x).cuda() for x in (mod.xy, mod.t, mod.f))) for mod in wl.models]
+    ss = [hgm.Scene(*(torch.from_numpy(x).cuda() for x in (sc.xy, sc.t, sc.f)), sc.n_frames) for sc in wl.scenes]
+    p = hgm.default_params(K=wl.K, window=wl.window, T=wl.T)
+    first, es, as_ = hgm.batch_layout(ms, ss, p)
+    e = torch.empty(int(es[-1]), dtype=torch.float32, device="cuda")
+    a = torch.empty(int(as_[-1]), dtype=torch.int32, device="cuda")
+    hgm.match_chains_batch(ms, ss, p, n_chains, e, a)
+    torch.cuda.synchronize()
+    e, a = e.cpu().numpy(), a.cpu().numpy()
+    samples = chain_samples(wl, first, es)
+    oracles = {}
+    for mi, si, q, k in samples:
+        if (mi, si) not in oracles:
+            mod, sc = wl.models[mi], wl.scenes[si]
+            oracles[(mi, si)] = oracle.ChainOracle(mod.xy, mod.t, mod.f, sc.xy, sc.t, sc.f, sc.n_frames, n_chains,
+                                                   K=wl.K, window=wl.window, T=wl.T, lambda1=wl.lambda1,
+                                                   lambda2=wl.lambda2, lambda3=wl.lambda3)
+
+    def run(sample):
+        mi, si, q, k = sample
+        M = wl.models[mi].n
+        return check_chain_offset(oracles[(mi, si)], int(first[q]) + k, float(e[es[q] + k]),
+                                  a[as_[q] + k * M: as_[q] + (k + 1) * M])
+
+    with ThreadPoolExecutor(max_workers=16) as ex:
+        results = list(ex.map(run, samples))
+    for (ok, why), smp in zip(results, samples):
+        assert ok, (smp, why)
+
+
+def chain_samples(wl, first, es, n=24, seed=2026):
+    """Seeded (model, scene, pair, offset slot) samples plus every implant's own offset."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(n):
+        mi = int(rng.integers(len(wl.models)))
+        si = int(rng.integers(len(wl.scenes)))
+        q = mi * len(wl.scenes) + si
+        out.append((mi, si, q, int(rng.integers(int(es[q + 1] - es[q])))))
+    for si, sc in enumerate(wl.scenes):
+        for imp in sc.implants:
+            q = imp.model * len(wl.scenes) + si
+            k = imp.offset - int(first[q])
+            if 0 <= k < es[q + 1] - es[q]:
+                out.append((imp.model, si, q, k))
+    return out
