@@ -523,7 +523,10 @@ class Stream:
 
 def stream_blocks(xy, t, f, n_frames: int, block_frames: int = 60, hop: int = 30):
     """Cuts a scene into blocks of block_frames frames starting every hop frames (the last block ends at the
-    scene's end). Yields (first_frame, xy, t - first_frame, f, caller indices) per block."""
+    scene's end; a scene shorter than a block is one block). With hop > block_frames the frames between
+    blocks are skipped. Yields (first_frame, xy, t - first_frame, f, caller indices) per block."""
+    if block_frames < 1 or hop < 1:
+        raise ValueError(f"block_frames and hop must be >= 1 (got {block_frames}, {hop})")
     t = np.asarray(t)
     starts = list(range(0, max(1, n_frames - block_frames + 1), hop))
     if starts[-1] + block_frames < n_frames:
