@@ -113,7 +113,8 @@ HGM_API void hgm_default_params(hgm_params *p);
  * order is the points' stable order by frame (Sec. 2.1: the hypergraph links
  * each point to its two frame-wise predecessors). M >= 3 (Eq. 9 needs one
  * triangle), 1 <= F <= 4096, frames >= 0, all values finite; else
- * HGM_EINVAL. */
+ * HGM_EINVAL. The first model or scene created on a device also creates the
+ * fixed 64 MiB scratch of hgm_match_noalloc there (HGM_ECUDA if that fails). */
 HGM_API hgm_status hgm_create_model(const float *xy, const int32_t *t, const float *desc, int32_t M, int32_t F,
                             void *stream, hgm_model **out);
 
@@ -121,7 +122,8 @@ HGM_API hgm_status hgm_create_model(const float *xy, const int32_t *t, const flo
  * is stored stably sorted by frame with its minnode table (Sec. 3.4: first
  * point of every frame). n_frames is the scene length F_s (frames are
  * 0..F_s-1); n_frames <= 0 means max(t)+1. S >= 0 (an empty scene has no
- * feasible offset), frames in [0, F_s), values finite; else HGM_EINVAL. */
+ * feasible offset), frames in [0, F_s), values finite; else HGM_EINVAL.
+ * Creates the scratch of hgm_match_noalloc as hgm_create_model does. */
 HGM_API hgm_status hgm_create_scene(const float *xy, const int32_t *t, const float *desc, int32_t S, int32_t F,
                             int32_t n_frames, void *stream, hgm_scene **out);
 
@@ -333,20 +335,28 @@ HGM_API int32_t hgm_get_recurse_variant(void);
  * that cannot afford the device-wide synchronisation cudaMalloc/cudaFree may
  * cause, or a host framework that reserves all GPU memory at start-up.
  * Same result as hgm_match for one (model, scene) pair and all its offsets
- * (params->offset_lo/hi respected), but every intermediate (unary table,
- * candidate lists, argmin tables, unit records) lives in one fixed 64 MiB
- * scratch array compiled into the library, which each GPU that loads the
- * library holds until the process exits. Offsets are processed in chunks that
- * fit the scratch. No cudaMalloc, cudaFree or allocating library call is made.
+ * (params->offset_lo/hi respected) on the FP32 exact path, but every
+ * intermediate (unary table, candidate lists, argmin tables, unit records)
+ * lives in one fixed 64 MiB scratch array compiled into the library. Offsets
+ * are processed in chunks that fit the scratch. No cudaMalloc, cudaFree or
+ * allocating library call is made.
  *  energy [n_offsets] float, assign [n_offsets x M] int32: DEVICE pointers
  *         (the layout of hgm_match; n_offsets from hgm_offsets).
- * Errors: HGM_EUNSUPPORTED (with the byte counts in the message) when one
- * offset of this pair does not fit the scratch -- the unary table alone needs
- * M x S x 4 bytes; HGM_EINVAL for host outputs or bad arguments.
- * The first call on a device looks up the scratch's device address
- * (cudaGetSymbolAddress); make that first call before any stream capture.
- * All calls share the scratch: calls whose GPU work may overlap (other
- * streams, other threads) race and must be serialised by the caller. */
+ * When the scratch appears: the first hgm_create_model or hgm_create_scene on
+ * a device creates it there (by looking up its device address, which loads
+ * the library code that holds it) and it stays until the process exits. So
+ * create the handles on a device before reserving its memory for other uses
+ * and before any stream capture; hgm_match_noalloc itself then neither
+ * allocates nor loads anything.
+ * Errors: params are checked as by hgm_match (HGM_EINVAL for invalid values);
+ * then HGM_EUNSUPPORTED, with a message, for the options this entry point
+ * leaves out: precision != 0, dummy_cost >= 0, prune != NULL, refine > 0.
+ * HGM_EUNSUPPORTED (with the byte counts in the message) also when one offset
+ * of this pair does not fit the scratch -- the unary table alone needs
+ * M x S x 4 bytes; HGM_EINVAL for host outputs or bad handles.
+ * All calls share the scratch and it keeps the last call's contents: calls
+ * whose GPU work may overlap (other streams, other threads) race and must be
+ * serialised by the caller. */
 HGM_API hgm_status hgm_match_noalloc(const hgm_model *model, const hgm_scene *scene, const hgm_params *params,
                                      void *stream, float *energy, int32_t *assign);
 

@@ -1029,6 +1029,11 @@ hgm_status single_pair_units(const hgm_model *m, const hgm_scene *s, const hgm_p
 
 }  // namespace
 
+namespace hgm {
+// The parameter check of every matching entry point, for other translation units of the library.
+hgm_status check_match_params(const hgm_params *p) { return check_params(p); }
+}  // namespace hgm
+
 extern "C" {
 
 void hgm_default_params(hgm_params *p)
@@ -1128,6 +1133,12 @@ hgm_status hgm_create_model(const float *xy, const int32_t *t, const float *desc
         delete m;
         return cuda_fail(e, "create model");
     }
+    // the fixed scratch of hgm_match_noalloc is created on this device now, not at its first call
+    if ((rc = noalloc_prepare())) {
+        free_model(m);
+        delete m;
+        return rc;
+    }
     *out = m;
     return HGM_OK;
 }
@@ -1194,6 +1205,11 @@ hgm_status hgm_create_scene(const float *xy, const int32_t *t, const float *desc
         free_scene(s);
         delete s;
         return cuda_fail(e, "create scene");
+    }
+    if ((rc = noalloc_prepare())) {   // as in hgm_create_model
+        free_scene(s);
+        delete s;
+        return rc;
     }
     *out = s;
     return HGM_OK;

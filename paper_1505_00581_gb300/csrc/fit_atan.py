@@ -7,6 +7,8 @@ polynomial of the absolute error. Prints the coefficients (highest degree
 first, for Horner evaluation) and the FP64 maximum error of the fit.
 
   python paper_1505_00581_gb300/csrc/fit_atan.py [DEG]
+
+DEG defaults to 6, the degree of the shipped coefficients (7 terms).
 """
 import sys
 
@@ -32,7 +34,7 @@ def fit(deg: int, n: int = 4000, passes: int = 60):
 
 
 if __name__ == "__main__":
-    deg = int(sys.argv[1]) if len(sys.argv) > 1 else 7
+    deg = int(sys.argv[1]) if len(sys.argv) > 1 else 6
     c, e = fit(deg)
     print(f"degree {deg} in r^2, max |err| = {e:.3e} rad")
     for v in c[::-1]:

@@ -170,6 +170,14 @@ cudaError_t launch_count(const Unit *units, int64_t n_units, const ModelRec *mod
                          Params p, const int32_t *cand_idx, const int32_t *cand_cnt, int64_t *triples,
                          cudaStream_t st);
 
+// Load the device code of a kernel family now (the runtime otherwise loads code at first use), so that a later
+// call allocates nothing for it: the kernels hgm_match_noalloc launches.
+cudaError_t preload_unary();
+cudaError_t preload_select();
+cudaError_t preload_recurse();
+cudaError_t preload_recurse_small();
+cudaError_t preload_backtrack();
+
 // Profiling hooks (api.cu).
 // k_block.cu: the whole-block problem (every scene point a candidate, no offsets).
 struct BlockGeo {            // band tables of one scene (see k_block.cu)
@@ -241,4 +249,9 @@ namespace hgm {
 hgm_status set_error(hgm_status s, const char *msg);
 bool valid_model(const hgm_model *m);
 bool valid_scene(const hgm_scene *s);
+// api.cu: the parameter check shared by the matching entry points (HGM_EINVAL / HGM_EUNSUPPORTED + message).
+hgm_status check_match_params(const hgm_params *p);
+// noalloc.cu: looks up (once per device) the device address of the fixed scratch of hgm_match_noalloc on the
+// current device, which makes the runtime load the code that holds the scratch, and so create it, now.
+hgm_status noalloc_prepare();
 }  // namespace hgm

@@ -95,4 +95,10 @@ cudaError_t launch_count(const Unit *units, int64_t n_units, const ModelRec *mod
     return cudaGetLastError();
 }
 
+cudaError_t preload_backtrack()
+{
+    cudaFuncAttributes a;
+    return cudaFuncGetAttributes(&a, backtrack_kernel);
+}
+
 }  // namespace hgm

@@ -204,4 +204,11 @@ cudaError_t launch_recurse_small(const Unit *units, int64_t n_units, const Model
     return launch_small<16>(units, n_units, models, scenes, p, cand_idx, cand_u, cand_cnt, beta, res, st);
 }
 
+cudaError_t preload_recurse_small()
+{
+    cudaFuncAttributes a;
+    cudaError_t e = cudaFuncGetAttributes(&a, recurse_small_kernel<8>);
+    return e == cudaSuccess ? cudaFuncGetAttributes(&a, recurse_small_kernel<16>) : e;
+}
+
 }  // namespace hgm

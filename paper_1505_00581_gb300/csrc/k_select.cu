@@ -195,4 +195,10 @@ cudaError_t launch_select(const Unit *units, int64_t n_units, const ModelRec *mo
     return cudaGetLastError();
 }
 
+cudaError_t preload_select()
+{
+    cudaFuncAttributes a;
+    return cudaFuncGetAttributes(&a, select_kernel);
+}
+
 }  // namespace hgm

@@ -117,4 +117,10 @@ cudaError_t launch_unary(const float *A, int R, const float *B, int S, int F, fl
     return cudaGetLastError();
 }
 
+cudaError_t preload_unary()
+{
+    cudaFuncAttributes a;
+    return cudaFuncGetAttributes(&a, unary_kernel);
+}
+
 }  // namespace hgm

@@ -9,12 +9,18 @@
 // one fixed scratch array that is part of the library image.
 //
 // The scratch is a file-scope __device__ array of kScratchBytes (64 MiB). The
-// CUDA runtime creates it on every GPU on which this library's device code is
-// loaded, and it stays there until the process exits. Host code cannot use
-// the array's name as a device address (on the host it names a stand-in
-// object), so the first call on each device asks the runtime for the real
-// address with cudaGetSymbolAddress, with that device current, and caches it.
-// That first call should therefore happen before any stream capture.
+// CUDA runtime creates it on a GPU when it loads this file's device code there,
+// and it stays there until the process exits. The runtime loads code lazily
+// (on first use) by default, so the array would otherwise appear only at the
+// first hgm_match_noalloc call, possibly after the caller has reserved all
+// device memory. Host code cannot use the array's name as a device address (on
+// the host it names a stand-in object), so noalloc_prepare() asks the runtime
+// for the real address with cudaGetSymbolAddress, with the device current, and
+// caches it per device; that lookup loads the code and creates the array. It
+// also has the runtime load the code of every kernel this entry point launches.
+// hgm_create_model and hgm_create_scene call noalloc_prepare(), so the scratch
+// exists on a device from the first handle created there, and the address is
+// known before the caller reserves memory or captures a stream.
 //
 // All calls share the one array and it keeps the previous call's contents:
 // the persistent-kernel work counter is cleared on every call, everything else
@@ -94,6 +100,23 @@ bool is_device(const void *p)
 }
 
 }  // namespace
+
+hgm_status noalloc_prepare()
+{
+    unsigned char *p = nullptr;
+    hgm_status rc = scratch_address(&p);
+    if (rc) return rc;
+    // the kernels this entry point launches: their code is loaded now as well
+    cudaFuncAttributes a;
+    cudaError_t e = cudaFuncGetAttributes(&a, fill_units_kernel);
+    if (e == cudaSuccess) e = preload_unary();
+    if (e == cudaSuccess) e = preload_select();
+    if (e == cudaSuccess) e = preload_recurse();
+    if (e == cudaSuccess) e = preload_recurse_small();
+    if (e == cudaSuccess) e = preload_backtrack();
+    if (e != cudaSuccess) return set_error(HGM_ECUDA, cudaGetErrorString(e));
+    return HGM_OK;
+}
 }  // namespace hgm
 
 using namespace hgm;
@@ -101,16 +124,20 @@ using namespace hgm;
 extern "C" hgm_status hgm_match_noalloc(const hgm_model *model, const hgm_scene *scene, const hgm_params *params,
                                         void *stream, float *energy, int32_t *assign)
 {
+    // the checks of hgm_match first (invalid values: HGM_EINVAL), then the options this entry point leaves out
+    hgm_status rc = check_match_params(params);
+    if (rc) return rc;
     if (!valid_model(model) || !valid_scene(scene)) return set_error(HGM_EINVAL, "invalid handle");
-    if (!params) return set_error(HGM_EINVAL, "params is NULL");
     if (model->F_user != scene->F_user)
         return set_error(HGM_EINVAL, "descriptor width differs between model and scene");
-    if (params->K < 1 || params->K > 255) return set_error(HGM_EINVAL, "K must be in 1..255");
-    if (params->K > kMaxK) return set_error(HGM_EUNSUPPORTED, "K > 64 is not supported by this library");
-    if (params->window < 0 || params->precision != 0 || params->offset_lo > params->offset_hi ||
-        params->dummy_cost >= 0 ||
-        !(params->lambda1 >= 0 && params->lambda2 >= 0 && params->lambda3 >= 0))
-        return set_error(HGM_EINVAL, "invalid parameters");
+    if (params->precision != 0)
+        return set_error(HGM_EUNSUPPORTED, "hgm_match_noalloc: only precision 0 (FP32 exact); use hgm_match");
+    if (params->dummy_cost >= 0)
+        return set_error(HGM_EUNSUPPORTED, "hgm_match_noalloc: no dummy assignment (dummy_cost >= 0); use hgm_match");
+    if (params->prune)
+        return set_error(HGM_EUNSUPPORTED, "hgm_match_noalloc: no pruning (prune != NULL); use hgm_match");
+    if (params->refine > 0)
+        return set_error(HGM_EUNSUPPORTED, "hgm_match_noalloc: no refinement (refine > 0); use hgm_match");
     if (!energy || !assign || !is_device(energy) || !is_device(assign))
         return set_error(HGM_EINVAL, "energy and assign must be device pointers");
     cudaStream_t st = (cudaStream_t)stream;
@@ -143,7 +170,7 @@ extern "C" hgm_status hgm_match_noalloc(const hgm_model *model, const hgm_scene 
     const int cap = (int)std::min<size_t>((kScratchBytes - fixed - slack) / per_unit, (size_t)n_off);
 
     unsigned char *base = nullptr;
-    hgm_status rc = scratch_address(&base);
+    rc = scratch_address(&base);
     if (rc) return rc;
     int *counter = reinterpret_cast<int *>(base);
     ModelRec *d_mr = reinterpret_cast<ModelRec *>(base + off_mr);

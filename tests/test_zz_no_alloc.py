@@ -81,3 +81,28 @@ def test_noalloc_rejects_a_unary_table_beyond_the_scratch(env):
         hgm.match_noalloc(m, s, p, e, a)
     assert err.value.status == hgm.HGM_EUNSUPPORTED
     assert "scratch" in str(err.value)
+
+
+@pytest.mark.parametrize("option", ["precision", "dummy_cost", "prune", "refine", "inf_lambda"])
+def test_noalloc_refuses_what_it_leaves_out(env, option):
+    """Parameters are checked as hgm_match checks them (an infinite lambda is invalid); the valid options this
+    entry point does not implement are refused with HGM_EUNSUPPORTED instead of being ignored."""
+    torch, hgm = env
+    wl = synth.single_match(0)
+    m, s = _handles(hgm, torch, wl.models[0], wl.scenes[0])
+    over = {"precision": dict(precision=1), "dummy_cost": dict(dummy_cost=4.0),
+            "refine": dict(refine=4), "inf_lambda": dict(lambda1=float("inf"))}.get(option, {})
+    prop = None
+    if option == "prune":
+        prop = hgm.Proposal(wl.models[0].F, seed=3)
+        over = dict(prune=prop)
+    p = hgm.default_params(K=wl.K, window=wl.window, T=wl.T, **over)
+    first, n = hgm.offsets(m, s, hgm.default_params(K=wl.K, window=wl.window, T=wl.T))
+    e = torch.empty(n, dtype=torch.float32, device="cuda")
+    a = torch.empty((n, wl.models[0].n), dtype=torch.int32, device="cuda")
+    with pytest.raises(hgm.HgmError) as err:
+        hgm.match_noalloc(m, s, p, e, a)
+    want = hgm.HGM_EINVAL if option == "inf_lambda" else hgm.HGM_EUNSUPPORTED
+    assert err.value.status == want, str(err.value)
+    if prop is not None:
+        prop.close()
