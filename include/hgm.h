@@ -230,14 +230,17 @@ HGM_API hgm_status hgm_match_block(const hgm_model *const *models, int32_t n_mod
 /* Streaming blocks (Sec. 4: for continuous video the scene is cut into
  * blocks of about 60 frames, each matched whole against every model as it
  * arrives). A stream keeps the models' rows, the band and argmin tables and
- * a pinned staging buffer between blocks, so a block costs one upload, six
- * kernel launches and the read-back of its results, with no device
- * allocation once the buffers have grown to the largest block seen.
+ * pinned staging buffers between blocks, all sized at creation for blocks of
+ * up to max_points points, so a block costs one upload, six kernel launches
+ * and the read-back of its results, and hgm_stream_match never allocates
+ * device or pinned memory.
  * hgm_stream_create: models (handles; they must outlive the stream), params
- * as for hgm_match_block, block_frames >= 1 (frames of one block).
- * Release with hgm_destroy. */
+ * as for hgm_match_block, block_frames >= 1 (frames of one block),
+ * max_points >= 1 (the largest block; the band tables are sized for
+ * max_points^2 cells, the argmin tables for sum(M - 2) x max_points^2 16-bit
+ * entries). HGM_ENOMEM if those do not fit. Release with hgm_destroy. */
 HGM_API hgm_status hgm_stream_create(const hgm_model *const *models, int32_t n_models, const hgm_params *params,
-                                     int32_t block_frames, void *stream, hgm_stream **out);
+                                     int32_t block_frames, int32_t max_points, void *stream, hgm_stream **out);
 
 /* Matches one block: n points (xy n x 2, t n with frames in [0, block_frames)
  * relative to the block's first frame, desc n x F; host or device) against
@@ -246,7 +249,8 @@ HGM_API hgm_status hgm_stream_create(const hgm_model *const *models, int32_t n_m
  * layout; assignments are indices into this call's point arrays. With host
  * outputs the call returns when the results are there (HGM_EINVAL if a
  * descriptor was non-finite); with device outputs it is asynchronous. Blocks
- * that overlap (e.g. 60 frames every 30) are separate calls. */
+ * that overlap (e.g. 60 frames every 30) are separate calls. A block of more
+ * than the stream's max_points points is HGM_EUNSUPPORTED. */
 HGM_API hgm_status hgm_stream_match(hgm_stream *s, const float *xy, const int32_t *t, const float *desc, int32_t n,
                                     void *stream, float *energy, int32_t *assign);
 

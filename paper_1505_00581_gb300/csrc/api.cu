@@ -201,6 +201,7 @@ struct hgm_stream {
     std::vector<const hgm_model *> models;
     hgm_params params;
     int32_t block_frames, F_user, Fp;
+    int32_t max_points;                // capacity: points of one block (every buffer is sized for it at creation)
     hgm::BlockBufs bb;
     hgm::Buffer sc_buf, raw;           // the block's sorted points (xy | t | perm | minnode), raw descriptors
     hgm::Buffer f;                     // sorted, padded descriptors
@@ -1809,8 +1810,76 @@ hgm_status hgm_match_block(const hgm_model *const *models, int32_t n_models, con
 }
 
 // ---- streaming blocks (Sec. 4: the scene cut into blocks of ~60 frames, matched as they arrive) ----------
+namespace hgm {
+namespace {
+size_t al16(size_t v) { return (v + 15) & ~(size_t)15; }
+
+// Byte layout of a streamed block's upload: sorted xy | t | permutation | minnode table | raw descriptors.
+struct StreamUpload {
+    size_t o_t, o_perm, o_fs, o_raw;
+    StreamUpload(int64_t n, int B)
+    {
+        o_t = al16((size_t)n * 8);
+        o_perm = o_t + al16((size_t)n * 4);
+        o_fs = o_perm + al16((size_t)n * 4);
+        o_raw = o_fs + al16((size_t)(B + 1) * 4);
+    }
+};
+
+// Every buffer a block of up to P points can need, allocated once: the upload staging (pinned) and its device
+// copy, the sorted descriptors, the band tables (at most P cells per point: a band holds points of the block),
+// the unary and argmin tables, the global alpha scratch when a band exceeds shared memory, the outputs.
+hgm_status stream_reserve(hgm_stream *s, int64_t P, cudaStream_t st)
+{
+    (void)st;
+    const int B = s->block_frames, F = s->F_user, Fp = s->Fp;
+    const int64_t nm = (int64_t)s->models.size();
+    int64_t R = 0, Rm2 = 0;
+    for (const hgm_model *m : s->models) {
+        R += m->d.M;
+        Rm2 += m->d.M - 2;
+    }
+    const StreamUpload up(P, B);
+    const size_t upload = up.o_raw + (size_t)P * F * sizeof(float);
+    CK(cudaMallocHost(&s->pinned, upload), "pinned staging");
+    s->pinned_bytes = upload;
+    CK(s->sc_buf.ensure(upload), "stream buffers");
+    CK(s->f.ensure((size_t)std::max<int64_t>(P, 1) * Fp * sizeof(float)), "stream buffers");
+    CK(s->flag.ensure(sizeof(int)), "stream buffers");
+    CK(s->dev_e.ensure((size_t)nm * sizeof(float)), "stream buffers");
+    CK(s->dev_a.ensure((size_t)std::max<int64_t>(R, 1) * sizeof(int32_t)), "stream buffers");
+    const size_t o_a = al16((size_t)nm * sizeof(float));
+    s->pin_out_bytes = o_a + al16((size_t)R * sizeof(int32_t)) + 16;
+    CK(cudaMallocHost(&s->pin_out, s->pin_out_bytes), "pinned staging");
+    // run_block's buffers for one scene of P points
+    BlockBufs &bb = s->bb;
+    auto al256 = [](size_t v) { return (v + 255) & ~(size_t)255; };
+    const size_t tab = al256((size_t)P * 4) + al256((size_t)(P + 1) * 8) + al256((size_t)nm * sizeof(BlockUnit)) +
+                       al256(sizeof(SceneRec)) + al256(sizeof(BlockGeo));
+    const int64_t cells = std::max<int64_t>(P * P, 1);
+    CK(bb.tab.ensure(tab), "stream buffers");
+    CK(cudaMallocHost(&bb.pinned, tab), "pinned staging");
+    bb.pinned_bytes = tab;
+    CK(bb.cellb.ensure((size_t)cells * sizeof(int32_t)), "stream buffers");
+    CK(bb.dir.ensure((size_t)cells * 2 * sizeof(float)), "stream buffers");
+    CK(bb.U.ensure((size_t)std::max<int64_t>(P * R, 1) * sizeof(float)), "stream buffers");
+    CK(bb.beta.ensure((size_t)std::max<int64_t>(Rm2 * cells, 1) * sizeof(uint16_t)), "stream buffers");
+    CK(bb.oe.ensure((size_t)nm * sizeof(float)), "stream buffers");
+    CK(bb.oa.ensure((size_t)std::max<int64_t>(R, 1) * sizeof(int32_t)), "stream buffers");
+    if (cells > block_smem_cells()) {
+        int dev = 0, sms = 0;
+        CK(cudaGetDevice(&dev), "device");
+        CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "device");
+        const int64_t grid = std::min<int64_t>(nm, (int64_t)sms * 2);
+        CK(bb.scratch.ensure((size_t)grid * 2 * cells * sizeof(float)), "stream buffers");
+    }
+    return HGM_OK;
+}
+}  // namespace
+}  // namespace hgm
+
 hgm_status hgm_stream_create(const hgm_model *const *models, int32_t n_models, const hgm_params *params,
-                             int32_t block_frames, void *stream, hgm_stream **out)
+                             int32_t block_frames, int32_t max_points, void *stream, hgm_stream **out)
 {
     std::lock_guard<std::mutex> lk(g_mu);
     g_err.clear();
@@ -1823,6 +1892,7 @@ hgm_status hgm_stream_create(const hgm_model *const *models, int32_t n_models, c
                     "the whole-block problem runs in plain FP32 only (precision 0, no pruning, no dummy)");
     if (n_models < 1 || !models) return fail(HGM_EINVAL, "need at least one model");
     if (block_frames < 1) return fail(HGM_EINVAL, "block_frames must be >= 1 (got %d)", block_frames);
+    if (max_points < 1) return fail(HGM_EINVAL, "max_points must be >= 1 (got %d)", max_points);
     int F;
     if ((rc = check_block_models(models, n_models, &F))) return rc;
     hgm_stream *s = new hgm_stream();
@@ -1830,6 +1900,7 @@ hgm_status hgm_stream_create(const hgm_model *const *models, int32_t n_models, c
     s->models.assign(models, models + n_models);
     s->params = *params;
     s->block_frames = block_frames;
+    s->max_points = max_points;
     s->F_user = F;
     s->Fp = models[0]->d.F;
     s->view.magic = kSceneMagic;
@@ -1837,6 +1908,7 @@ hgm_status hgm_stream_create(const hgm_model *const *models, int32_t n_models, c
     s->bb.own_pinned = true;
     cudaStream_t st = (cudaStream_t)stream;
     rc = prep_block_models(s->bb, s->models.data(), n_models, st);
+    if (!rc) rc = stream_reserve(s, max_points, st);
     cudaError_t e = cudaStreamSynchronize(st);
     if (!rc && e != cudaSuccess) rc = cuda_fail(e, "stream create");
     if (rc) {
@@ -1856,6 +1928,8 @@ hgm_status hgm_stream_match(hgm_stream *s, const float *xy, const int32_t *t, co
     g_err.clear();
     if (!valid_stream(s)) return fail(HGM_EINVAL, "not a stream handle");
     if (n < 0) return fail(HGM_EINVAL, "n must be >= 0");
+    if (n > s->max_points)
+        return fail(HGM_EUNSUPPORTED, "block of %d points; this stream was created for at most %d", n, s->max_points);
     if (n > 0 && (!xy || !t || !desc)) return fail(HGM_EINVAL, "NULL input array");
     cudaStream_t st = (cudaStream_t)stream;
     const int B = s->block_frames, F = s->F_user, Fp = s->Fp;
@@ -1876,22 +1950,12 @@ hgm_status hgm_stream_match(hgm_stream *s, const float *xy, const int32_t *t, co
         std::vector<int32_t> w(fs.begin(), fs.end() - 1);
         for (int32_t k = 0; k < n; ++k) perm[(size_t)w[(size_t)ht[(size_t)k]]++] = k;
     }
-    const size_t o_xy = 0, o_t = o_xy + (((size_t)n * 8 + 15) & ~(size_t)15);
-    const size_t o_perm = o_t + (((size_t)n * 4 + 15) & ~(size_t)15);
-    const size_t o_fs = o_perm + (((size_t)n * 4 + 15) & ~(size_t)15);
-    const size_t o_raw = o_fs + (((size_t)(B + 1) * 4 + 15) & ~(size_t)15);
+    const StreamUpload up(n, B);
+    const size_t o_xy = 0, o_t = up.o_t, o_perm = up.o_perm, o_fs = up.o_fs, o_raw = up.o_raw;
     const bool desc_dev = n > 0 && is_device_ptr(desc);
     const size_t total = o_raw + (desc_dev ? 0 : (size_t)n * F * sizeof(float));
-    if (total > s->pinned_bytes) {
-        CK(cudaStreamSynchronize(st), "synchronise before growing the staging buffer");
-        if (s->pinned) cudaFreeHost(s->pinned);
-        s->pinned = nullptr;
-        s->pinned_bytes = 0;
-        CK(cudaMallocHost(&s->pinned, total * 2), "pinned staging");
-        s->pinned_bytes = total * 2;
-    } else {
-        CK(cudaStreamSynchronize(st), "synchronise the staging buffer");   // the previous block's upload
-    }
+    if (total > s->pinned_bytes) return fail(HGM_ECUDA, "stream staging smaller than its capacity (internal)");
+    CK(cudaStreamSynchronize(st), "synchronise the staging buffer");   // the previous block's upload
     char *h = static_cast<char *>(s->pinned);
     float2 *sxy = reinterpret_cast<float2 *>(h + o_xy);
     int32_t *stt = reinterpret_cast<int32_t *>(h + o_t);
@@ -1934,15 +1998,9 @@ hgm_status hgm_stream_match(hgm_stream *s, const float *xy, const int32_t *t, co
     CK(s->dev_a.ensure(std::max<size_t>(a_total, 1) * sizeof(int32_t)), "stream buffers");
     rc = run_block(s->bb, ms.data(), (int)nm, &sv, 1, &s->params, st, s->dev_e.as<float>(), s->dev_a.as<int32_t>());
     if (rc) return rc;
-    const size_t o_a = (nm * sizeof(float) + 15) & ~(size_t)15;
-    const size_t o_f = o_a + ((a_total * sizeof(int32_t) + 15) & ~(size_t)15);
-    if (o_f + 16 > s->pin_out_bytes) {
-        if (s->pin_out) cudaFreeHost(s->pin_out);
-        s->pin_out = nullptr;
-        s->pin_out_bytes = 0;
-        CK(cudaMallocHost(&s->pin_out, o_f + 16), "pinned staging");
-        s->pin_out_bytes = o_f + 16;
-    }
+    const size_t o_a = al16(nm * sizeof(float));
+    const size_t o_f = o_a + al16(a_total * sizeof(int32_t));
+    if (o_f + 16 > s->pin_out_bytes) return fail(HGM_ECUDA, "stream read-back smaller than its capacity (internal)");
     char *ho = static_cast<char *>(s->pin_out);
     CK(cudaMemcpyAsync(ho, s->dev_e.p, nm * sizeof(float), cudaMemcpyDeviceToHost, st), "copy energy");
     CK(cudaMemcpyAsync(ho + o_a, s->dev_a.p, a_total * sizeof(int32_t), cudaMemcpyDeviceToHost, st), "copy assign");

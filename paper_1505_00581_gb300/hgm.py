@@ -67,7 +67,7 @@ SIGNATURES = {
     "hgm_plan_check": (_i32, [_vp, _vp]),
     "hgm_prop_scores": (_i32, [_vp, _vp, _vp, _vp, _i32, _i32, _vp, _vp]),
     "hgm_match_chains": (_i32, [_vp, _vp, _PP, _i32, _vp, _p32, _p32, _vp, _vp]),
-    "hgm_stream_create": (_i32, [ctypes.POINTER(_vp), _i32, _PP, _i32, _vp, ctypes.POINTER(_vp)]),
+    "hgm_stream_create": (_i32, [ctypes.POINTER(_vp), _i32, _PP, _i32, _i32, _vp, ctypes.POINTER(_vp)]),
     "hgm_stream_match": (_i32, [_vp, _vp, _vp, _vp, _i32, _vp, _vp, _vp]),
     "hgm_match_block": (_i32, [ctypes.POINTER(_vp), _i32, ctypes.POINTER(_vp), _i32, _PP, _vp, _vp, _vp]),
     "hgm_match_chains_batch": (_i32, [ctypes.POINTER(_vp), _i32, ctypes.POINTER(_vp), _i32, _PP, _i32, _vp, _vp,
@@ -483,18 +483,21 @@ def match_block(models: Sequence[Model], scenes: Sequence[Scene], params: Params
 
 
 class Stream:
-    """hgm_stream_*: blocks of block_frames frames matched whole against fixed models as they arrive."""
+    """hgm_stream_*: blocks of block_frames frames matched whole against fixed models as they arrive. Every
+    buffer is sized at creation for blocks of up to max_points points (larger blocks are refused)."""
 
-    def __init__(self, models: Sequence[Model], params: Params, block_frames: int, stream=None):
+    def __init__(self, models: Sequence[Model], params: Params, block_frames: int, stream=None,
+                 max_points: int = 256):
         self.lib = load()
         self.models = list(models)     # the handles must outlive the stream
         self.params = params
         self.block_frames = int(block_frames)
+        self.max_points = int(max_points)
         self.starts = block_layout(self.models, 1)
         mh = (ctypes.c_void_p * len(self.models))(*[m.handle for m in self.models])
         h = ctypes.c_void_p()
         _check(self.lib.hgm_stream_create(mh, len(self.models), ctypes.byref(params), self.block_frames,
-                                          _stream(stream), ctypes.byref(h)))
+                                          self.max_points, _stream(stream), ctypes.byref(h)))
         self.handle = h
 
     def match(self, xy, t, f, energy=None, assign=None, stream=None):

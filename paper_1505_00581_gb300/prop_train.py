@@ -216,11 +216,12 @@ def implant_masks(wl, first, es):
 
 
 def train_default(torch, wl, steps: int = 2000, batch: int = 4096, n_pairs: int = 1 << 20, seed: int = 101,
-                  lr: float = 1e-3):
-    """Trains on the workload's own models matched against separately seeded scenes (3 scenes)."""
+                  lr: float = 1e-3, train_wl=None):
+    """Trains on the workload's own models matched against separately seeded scenes: train_wl if given,
+    else 3 scenes shaped like the batched workload's (synth.training_scenes)."""
     t0 = time.time()
     F = wl.models[0].F
-    wl = synth.training_scenes(wl, seed)
+    wl = train_wl if train_wl is not None else synth.training_scenes(wl, seed)
     data = training_pairs(torch, wl, n_pairs=n_pairs, seed=seed)
     t1 = time.time()
     prop, hist = train(torch, data, F, steps=steps, batch=batch, lr=lr, seed=seed, log_every=max(1, steps // 10))

@@ -139,14 +139,31 @@ class Workload:
     lambda2: float = 0.2
     lambda3: float = 5.0
     T: int = 10
+    # optional offset range applied to every pair (hgm_params offset_lo / offset_hi), and the scene frames a
+    # pass over the workload stands for (blocks cut from longer scenes: the frames whose offsets they own)
+    offset_lo: Optional[int] = None
+    offset_hi: Optional[int] = None
+    frames_credit: Optional[int] = None
 
     @property
     def total_frames(self) -> int:
+        if self.frames_credit is not None:
+            return int(self.frames_credit)
         return int(sum(s.n_frames for s in self.scenes))
 
-    def n_offsets(self, m: int, s: int) -> int:
+    def offset_range(self, m: int, s: int) -> Tuple[int, int]:
+        """[first, last] offset of pair (m, s): o in [-t_1, F_s-1-t_M] within the optional offset range."""
         mod, sc = self.models[m], self.scenes[s]
-        return max(0, sc.n_frames - int(mod.t.max() - mod.t.min()))
+        lo, hi = -int(mod.t.min()), sc.n_frames - 1 - int(mod.t.max())
+        if self.offset_lo is not None:
+            lo = max(lo, self.offset_lo)
+        if self.offset_hi is not None:
+            hi = min(hi, self.offset_hi)
+        return lo, hi
+
+    def n_offsets(self, m: int, s: int) -> int:
+        lo, hi = self.offset_range(m, s)
+        return max(0, hi - lo + 1)
 
 
 def single_match(seed: int = 0) -> Workload:
@@ -205,28 +222,137 @@ def precision_long(seed: int = 2, n_models: int = 50, n_frames: int = 30000, M_r
     return Workload(f"precision_long_{n_models}x1x{n_frames}_K64", models, [sc], K=64, window=3)
 
 
+class CombinedScenes:
+    """The full combined workload, its scenes generated on demand: models of M in 16..256 points (drawn as by
+    make_model) against n_scenes scenes of 10k-100k frames at 640x480 with Poisson(lam) clutter points per
+    frame, implants of random models at about implant_frac of the offsets (each implant is seen by the 2w+1
+    offsets around it); K = 64, w = 3.
+
+    Sixteen scenes of up to 100k frames hold about 70 M points (46 GB of FP32 descriptors), so a scene is
+    never built whole unless asked for: the clutter of every 64-frame chunk of scene s is drawn from its own
+    seeded stream (seed, s, chunk), and every implant from its own stream (seed, s, 10^6 + k), so any run of
+    frames [f0, f1) of a scene is generated alone (block), point for point the same as in the whole scene.
+    Within a block the clutter comes first in frame order, then the implant points that fall in it, implant
+    by implant (not time sorted, as make_scene)."""
+
+    CHUNK = 64
+
+    def __init__(self, seed: int = 3, n_models: int = 100, n_scenes: int = 16, M_range=(16, 256),
+                 frames_range=(10_000, 100_000), lam: float = 80.0, implant_frac: float = 0.05,
+                 frame=(640.0, 480.0), window: int = 3, K: int = 64, F: int = 162):
+        rng = np.random.default_rng(seed)
+        self.seed, self.lam, self.frame, self.window, self.K, self.F = seed, lam, frame, window, K, F
+        self.models = [make_model(rng, int(rng.integers(M_range[0], M_range[1] + 1)), F=F) for _ in range(n_models)]
+        self.pool = np.concatenate([m.centres for m in self.models])
+        self.n_frames: List[int] = []
+        self.implants: List[List[Tuple[int, int]]] = []
+        for _ in range(n_scenes):
+            nf = int(rng.integers(frames_range[0], frames_range[1] + 1))
+            n_imp = max(1, int(round(implant_frac * nf / (2 * window + 1))))
+            imp = []
+            for _ in range(n_imp):
+                m = int(rng.integers(0, n_models))
+                span = int(self.models[m].t.max())
+                imp.append((m, int(rng.integers(0, max(1, nf - span)))))
+            self.n_frames.append(nf)
+            self.implants.append(imp)
+
+    @property
+    def total_frames(self) -> int:
+        return int(sum(self.n_frames))
+
+    def _chunk(self, s: int, c: int):
+        rng = np.random.default_rng([self.seed, s, c])
+        counts = rng.poisson(self.lam, size=self.CHUNK)
+        n = int(counts.sum())
+        t = c * self.CHUNK + np.repeat(np.arange(self.CHUNK, dtype=np.int64), counts)
+        xy = rng.uniform((0.0, 0.0), self.frame, size=(n, 2))
+        ci = rng.integers(0, self.pool.shape[0], size=n)
+        f = (self.pool[ci] + 0.3 * rng.standard_normal((n, self.F))).astype(np.float32)
+        return xy.astype(np.float32), t, f
+
+    def _implant(self, s: int, k: int):
+        m, o = self.implants[s][k]
+        mod, nf = self.models[m], self.n_frames[s]
+        rng = np.random.default_rng([self.seed, s, 1_000_000 + k])
+        mxy = mod.xy.astype(np.float64) + 2.0 * rng.standard_normal((mod.n, 2))
+        lo = -mxy.min(axis=0)
+        hi = np.asarray(self.frame) - mxy.max(axis=0)
+        mxy = mxy + rng.uniform(np.minimum(lo, hi), np.maximum(lo, hi))
+        mt = np.clip(mod.t.astype(np.int64) + o + np.rint(rng.standard_normal(mod.n)).astype(np.int64), 0, nf - 1)
+        mf = (mod.f.astype(np.float64) + 0.1 * rng.standard_normal((mod.n, self.F))).astype(np.float32)
+        return mxy.astype(np.float32), mt, mf
+
+    def block(self, s: int, f0: int, f1: int) -> Scene:
+        """Frames [f0, f1) of scene s as a scene of f1 - f0 frames (frame f0 becomes 0)."""
+        nf = self.n_frames[s]
+        if not (0 <= f0 < f1 <= nf):
+            raise ValueError(f"block [{f0}, {f1}) outside scene {s} of {nf} frames")
+        xs, ts, fs = [], [], []
+        for c in range(f0 // self.CHUNK, (f1 - 1) // self.CHUNK + 1):
+            xy, t, f = self._chunk(s, c)
+            sel = (t >= f0) & (t < f1)
+            xs.append(xy[sel]); ts.append(t[sel]); fs.append(f[sel])
+        recs = []
+        base = int(sum(len(t) for t in ts))
+        for k, (m, o) in enumerate(self.implants[s]):
+            if o + int(self.models[m].t.max()) + 8 < f0 or o - 8 >= f1:
+                continue            # frame jitter moves a point by a few frames at most
+            xy, t, f = self._implant(s, k)
+            sel = (t >= f0) & (t < f1)
+            if not sel.any():
+                continue
+            xs.append(xy[sel]); ts.append(t[sel]); fs.append(f[sel])
+            n = int(sel.sum())
+            recs.append(Implant(m, o - f0, np.arange(base, base + n)))
+            base += n
+        return Scene(np.concatenate(xs).astype(np.float32), (np.concatenate(ts) - f0).astype(np.int32),
+                     np.concatenate(fs).astype(np.float32), None, f1 - f0, recs)
+
+    def scene(self, s: int) -> Scene:
+        return self.block(s, 0, self.n_frames[s])
+
+    def training_scenes(self, seed: int, n_scenes: int = 3, n_frames: int = 300) -> Workload:
+        """The same models against separately seeded scenes of the same shape (Poisson(lam) clutter at
+        640x480, implants at about 5% of the offsets): the proposal network's training data."""
+        rng = np.random.default_rng(seed)
+        w = self.window
+        scenes = []
+        for _ in range(n_scenes):
+            n_imp = max(1, int(round(0.05 * n_frames / (2 * w + 1))))
+            imp = []
+            for _ in range(n_imp):
+                m = int(rng.integers(0, len(self.models)))
+                imp.append((m, int(rng.integers(0, max(1, n_frames - int(self.models[m].t.max()))))))
+            scenes.append(make_scene(rng, n_frames, self.frame, ("poisson", self.lam), self.pool, self.models, imp))
+        return Workload(f"combined_train{seed}", self.models, scenes, K=self.K, window=w)
+
+    def step(self, hop: int = 256, seed: int = 0, span: int = 29) -> Workload:
+        """One pass over a sample of the job: every model against one block of each scene. Block s covers
+        frames [f0 - w, f0 + hop + span + w) of scene s, f0 a seeded multiple of hop, and every pair is
+        restricted to the block's offsets w .. w + hop - 1: those are the full scene's offsets f0 .. f0+hop-1,
+        whose windows (model frames 0..span, +-w) lie inside the block, so their candidate lists and results
+        are the full scene's. Tiling a scene with such blocks (hop apart) evaluates every offset once; a
+        pass therefore stands for n_scenes x hop scene frames (frames_credit)."""
+        w = self.window
+        rng = np.random.default_rng([self.seed, 7_000_000 + seed])
+        blocks = []
+        for s, nf in enumerate(self.n_frames):
+            n_pos = (nf - span - 2 * w) // hop
+            f0 = w + hop * int(rng.integers(0, max(1, n_pos)))
+            blocks.append(self.block(s, f0 - w, min(nf, f0 + hop + span + w)))
+        return Workload(f"combined_{len(self.models)}x{len(self.n_frames)}_K{self.K}_hop{hop}", self.models, blocks,
+                        K=self.K, window=w, offset_lo=w, offset_hi=w + hop - 1, frames_credit=len(blocks) * hop)
+
+
 def combined(seed: int = 3, n_models: int = 100, n_scenes: int = 16, M_range=(16, 256),
              frames_range=(10_000, 100_000), lam: float = 80.0, implant_frac: float = 0.05,
              frame=(640.0, 480.0)) -> Workload:
-    """The full combined workload: models of M in 16..256 points vs scenes of 10k-100k frames at 640x480 with
-    Poisson(80) points per frame; implants of random models cover about implant_frac of the offsets (each
-    implant is seen by the 2w+1 offsets around it); K=64, w=3. Scaled-down instances (fewer models and
-    scenes, shorter scenes) keep the same shape."""
-    rng = np.random.default_rng(seed)
-    models = [make_model(rng, int(rng.integers(M_range[0], M_range[1] + 1))) for _ in range(n_models)]
-    pool = np.concatenate([m.centres for m in models])
-    scenes = []
-    w = 3
-    for _ in range(n_scenes):
-        nf = int(rng.integers(frames_range[0], frames_range[1] + 1))
-        n_imp = max(1, int(round(implant_frac * nf / (2 * w + 1))))
-        imp = []
-        for _ in range(n_imp):
-            m = int(rng.integers(0, n_models))
-            span = int(models[m].t.max())
-            imp.append((m, int(rng.integers(0, max(1, nf - span)))))
-        scenes.append(make_scene(rng, nf, frame, ("poisson", lam), pool, models, imp))
-    return Workload(f"combined_{n_models}x{n_scenes}_K64", models, scenes, K=64, window=w)
+    """The combined workload with its scenes built whole (CombinedScenes.scene); meant for scaled-down
+    instances (fewer models and scenes, shorter scenes) of the same shape."""
+    cs = CombinedScenes(seed, n_models, n_scenes, M_range, frames_range, lam, implant_frac, frame)
+    return Workload(f"combined_{n_models}x{n_scenes}_K64", cs.models, [cs.scene(s) for s in range(n_scenes)],
+                    K=64, window=3)
 
 
 def paper_model(rng: np.random.Generator, M: int = 30, F: int = 162, frame: Tuple[float, float] = (160.0, 120.0),

@@ -92,11 +92,12 @@ def test_validation_of_the_wider_forms(lib):
         p = hgm.default_params(**over)
         assert lib.hgm_match_block(nil, 1, nil, 1, ctypes.byref(p), None, None, None) == hgm.HGM_EUNSUPPORTED
         h = ctypes.c_void_p()
-        assert lib.hgm_stream_create(nil, 1, ctypes.byref(p), 60, None, ctypes.byref(h)) == hgm.HGM_EUNSUPPORTED
+        assert lib.hgm_stream_create(nil, 1, ctypes.byref(p), 60, 100, None, ctypes.byref(h)) == hgm.HGM_EUNSUPPORTED
         assert not h.value
     p = hgm.default_params()
     h = ctypes.c_void_p()
-    assert lib.hgm_stream_create(nil, 1, ctypes.byref(p), 0, None, ctypes.byref(h)) == hgm.HGM_EINVAL
+    assert lib.hgm_stream_create(nil, 1, ctypes.byref(p), 0, 100, None, ctypes.byref(h)) == hgm.HGM_EINVAL
+    assert lib.hgm_stream_create(nil, 1, ctypes.byref(p), 60, 0, None, ctypes.byref(h)) == hgm.HGM_EINVAL
     e = np.zeros(4, np.float32)
     assert lib.hgm_match_chains(None, None, ctypes.byref(p), 3, None, None, None, e.ctypes.data, None) == hgm.HGM_EINVAL
     assert lib.hgm_match_chains_batch(nil, 1, nil, 1, ctypes.byref(p), 0, None, e.ctypes.data, None) == hgm.HGM_EINVAL

@@ -60,17 +60,21 @@ def test_stream_blocks_match_oracle_and_block_call(env):
     assert n_blocks == 7 and finite >= 10
 
 
-def test_stream_growth_device_inputs_and_errors(env):
+def test_stream_capacity_device_inputs_and_errors(env):
+    """Blocks of very different sizes within the capacity fixed at creation (the buffers are never grown),
+    device inputs and outputs equal to host ones, a block above the capacity refused with the stream still
+    usable afterwards, and an out-of-range frame rejected."""
     torch, hgm, oracle = env
     mods, _ = _long_scene(6, n_models=2)
     M = [hgm.Model(m.xy, m.t, m.f) for m in mods]
     p = hgm.default_params()
-    st = hgm.Stream(M, p, 60)
+    st = hgm.Stream(M, p, 60, max_points=420)
     rng = np.random.default_rng(3)
     pool = np.concatenate([m.centres for m in mods])
     dev = torch.device("cuda")
-    for lam in (0.5, 6.0, 1.0):      # the second block grows every buffer; the third reuses them
+    for lam in (0.5, 6.0, 1.0):      # about 30, 360 and 60 points per block
         sc = synth.make_scene(rng, 60, (160.0, 120.0), ("poisson", lam), pool, mods, [(0, 12)])
+        assert sc.n <= 420
         e, a = st.match(sc.xy, sc.t, sc.f)
         ed = torch.empty(2, dtype=torch.float32, device=dev)
         ad = torch.empty(int(st.starts[-1]), dtype=torch.int32, device=dev)
@@ -81,6 +85,13 @@ def test_stream_growth_device_inputs_and_errors(env):
         orc = oracle.Oracle(mods[0].xy, mods[0].t, mods[0].f, sc.xy, sc.t, sc.f, 60, K=8, window=1, T=10, **LAM)
         e64, _, _ = orc.match_block()
         assert abs(e[0] - e64) <= 1e-5 * e64 + 1e-6
+    big = synth.make_scene(rng, 60, (160.0, 120.0), 8, pool, mods, [])       # 480 points > 420
+    with pytest.raises(hgm.HgmError) as err:
+        st.match(big.xy, big.t, big.f)
+    assert err.value.status == hgm.HGM_EUNSUPPORTED
+    e, a = st.match(sc.xy, sc.t, sc.f)            # the last block again: same result after the refusal
+    orc = oracle.Oracle(mods[0].xy, mods[0].t, mods[0].f, sc.xy, sc.t, sc.f, 60, K=8, window=1, T=10, **LAM)
+    assert abs(e[0] - orc.match_block()[0]) <= 1e-5 * orc.match_block()[0] + 1e-6
     bad_t = np.full(4, 60, np.int32)
     with pytest.raises(hgm.HgmError) as err:
         st.match(np.zeros((4, 2), np.float32), bad_t, np.zeros((4, mods[0].F), np.float32))
