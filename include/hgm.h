@@ -392,9 +392,14 @@ HGM_API hgm_status hgm_unary_bf16(const hgm_model *model, const hgm_scene *scene
 /* Candidate lists for offsets first..first+n-1 (all must be valid offsets):
  *  idx [n x M x K] int32 (device): sorted scene indices of C_i(o) in
  *      ascending order, -1 after the last one; i is the sorted model index.
- *  cnt [n x M] int32 (device): |C_i(o)|. */
+ *  cnt [n x M] int32 (device): |C_i(o)|.
+ *  cost [n x M x K] float (device, or NULL): the unary cost of each
+ *      candidate as the recursion receives it, +inf after the last one. With
+ *      precision 1 the lists are ranked on the BF16 table and the 8 smallest
+ *      of each list (ties: lower slot) carry their FP32 cost, computed as
+ *      hgm_unary computes it (the same bits); the others keep the BF16 value. */
 HGM_API hgm_status hgm_candidates(const hgm_model *model, const hgm_scene *scene, const hgm_params *params,
-                          int32_t first, int32_t n, void *stream, int32_t *idx, int32_t *cnt);
+                          int32_t first, int32_t n, void *stream, int32_t *idx, int32_t *cnt, float *cost);
 
 /* The proposal network's logit for every candidate of offsets first..first+n-1
  * of one pair, as the pruning pass computes it: the first layer from the

@@ -14,7 +14,10 @@ against:
 
 with dx = x'_j - x_i, dy = y'_j - y_i, dt = t'_j - (t_i + o) and w the window
 half-width. Gradients are written out by the chain rule; Adam follows Kingma
-and Ba (2015), bias-corrected. Only tests/ and bench.py's CPU legs import it.
+and Ba (2015), bias-corrected. forward_bf16 / backward_bf16 are the same
+definitions with the operands of the tensor-core products rounded to BF16
+(the kernels' arithmetic up to FP32 accumulation order). Only tests/ and
+bench.py's CPU legs import it.
 """
 from __future__ import annotations
 
@@ -75,6 +78,74 @@ def backward(p, x, y):
     g["W1"] = dz1.T @ x
     g["b1"] = dz1.sum(axis=0)
     return g
+
+
+def bf16(x):
+    """Rounds to the nearest BF16 value (8 significant bits), ties to even, returned as float64. The value is
+    first taken to FP32, as the kernels hold it, then its low 16 bits are rounded away."""
+    b = np.asarray(x, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    b = ((b + 0x7FFF + ((b >> 16) & 1)) >> 16) << 16
+    return b.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def forward_bf16(p, x, rnd=bf16):
+    """forward() with the operands of the two hidden layers' products rounded to BF16 first -- the inputs
+    the tensor cores receive (x and W1; h1 and W2) -- and everything else in FP64. The output layer
+    (w3 . h2 + b3) and the biases stay unrounded. rnd is the rounding (identity gives forward())."""
+    z1 = rnd(x) @ rnd(p["W1"]).T + p["b1"]
+    h1 = np.maximum(z1, 0.0)
+    z2 = rnd(h1) @ rnd(p["W2"]).T + p["b2"]
+    h2 = np.maximum(z2, 0.0)
+    z3 = h2 @ p["w3"] + p["b3"][0]
+    return {"z1": z1, "h1": h1, "z2": z2, "h2": h2, "z3": z3}
+
+
+def backward_bf16(p, x, y, rnd=bf16):
+    """backward() through forward_bf16, with the operands of every product the backward pass runs on the
+    tensor cores rounded to BF16: dz2 and h1 (gradient of W2), dz2 and W2 (gradient of h1), dz1 and x
+    (gradient of W1). Returns (loss, gradients, scale): scale[k] is, per element of gradient k, the same
+    backward pass run on absolute values (every factor replaced by its magnitude, so sums cannot cancel):
+    the size of all the terms the element is built from, through every layer above it, against which
+    rounding differences of that element are measured. rnd is the rounding (identity gives backward())."""
+    c = forward_bf16(p, x, rnd)
+    B = x.shape[0]
+    z3 = c["z3"]
+    loss_v = float(np.mean(np.logaddexp(0.0, z3) - y * z3))
+    dz3 = (1.0 / (1.0 + np.exp(-z3)) - y) / B
+    g = {"w3": c["h2"].T @ dz3, "b3": np.array([dz3.sum()])}
+    scale = {"w3": np.abs(c["h2"]).T @ np.abs(dz3), "b3": np.array([np.abs(dz3).sum()])}
+    dz2 = np.outer(dz3, p["w3"]) * (c["z2"] > 0)
+    m2 = np.abs(dz2)
+    g["b2"] = dz2.sum(axis=0)
+    scale["b2"] = m2.sum(axis=0)
+    A2, H1 = rnd(dz2), rnd(c["h1"])
+    g["W2"] = A2.T @ H1
+    scale["W2"] = m2.T @ np.abs(c["h1"])
+    dh1 = A2 @ rnd(p["W2"])
+    dz1 = dh1 * (c["z1"] > 0)
+    m1 = (m2 @ np.abs(p["W2"])) * (c["z1"] > 0)
+    g["b1"] = dz1.sum(axis=0)
+    scale["b1"] = m1.sum(axis=0)
+    A1, X = rnd(dz1), rnd(x)
+    g["W1"] = A1.T @ X
+    scale["W1"] = m1.T @ np.abs(x)
+    return loss_v, g, scale
+
+
+def score_split_bf16(p, x, model_xy, scene_xy, F, rnd=bf16):
+    """The logit z3 as the pruning pass computes it: the first layer split into a model-point part
+    P = W1a f_i + b1 - W1c (x_i, y_i) / 100 (BF16 operands, FP32 result), a scene-point part
+    Q = W1b f'_j + W1c (x'_j, y'_j) / 100 rounded once to BF16 (BF16 operands), and the time term
+    W1c_t dt / w per candidate; then layer 2 on BF16 operands and the output layer unrounded. x holds the
+    rows of features() (the dx, dy columns are not used; the positions come in separately). With the
+    identity as rnd it is forward()'s z3, the split being exact algebra."""
+    W1 = p["W1"]
+    Wa, Wb, Wxy, Wt = W1[:, :F], W1[:, F:2 * F], W1[:, 2 * F:2 * F + 2], W1[:, 2 * F + 2:]
+    P = rnd(x[:, :F]) @ rnd(Wa).T + p["b1"] - (model_xy @ Wxy.T) / 100.0
+    Q = rnd(rnd(x[:, F:2 * F]) @ rnd(Wb).T + (scene_xy @ Wxy.T) / 100.0)
+    z1 = P + Q + x[:, 2 * F + 2:] @ Wt.T
+    z2 = rnd(np.maximum(z1, 0.0)) @ rnd(p["W2"]).T + p["b2"]
+    return np.maximum(z2, 0.0) @ p["w3"] + p["b3"][0]
 
 
 def adam(p, g, state, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8):

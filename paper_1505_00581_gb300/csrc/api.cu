@@ -2096,21 +2096,25 @@ hgm_status hgm_unary_bf16(const hgm_model *model, const hgm_scene *scene, float 
 }
 
 hgm_status hgm_candidates(const hgm_model *model, const hgm_scene *scene, const hgm_params *params, int32_t first,
-                          int32_t n, void *stream, int32_t *idx, int32_t *cnt)
+                          int32_t n, void *stream, int32_t *idx, int32_t *cnt, float *cost)
 {
     std::lock_guard<std::mutex> lk(g_mu);
     g_err.clear();
     WsGuard wsg((cudaStream_t)stream);
-    if (!idx || !cnt || !is_device_ptr(idx) || !is_device_ptr(cnt)) return fail(HGM_EINVAL, "outputs must be device pointers");
+    if (!idx || !cnt || !is_device_ptr(idx) || !is_device_ptr(cnt) || (cost && !is_device_ptr(cost)))
+        return fail(HGM_EINVAL, "outputs must be device pointers");
     cudaStream_t st = (cudaStream_t)stream;
     Params p;
     int R;
     hgm_status rc = single_pair_units(model, scene, params, first, n, st, p, R);
     if (rc) return rc;
     if (n == 0) return HGM_OK;
-    CK(g_ws.cand_u.ensure((size_t)n * model->d.M * p.K * sizeof(float)), "workspace (candidates)");
+    if (!cost) {
+        CK(g_ws.cand_u.ensure((size_t)n * model->d.M * p.K * sizeof(float)), "workspace (candidates)");
+        cost = g_ws.cand_u.as<float>();
+    }
     CK(launch_select(g_ws.units.as<Unit>(), n, g_ws.mrec.as<ModelRec>(), g_ws.srec.as<SceneRec>(), p, model->d.M, idx,
-                     g_ws.cand_u.as<float>(), cnt, st),
+                     cost, cnt, st),
        "select kernel");
     return HGM_OK;
 }

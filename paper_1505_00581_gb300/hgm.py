@@ -76,7 +76,7 @@ SIGNATURES = {
     "hgm_scene_order": (_i32, [_vp, _p32]),
     "hgm_unary": (_i32, [_vp, _vp, _f32, _vp, _vp]),
     "hgm_unary_bf16": (_i32, [_vp, _vp, _f32, _vp, _vp]),
-    "hgm_candidates": (_i32, [_vp, _vp, _PP, _i32, _i32, _vp, _vp, _vp]),
+    "hgm_candidates": (_i32, [_vp, _vp, _PP, _i32, _i32, _vp, _vp, _vp, _vp]),
     "hgm_count_triples": (_i32, [_vp, _vp, _PP, _i32, _i32, _vp, _vp]),
     "hgm_atan2_f32": (_i32, [_vp, _vp, _i64, _vp, _vp]),
     "hgm_debug_timeout": (_i32, [ctypes.c_uint32, _vp, _vp]),
@@ -563,10 +563,11 @@ def unary_bf16(model: Model, scene: Scene, lambda1: float, out, stream=None):
     return ko
 
 
-def candidates(model: Model, scene: Scene, params: Params, first: int, n: int, idx, cnt, stream=None):
+def candidates(model: Model, scene: Scene, params: Params, first: int, n: int, idx, cnt, stream=None, cost=None):
     (pi, ki), (pc, kc) = _ptr(idx), _ptr(cnt)
+    pu = None if cost is None else _ptr(cost)[0]
     _check(load().hgm_candidates(model.handle, scene.handle, ctypes.byref(params), int(first), int(n),
-                                 _stream(stream), pi, pc))
+                                 _stream(stream), pi, pc, pu))
     return ki, kc
 
 

@@ -138,3 +138,127 @@ def test_precision_long_full_size_sampled(env):
     rel = np.array(rel)
     assert checked >= 40
     assert rel.mean() <= 2e-3 and rel.max() <= 3e-2, (rel.mean(), rel.max())
+
+
+def _bits(x):
+    return np.ascontiguousarray(x, dtype=np.float32).view(np.uint32)
+
+
+def _precision_pair(seed, F_pad=None):
+    rng = np.random.default_rng(seed)
+    mod = synth.make_model(rng, 40)
+    sc = synth.make_scene(rng, 160, (320.0, 240.0), ("poisson", 30.0), mod.centres, [mod], [(0, 60)], F_pad=F_pad)
+    if F_pad:
+        mod = synth.pad_model(mod, F_pad)
+    return mod, sc
+
+
+@pytest.mark.parametrize("F_pad", [None, 176])
+def test_rescored_costs_equal_fp32_bit_for_bit(env, F_pad):
+    """Precision mode: the lists are ranked on the BF16 table; the 8 smallest BF16 costs of every list (ties:
+    lower slot) are replaced by the FP32 cost hgm_unary computes, bit for bit, and every other candidate
+    keeps its BF16 table value, bit for bit."""
+    torch, hgm, oracle = env
+    mod, sc = _precision_pair(31, F_pad)
+    m, s = handles(hgm, mod, sc, torch)
+    p = hgm.default_params(K=64, window=3, precision=1)
+    first, n = hgm.offsets(m, s, p)
+    K = 64
+    idx = torch.empty((n, mod.n, K), dtype=torch.int32, device="cuda")
+    cnt = torch.empty((n, mod.n), dtype=torch.int32, device="cuda")
+    cost = torch.empty((n, mod.n, K), dtype=torch.float32, device="cuda")
+    hgm.candidates(m, s, p, first, n, idx, cnt, cost=cost)
+    U32 = torch.empty((mod.n, sc.n), dtype=torch.float32, device="cuda")
+    U16 = torch.empty((mod.n, sc.n), dtype=torch.float32, device="cuda")
+    hgm.unary(m, s, 0.6, U32)
+    hgm.unary_bf16(m, s, 0.6, U16)
+    torch.cuda.synchronize()
+    idx, cnt, cost = idx.cpu().numpy(), cnt.cpu().numpy(), cost.cpu().numpy()
+    U32, U16 = U32.cpu().numpy(), U16.cpu().numpy()
+    lists = rescored = 0
+    for k in range(n):
+        for i in range(mod.n):
+            c = int(cnt[k, i])
+            if c == 0:
+                continue
+            j = idx[k, i, :c]
+            bf = U16[i, j]
+            order = np.lexsort((np.arange(c), bf))      # by BF16 cost, then slot
+            top = np.zeros(c, bool)
+            top[order[:8]] = True
+            assert np.array_equal(_bits(cost[k, i, :c][top]), _bits(U32[i, j[top]])), (k, i)
+            assert np.array_equal(_bits(cost[k, i, :c][~top]), _bits(bf[~top])), (k, i)
+            assert np.all(np.isinf(cost[k, i, c:]))
+            lists += 1
+            rescored += int(top.sum())
+    assert lists > 4000 and rescored == 8 * lists - sum(max(0, 8 - int(c)) for c in cnt.reshape(-1) if c)
+
+
+@pytest.mark.parametrize("case", ["K8", "sparse", "dense"])
+def test_precision_energy_exact_where_optima_use_rescored_candidates(env, case):
+    """Where the precision path's optimum and the FP32 path's optimum both use only re-scored candidates
+    (FP32 costs, the same bits), the two minima are the same FP32 number: each is the other's chain evaluated
+    in the same arithmetic. Where only the precision optimum does, it is a chain of the FP32 problem evaluated
+    exactly as the FP32 path evaluates it, so it cannot be below the FP32 minimum. With K = 8, or windows of
+    at most 8 points (about one point per frame, the paper's scenes), every candidate is re-scored; on the
+    dense batched-workload pair only the implant's offsets qualify."""
+    torch, hgm, oracle = env
+    if case == "sparse":
+        rng = np.random.default_rng(23)
+        mod = synth.make_model(rng, 30)
+        sc = synth.make_scene(rng, 400, (160.0, 120.0), ("poisson", 1.0), mod.centres, [mod], [(0, 60), (0, 300)])
+    else:
+        mod, sc = _precision_pair(21)
+    m, s = handles(hgm, mod, sc, torch)
+    K = 8 if case == "K8" else 64
+    p0 = hgm.default_params(K=K, window=3)
+    p1 = hgm.default_params(K=K, window=3, precision=1)
+    first, n = hgm.offsets(m, s, p0)
+    res = {}
+    for name, p in (("fp32", p0), ("bf16", p1)):
+        e = torch.empty(n, dtype=torch.float32, device="cuda")
+        a = torch.empty((n, mod.n), dtype=torch.int32, device="cuda")
+        hgm.match(m, s, p, e, a)
+        idx = torch.empty((n, mod.n, K), dtype=torch.int32, device="cuda")
+        cnt = torch.empty((n, mod.n), dtype=torch.int32, device="cuda")
+        cost = torch.empty((n, mod.n, K), dtype=torch.float32, device="cuda")
+        hgm.candidates(m, s, p, first, n, idx, cnt, cost=cost)
+        torch.cuda.synchronize()
+        res[name] = (e.cpu().numpy(), a.cpu().numpy(), idx.cpu().numpy(), cnt.cpu().numpy(), cost.cpu().numpy())
+    U32 = torch.empty((mod.n, sc.n), dtype=torch.float32, device="cuda")
+    hgm.unary(m, s, 0.6, U32)
+    torch.cuda.synchronize()
+    U32 = U32.cpu().numpy()
+    mperm, sperm = m.order(), s.order()
+    sinv = np.empty(sc.n, np.int64)
+    sinv[sperm] = np.arange(sc.n)
+
+    def sorted_chain(a_row):
+        return sinv[a_row[mperm]]           # sorted scene index of sorted model point i
+
+    def in_lists(z, idx, cnt, cost, k, need_fp32):
+        for i, j in enumerate(z):
+            c = int(cnt[k, i])
+            hit = np.nonzero(idx[k, i, :c] == j)[0]
+            if hit.size == 0:
+                return False
+            if need_fp32 and _bits(cost[k, i, hit[0]]) != _bits(U32[i, j]):
+                return False
+        return True
+
+    e32, a32, i32, c32, u32 = res["fp32"]
+    ep, ap, ip, cp, up = res["bf16"]
+    both = only_p = 0
+    for k in range(n):
+        if not (np.isfinite(e32[k]) and np.isfinite(ep[k])):
+            assert np.isfinite(e32[k]) == np.isfinite(ep[k])
+            continue
+        zp, z32 = sorted_chain(ap[k]), sorted_chain(a32[k])
+        p_rescored = in_lists(zp, ip, cp, up, k, True)
+        if p_rescored and in_lists(z32, ip, cp, up, k, True):
+            assert _bits(ep[k]) == _bits(e32[k]), (k, ep[k], e32[k])
+            both += 1
+        elif p_rescored and in_lists(zp, i32, c32, u32, k, False):
+            assert ep[k] >= e32[k], (k, ep[k], e32[k])
+            only_p += 1
+    assert both >= {"K8": 40, "sparse": 25, "dense": 3}[case], (both, only_p, n)
