@@ -103,6 +103,11 @@ def workload(name: str, rank: int, hop: int = 256):
                        f"scenes (block {hop} + 35 frames: the windows of its offsets lie inside it); the whole "
                        f"job is {cs.total_frames / wl.total_frames:.1f} such steps"}
         return wl, job
+    if name == "combined_small":     # 2 blocks of 16 offsets: the profiling case of the combined workload
+        cs = synth.CombinedScenes(seed=3)
+        wl = cs.step(hop=16, seed=rank)
+        wl.scenes, wl.frames_credit, wl.name = wl.scenes[:2], 2 * 16, wl.name + "_2blocks"
+        return wl, None
     if name == "batched_exact":
         return synth.batched_exact(seed=1 + 1000 * rank), None
     if name == "batched_small":      # one 300-frame scene: the profiling case (a few hundred MB on the device)
@@ -618,7 +623,7 @@ def main():
     t_gen = time.time()
     wl, job = workload(args.workload, rank, args.hop)
     job_cs = None
-    if args.workload == "combined":
+    if args.workload.startswith("combined"):
         from paper_1505_00581_gb300 import synth
         job_cs = synth.CombinedScenes(seed=3)
     t_gen = time.time() - t_gen

@@ -4,6 +4,8 @@ learned pruning with exact fallback, recorded as a CUDA graph -- at a reduced sc
 4,000-frame scene). The graph replay equals the direct call bit for bit; on a seeded sample of offsets the
 pruned optimum is a restriction of the exact problem: feasible exactly where the FP64 optimum is, never
 below it, and a real chain whose FP64 energy matches the reported one."""
+import os
+
 import numpy as np
 import pytest
 
@@ -74,3 +76,73 @@ def test_combined_sample_bf16_pruned_graph(env):
                 checked += 1
             del orc
     assert checked >= 16
+
+
+def test_combined_full_model_set_full_length_scene(env):
+    """The combined workload's full model set (100 models of 16-256 points) against one of its full-length
+    scenes (the shortest of the 16, about 19k frames of Poisson(80) points at 640x480, implants at about 5%
+    of the offsets), every offset of every model in one batch, in both forms the benchmark times:
+    plain exact FP32 -- on seeded offsets and on implant offsets every energy within 1e-5 of the FP64 oracle
+    and every assignment the oracle's or one of the same FP64 energy -- and BF16 distances + learned pruning
+    (network trained as the benchmark trains it, keep 8, exact fallback) -- on the same offsets a restriction
+    of the exact problem: feasible exactly where the oracle is, never more than the BF16 error below it, and
+    a real chain whose FP64 energy matches the reported one."""
+    from concurrent.futures import ThreadPoolExecutor
+
+    from gpu_util import check_offset
+    from paper_1505_00581_gb300 import prop_train
+    torch, hgm, oracle = env
+    cs = synth.CombinedScenes(seed=3)
+    s_idx = int(np.argmin(cs.n_frames))
+    sc = cs.scene(s_idx)
+    wl = synth.Workload("combined_full_scene", cs.models, [sc], K=64, window=3)
+    dev = torch.device("cuda")
+    ms = [hgm.Model(*(torch.from_numpy(a).to(dev) for a in (mod.xy, mod.t, mod.f))) for mod in wl.models]
+    s = hgm.Scene(*(torch.from_numpy(a).to(dev) for a in (sc.xy, sc.t, sc.f)), sc.n_frames)
+    p = hgm.default_params(K=64, window=3)
+    first, es, as_ = hgm.batch_layout(ms, [s], p)
+    e = torch.empty(int(es[-1]), dtype=torch.float32, device=dev)
+    a = torch.empty(int(as_[-1]), dtype=torch.int32, device=dev)
+    hgm.match_batch(ms, [s], p, e, a)
+    torch.cuda.synchronize()
+    e_ex, a_ex = e.cpu().numpy(), a.cpu().numpy()
+    prop, _ = prop_train.train_default(torch, wl, steps=2000, seed=101, train_wl=cs.training_scenes(101))
+    pp = hgm.default_params(K=64, window=3, precision=1, prune=prop, keep=8)
+    hgm.match_batch(ms, [s], pp, e, a)
+    torch.cuda.synchronize()
+    e_pr, a_pr = e.cpu().numpy(), a.cpu().numpy()
+    prop.close()
+
+    rng = np.random.default_rng(17)
+    picks = [(int(m), int(first[m]) + int(rng.integers(int(es[m + 1] - es[m]))))
+             for m in rng.integers(0, len(wl.models), size=20)]
+    for imp in sc.implants[:4]:
+        picks.append((imp.model, imp.offset))
+
+    def solve(mo):
+        m, o = mo
+        orc, o_sub, keep = _sub_oracle(oracle, wl, m, o)
+        e64, z64, _ = orc.match(o_sub)
+        return orc, o_sub, keep, e64, z64
+
+    with ThreadPoolExecutor(max_workers=min(16, os.cpu_count() or 1)) as ex:
+        solved = list(ex.map(solve, picks))
+    for (m, o), (orc, o_sub, keep, e64, z64) in zip(picks, solved):
+        k = o - int(first[m])
+        M = wl.models[m].n
+        row = slice(int(as_[m]) + k * M, int(as_[m]) + (k + 1) * M)
+        # exact form: the parity rule of every exact-path test
+        z_ex = a_ex[row]
+        z_sub = np.searchsorted(keep, z_ex) if np.isfinite(e64) else z_ex
+        if np.isfinite(e64):
+            assert np.all(keep[z_sub] == z_ex), (m, o)
+        ok, tie, why = check_offset(orc, o_sub, float(e_ex[int(es[m]) + k]), z_sub, e64, z64)
+        assert ok, (m, o, why)
+        # pruned + BF16 form: a restriction of the exact problem
+        ep = float(e_pr[int(es[m]) + k])
+        assert np.isfinite(e64) == np.isfinite(ep), (m, o)
+        if np.isfinite(e64):
+            assert ep >= e64 * (1 - 3e-2), (m, o, ep, e64)
+            zp = np.searchsorted(keep, a_pr[row])
+            assert np.all(keep[zp] == a_pr[row])
+            assert abs(orc.energy(zp) - ep) <= 3e-2 * e64
