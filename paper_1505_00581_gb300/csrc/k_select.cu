@@ -7,11 +7,16 @@
 // the smallest unary cost are kept (ties to the lower scene index), and the
 // kept points are listed in ascending scene index (hence ascending frame).
 //
-// One warp per (unit, i). The K-th smallest key is found exactly by a 4-pass
-// radix select on the IEEE bit patterns (unary costs are >= 0, so the bit
-// pattern orders like the value); a final ballot pass keeps every key below
-// the threshold plus the first equal ones in index order. Integer decisions
-// therefore depend only on the FP32 keys of kernel (a), bit for bit.
+// One warp per (unit, i). The K-th smallest key is found exactly by a radix
+// select on the IEEE bit patterns (unary costs are >= 0, so the bit pattern
+// orders like the value), one 8-bit digit per pass from the top; a final
+// ballot pass keeps every key below the threshold plus the first equal ones in
+// index order. Integer decisions therefore depend only on the FP32 keys of
+// kernel (a), bit for bit. The costs of one window share their top bits (same
+// exponent range), so the digits on which all keys agree are read off an AND
+// and an OR of the keys instead of being histogrammed: the first pass that
+// would otherwise put every key into one shared-memory bin -- 32 lanes adding
+// to the same counter, serialised -- is skipped.
 #include "hgm_internal.cuh"
 #include "unary_common.cuh"
 
@@ -19,7 +24,7 @@ namespace hgm {
 namespace {
 
 constexpr int kWarps = 8;
-constexpr int kKeyRegs = 8;   // windows of up to 32 x 8 = 256 keys are selected from registers
+constexpr int kKeyRegs = 20;  // windows of up to 32 x 20 = 640 keys are selected from registers
 
 __device__ __forceinline__ uint32_t lanemask_lt()
 {
@@ -28,7 +33,7 @@ __device__ __forceinline__ uint32_t lanemask_lt()
     return m;
 }
 
-__global__ void __launch_bounds__(kWarps * 32, 3) select_kernel(const Unit *__restrict__ units, int64_t n_units,
+__global__ void __launch_bounds__(kWarps * 32, 2) select_kernel(const Unit *__restrict__ units, int64_t n_units,
                                                              const ModelRec *__restrict__ models,
                                                              const SceneRec *__restrict__ scenes, Params p,
                                                              int32_t *__restrict__ cand_idx,
@@ -72,9 +77,33 @@ __global__ void __launch_bounds__(kWarps * 32, 3) select_kernel(const Unit *__re
                     const int e = lane + 32 * q;
                     kb[q] = inreg && e < n ? __float_as_uint(key[e]) : 0xffffffffu;
                 }
+                // bits on which every key of the window agrees
+                uint32_t kand = 0xffffffffu, kor = 0u;
+                if (inreg) {
+#pragma unroll
+                    for (int q = 0; q < kKeyRegs; ++q)
+                        if (lane + 32 * q < n) { kand &= kb[q]; kor |= kb[q]; }
+                } else {
+                    for (int e = lane; e < n; e += 32) {
+                        const uint32_t b = __float_as_uint(key[e]);
+                        kand &= b;
+                        kor |= b;
+                    }
+                }
+#pragma unroll
+                for (int off = 16; off > 0; off >>= 1) {
+                    kand &= __shfl_xor_sync(0xffffffffu, kand, off);
+                    kor |= __shfl_xor_sync(0xffffffffu, kor, off);
+                }
+                const uint32_t differ = kand ^ kor;
                 uint32_t prefix = 0, mask = 0;
                 int kk = K;
                 for (int shift = 24; shift >= 0; shift -= 8) {
+                    if (((differ >> shift) & 255u) == 0) {   // one digit value for every key: no histogram
+                        prefix |= kand & (255u << shift);
+                        mask |= 255u << shift;
+                        continue;
+                    }
                     for (int d = lane; d < 256; d += 32) hist[warp][d] = 0;
                     __syncwarp();
                     if (inreg) {

@@ -196,10 +196,10 @@ def test_rescored_costs_equal_fp32_bit_for_bit(env, F_pad):
 
 @pytest.mark.parametrize("case", ["K8", "sparse", "dense"])
 def test_precision_energy_exact_where_optima_use_rescored_candidates(env, case):
-    """Where the precision path's optimum and the FP32 path's optimum both use only re-scored candidates
-    (FP32 costs, the same bits), the two minima are the same FP32 number: each is the other's chain evaluated
-    in the same arithmetic. Where only the precision optimum does, it is a chain of the FP32 problem evaluated
-    exactly as the FP32 path evaluates it, so it cannot be below the FP32 minimum. With K = 8, or windows of
+    """Where the precision path's optimum is a chain of the FP32 problem whose costs are all re-scored ones
+    (FP32, the same bits), it is evaluated exactly as the FP32 path evaluates it, so it cannot be below the
+    FP32 minimum; where moreover the FP32 optimum is a chain of the precision problem with re-scored costs,
+    the two minima are the same FP32 number, each being the other's chain in the same arithmetic. With K = 8, or windows of
     at most 8 points (about one point per frame, the paper's scenes), every candidate is re-scored; on the
     dense batched-workload pair only the implant's offsets qualify."""
     torch, hgm, oracle = env
@@ -254,11 +254,13 @@ def test_precision_energy_exact_where_optima_use_rescored_candidates(env, case):
             assert np.isfinite(e32[k]) == np.isfinite(ep[k])
             continue
         zp, z32 = sorted_chain(ap[k]), sorted_chain(a32[k])
-        p_rescored = in_lists(zp, ip, cp, up, k, True)
-        if p_rescored and in_lists(z32, ip, cp, up, k, True):
+        # the precision optimum is a chain of the FP32 problem, with its FP32 costs
+        p_in_fp32 = in_lists(zp, ip, cp, up, k, True) and in_lists(zp, i32, c32, u32, k, False)
+        if not p_in_fp32:
+            continue
+        assert ep[k] >= e32[k], (k, ep[k], e32[k])
+        only_p += 1
+        if in_lists(z32, ip, cp, up, k, True):     # and the FP32 optimum a chain of the precision problem
             assert _bits(ep[k]) == _bits(e32[k]), (k, ep[k], e32[k])
             both += 1
-        elif p_rescored and in_lists(zp, i32, c32, u32, k, False):
-            assert ep[k] >= e32[k], (k, ep[k], e32[k])
-            only_p += 1
     assert both >= {"K8": 40, "sparse": 25, "dense": 3}[case], (both, only_p, n)
