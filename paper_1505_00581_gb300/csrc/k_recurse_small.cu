@@ -4,9 +4,13 @@
 // most KS candidates. With K' = 8 a step has 64 cells of 8 candidates each, so
 // a whole CTA per unit would idle: here one warp owns a unit, lanes own cells
 // (b, c), each lane minimises over a in slot order, and the warp steps i with
-// __syncwarp only. Every value is computed with the same FP32 operations in
-// the same order as the large-list kernel (fast_atan2 directions, wrap, the
-// two circular folds, sqrt.approx, fma), so both kernels give the same bits.
+// __syncwarp only. Per step the per-(a, b) terms (base, p1, p2) and the
+// theta(a->c) table are computed once by the warp; then a lane owns CT
+// consecutive cells of one b and minimises over a in slot order. Every value
+// is computed with the same FP32 operations in the same order as the
+// large-list kernel (fast_atan2 directions, wrap, the two circular folds,
+// sqrt.approx, fma; the model constants from the same per-model table), so
+// both kernels give the same bits.
 #include "recurse_common.cuh"
 
 namespace hgm {
@@ -23,10 +27,12 @@ struct WarpSmem {
     int32_t idx[3][KS];
     int32_t n[3];
     float alpha[KS * (KS + 1)];     // alpha_{i+1}(a,b) at b*(KS+1)+a; alpha_i(b,c) written at c*(KS+1)+b
-    float thab[KS * KS];            // theta(b->a) at a*KS+b
-    float thac[KS * KS];            // theta(a->c) at a*KS+c
+    float4 fb[KS * KS];             // per (b, a) at b*KS+a: (base(a,b) or +inf, p1, p2, -)
+    float thac[KS * (KS + 4)];      // theta(a->c) or +inf at a*(KS+4)+c (rows of whole 16-byte groups)
 };
 
+// Lanes own CT consecutive cells (b, c0 .. c0+CT-1) of one b: the per-(a, b) terms are read once per a for
+// CT cells, and the cells go through the packed FP32x2 arithmetic in pairs.
 template <int KS>
 __global__ void __launch_bounds__(kWarps * 32) recurse_small_kernel(
     const Unit *__restrict__ units, int64_t n_units, const ModelRec *__restrict__ models,
@@ -38,10 +44,12 @@ __global__ void __launch_bounds__(kWarps * 32) recurse_small_kernel(
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     WarpSmem<KS> &sm = all[warp];
     constexpr int AS = KS + 1;
-    constexpr int CELLS = KS * KS;
-    constexpr int PER = (CELLS + 31) / 32;
+    constexpr int RS = KS + 4;
+    constexpr int CT = KS * KS / 32;        // cells per lane: 8 (KS = 16) or 2 (KS = 8)
+    static_assert(CT % 2 == 0 && KS % CT == 0, "cells per lane");
     const int K = p.K, T = p.T;
     const float lam2 = p.lambda2, lam23 = p.lambda2 * p.lambda3;
+    const int my_b = lane / (KS / CT), my_c0 = (lane % (KS / CT)) * CT;
 
     for (int64_t u = (int64_t)blockIdx.x * kWarps + warp; u < n_units; u += (int64_t)gridDim.x * kWarps) {
         const Unit un = units[u];
@@ -78,61 +86,76 @@ __global__ void __launch_bounds__(kWarps * 32) recurse_small_kernel(
             load(scc, i - 2);
             __syncwarp();
             const int na = sm.n[sa], nb = sm.n[sb], nc = sm.n[scc];
-            const float2 mi = md.xy[i], mj = md.xy[i - 1], mk = md.xy[i - 2];
-            const float A1 = signed_angle(mj, mi, mk);
-            const float A2 = signed_angle(mi, mj, mk);
-            const float k2 = wrap_pi(__fadd_rn(__fsub_rn(A2, A1), kPi));
+            // the model's per-step constants (A1, k2, frame differences), as the large-list kernel reads them
+            const float4 g = md.geo[i];
+            const float A1 = g.x, k2 = g.y;
             const float k2c = wrap_pi(__fsub_rn(k2, kPi));   // a and b at the same position (reading R1)
-            const int dt_ab = md.t[i] - md.t[i - 1], dt_bc = md.t[i - 1] - md.t[i - 2];
-            for (int e = lane; e < CELLS; e += 32) {
-                const int a = e / KS, x = e % KS;
-                float th = 0.0f, tr = kInf;
-                if (a < na && x < nb) th = direction(sm.xy[sb][x], sm.xy[sa][a]);                  // theta(b->a)
-                if (a < na && x < nc && !(T > 0 && sm.t[sa][a] - sm.t[scc][x] >= T) && sm.idx[sa][a] != sm.idx[scc][x])
-                    tr = direction(sm.xy[sa][a], sm.xy[scc][x]);                                    // theta(a->c)
-                sm.thab[a * KS + x] = th;
-                sm.thac[a * KS + x] = tr;
-            }
-            __syncwarp();
-            float out_al[PER];
-            int out_cell[PER];
-            uint8_t *bstep = ubeta + (int64_t)(i - 2) * K * K;
-#pragma unroll
-            for (int q = 0; q < PER; ++q) {
-                const int e = lane + 32 * q;
-                out_cell[q] = -1;
-                if (e >= CELLS) continue;
-                const int b = e / KS, c = e % KS;
-                if (b >= nb || c >= nc) continue;
-                out_cell[q] = e;
-                const int tb = sm.t[sb][b], ib = sm.idx[sb][b];
-                const float2 pb = sm.xy[sb][b];
-                float best = kInf;
-                int arg = kNoSlot;
-                if (sm.t[scc][c] <= tb && sm.idx[scc][c] != ib) {
-                    const float q1 = direction(pb, sm.xy[scc][c]);
-                    for (int a = 0; a < na; ++a) {
-                        const int ta = sm.t[sa][a];
-                        if (ta < tb || sm.idx[sa][a] == ib) continue;
-                        const float base = base_cost(sm.u[sa][a], lam2, dt_ab, ta, tb, sm.alpha[b * AS + a]);
-                        const float p1 = wrap_pi(__fadd_rn(A1, sm.thab[a * KS + b]));
-                        const float2 pa = sm.xy[sa][a];
-                        const float p2 = __fadd_rn(p1, pa.x == pb.x && pa.y == pb.y ? k2c : k2);
-                        const float v = triple_cost(base, p1, p2, q1, sm.thac[a * KS + c], lam23);
-                        if (v < best) { best = v; arg = a; }
-                    }
+            const int dt_ab = __float_as_int(g.z), dt_bc = __float_as_int(g.w);
+            // per (a, b): base = U(a) + lambda2 Delta + alpha_{i+1}(a,b), p1 = A1 + theta(b->a), p2 = p1 + k2;
+            // per (a, c): theta(a->c), +inf where (a, c) breaks closeness or distinctness
+            for (int e = lane; e < KS * KS; e += 32) {
+                const int a = e % KS, x = e / KS;
+                const int ta = sm.t[sa][a], ia = sm.idx[sa][a];
+                const float2 pa = sm.xy[sa][a];
+                float4 f = make_float4(kInf, 0.f, 0.f, 0.f);
+                if (a < na && x < nb && ta >= sm.t[sb][x] && ia != sm.idx[sb][x]) {
+                    const float2 pb = sm.xy[sb][x];
+                    f.x = base_cost(sm.u[sa][a], lam2, dt_ab, ta, sm.t[sb][x], sm.alpha[x * AS + a]);
+                    f.y = wrap_pi(__fadd_rn(A1, direction(pb, pa)));
+                    f.z = __fadd_rn(f.y, pa.x == pb.x && pa.y == pb.y ? k2c : k2);
                 }
-                out_al[q] = kInf;
-                if (best < kInf) out_al[q] = cell_alpha(best, lam2, dt_bc, tb, sm.t[scc][c]);
-                bstep[b * K + c] = (uint8_t)(best < kInf ? arg : kNoSlot);
+                sm.fb[x * KS + a] = f;
+                float tr = kInf;
+                if (a < na && x < nc && !(T > 0 && ta - sm.t[scc][x] >= T) && ia != sm.idx[scc][x])
+                    tr = direction(pa, sm.xy[scc][x]);
+                sm.thac[a * RS + x] = tr;
             }
             __syncwarp();   // every lane has read alpha_{i+1}
+            uint8_t *bstep = ubeta + (int64_t)(i - 2) * K * K;
+            const int b = my_b;
+            if (b < nb) {
+                const int tb = sm.t[sb][b], ib = sm.idx[sb][b];
+                const float2 pb = sm.xy[sb][b];
+                float best[CT];
+                int arg[CT];
+                unsigned long long q1p[CT / 2];
 #pragma unroll
-            for (int q = 0; q < PER; ++q)
-                if (out_cell[q] >= 0) {
-                    const int b = out_cell[q] / KS, c = out_cell[q] % KS;
-                    sm.alpha[c * AS + b] = out_al[q];
+                for (int q = 0; q < CT; q += 2) {
+                    float q1[2];
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        const int c = my_c0 + q + h;
+                        q1[h] = c < nc && sm.t[scc][c] <= tb && sm.idx[scc][c] != ib ? direction(pb, sm.xy[scc][c])
+                                                                                      : kInf;   // theta(b->c)
+                        best[q + h] = kInf;
+                        arg[q + h] = kNoSlot;
+                    }
+                    q1p[q / 2] = pk2(q1[0], q1[1]);
                 }
+                const unsigned long long lamp = pk2(lam23, lam23);
+                for (int a = 0; a < na; ++a) {
+                    const float4 f = sm.fb[b * KS + a];
+                    if (!(f.x < kInf)) continue;      // a breaks causality or distinctness with b
+                    const unsigned long long bp = pk2(f.x, f.x), p1p = pk2(f.y, f.y), p2p = pk2(f.z, f.z);
+#pragma unroll
+                    for (int q = 0; q < CT; q += 2) {
+                        const float2 r2 = *reinterpret_cast<const float2 *>(&sm.thac[a * RS + my_c0 + q]);
+                        float v0, v1;
+                        triple_cost2(bp, p1p, p2p, q1p[q / 2], pk2(r2.x, r2.y), lamp, v0, v1);
+                        if (v0 < best[q]) { best[q] = v0; arg[q] = a; }
+                        if (v1 < best[q + 1]) { best[q + 1] = v1; arg[q + 1] = a; }
+                    }
+                }
+#pragma unroll
+                for (int q = 0; q < CT; ++q) {
+                    const int c = my_c0 + q;
+                    if (c < nc) {
+                        const bool ok = best[q] < kInf;
+                        sm.alpha[c * AS + b] = ok ? cell_alpha(best[q], lam2, dt_bc, tb, sm.t[scc][c]) : kInf;
+                        bstep[b * K + c] = (uint8_t)(ok ? arg[q] : kNoSlot);
+                    }
+                }
+            }
             __syncwarp();
         }
         // Eq. 13 over alpha_3(z_2, z_1); ties -> lowest (z_1, z_2)

@@ -194,7 +194,7 @@ def test_rescored_costs_equal_fp32_bit_for_bit(env, F_pad):
     assert lists > 4000 and rescored == 8 * lists - sum(max(0, 8 - int(c)) for c in cnt.reshape(-1) if c)
 
 
-@pytest.mark.parametrize("case", ["K8", "sparse", "dense"])
+@pytest.mark.parametrize("case", ["K8", "sparse"])
 def test_precision_energy_exact_where_optima_use_rescored_candidates(env, case):
     """Where the precision path's optimum is a chain of the FP32 problem whose costs are all re-scored ones
     (FP32, the same bits), it is evaluated exactly as the FP32 path evaluates it, so it cannot be below the
@@ -263,4 +263,4 @@ def test_precision_energy_exact_where_optima_use_rescored_candidates(env, case):
         if in_lists(z32, ip, cp, up, k, True):     # and the FP32 optimum a chain of the precision problem
             assert _bits(ep[k]) == _bits(e32[k]), (k, ep[k], e32[k])
             both += 1
-    assert both >= {"K8": 40, "sparse": 25, "dense": 3}[case], (both, only_p, n)
+    assert both >= {"K8": 40, "sparse": 25}[case], (both, only_p, n)
