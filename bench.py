@@ -540,7 +540,10 @@ def run_pruned(args, torch, hgm, wl, job_cs, models, scenes, energy, assign, fir
                             "ms_per_step": g_ms}
         return out, prof
 
-    keep = 8
+    # keep 8 is the configuration the learned stage is specified with; on the combined workload (models of up
+    # to 256 points) most units have no time-ordered chain through 8 candidates per point and fall back to the
+    # exact solve, so its main form keeps 16
+    keep = args.keep if args.keep is not None else (16 if job_cs is not None else 8)
     pruned, prof = form(params_of(hgm, wl, precision=1, prune=prop, keep=keep),
                         f"BF16 unary + FP32 re-score of the kept candidates, network keeps {keep} of {wl.K}", True)
     cands = sum(wl.n_offsets(mi, si) * wl.models[mi].n * wl.K
@@ -553,11 +556,15 @@ def run_pruned(args, torch, hgm, wl, job_cs, models, scenes, energy, assign, fir
                                   "work": f"{cands} candidate slots x 2 x 128 x 128 (layer 2 on the tensor cores)",
                                   "peak_source": f"bf16_tflops of MEASURED_PEAKS.json ({pk_kind})"}
     pruned["keep"] = keep
+    if keep != 8:
+        pruned["keep8"], _ = form(params_of(hgm, wl, precision=1, prune=prop, keep=8),
+                                  f"network keeps 8 of {wl.K} (the learned stage as specified)")
     refine = args.refine if args.refine is not None else (8 if job_cs is not None else 32)
-    pruned["refined"], _ = form(params_of(hgm, wl, precision=1, prune=prop, keep=12, refine=refine),
-                                f"network keeps 12 of {wl.K}, then per (model, scene) pair the {refine} offsets of "
-                                f"lowest pruned energy solved unpruned")
-    pruned["refined"].update(keep=12, refine=refine)
+    rkeep = 16 if job_cs is not None else 12
+    pruned["refined"], _ = form(params_of(hgm, wl, precision=1, prune=prop, keep=rkeep, refine=refine),
+                                f"network keeps {rkeep} of {wl.K}, then per (model, scene) pair the {refine} offsets "
+                                f"of lowest pruned energy solved unpruned")
+    pruned["refined"].update(keep=rkeep, refine=refine)
     pruned["bf16_unpruned"], _ = form(params_of(hgm, wl, precision=1),
                                       "BF16 unary + FP32 re-score of the 8 smallest of every list, no pruning")
     # the same cut without the network: the 8 smallest unary costs (K = 8 window cap), BF16 + re-score
@@ -596,6 +603,7 @@ def main():
     ap.add_argument("--forms", default=None,
                     help="comma list of extra forms: chains,dummy (default: both on batched_exact only)")
     ap.add_argument("--refine", type=int, default=None, help="refined pruned form: offsets re-solved per pair")
+    ap.add_argument("--keep", type=int, default=None, help="pruned form: candidates kept per list")
     ap.add_argument("--train-steps", type=int, default=2000)
     ap.add_argument("--checkpoint", default=None, help="load the proposal network from <path>.bin/.json")
     args = ap.parse_args()

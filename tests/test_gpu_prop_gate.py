@@ -5,10 +5,11 @@ on separately seeded scenes) is compared with the same cut made without it -- th
 costs, K = keep -- on the 10-model x 8-scene batched workload, both in the BF16 + FP32 re-score mode and
 against this run's exact FP32 results.
 
-* Per offset, at equal keep, the network keeps the exact optimum's candidate more often (point recall), and
-  neither cut reaches the per-offset bar of 99% recall: on offsets whose windows hold only clutter the
-  optimum is a chain among near-equal ones, decided by time order and geometry, not by one candidate's
-  features.
+* Per offset, at the keep the learned stage is specified with (8 of 64), the network keeps the exact
+  optimum's candidate more often than the unary cut (point recall), and neither cut reaches the per-offset
+  bar of 99% recall: on offsets whose windows hold only clutter the optimum is a chain among near-equal
+  ones, decided by time order and geometry, not by one candidate's features. (From keep 12 on, the unary
+  cut keeps it as often or more: the network's gain is in the first few places of its ranking.)
 * Per (model, scene) pair -- the matching distance recognition uses is the minimum over offsets -- keep 12
   with the 32 offsets of lowest pruned energy re-solved unpruned meets the bar: recall of the exact best
   assignment >= 0.99 and mean relative gap of the pair minimum <= 1e-3, faster than the exact path.
@@ -67,7 +68,7 @@ def _quality(env, e, a):
     return env["prop_train"].compare(*env["ref"], e.cpu().numpy(), a.cpu().numpy(), env["M_rows"], env["e_rows"])
 
 
-@pytest.mark.parametrize("keep", [8, 12])
+@pytest.mark.parametrize("keep", [8])
 def test_network_keeps_the_optimum_more_often_than_the_unary_cut(env, keep):
     torch, hgm = env["torch"], env["hgm"]
     pn = hgm.default_params(K=64, window=3, precision=1, prune=env["prop"], keep=keep)
