@@ -107,10 +107,12 @@ __global__ void __launch_bounds__(kWarps * 32, 2) select_kernel(const Unit *__re
                     for (int d = lane; d < 256; d += 32) hist[warp][d] = 0;
                     __syncwarp();
                     if (inreg) {
+                        // slots past the window hold 0xffffffff: costs are >= 0 (bit 31 clear), so such a slot
+                        // either fails the prefix test or lands in bin 255, above every real key's bin
 #pragma unroll
                         for (int q = 0; q < kKeyRegs; ++q) {
                             const uint32_t b = kb[q];
-                            if (lane + 32 * q < n && (b & mask) == prefix) atomicAdd(&hist[warp][(b >> shift) & 255u], 1u);
+                            if ((b & mask) == prefix) atomicAdd(&hist[warp][(b >> shift) & 255u], 1u);
                         }
                     } else {
                         for (int e = lane; e < n; e += 32) {
@@ -149,32 +151,32 @@ __global__ void __launch_bounds__(kWarps * 32, 2) select_kernel(const Unit *__re
                     kk -= (int)below;
                     __syncwarp();
                 }
-                // keep keys < tau, plus the first kk keys == tau in index order
+                // keep keys < tau, plus the first kk keys == tau in index order (tau is a real key's bits, so
+                // the 0xffffffff of slots past the window is never kept)
                 const uint32_t tau = prefix;
+                const uint32_t lt_mask = lanemask_lt();
                 int base = 0, eqseen = 0;
-                for (int c0 = 0; c0 < n; c0 += 32) {
-                    int e = c0 + lane;
-                    bool valid = e < n;
-                    float kv = 0.0f;
-                    if (inreg) {
-#pragma unroll
-                        for (int q = 0; q < kKeyRegs; ++q)
-                            if (c0 == 32 * q) kv = __uint_as_float(kb[q]);
-                        kv = valid ? kv : 0.0f;
-                    } else {
-                        kv = valid ? key[e] : 0.0f;
-                    }
-                    uint32_t b = __float_as_uint(kv);
-                    bool lt = valid && b < tau;
-                    bool eq = valid && b == tau;
-                    uint32_t eqm = __ballot_sync(0xffffffffu, eq);
-                    int eqrank = eqseen + __popc(eqm & lanemask_lt());
-                    bool keep = lt || (eq && eqrank < kk);
-                    uint32_t km = __ballot_sync(0xffffffffu, keep);
-                    int pos = base + __popc(km & lanemask_lt());
-                    if (keep && pos < K) { oidx[pos] = j0 + e; ou[pos] = kv; }
+                auto keep_step = [&](uint32_t b, int e) {
+                    const bool lt = b < tau;
+                    const bool eq = b == tau;
+                    const uint32_t eqm = __ballot_sync(0xffffffffu, eq);
+                    const int eqrank = eqseen + __popc(eqm & lt_mask);
+                    const bool keep = lt || (eq && eqrank < kk);
+                    const uint32_t km = __ballot_sync(0xffffffffu, keep);
+                    const int pos = base + __popc(km & lt_mask);
+                    if (keep && pos < K) { oidx[pos] = j0 + e; ou[pos] = __uint_as_float(b); }
                     base += __popc(km);
                     eqseen += __popc(eqm);
+                };
+                if (inreg) {
+#pragma unroll
+                    for (int q = 0; q < kKeyRegs; ++q)
+                        if (32 * q < n) keep_step(kb[q], lane + 32 * q);
+                } else {
+                    for (int c0 = 0; c0 < n; c0 += 32) {
+                        const int e = c0 + lane;
+                        keep_step(e < n ? __float_as_uint(key[e]) : 0xffffffffu, e);
+                    }
                 }
             }
             if (lane == 0) cand_cnt[un.cand / K + i] = kept;
