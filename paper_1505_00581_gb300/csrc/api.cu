@@ -637,6 +637,8 @@ hgm_status run_batch(Exec &ex, const hgm_model *const *models, int nm, const hgm
     const int K = p.K;
     const int F = models[0]->d.F;
     p.F = F;
+    p.max_window = 0;
+    for (int s = 0; s < ns; ++s) p.max_window = std::max(p.max_window, max_window_points(scenes[s], p.window));
 
     // model rows of the unary table (all models of the batch)
     int R = 0, max_M = 0, tmin_all = INT32_MAX, tmax_all = INT32_MIN;
@@ -984,6 +986,7 @@ hgm_status single_pair_units(const hgm_model *m, const hgm_scene *s, const hgm_p
         return fail(HGM_EINVAL, "offsets [%d, %d) outside the valid range [%d, %d)", first, first + n, f0, f0 + nall);
     p = to_params(hp);
     p.F = m->d.F;
+    p.max_window = max_window_points(s, p.window);
     R = m->d.M;
     const int K = p.K;
     const int64_t pitch = round_up4(std::max(s->d.S, 1));
@@ -1033,6 +1036,15 @@ hgm_status single_pair_units(const hgm_model *m, const hgm_scene *s, const hgm_p
 namespace hgm {
 // The parameter check of every matching entry point, for other translation units of the library.
 hgm_status check_match_params(const hgm_params *p) { return check_params(p); }
+
+int32_t max_window_points(const hgm_scene *s, int window)
+{
+    const std::vector<int32_t> &fs = s->fs_host;
+    const int nf = s->d.n_frames, span = 2 * std::max(window, 0) + 1;
+    int32_t best = 0;
+    for (int f = 0; f < nf; ++f) best = std::max(best, fs[(size_t)std::min(nf, f + span)] - fs[(size_t)f]);
+    return best;
+}
 }  // namespace hgm
 
 extern "C" {

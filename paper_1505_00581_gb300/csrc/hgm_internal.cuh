@@ -85,6 +85,7 @@ struct Params {
     int32_t F = 0;       // descriptor row stride (padded width)
     int32_t rescore = 0; // 0, or: recompute the U of the `rescore` smallest candidates per list in FP32
     float dummy = -1.0f; // W^d of the dummy assignment (k_dummy.cu), < 0: none
+    int32_t max_window = 1 << 30;   // most scene points any candidate window of the call can hold (host bound)
 };
 
 constexpr int kRescore = 8;   // candidates per list re-scored in FP32 by the BF16 precision mode
@@ -251,6 +252,8 @@ bool valid_model(const hgm_model *m);
 bool valid_scene(const hgm_scene *s);
 // api.cu: the parameter check shared by the matching entry points (HGM_EINVAL / HGM_EUNSUPPORTED + message).
 hgm_status check_match_params(const hgm_params *p);
+// api.cu: the most points any 2w+1 consecutive frames of the scene hold (the largest candidate window).
+int32_t max_window_points(const hgm_scene *s, int window);
 // noalloc.cu: looks up (once per device) the device address of the fixed scratch of hgm_match_noalloc on the
 // current device, which makes the runtime load the code that holds the scratch, and so create it, now.
 hgm_status noalloc_prepare();

@@ -45,7 +45,9 @@
 // The per-step model constants come from a table built at model creation, and
 // the list C of the next step is fetched from global memory during phase 2 and
 // stored in the buffer of the list A, which phase 3 no longer reads, so no step
-// waits on a global load.
+// waits on a global load. Argmin bytes are written for the tiled cells only, a
+// tile's four at once: the cells past b's time prefix are never on a chain, so
+// the backtrack never reads them.
 #include "backtrack.cuh"
 #include "recurse_common.cuh"
 
@@ -470,27 +472,44 @@ recurse_kernel(const Unit *__restrict__ units, int64_t n_units, const ModelRec *
                             if (v[q] < best[q4 + q]) { best[q4 + q] = v[q]; arg[q4 + q] = a; }
                     }
                 }
+                // argmin bytes of the tile's cells, four at a time (c0 is a multiple of 4, and K, the row
+                // stride, is a multiple of 4 whenever a tile reaches past c0 + 3: the packed store is used
+                // only then)
+                uint32_t packed[CT / 4];
+#pragma unroll
+                for (int q4 = 0; q4 < CT / 4; ++q4) packed[q4] = 0;
 #pragma unroll
                 for (int q = 0; q < CT; ++q) {
                     const int c = c0 + q;
-                    if (c < nc) {
-                        float al = kInf;
-                        int bt = kNoSlot;
-                        if (best[q] < kInf) {
-                            al = cell_alpha(best[q], lam2, dt_bc, tb, tcq[q]);
-                            bt = arg[q];
-                        }
-                        sm.alpha[c * AS + b] = al;
-                        bstep[b * K + c] = (uint8_t)bt;
+                    float al = kInf;
+                    int bt = kNoSlot;
+                    if (best[q] < kInf) {
+                        al = cell_alpha(best[q], lam2, dt_bc, tb, tcq[q]);
+                        bt = arg[q];
+                    }
+                    if (c < nc) sm.alpha[c * AS + b] = al;
+                    packed[q / 4] |= (uint32_t)bt << (8 * (q % 4));
+                }
+                const bool aligned = (K & 3) == 0;
+#pragma unroll
+                for (int q4 = 0; q4 < CT / 4; ++q4) {
+                    const int c = c0 + 4 * q4;
+                    if (aligned && c + 3 < K) {
+                        *reinterpret_cast<uint32_t *>(bstep + b * K + c) = packed[q4];
+                    } else {
+#pragma unroll
+                        for (int q = 0; q < 4; ++q)
+                            if (c + q < nc) bstep[b * K + c + q] = (uint8_t)(packed[q4] >> (8 * q));
                     }
                 }
             }
-            // cells (b, c) beyond the tiled prefix are infeasible
-            for (int b = warp; b < nb; b += NW) {
-                const int covered = sm.tcount[b] * CT;
-                for (int c = covered + lane; c < nc; c += 32) {
-                    sm.alpha[c * AS + b] = kInf;
-                    bstep[b * K + c] = (uint8_t)kNoSlot;
+            // cells (b, c) beyond the tiled prefix are infeasible: the backtrack never reads their argmin (a
+            // chain's cells are feasible) and the next step never reads their alpha (the pair (b, c) is
+            // infeasible there); only the initial pair search of Eq. 13 reads every cell of the last step
+            if (i == 2) {
+                for (int b = warp; b < nb; b += NW) {
+                    const int covered = sm.tcount[b] * CT;
+                    for (int c = covered + lane; c < nc; c += 32) sm.alpha[c * AS + b] = kInf;
                 }
             }
             __syncthreads();

@@ -24,7 +24,6 @@ namespace hgm {
 namespace {
 
 constexpr int kWarps = 8;
-constexpr int kKeyRegs = 20;  // windows of up to 32 x 20 = 640 keys are selected from registers
 
 __device__ __forceinline__ uint32_t lanemask_lt()
 {
@@ -33,7 +32,11 @@ __device__ __forceinline__ uint32_t lanemask_lt()
     return m;
 }
 
-__global__ void __launch_bounds__(kWarps * 32, 2) select_kernel(const Unit *__restrict__ units, int64_t n_units,
+// kKeyRegs keys per lane are held in registers: windows of up to 32 kKeyRegs keys are selected from them,
+// longer ones from memory in every pass. The launch picks 8 (three CTAs per SM) when no window of the call
+// exceeds 256 points, else 20 (two CTAs per SM, the registers the larger arrays need).
+template <int kKeyRegs, int kMinBlocks>
+__global__ void __launch_bounds__(kWarps * 32, kMinBlocks) select_kernel(const Unit *__restrict__ units, int64_t n_units,
                                                              const ModelRec *__restrict__ models,
                                                              const SceneRec *__restrict__ scenes, Params p,
                                                              int32_t *__restrict__ cand_idx,
@@ -68,7 +71,7 @@ __global__ void __launch_bounds__(kWarps * 32, 2) select_kernel(const Unit *__re
                     ou[e] = e < n ? key[e] : __int_as_float(0x7f800000);
                 }
             } else {
-                // radix select of the K-th smallest key (1-based rank kk); windows of up to 256 keys are
+                // radix select of the K-th smallest key (1-based rank kk); windows of up to 32 kKeyRegs keys are
                 // read once into registers (lane + 32 q), longer ones from memory in every pass
                 const bool inreg = n <= 32 * kKeyRegs;
                 uint32_t kb[kKeyRegs];
@@ -220,8 +223,12 @@ cudaError_t launch_select(const Unit *units, int64_t n_units, const ModelRec *mo
     if (n_units <= 0) return cudaSuccess;
     int64_t blocks = n_units < (int64_t)1 << 20 ? n_units : (int64_t)1 << 20;
     prof_begin(kProfSelect, st);
-    select_kernel<<<(unsigned)blocks, kWarps * 32, 0, st>>>(units, n_units, models, scenes, p, cand_idx, cand_u,
-                                                            cand_cnt);
+    if (p.max_window <= 32 * 8)
+        select_kernel<8, 3><<<(unsigned)blocks, kWarps * 32, 0, st>>>(units, n_units, models, scenes, p, cand_idx,
+                                                                      cand_u, cand_cnt);
+    else
+        select_kernel<20, 2><<<(unsigned)blocks, kWarps * 32, 0, st>>>(units, n_units, models, scenes, p, cand_idx,
+                                                                       cand_u, cand_cnt);
     prof_end(kProfSelect, st);
     return cudaGetLastError();
 }
@@ -229,7 +236,8 @@ cudaError_t launch_select(const Unit *units, int64_t n_units, const ModelRec *mo
 cudaError_t preload_select()
 {
     cudaFuncAttributes a;
-    return cudaFuncGetAttributes(&a, select_kernel);
+    cudaError_t e = cudaFuncGetAttributes(&a, select_kernel<8, 3>);
+    return e == cudaSuccess ? cudaFuncGetAttributes(&a, select_kernel<20, 2>) : e;
 }
 
 }  // namespace hgm
