@@ -164,7 +164,8 @@ __global__ void __launch_bounds__(kDummyThreads, 2) dummy_recurse_kernel(
                             const int os = __shfl_xor_sync(full, s, off);
                             if (key_less(om, os, m, s)) { m = om; s = os; }
                         }
-                        if (m < inf) {
+                        // the second bound can only matter below base(b, eps): skip its feasibility scan otherwise
+                        if (m < inf && m + gmax + 1e-6f * fabsf(m) < thr) {
                             // a1 = s must be feasible with every open c and with (b, eps)
                             const int t1 = sm.t[0][s], i1 = sm.id[0][s];
                             bool bad = lane == 0 && p.T > 0 && t1 - tb >= p.T;

@@ -13,16 +13,10 @@
 //
 // The scoring kernel stages 128 candidates per tile (128 / 2^ceil(log2 K)
 // lists) as BF16 and runs layer 2 (128 x 128) as tcgen05.mma with W2 resident
-// in shared memory. The gathers are issued a tile ahead: a tile's candidate
-// indices are loaded into registers while the previous tile is built, and its
-// Q rows and scene frames are copied by cp.async into thread-private shared
-// slots while the previous tile's MMA and epilogue run, so neither of the two
-// dependent global round trips stalls the build. The accumulator is
-// double-buffered in tensor memory: tile k's epilogue (relu(+b2), dot with
-// w3) follows the issue of tile k + 1's MMA, and the two column halves of a
-// row are summed one tile later, so one barrier per tile suffices. The A
-// operand has one buffer: the MMA reading it completes during the next
-// epilogue, before the following build (which waits for it, bounded).
+// in shared memory. Tiles are double-buffered in shared memory and in tensor
+// memory: tile k is gathered while the MMA of tile k - 1 runs, its epilogue
+// (relu(+b2), dot with w3) follows the issue of tile k, and the two column
+// halves of a row are summed one tile later, so one barrier per tile suffices.
 #include "hgm_internal.cuh"
 #include "prop.cuh"
 #include "tc05.cuh"
@@ -39,20 +33,9 @@ constexpr uint32_t kSBO = (H / 8) * 128;   // K = 128 components per row
 constexpr uint32_t kPolls = 1u << 26;
 constexpr float kNegInf = -__builtin_huge_valf();
 
-__device__ __forceinline__ void cp_async16(void *smem, const void *gmem)
-{
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(tc05::smem_u32(smem)), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async4(void *smem, const void *gmem)
-{
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(tc05::smem_u32(smem)), "l"(gmem) : "memory");
-}
-
 struct Smem {
-    unsigned char a[TM * H * 2];     // hidden layer 1 of the tile, BF16, canonical K-major
+    unsigned char a[2][TM * H * 2];  // hidden layer 1 of two tiles, BF16, canonical K-major
     unsigned char w2[H * H * 2];     // W2 (rows = output units), BF16
-    uint4 qs[8][256];                // per thread, its 8 rows' 16-byte Q chunks of the next tile (cp.async)
-    int32_t ts[8][256];              // and those rows' scene frames
     float part[2][2][TM];            // [buffer][column half][row]: half-sums of the last layer
     float b2[H], w3[H];              // layer-2 bias and output weights
     float b3;
@@ -80,7 +63,7 @@ __global__ void fold_xy_kernel(float *__restrict__ rows, int64_t n, const float2
 
 // Final logit of every candidate of every list: scores [n_lists x K] (-inf for empty slots).
 // 256 threads. Building a tile: warp w owns hidden units [32 (w%4), +32) of rows [64 (w/4), +64); lane l
-// takes row 8g + l%8 of each group g of 8 and the 8 units 32 (w%4) + 8 (l/8) .. +8, so a warp gathers 8 BF16
+// takes row 8g + l/4 of each group g of 8 and the 8 units 32 (w%4) + 8 (l%4) .. +8, so a warp reads 8 BF16
 // Q rows as whole 32-byte sectors and writes 4 contiguous core matrices of the A tile. Epilogue: row
 // r = tid % 128, half = tid / 128 owns accumulator columns [64 half, 64 half + 64).
 __global__ void __launch_bounds__(256, 2) prop_score_kernel(const Unit *__restrict__ units, int64_t n_units,
@@ -99,11 +82,10 @@ __global__ void __launch_bounds__(256, 2) prop_score_kernel(const Unit *__restri
     const int lpt = TM >> kp_log2;                                  // lists per tile
     const int lsub = row >> kp_log2, slot = row & ((1 << kp_log2) - 1);
     // build-phase roles
-    // lanes 8q .. 8q+7 of a warp take rows 0..7 of a group for one 16-byte chunk of hidden units, so each
-    // quarter-warp stores one whole core matrix of the A tile (128 contiguous bytes, no bank conflict); the
-    // gathers (cp.async, thread-private slots) still read every row's chunks as whole 32-byte sectors
-    const int bh0 = 32 * (warp & 3) + 8 * (lane >> 3);              // first of this lane's 8 hidden units
-    const int brow0 = 64 * (warp >> 2) + (lane & 7);                 // its row in group 0 (+8 per group)
+    // a row's four 16-byte chunks sit on adjacent lanes (measured faster for the gathers than the
+    // bank-conflict-free order of the A-tile stores)
+    const int bh0 = 32 * (warp & 3) + 8 * (lane & 3);              // first of this lane's 8 hidden units
+    const int brow0 = 64 * (warp >> 2) + (lane >> 2);                // its row in group 0 (+8 per group)
     float w1t[8];                                                    // W1c_t / w for those units
 #pragma unroll
     for (int e = 0; e < 8; ++e) w1t[e] = pi.w1c[(int64_t)(bh0 + e) * pi.dp + 2] * pi.inv_window;
@@ -179,137 +161,97 @@ __global__ void __launch_bounds__(256, 2) prop_score_kernel(const Unit *__restri
         if (o >= 0) scores[o] = v ? sm.b3 + sm.part[b][0][row] + sm.part[b][1][row] : kNegInf;
     };
 
-    // tile cursor: unit u (grid-strided) and the first list i0 of the tile; the fields the gathers need
-    struct Tile {
-        int64_t u, cand, lbase;
-        int i0, M, offset, urow;
-        const int32_t *mt, *st;
-        const __nv_bfloat16 *pq;
-        int64_t ucol0;
-    };
-    auto open_unit = [&](Tile &t, int64_t u) {
-        t.u = u;
-        t.i0 = 0;
-        if (u < n_units) {
-            const Unit un = units[u];
-            const ModelRec &md = models[un.model];
-            const SceneRec &sc = scenes[un.scene];
-            t.cand = un.cand;
-            t.lbase = un.cand / K;
-            t.M = md.M;
-            t.offset = un.offset;
-            t.urow = md.urow;
-            t.mt = md.t;
-            t.st = sc.t;
-            t.pq = sc.pq;
-            t.ucol0 = sc.ucol0;
-        }
-    };
-    // the candidate indices of this thread's 8 rows of tile t (bit g of the mask: row g is a candidate)
-    auto gather_idx = [&](const Tile &t, int (&jg)[8]) {
-        uint32_t vm = 0;
+    for (int64_t u = blockIdx.x; u < n_units && !stop; u += gridDim.x) {
+        const Unit un = units[u];
+        const ModelRec md = models[un.model];
+        const SceneRec sc = scenes[un.scene];
+        const int M = md.M;
+        const int64_t lbase = un.cand / K;
+        for (int i0 = 0; i0 < M; i0 += lpt) {
+            const int buf = (int)(k & 1);
+            unsigned char *arow = sm.a[buf];
+            // gather: the 8 row groups' candidate indices first, then their frames and Q chunks
+            int jg[8];
+            bool vg[8];
 #pragma unroll
-        for (int g = 0; g < 8; ++g) {
-            const int r = brow0 + 8 * g, lst = t.i0 + (r >> kp_log2), sl = r & ((1 << kp_log2) - 1);
-            const bool v = t.u < n_units && lst < t.M && sl < cand_cnt[t.lbase + (lst < t.M ? lst : 0)];
-            jg[g] = v ? cand_idx[t.cand + (int64_t)lst * K + sl] : 0;
-            vm |= (uint32_t)v << g;
-        }
-        return vm;
-    };
-    // their Q chunks and frames into this thread's staging slots (completion: cp.async.wait_all)
-    auto gather_rows = [&](const Tile &t, const int (&jg)[8], uint32_t vm) {
-#pragma unroll
-        for (int g = 0; g < 8; ++g)
-            if ((vm >> g) & 1u) {
-                cp_async16(&sm.qs[g][tid], t.pq + (int64_t)(jg[g] - t.ucol0) * H + bh0);
-                cp_async4(&sm.ts[g][tid], t.st + jg[g]);
+            for (int g = 0; g < 8; ++g) {
+                const int r = brow0 + 8 * g, lst = i0 + (r >> kp_log2), sl = r & ((1 << kp_log2) - 1);
+                // count and index loaded together (the slot clamped into the unit's lists), so the index load
+                // does not wait for the count
+                const int lc = lst < M ? lst : M - 1, sc_ = sl < K ? sl : K - 1;
+                const int cnt = cand_cnt[lbase + lc];
+                const int jraw = cand_idx[un.cand + (int64_t)lc * K + sc_];
+                vg[g] = lst < M && sl < cnt;
+                jg[g] = vg[g] ? jraw : 0;
             }
-        asm volatile("cp.async.commit_group;" ::: "memory");
-    };
-
-    Tile cur;
-    open_unit(cur, blockIdx.x);
-    int jn[8];
-    uint32_t vcur = gather_idx(cur, jn);
-    gather_rows(cur, jn, vcur);
-    while (cur.u < n_units && !stop) {
-        Tile nxt = cur;
-        nxt.i0 += lpt;
-        if (nxt.i0 >= nxt.M) open_unit(nxt, cur.u + gridDim.x);
-        const uint32_t vnxt = gather_idx(nxt, jn);   // in flight during this tile's build
-        asm volatile("cp.async.wait_all;" ::: "memory");
-        // the single A buffer: the MMA of tile k - 1 must have read it (it ran during the last epilogue)
-        if (k >= 1) {
-            const int pb = (int)((k - 1) & 1);
-            if (!tc05::mbar_wait(&sm.mbar[pb], (parity >> pb) & 1u, kPolls)) {
-                bad = true;
-                if (lane == 0) atomicExch(status, 1);
-            }
-        }
-        unsigned char *arow = sm.a;
-        int plist = -1;
-        float pv[8];
+            int tg[8];
+            uint4 qg[8];
 #pragma unroll
-        for (int g = 0; g < 8; ++g) {
-            const int r = brow0 + 8 * g, lst = cur.i0 + (r >> kp_log2);
-            __align__(16) __nv_bfloat162 hh[4];
-            if ((vcur >> g) & 1u) {
-                if (lst != plist) {   // the row's list: this lane's 8 units of P (rows of a group share it)
-                    const float4 *P4 = reinterpret_cast<const float4 *>(pi.P + (int64_t)(cur.urow + lst) * H + bh0);
-                    const float4 pa = __ldg(P4), pb = __ldg(P4 + 1);
-                    pv[0] = pa.x; pv[1] = pa.y; pv[2] = pa.z; pv[3] = pa.w;
-                    pv[4] = pb.x; pv[5] = pb.y; pv[6] = pb.z; pv[7] = pb.w;
-                    plist = lst;
+            for (int g = 0; g < 8; ++g) {
+                if (vg[g]) {
+                    tg[g] = sc.t[jg[g]];
+                    qg[g] = __ldg(reinterpret_cast<const uint4 *>(sc.pq + (int64_t)(jg[g] - sc.ucol0) * H + bh0));
+                } else {
+                    tg[g] = 0;
+                    qg[g] = make_uint4(0, 0, 0, 0);
                 }
-                const uint4 qg = sm.qs[g][tid];
-                const float dt = (float)(sm.ts[g][tid] - cur.mt[lst] - cur.offset);
-                const __nv_bfloat162 *q2 = reinterpret_cast<const __nv_bfloat162 *>(&qg);
-#pragma unroll
-                for (int e = 0; e < 4; ++e) {   // two hidden units per packed FP32x2 add and FMA
-                    const float2 qf = __bfloat1622float2(q2[e]);
-                    float x0, x1;
-                    upk2(fma2(pk2(w1t[2 * e], w1t[2 * e + 1]), pk2(dt, dt),
-                              add2(pk2(pv[2 * e], pv[2 * e + 1]), pk2(qf.x, qf.y))),
-                         x0, x1);
-                    hh[e] = __floats2bfloat162_rn(fmaxf(x0, 0.0f), fmaxf(x1, 0.0f));
-                }
-            } else {
-#pragma unroll
-                for (int e = 0; e < 4; ++e) hh[e] = __floats2bfloat162_rn(0.0f, 0.0f);
             }
-            *reinterpret_cast<uint4 *>(arow + tc05::kmajor_offset(r, bh0, kLBO, kSBO)) =
-                *reinterpret_cast<uint4 *>(hh);
+            int plist = -1;
+            float pv[8];
+#pragma unroll
+            for (int g = 0; g < 8; ++g) {
+                const int r = brow0 + 8 * g, lst = i0 + (r >> kp_log2);
+                __align__(16) __nv_bfloat162 hh[4];
+                if (vg[g]) {
+                    if (lst != plist) {   // the row's list: this lane's 8 units of P (rows of a group share it)
+                        const float4 *P4 = reinterpret_cast<const float4 *>(pi.P + (int64_t)(md.urow + lst) * H + bh0);
+                        const float4 pa = __ldg(P4), pb = __ldg(P4 + 1);
+                        pv[0] = pa.x; pv[1] = pa.y; pv[2] = pa.z; pv[3] = pa.w;
+                        pv[4] = pb.x; pv[5] = pb.y; pv[6] = pb.z; pv[7] = pb.w;
+                        plist = lst;
+                    }
+                    const float dt = (float)(tg[g] - md.t[lst] - un.offset);
+                    const __nv_bfloat162 *q2 = reinterpret_cast<const __nv_bfloat162 *>(&qg[g]);
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {   // two hidden units per packed FP32x2 add and FMA
+                        const float2 qf = __bfloat1622float2(q2[e]);
+                        float x0, x1;
+                        upk2(fma2(pk2(w1t[2 * e], w1t[2 * e + 1]), pk2(dt, dt),
+                                  add2(pk2(pv[2 * e], pv[2 * e + 1]), pk2(qf.x, qf.y))),
+                             x0, x1);
+                        hh[e] = __floats2bfloat162_rn(fmaxf(x0, 0.0f), fmaxf(x1, 0.0f));
+                    }
+                } else {
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) hh[e] = __floats2bfloat162_rn(0.0f, 0.0f);
+                }
+                *reinterpret_cast<uint4 *>(arow + tc05::kmajor_offset(r, bh0, kLBO, kSBO)) =
+                    *reinterpret_cast<uint4 *>(hh);
+            }
+            // this thread's epilogue row
+            const int list = i0 + lsub;
+            const bool valid = list < M && slot < cand_cnt[lbase + (list < M ? list : 0)];
+            const int64_t o0 = (half == 0 && list < M && slot < K) ? (lbase + list) * K + slot : -1;
+            tc05::fence_proxy_async_smem();
+            tc05::fence_before_sync();
+            stop = __syncthreads_or(bad) != 0;
+            tc05::fence_after_sync();
+            if (stop) break;
+            final_score(o2, v2, buf);   // tile k-2: both halves were written in the previous iteration
+            if (tid == 0) {
+                const uint32_t a0 = tc05::smem_u32(arow), b0 = tc05::smem_u32(sm.w2);
+                for (int ks = 0; ks < H / 16; ++ks)
+                    tc05::mma_bf16(taddr + (uint32_t)(H * buf), tc05::smem_desc(a0 + ks * 2 * kLBO, kLBO, kSBO),
+                                   tc05::smem_desc(b0 + ks * 2 * kLBO, kLBO, kSBO), idesc, ks > 0);
+                tc05::mma_commit(&sm.mbar[buf]);
+            }
+            pending |= 1u << buf;
+            if (k >= 1) epilogue(buf ^ 1);
+            o2 = o1; v2 = v1;
+            o1 = o0; v1 = valid;
+            ++k;
         }
-        // the staging slots are free again: the next tile's rows start arriving
-        gather_rows(nxt, jn, vnxt);
-        // this thread's epilogue row
-        const int list = cur.i0 + lsub;
-        const bool valid = list < cur.M && slot < cand_cnt[cur.lbase + (list < cur.M ? list : 0)];
-        const int64_t o0 = (half == 0 && list < cur.M && slot < K) ? (cur.lbase + list) * K + slot : -1;
-        const int buf = (int)(k & 1);
-        tc05::fence_proxy_async_smem();
-        tc05::fence_before_sync();
-        stop = __syncthreads_or(bad) != 0;
-        tc05::fence_after_sync();
-        if (stop) break;
-        final_score(o2, v2, buf);   // tile k-2: both halves were written in the previous iteration
-        if (tid == 0) {
-            const uint32_t a0 = tc05::smem_u32(arow), b0 = tc05::smem_u32(sm.w2);
-            for (int ks = 0; ks < H / 16; ++ks)
-                tc05::mma_bf16(taddr + (uint32_t)(H * buf), tc05::smem_desc(a0 + ks * 2 * kLBO, kLBO, kSBO),
-                               tc05::smem_desc(b0 + ks * 2 * kLBO, kLBO, kSBO), idesc, ks > 0);
-            tc05::mma_commit(&sm.mbar[buf]);
-        }
-        pending |= 1u << buf;
-        if (k >= 1) epilogue(buf ^ 1);
-        o2 = o1; v2 = v1;
-        o1 = o0; v1 = valid;
-        ++k;
-        cur = nxt;
-        vcur = vnxt;
     }
-    asm volatile("cp.async.wait_all;" ::: "memory");   // no copy may land after the CTA exits
     // drain: the last iteration's reads of part[] (tile k-3) come before the last tile's epilogue writes
     tc05::fence_before_sync();
     stop = __syncthreads_or(bad) != 0;
@@ -514,7 +456,7 @@ cudaError_t launch_prop_score(const Unit *units, int64_t n_units, const ModelRec
     int dev = 0, sms = 0;
     if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
     if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-    // two CTAs per SM: 2 x ~108 KB of shared memory, 2 x 256 of the SM's 512 TMEM columns
+    // two CTAs per SM: 2 x ~101 KB of shared memory, 2 x 256 of the SM's 512 TMEM columns
     const int64_t grid = std::min<int64_t>(n_units, (int64_t)sms * 2);
     prop_score_kernel<<<(unsigned)grid, 256, smem, st>>>(units, n_units, models, scenes, p, pi, kp_log2, cand_idx,
                                                          cand_cnt, scores, status);
