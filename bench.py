@@ -42,8 +42,8 @@ L2_NOTE = "flushed (512 MiB write) before every step"
 # a small case, with the sources of the kernel it captured and the capture's argmin-table bytes
 # sum n_offsets (M - 2) K^2. Both the tables written and the lists read grow in proportion to that sum,
 # so a full launch's traffic is scaled by it; a changed kernel source voids the figure.
-RECURSE_NCU = {"sources_sha256": "142bae4331dc3a7b18edefa543aed14bbd5a624949445c5da4791af45f3afeb0",
-               "bytes": 52_798_720 + 333_985_024, "beta_bytes": 393_031_680, "case": "batched_small"}
+RECURSE_NCU = {"sources_sha256": "79958b1f0a94cd03b633d216f8d6648011a21dd6f9f811969b90b30731098cbf",
+               "bytes": 846_869_248 + 1_285_779_456, "beta_bytes": 1_667_760_128, "case": "combined_small"}
 RECURSE_SOURCES = ("k_recurse.cu", "recurse_common.cuh", "f32x2.cuh")
 
 
@@ -484,6 +484,18 @@ def fp64_errors(sampled, wl, first, es, as_, e_h, a_h):
             "assignment_equal": same / max(len(sampled), 1)}
 
 
+def dump_sample(args, wl, first, es, e_exact, e_bf16):
+    """The exact and BF16 forms' energies at a seeded sample of the units, for an FP64 check off the GPU machine
+    (tests/fp64_sample_report.py solves the same units with the oracle)."""
+    n_s = max(1, int(round(args.fp64_sample_frac * total_units(wl))))
+    picks = np.array(sample_units(wl, n_s, 21), dtype=np.int64)
+    rows = np.array([int(es[m_ * len(wl.scenes) + s_]) + o_ - int(first[m_ * len(wl.scenes) + s_])
+                     for m_, s_, o_ in picks], dtype=np.int64)
+    np.savez(args.fp64_dump, workload=args.workload, hop=args.hop, units=picks, e_exact=e_exact[rows],
+             e_bf16=e_bf16[rows])
+    return {"path": args.fp64_dump, "units": int(n_s), "fraction": args.fp64_sample_frac}
+
+
 def run_pruned(args, torch, hgm, wl, job_cs, models, scenes, energy, assign, first, es, as_, dev, stream, world,
                flush, sampled, dist=None):
     """The BF16-distance + learned-pruning forms on the same batch: BF16 tensor-core unary table, the
@@ -496,7 +508,9 @@ def run_pruned(args, torch, hgm, wl, job_cs, models, scenes, energy, assign, fir
     a_ref = assign.cpu().numpy().copy()
     t0 = time.time()
     rank = int(os.environ.get("RANK", "0"))
-    if args.checkpoint:
+    if args.no_network:
+        prop, info = None, {}
+    elif args.checkpoint:
         prop, info = prop_train.load_checkpoint(args.checkpoint), {"checkpoint": args.checkpoint}
     else:
         train_wl = job_cs.training_scenes(101 + 1000 * rank) if job_cs is not None else None
@@ -540,6 +554,13 @@ def run_pruned(args, torch, hgm, wl, job_cs, models, scenes, energy, assign, fir
                             "ms_per_step": g_ms}
         return out, prof
 
+    if prop is None:   # the precision form alone (no learned stage)
+        out, _ = form(params_of(hgm, wl, precision=1),
+                      "BF16 unary + FP32 re-score of the 8 smallest of every list, no pruning", True)
+        out["speedup_note"] = "precision form only (--no-network)"
+        if args.fp64_dump:
+            out["fp64_dump"] = dump_sample(args, wl, first, es, e_ref, e2.cpu().numpy())
+        return out
     # keep 8 is the configuration the learned stage is specified with; on the combined workload (models of up
     # to 256 points) most units have no time-ordered chain through 8 candidates per point and fall back to the
     # exact solve, so its main form keeps 16
@@ -567,6 +588,8 @@ def run_pruned(args, torch, hgm, wl, job_cs, models, scenes, energy, assign, fir
     pruned["refined"].update(keep=rkeep, refine=refine)
     pruned["bf16_unpruned"], _ = form(params_of(hgm, wl, precision=1),
                                       "BF16 unary + FP32 re-score of the 8 smallest of every list, no pruning")
+    if args.fp64_dump:
+        pruned["fp64_dump"] = dump_sample(args, wl, first, es, e_ref, e2.cpu().numpy())
     # the same cut without the network: the 8 smallest unary costs (K = 8 window cap), BF16 + re-score
     pb = params_of(hgm, wl, K=8, precision=1)
     _, es8, as8 = hgm.batch_layout(models, scenes, pb)
@@ -604,6 +627,11 @@ def main():
                     help="comma list of extra forms: chains,dummy (default: both on batched_exact only)")
     ap.add_argument("--refine", type=int, default=None, help="refined pruned form: offsets re-solved per pair")
     ap.add_argument("--keep", type=int, default=None, help="pruned form: candidates kept per list")
+    ap.add_argument("--no-network", action="store_true",
+                    help="pruned_bf16 holds only the BF16-distance form (no proposal network is trained)")
+    ap.add_argument("--fp64-dump", default=None,
+                    help="write the exact and BF16 forms' energies at a seeded sample of units to this .npz")
+    ap.add_argument("--fp64-sample-frac", type=float, default=0.01, help="fraction of units in --fp64-dump")
     ap.add_argument("--train-steps", type=int, default=2000)
     ap.add_argument("--checkpoint", default=None, help="load the proposal network from <path>.bin/.json")
     args = ap.parse_args()

@@ -40,6 +40,7 @@ struct DummySmem {
     uint8_t srt[kL][kMaxK];            // per row b: the kept real a by increasing base(b, a) (ties: lower slot)
     uint8_t kept[kL];                  // per row b: how many a srt[b] holds
     int cnt[3];
+    float ang[2];                      // the step's model angles A1, A2 (one thread computes them)
 };
 static_assert(2 * (sizeof(DummySmem) + 1024 + 128) <= 228 * 1024, "two CTAs per SM");
 
@@ -94,9 +95,13 @@ __global__ void __launch_bounds__(kDummyThreads, 2) dummy_recurse_kernel(
         const int32_t *ccnt = cand_cnt + un.cand / K;
         int cur = 0;
         for (int i = M - 1; i >= 2; --i) {
-            // lists of this step: slot s < cnt real, slot K eps
-            for (int e = threadIdx.x; e < 3 * L; e += blockDim.x) {
-                const int w = (int)__umulhi((unsigned)e, divL), s = e - w * L, li = i - w;
+            // list buffers rotate with the chain index (list i in buffer i % 3): the first step loads the three
+            // lists, every later step only list i - 2; slot s < cnt real, slot K eps
+            const int sA = i % 3, sB = (i - 1) % 3, sC = (i - 2) % 3;
+            const int nload = i == M - 1 ? 3 : 1, w0 = i == M - 1 ? 0 : 2;
+            for (int e = threadIdx.x; e < nload * L; e += blockDim.x) {
+                const int q = (int)__umulhi((unsigned)e, divL), s = e - q * L, li = i - (w0 + q);
+                const int w = li % 3;
                 const int n = ccnt[li];
                 if (s < n) {
                     const int j = cidx[(int64_t)li * K + s];
@@ -112,12 +117,15 @@ __global__ void __launch_bounds__(kDummyThreads, 2) dummy_recurse_kernel(
                 }
                 if (s == 0) sm.cnt[w] = n;
             }
+            if (threadIdx.x == 0) {
+                const float2 mi = md.xy[i], mj = md.xy[i - 1], mk = md.xy[i - 2];
+                sm.ang[0] = signed_angle(mj, mi, mk);   // A1: at i-1, from ->i to ->i-2
+                sm.ang[1] = signed_angle(mi, mj, mk);   // A2: at i, from ->i-1 to ->i-2
+            }
             __syncthreads();
-            const float2 mi = md.xy[i], mj = md.xy[i - 1], mk = md.xy[i - 2];
-            const float A1 = signed_angle(mj, mi, mk);   // at i-1, from ->i to ->i-2
-            const float A2 = signed_angle(mi, mj, mk);   // at i, from ->i-1 to ->i-2
+            const float A1 = sm.ang[0], A2 = sm.ang[1];
             const int dt1 = md.t[i] - md.t[i - 1], dt2 = md.t[i - 1] - md.t[i - 2];
-            const int na = sm.cnt[0], nb = sm.cnt[1], nc = sm.cnt[2];
+            const int na = sm.cnt[sA], nb = sm.cnt[sB], nc = sm.cnt[sC];
             const float *an = sm.alpha[cur];
             const bool last = i == M - 1;
             // base(b, a) and directions; rows/columns of empty slots are never read
@@ -127,13 +135,13 @@ __global__ void __launch_bounds__(kDummyThreads, 2) dummy_recurse_kernel(
                 if ((ra || a == E) && (rb || b == E)) {
                     const float al = last ? 0.0f : an[a * L + b];   // alpha_{i+1}(z_i = a, z_{i-1} = b)
                     float bs;
-                    if (ra && rb) bs = base_cost(sm.u[0][a], lam2, dt1, sm.t[0][a], sm.t[1][b], al);
-                    else bs = __fadd_rn(sm.u[0][a], al);
+                    if (ra && rb) bs = base_cost(sm.u[sA][a], lam2, dt1, sm.t[sA][a], sm.t[sB][b], al);
+                    else bs = __fadd_rn(sm.u[sA][a], al);
                     sm.base[b * L + a] = bs;
                 }
                 const int a2 = b, c = a;   // R(a, c) over the same index space, where (a, c) can be feasible
-                if (a2 < na && c < nc && sm.t[2][c] <= sm.t[0][a2] && !(p.T > 0 && sm.t[0][a2] - sm.t[2][c] >= p.T))
-                    sm.r[a2 * kRL + c] = direction(sm.xy[0][a2], sm.xy[2][c]);
+                if (a2 < na && c < nc && sm.t[sC][c] <= sm.t[sA][a2] && !(p.T > 0 && sm.t[sA][a2] - sm.t[sC][c] >= p.T))
+                    sm.r[a2 * kRL + c] = direction(sm.xy[sA][a2], sm.xy[sC][c]);
             }
             __syncthreads();
             // branch and bound (exact): v(a, b, c) >= base(b, a), and no open cell of row b has a best above
@@ -146,12 +154,12 @@ __global__ void __launch_bounds__(kDummyThreads, 2) dummy_recurse_kernel(
                     if (!(b < nb || b == E)) continue;
                     const bool rb = b < nb;
                     const float *brow = sm.base + b * L;
-                    const int tb = rb ? sm.t[1][b] : 0, ib = rb ? sm.id[1][b] : -3;
+                    const int tb = rb ? sm.t[sB][b] : 0, ib = rb ? sm.id[sB][b] : -3;
                     float key[2];
 #pragma unroll
                     for (int h = 0; h < 2; ++h) {
                         const int a = lane + 32 * h;
-                        key[h] = a < na && (!rb || (sm.id[0][a] != ib && sm.t[0][a] >= tb)) ? brow[a] : inf;
+                        key[h] = a < na && (!rb || (sm.id[sA][a] != ib && sm.t[sA][a] >= tb)) ? brow[a] : inf;
                     }
                     float thr = brow[E];
                     if (rb) {
@@ -167,10 +175,10 @@ __global__ void __launch_bounds__(kDummyThreads, 2) dummy_recurse_kernel(
                         // the second bound can only matter below base(b, eps): skip its feasibility scan otherwise
                         if (m < inf && m + gmax + 1e-6f * fabsf(m) < thr) {
                             // a1 = s must be feasible with every open c and with (b, eps)
-                            const int t1 = sm.t[0][s], i1 = sm.id[0][s];
+                            const int t1 = sm.t[sA][s], i1 = sm.id[sA][s];
                             bool bad = lane == 0 && p.T > 0 && t1 - tb >= p.T;
                             for (int c = lane; c < nc; c += 32) {
-                                const int tc = sm.t[2][c], ic = sm.id[2][c];
+                                const int tc = sm.t[sC][c], ic = sm.id[sC][c];
                                 const bool open = ic != ib && tc <= tb && (p.T <= 0 || tb - tc < p.T);
                                 if (open && (i1 == ic || (p.T > 0 && t1 - tc >= p.T))) bad = true;
                             }
@@ -200,11 +208,11 @@ __global__ void __launch_bounds__(kDummyThreads, 2) dummy_recurse_kernel(
                     if (rb) {
                         __syncwarp();
                         const int nk = __popc(m0) + __popc(m1);
-                        const float2 xb = sm.xy[1][b];
+                        const float2 xb = sm.xy[sB][b];
                         for (int r = lane; r < nk; r += 32) {
                             const int a = sm.srt[b][r];
-                            sm.p1[b * L + a] = __fadd_rn(A1, direction(xb, sm.xy[0][a]));
-                            sm.p2[b * L + a] = __fadd_rn(A2, direction(sm.xy[0][a], xb));
+                            sm.p1[b * L + a] = __fadd_rn(A1, direction(xb, sm.xy[sA][a]));
+                            sm.p2[b * L + a] = __fadd_rn(A2, direction(sm.xy[sA][a], xb));
                         }
                     }
                 }
@@ -218,7 +226,7 @@ __global__ void __launch_bounds__(kDummyThreads, 2) dummy_recurse_kernel(
             const unsigned divG = 0xffffffffu / (unsigned)max(G, 2) + 1u;   // e / G as for e / L
             for (int e = threadIdx.x; e < nb * G; e += blockDim.x) {
                 const int b = G == 1 ? e : (int)__umulhi((unsigned)e, divG), c0 = 4 * (e - b * G);
-                const int tb = sm.t[1][b], ib = sm.id[1][b];
+                const int tb = sm.t[sB][b], ib = sm.id[sB][b];
                 const float *brow = sm.base + b * L;
                 const int nk = sm.kept[b];   // 0: every open cell of the group takes eps, no direction needed
                 float best[4], q1[4];
@@ -228,10 +236,10 @@ __global__ void __launch_bounds__(kDummyThreads, 2) dummy_recurse_kernel(
                 for (int q = 0; q < 4; ++q) {
                     const int c = c0 + q;
                     const bool inc = c < nc;
-                    tcq[q] = inc ? sm.t[2][c] : 0;
-                    icq[q] = inc ? sm.id[2][c] : -3;
+                    tcq[q] = inc ? sm.t[sC][c] : 0;
+                    icq[q] = inc ? sm.id[sC][c] : -3;
                     open[q] = inc && icq[q] != ib && tcq[q] <= tb && (p.T <= 0 || tb - tcq[q] < p.T);
-                    q1[q] = open[q] && nk > 0 ? direction(sm.xy[1][b], sm.xy[2][c]) : 0.0f;
+                    q1[q] = open[q] && nk > 0 ? direction(sm.xy[sB][b], sm.xy[sC][c]) : 0.0f;
                     best[q] = open[q] ? brow[E] : inf;   // (eps, b, c) is feasible with every open cell
                     arg[q] = open[q] ? E : 255;
                 }
@@ -247,7 +255,7 @@ __global__ void __launch_bounds__(kDummyThreads, 2) dummy_recurse_kernel(
                     for (int q = 0; q < 4; ++q) bmax = fmaxf(bmax, open[q] ? best[q] : -inf);
                     if (ba > bmax) break;
                     if constexpr (kCount) n_eval += nopen;
-                    const int ta = sm.t[0][a], ia = sm.id[0][a];   // kept: ia != ib, ta >= tb
+                    const int ta = sm.t[sA][a], ia = sm.id[sA][a];   // kept: ia != ib, ta >= tb
                     const float p1 = sm.p1[b * L + a], p2 = sm.p2[b * L + a];
                     // R past the last c is never initialised: those lanes of v are discarded (open is false)
                     const float4 r4 = *reinterpret_cast<const float4 *>(sm.r + a * kRL + c0);
@@ -281,16 +289,16 @@ __global__ void __launch_bounds__(kDummyThreads, 2) dummy_recurse_kernel(
                 const bool rb = b < nb, rc = c < nc;
                 const float *brow = sm.base + b * L;
                 const uint8_t *order = sm.srt[b];
-                const int tr = rc ? sm.t[2][c] : (rb ? sm.t[1][b] : 0);   // the other real point
-                const int ir = rc ? sm.id[2][c] : (rb ? sm.id[1][b] : -3);
+                const int tr = rc ? sm.t[sC][c] : (rb ? sm.t[sB][b] : 0);   // the other real point
+                const int ir = rc ? sm.id[sC][c] : (rb ? sm.id[sB][b] : -3);
                 const bool any = !rb && !rc;
                 float best = inf;
                 int arg = 255;
                 const int nk = sm.kept[b];
                 for (int k = 0; k < nk; ++k) {
                     const int a = order[k];
-                    const int ta = sm.t[0][a];
-                    if (!any && (sm.id[0][a] == ir || ta < tr || (p.T > 0 && ta - tr >= p.T))) continue;
+                    const int ta = sm.t[sA][a];
+                    if (!any && (sm.id[sA][a] == ir || ta < tr || (p.T > 0 && ta - tr >= p.T))) continue;
                     best = brow[a];
                     arg = a;
                     break;
