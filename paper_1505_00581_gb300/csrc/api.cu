@@ -153,6 +153,7 @@ struct Workspace {
     Buffer fb_total;   // fallback units since the last hgm_prune_counters reset (device counter)
     Buffer chain_e, chain_a, chain_tab, chain_oe, chain_oa;   // independent-chains variant
     Buffer rf_e, rf_a;        // refinement of the pruned form: device outputs when the caller's are on the host
+    Buffer ubf;               // precision mode: BF16 copies of the unary table's operands (TMA-staged kernel)
     Buffer beta_dummy;        // per-CTA argmin tables of the dummy-assignment recursion
 };
 
@@ -638,7 +639,7 @@ hgm_status run_batch(Exec &ex, const hgm_model *const *models, int nm, const hgm
     const int F = models[0]->d.F;
     p.F = F;
     p.max_window = 0;
-    for (int s = 0; s < ns; ++s) p.max_window = std::max(p.max_window, max_window_points(scenes[s], p.window));
+    for (int s = 0; s < ns; ++s) p.max_window = std::max(p.max_window, typical_window_points(scenes[s], p.window));
 
     // model rows of the unary table (all models of the batch)
     int R = 0, max_M = 0, tmin_all = INT32_MAX, tmax_all = INT32_MIN;
@@ -807,7 +808,10 @@ hgm_status run_batch(Exec &ex, const hgm_model *const *models, int nm, const hgm
         }
         CK(ws.srec.ensure((size_t)ng * sizeof(SceneRec)), "workspace");
         if ((rc = h2d(ex, ws.srec.p, srec.data(), (size_t)ng * sizeof(SceneRec), st))) return rc;
-        if (hp->precision == 1) CK(ws.snorm.ensure((size_t)std::max<int64_t>(smax, 1) * sizeof(float)), "workspace");
+        if (hp->precision == 1) {
+            CK(ws.snorm.ensure((size_t)std::max<int64_t>(smax, 1) * sizeof(float)), "workspace");
+            CK(ws.ubf.ensure(unary_bf16_scratch_bytes(R, smax, F)), "workspace (BF16 operands)");
+        }
         for (int g = 0; g < ng; ++g) {
             const Segment &sg = segs[gbegin + g];
             const SceneDev &d = scenes[sg.s]->d;
@@ -818,7 +822,7 @@ hgm_status run_batch(Exec &ex, const hgm_model *const *models, int nm, const hgm
                 CK(launch_sqnorm_bf16(segf, pts, F, F, ws.snorm.as<float>(), st), "norm kernel");
                 CK(launch_unary_bf16(ws.modelcat.as<float>(), R, segf, pts, F, F, ws.mnorm.as<float>(),
                                      ws.snorm.as<float>(), p.lambda1, U, srec[(size_t)g].upitch,
-                                     ws.status.as<int>(), st),
+                                     ws.status.as<int>(), ws.ubf.p, ws.ubf.bytes, st),
                    "BF16 unary kernel");
             } else {
                 CK(launch_unary(ws.modelcat.as<float>(), R, segf, pts, F, p.lambda1, U, (int)srec[(size_t)g].upitch,
@@ -986,7 +990,7 @@ hgm_status single_pair_units(const hgm_model *m, const hgm_scene *s, const hgm_p
         return fail(HGM_EINVAL, "offsets [%d, %d) outside the valid range [%d, %d)", first, first + n, f0, f0 + nall);
     p = to_params(hp);
     p.F = m->d.F;
-    p.max_window = max_window_points(s, p.window);
+    p.max_window = typical_window_points(s, p.window);
     R = m->d.M;
     const int K = p.K;
     const int64_t pitch = round_up4(std::max(s->d.S, 1));
@@ -1005,8 +1009,10 @@ hgm_status single_pair_units(const hgm_model *m, const hgm_scene *s, const hgm_p
         CK(cudaMemsetAsync(g_ws.status.p, 0, sizeof(int), st), "memset");
         CK(launch_sqnorm_bf16(m->d.f, R, m->d.F, m->d.F, g_ws.mnorm.as<float>(), st), "norm kernel");
         CK(launch_sqnorm_bf16(s->d.f, s->d.S, m->d.F, m->d.F, g_ws.snorm.as<float>(), st), "norm kernel");
+        CK(g_ws.ubf.ensure(unary_bf16_scratch_bytes(R, s->d.S, m->d.F)), "workspace (BF16 operands)");
         CK(launch_unary_bf16(m->d.f, R, s->d.f, s->d.S, m->d.F, m->d.F, g_ws.mnorm.as<float>(), g_ws.snorm.as<float>(),
-                             p.lambda1, g_ws.U.as<float>(), pitch, g_ws.status.as<int>(), st),
+                             p.lambda1, g_ws.U.as<float>(), pitch, g_ws.status.as<int>(), g_ws.ubf.p, g_ws.ubf.bytes,
+                             st),
            "BF16 unary kernel");
     } else {
         CK(launch_unary(m->d.f, R, s->d.f, s->d.S, m->d.F, p.lambda1, g_ws.U.as<float>(), (int)pitch, st),
@@ -1037,13 +1043,12 @@ namespace hgm {
 // The parameter check of every matching entry point, for other translation units of the library.
 hgm_status check_match_params(const hgm_params *p) { return check_params(p); }
 
-int32_t max_window_points(const hgm_scene *s, int window)
+int32_t typical_window_points(const hgm_scene *s, int window)
 {
-    const std::vector<int32_t> &fs = s->fs_host;
-    const int nf = s->d.n_frames, span = 2 * std::max(window, 0) + 1;
-    int32_t best = 0;
-    for (int f = 0; f < nf; ++f) best = std::max(best, fs[(size_t)std::min(nf, f + span)] - fs[(size_t)f]);
-    return best;
+    const int nf = s->d.n_frames;
+    if (nf <= 0) return 0;
+    const int64_t span = std::min<int64_t>(2 * std::max(window, 0) + 1, nf);
+    return (int32_t)(((int64_t)s->d.S * span + nf - 1) / nf);
 }
 }  // namespace hgm
 
@@ -2097,8 +2102,9 @@ hgm_status hgm_unary_bf16(const hgm_model *model, const hgm_scene *scene, float 
     CK(cudaMemsetAsync(g_ws.status.p, 0, sizeof(int), st), "memset");
     CK(launch_sqnorm_bf16(model->d.f, M, F, F, g_ws.mnorm.as<float>(), st), "norm kernel");
     CK(launch_sqnorm_bf16(scene->d.f, S, F, F, g_ws.snorm.as<float>(), st), "norm kernel");
+    CK(g_ws.ubf.ensure(unary_bf16_scratch_bytes(M, S, F)), "workspace (BF16 operands)");
     CK(launch_unary_bf16(model->d.f, M, scene->d.f, S, F, F, g_ws.mnorm.as<float>(), g_ws.snorm.as<float>(), lambda1,
-                         U, S, g_ws.status.as<int>(), st),
+                         U, S, g_ws.status.as<int>(), g_ws.ubf.p, g_ws.ubf.bytes, st),
        "BF16 unary kernel");
     int status = 0;
     CK(cudaMemcpyAsync(&status, g_ws.status.p, sizeof(int), cudaMemcpyDeviceToHost, st), "status");

@@ -85,7 +85,8 @@ struct Params {
     int32_t F = 0;       // descriptor row stride (padded width)
     int32_t rescore = 0; // 0, or: recompute the U of the `rescore` smallest candidates per list in FP32
     float dummy = -1.0f; // W^d of the dummy assignment (k_dummy.cu), < 0: none
-    int32_t max_window = 1 << 30;   // most scene points any candidate window of the call can hold (host bound)
+    int32_t max_window = 1 << 30;   // scene points of a typical candidate window of the call (host estimate from
+                                    // the scenes' mean density; longer windows are still selected, from memory)
 };
 
 constexpr int kRescore = 8;   // candidates per list re-scored in FP32 by the BF16 precision mode
@@ -131,9 +132,12 @@ cudaError_t launch_unary(const float *A, int R, const float *B, int S, int F, fl
                          int ldu, cudaStream_t st);
 // k_rowdot.cu: BF16 tensor-core products.
 cudaError_t launch_sqnorm_bf16(const float *X, int64_t n, int ld, int F, float *out, cudaStream_t st);
+// scratch: device memory of at least unary_bf16_scratch_bytes(R, S, F) for the BF16 copies of the operands
+// the TMA-staged kernel reads (with less, or F > 256, the operands are staged by the threads instead).
+size_t unary_bf16_scratch_bytes(int R, int64_t S, int F);
 cudaError_t launch_unary_bf16(const float *model, int R, const float *scene, int S, int F, int ld,
                               const float *mnorm, const float *snorm, float lambda1, float *U, int64_t ldu,
-                              int *status, cudaStream_t st);
+                              int *status, void *scratch, size_t scratch_bytes, cudaStream_t st);
 cudaError_t launch_rowdot_plain(const float *X, int64_t nrows, int ldx, const float *W, int ncols, int ldw, int F,
                                 const float *bias, float *Y, int64_t ldy, int *status, cudaStream_t st);
 cudaError_t launch_select(const Unit *units, int64_t n_units, const ModelRec *models, const SceneRec *scenes,
@@ -252,8 +256,8 @@ bool valid_model(const hgm_model *m);
 bool valid_scene(const hgm_scene *s);
 // api.cu: the parameter check shared by the matching entry points (HGM_EINVAL / HGM_EUNSUPPORTED + message).
 hgm_status check_match_params(const hgm_params *p);
-// api.cu: the most points any 2w+1 consecutive frames of the scene hold (the largest candidate window).
-int32_t max_window_points(const hgm_scene *s, int window);
+// api.cu: the points 2w+1 consecutive frames of the scene hold on average (a typical candidate window).
+int32_t typical_window_points(const hgm_scene *s, int window);
 // noalloc.cu: looks up (once per device) the device address of the fixed scratch of hgm_match_noalloc on the
 // current device, which makes the runtime load the code that holds the scratch, and so create it, now.
 hgm_status noalloc_prepare();

@@ -11,6 +11,9 @@
 // tcgen05.mma (kind::f16) accumulate the 128 x 128 FP32 tile in tensor memory,
 // then each warp reads its 32 rows back (tcgen05.ld) and applies the epilogue.
 // Two CTAs share an SM (91 KB of shared memory and 128 TMEM columns each).
+#include <cuda.h>            // CUtensorMap and its enums (types only: the encoder is fetched at run time)
+#include <cudaTypedefs.h>    // PFN_cuTensorMapEncodeTiled
+
 #include "hgm_internal.cuh"
 #include "tc05.cuh"
 
@@ -152,6 +155,175 @@ __global__ void __launch_bounds__(128) rowdot_kernel(const float *__restrict__ X
     if (warp == 0) tc05::tmem_dealloc<TN>(taddr);
 }
 
+// ---- the precision mode's unary table with TMA-staged operands ---------------------------------------------
+//
+// Both operands are first written once as BF16 rows of Kp = F rounded up to 16 components (zeros after F),
+// so that the tensor memory accelerator can copy them into shared memory as they are: per 128-row tile and
+// 16-byte chunk k8 of K, one cp.async.bulk.tensor box of 8 components x 128 rows lands 128 rows x 16 bytes
+// contiguously at k8 x 2048 bytes -- the canonical no-swizzle K-major layout with a K-direction core-matrix
+// stride (LBO) of 2048 bytes and a row-group stride (SBO) of 128 bytes. Every box starts at an inner
+// coordinate that is a multiple of 8 components (16 bytes); rows past the end of a matrix arrive as zeros.
+// A CTA owns 128 scene rows (loaded once) and sweeps the model rows in tiles of 128: one thread issues the
+// B tile's boxes on an mbarrier with the expected byte count, waits, issues the MMAs and commits; the 128
+// threads read the accumulator (thread = scene row) and write U. Two CTAs share an SM, so one's epilogue
+// overlaps the other's copies and MMAs.
+
+constexpr uint32_t kTmaLBO = 2048, kTmaSBO = 128;
+
+__global__ void to_bf16_kernel(const float *__restrict__ X, int64_t n, int ld, int F, int Kp,
+                               __nv_bfloat16 *__restrict__ out)
+{
+    const int64_t total = n * (Kp / 2);
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = e / (Kp / 2);
+        const int k = (int)(e - r * (Kp / 2)) * 2;
+        const float a = k < F ? X[r * ld + k] : 0.0f, b = k + 1 < F ? X[r * ld + k + 1] : 0.0f;
+        reinterpret_cast<__nv_bfloat162 *>(out)[e] = __floats2bfloat162_rn(a, b);
+    }
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *mbar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(tc05::smem_u32(mbar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *tmap, int x, int y, uint64_t *mbar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::
+            "r"(tc05::smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(tmap)), "r"(x), "r"(y), "r"(tc05::smem_u32(mbar))
+        : "memory");
+}
+
+__global__ void __launch_bounds__(128) unary_tma_kernel(const __grid_constant__ CUtensorMap tmA,
+                                                        const __grid_constant__ CUtensorMap tmB, int64_t S, int R,
+                                                        int Kp, const float *__restrict__ snorm,
+                                                        const float *__restrict__ mnorm, float lambda1,
+                                                        float *__restrict__ U, int64_t ldu, int *__restrict__ status)
+{
+    // the tiles start on a 1024-byte boundary of the shared window (TMA destinations want 128), whatever the
+    // placement of the dynamic array after the static variables: the launch asks for 1024 bytes more
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char *sA = smem_raw + ((1024u - (tc05::smem_u32(smem_raw) & 1023u)) & 1023u);
+    unsigned char *sB = sA + (size_t)TM * Kp * 2;
+    __shared__ uint64_t tma_bar, mma_bar;
+    __shared__ uint32_t tslot;
+    __shared__ float wn[TN];
+    __shared__ int bad;
+    const int tid = threadIdx.x, warp = tid >> 5;
+    if (warp == 0) tc05::tmem_alloc<TN>(&tslot);
+    if (tid == 0) {
+        tc05::mbar_init(&tma_bar, 1);
+        tc05::mbar_init(&mma_bar, 1);
+        bad = 0;
+    }
+    tc05::fence_before_sync();
+    __syncthreads();
+    tc05::fence_after_sync();
+    const uint32_t taddr = tslot;
+    const uint32_t tlane = taddr + ((uint32_t)(32 * warp) << 16);
+    constexpr uint32_t idesc = tc05::idesc_bf16_f32(TM, TN);
+    const int nk8 = Kp / 8;
+    const uint32_t tile_bytes = (uint32_t)TM * Kp * 2;
+    uint32_t tphase = 0, mphase = 0;
+    const int64_t ntiles = (S + TM - 1) / TM;
+    for (int64_t tile = blockIdx.x; tile < ntiles && !bad; tile += gridDim.x) {
+        const int64_t r0 = tile * TM;
+        const int64_t row = r0 + tid;
+        const float xn = row < S ? snorm[row] : 0.0f;
+        for (int m0 = 0; m0 < R && !bad; m0 += TN) {
+            if (tid == 0) {
+                // sA and sB are free: the previous tile's MMAs completed (mma_bar) before the last barrier
+                mbar_expect_tx(&tma_bar, m0 == 0 ? 2 * tile_bytes : tile_bytes);
+                if (m0 == 0)
+                    for (int k8 = 0; k8 < nk8; ++k8) tma_load_2d(sA + (size_t)k8 * kTmaLBO, &tmA, 8 * k8, (int)r0, &tma_bar);
+                for (int k8 = 0; k8 < nk8; ++k8) tma_load_2d(sB + (size_t)k8 * kTmaLBO, &tmB, 8 * k8, m0, &tma_bar);
+            }
+            wn[tid] = m0 + tid < R ? mnorm[m0 + tid] : 0.0f;
+            if (tid == 0) {
+                if (tc05::mbar_wait(&tma_bar, tphase, kPolls)) {
+                    tc05::fence_after_sync();
+                    const uint32_t a0 = tc05::smem_u32(sA), b0 = tc05::smem_u32(sB);
+                    for (int ks = 0; ks < Kp / 16; ++ks)
+                        tc05::mma_bf16(taddr, tc05::smem_desc(a0 + ks * 2 * kTmaLBO, kTmaLBO, kTmaSBO),
+                                       tc05::smem_desc(b0 + ks * 2 * kTmaLBO, kTmaLBO, kTmaSBO), idesc, ks > 0);
+                    tc05::mma_commit(&mma_bar);
+                } else {
+                    // give the copies in flight a second bounded wait before the CTA leaves
+                    tc05::mbar_wait(&tma_bar, tphase, kPolls);
+                    if (status) atomicExch(status, 1);
+                    bad = 1;
+                }
+            }
+            tphase ^= 1u;
+            __syncthreads();   // wn is written; bad is seen by every thread
+            if (bad) break;
+            if (!tc05::mbar_wait(&mma_bar, mphase, kPolls)) {
+                if (status) atomicExch(status, 1);
+                bad = 1;
+            }
+            mphase ^= 1u;
+            tc05::fence_after_sync();
+            if (!bad) {
+                for (int cc = 0; cc < TN && m0 + cc < R; cc += 32) {
+                    float v[32];
+                    tc05::tmem_ld32(tlane + (uint32_t)cc, v);
+                    if (row < S) {
+#pragma unroll
+                        for (int j = 0; j < 32; ++j) {
+                            const int c = m0 + cc + j;
+                            if (c < R) {
+                                const float d2 = fmaxf(xn + wn[cc + j] - 2.0f * v[j], 0.0f);
+                                U[(int64_t)c * ldu + row] = lambda1 * sqrtf(d2);
+                            }
+                        }
+                    }
+                }
+            }
+            tc05::fence_before_sync();
+            __syncthreads();   // TMEM, sB and wn are free again
+            tc05::fence_after_sync();
+        }
+    }
+    tc05::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) tc05::tmem_dealloc<TN>(taddr);
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder()
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+        else
+            cudaGetLastError();
+    }
+    return fn;
+}
+
+// 2-D tensor map of n BF16 rows of Kp components, boxes of 8 components x 128 rows.
+bool encode_rows(CUtensorMap *tm, const __nv_bfloat16 *base, int64_t n, int Kp)
+{
+    PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+    if (!enc) return false;
+    const cuuint64_t dims[2] = {(cuuint64_t)Kp, (cuuint64_t)n};
+    const cuuint64_t strides[1] = {(cuuint64_t)Kp * 2};
+    const cuuint32_t box[2] = {8, (cuuint32_t)TM};
+    const cuuint32_t elem[2] = {1, 1};
+    return enc(tm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<__nv_bfloat16 *>(base), dims, strides, box, elem,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 constexpr int KC = 256;    // largest K staged at once (A + B tiles: 2 x 128 x 256 x 2 B = 128 KB)
 
 bool aligned16(const void *p, int ld) { return ((reinterpret_cast<uintptr_t>(p) & 15) == 0) && ((ld & 3) == 0); }
@@ -190,13 +362,46 @@ cudaError_t launch_sqnorm_bf16(const float *X, int64_t n, int ld, int F, float *
     return cudaGetLastError();
 }
 
+size_t unary_bf16_scratch_bytes(int R, int64_t S, int F)
+{
+    const int64_t Kp = (F + 15) / 16 * 16;
+    return (size_t)((R + 255) / 256 * 256 + (S + 255) / 256 * 256) * (size_t)Kp * 2;
+}
+
 cudaError_t launch_unary_bf16(const float *model, int R, const float *scene, int S, int F, int ld,
                               const float *mnorm, const float *snorm, float lambda1, float *U, int64_t ldu,
-                              int *status, cudaStream_t st)
+                              int *status, void *scratch, size_t scratch_bytes, cudaStream_t st)
 {
+    if (R <= 0 || S <= 0) return cudaSuccess;
     prof_begin(kProfUnary, st);
-    cudaError_t e = launch_rowdot<kDist>(scene, S, ld, model, R, ld, F, snorm, mnorm, lambda1, nullptr, U, ldu, status,
-                                         st);
+    const int Kp = (F + 15) / 16 * 16;
+    cudaError_t e = cudaSuccess;
+    CUtensorMap tmA, tmB;
+    __nv_bfloat16 *mb = static_cast<__nv_bfloat16 *>(scratch);
+    __nv_bfloat16 *sb = mb + (size_t)(R + 255) / 256 * 256 * Kp;
+    if (Kp <= KC && scratch && scratch_bytes >= unary_bf16_scratch_bytes(R, S, F) &&
+        encode_rows(&tmA, sb, S, Kp) && encode_rows(&tmB, mb, R, Kp)) {
+        // BF16 copies of both operands, then the TMA-staged contraction
+        const int64_t bm = std::min<int64_t>(((int64_t)R * Kp / 2 + 255) / 256, 65536);
+        const int64_t bs = std::min<int64_t>(((int64_t)S * Kp / 2 + 255) / 256, 65536);
+        to_bf16_kernel<<<(unsigned)bm, 256, 0, st>>>(model, R, ld, F, Kp, mb);
+        to_bf16_kernel<<<(unsigned)bs, 256, 0, st>>>(scene, S, ld, F, Kp, sb);
+        const size_t smem = (size_t)2 * TM * Kp * 2 + 1024;
+        e = cudaFuncSetAttribute(unary_tma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        int dev = 0, sms = 0, per_sm = 0;
+        if (e == cudaSuccess) e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, unary_tma_kernel, 128, smem);
+        if (e == cudaSuccess) {
+            per_sm = per_sm < 1 ? 1 : (per_sm > 4 ? 4 : per_sm);   // 4 x 128 TMEM columns = the SM's 512
+            const int64_t grid = std::min<int64_t>(((int64_t)S + TM - 1) / TM, (int64_t)sms * per_sm);
+            unary_tma_kernel<<<(unsigned)grid, 128, smem, st>>>(tmA, tmB, S, R, Kp, snorm, mnorm, lambda1, U, ldu,
+                                                                status);
+            e = cudaGetLastError();
+        }
+    } else {
+        e = launch_rowdot<kDist>(scene, S, ld, model, R, ld, F, snorm, mnorm, lambda1, nullptr, U, ldu, status, st);
+    }
     prof_end(kProfUnary, st);
     return e;
 }

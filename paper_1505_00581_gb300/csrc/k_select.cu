@@ -33,8 +33,9 @@ __device__ __forceinline__ uint32_t lanemask_lt()
 }
 
 // kKeyRegs keys per lane are held in registers: windows of up to 32 kKeyRegs keys are selected from them,
-// longer ones from memory in every pass. The launch picks 8 (three CTAs per SM) when no window of the call
-// exceeds 256 points, else 20 (two CTAs per SM, the registers the larger arrays need).
+// longer ones from memory in every pass. The launch picks 8 (three CTAs per SM) when the call's typical
+// window (the scenes' mean density over 2w+1 frames) fits 256 keys, else 20 (two CTAs per SM, the registers
+// the larger arrays need).
 template <int kKeyRegs, int kMinBlocks>
 __global__ void __launch_bounds__(kWarps * 32, kMinBlocks) select_kernel(const Unit *__restrict__ units, int64_t n_units,
                                                              const ModelRec *__restrict__ models,

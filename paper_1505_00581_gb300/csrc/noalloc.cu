@@ -198,7 +198,7 @@ extern "C" hgm_status hgm_match_noalloc(const hgm_model *model, const hgm_scene 
     p.T = params->T;
     p.window = params->window;
     p.K = K;
-    p.max_window = max_window_points(scene, p.window);
+    p.max_window = typical_window_points(scene, p.window);
     const ModelRec mr{model->d.xy, model->d.t, model->d.perm, M, 0, model->d.f, model->d.geo};
     const SceneRec sr{scene->d.xy, scene->d.t, scene->d.frame_start, scene->d.perm, d_U, pitch, S, scene->d.n_frames};
 
