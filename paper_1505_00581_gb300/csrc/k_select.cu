@@ -24,19 +24,6 @@ namespace hgm {
 namespace {
 
 constexpr int kWarps = 8;
-constexpr int kRowChunks = 8;   // staged re-score: descriptor rows of up to 32 x 8 = 256 components
-
-// The FP32 unary cost of Eq. 2 from two rows in shared memory, in unary_fp32's order (component 0 first,
-// one rounded subtraction and one fused multiply-add per component), hence the same bits.
-__device__ __forceinline__ float unary_fp32_rows(const float *a, const float *b, int F, float lambda1)
-{
-    float s = 0.0f;
-    for (int k = 0; k < F; ++k) {
-        const float d = __fsub_rn(a[k], b[k]);
-        s = __fmaf_rn(d, d, s);
-    }
-    return __fmul_rn(lambda1, __fsqrt_rn(s));
-}
 
 __device__ __forceinline__ uint32_t lanemask_lt()
 {
@@ -55,11 +42,8 @@ __global__ void __launch_bounds__(kWarps * 32, kMinBlocks) select_kernel(const U
                                                              const SceneRec *__restrict__ scenes, Params p,
                                                              int32_t *__restrict__ cand_idx,
                                                              float *__restrict__ cand_u,
-                                                             int32_t *__restrict__ cand_cnt, int rs_stride)
+                                                             int32_t *__restrict__ cand_cnt)
 {
-    // rs_stride > 0: the precision mode's re-score stages its rows in the dynamic shared array, p.rescore + 1
-    // rows of rs_stride floats per warp (odd stride: the 8 lanes' rows fall in different banks)
-    extern __shared__ float rs_buf[];
     __shared__ uint32_t hist[kWarps][256];
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
@@ -222,40 +206,7 @@ __global__ void __launch_bounds__(kWarps * 32, kMinBlocks) select_kernel(const U
                     if (bs == lane) kv[0] = __int_as_float(0x7f800000);
                     if (bs == lane + 32) kv[1] = __int_as_float(0x7f800000);
                 }
-                if (rs_stride > 0) {
-                    // the rows are gathered by the whole warp first (32 loads in flight per lane), then the
-                    // re-scoring lanes sum from shared memory in the same order
-                    const int srow = mine >= 0 && mine < kept ? oidx[mine] : 0;
-                    const float *mrow = md.f + (int64_t)i * p.F;
-                    float *buf = rs_buf + (size_t)warp * (p.rescore + 1) * rs_stride;
-                    __syncwarp();   // the previous list's sums have read buf
-                    for (int r0 = 0; r0 <= rounds; r0 += 4) {
-                        float v[4][kRowChunks];
-#pragma unroll
-                        for (int rr = 0; rr < 4; ++rr) {
-                            const int r = r0 + rr;
-                            const int sr = __shfl_sync(0xffffffffu, srow, r & 31);
-                            const float *src = r < rounds ? sc.f + (int64_t)sr * p.F : mrow;
-#pragma unroll
-                            for (int c = 0; c < kRowChunks; ++c) {
-                                const int k = lane + 32 * c;
-                                v[rr][c] = r <= rounds && k < p.F ? src[k] : 0.0f;
-                            }
-                        }
-#pragma unroll
-                        for (int rr = 0; rr < 4; ++rr) {
-                            const int r = r0 + rr;
-#pragma unroll
-                            for (int c = 0; c < kRowChunks; ++c) {
-                                const int k = lane + 32 * c;
-                                if (r <= rounds && k < p.F) buf[r * rs_stride + k] = v[rr][c];
-                            }
-                        }
-                    }
-                    __syncwarp();
-                    if (mine >= 0 && mine < kept)
-                        ou[mine] = unary_fp32_rows(buf + rounds * rs_stride, buf + lane * rs_stride, p.F, p.lambda1);
-                } else if (mine >= 0 && mine < kept) {
+                if (mine >= 0 && mine < kept) {
                     ou[mine] = unary_fp32(md.f + (int64_t)i * p.F, sc.f + (int64_t)oidx[mine] * p.F, p.F, p.lambda1);
                 }
             }
@@ -272,22 +223,13 @@ cudaError_t launch_select(const Unit *units, int64_t n_units, const ModelRec *mo
     (void)max_M;
     if (n_units <= 0) return cudaSuccess;
     int64_t blocks = n_units < (int64_t)1 << 20 ? n_units : (int64_t)1 << 20;
-    const bool small = p.max_window <= 32 * 8;
-    // the staged re-score needs rows of at most 32 kRowChunks components and 32 lanes for its rows
-    const int rs_stride = p.rescore > 0 && p.rescore <= 31 && p.F <= 32 * kRowChunks ? (p.F | 1) : 0;
-    const size_t smem = (size_t)kWarps * (p.rescore + 1) * rs_stride * sizeof(float);
-    if (smem > 0) {
-        cudaError_t e = cudaFuncSetAttribute(small ? select_kernel<8, 3> : select_kernel<20, 2>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-    }
     prof_begin(kProfSelect, st);
-    if (small)
-        select_kernel<8, 3><<<(unsigned)blocks, kWarps * 32, smem, st>>>(units, n_units, models, scenes, p, cand_idx,
-                                                                         cand_u, cand_cnt, rs_stride);
+    if (p.max_window <= 32 * 8)
+        select_kernel<8, 3><<<(unsigned)blocks, kWarps * 32, 0, st>>>(units, n_units, models, scenes, p, cand_idx,
+                                                                      cand_u, cand_cnt);
     else
-        select_kernel<20, 2><<<(unsigned)blocks, kWarps * 32, smem, st>>>(units, n_units, models, scenes, p, cand_idx,
-                                                                          cand_u, cand_cnt, rs_stride);
+        select_kernel<20, 2><<<(unsigned)blocks, kWarps * 32, 0, st>>>(units, n_units, models, scenes, p, cand_idx,
+                                                                       cand_u, cand_cnt);
     prof_end(kProfSelect, st);
     return cudaGetLastError();
 }
