@@ -132,19 +132,23 @@ def backward_bf16(p, x, y, rnd=bf16):
     return loss_v, g, scale
 
 
-def score_split_bf16(p, x, model_xy, scene_xy, F, rnd=bf16):
-    """The logit z3 as the pruning pass computes it: the first layer split into a model-point part
-    P = W1a f_i + b1 - W1c (x_i, y_i) / 100 (BF16 operands, FP32 result), a scene-point part
-    Q = W1b f'_j + W1c (x'_j, y'_j) / 100 rounded once to BF16 (BF16 operands), and the time term
-    W1c_t dt / w per candidate; then layer 2 on BF16 operands and the output layer unrounded. x holds the
-    rows of features() (the dx, dy columns are not used; the positions come in separately). With the
-    identity as rnd it is forward()'s z3, the split being exact algebra."""
+def score_split_bf16(p, x, model_xy, scene_xy, F, rnd=bf16, window=3):
+    """The logit z3 as the pruning pass computes it. The first layer is split into a model-point part
+    P = W1a f_i + b1 - W1c (x_i, y_i) / 100 and a scene-point part Q = W1b f'_j + W1c (x'_j, y'_j) / 100
+    (both products on BF16 operands, each part rounded once to BF16), and a time term: the hidden units are
+    h1 = relu(rnd(dt * rnd(W1c_t / w) + rnd(P + Q))), dt = t'_j - t_i - o the integer frame difference and
+    w = window (at least 1) -- one BF16 add and one fused BF16 multiply-add per unit, as BF16x2 arithmetic
+    does it. Layer 2 then runs on BF16 operands (h1 is one already) and the output layer is unrounded.
+    x holds the rows of features() built with the same window (the dx, dy columns are not used; the positions
+    come in separately). With the identity as rnd it is forward()'s z3, the split being exact algebra."""
     W1 = p["W1"]
-    Wa, Wb, Wxy, Wt = W1[:, :F], W1[:, F:2 * F], W1[:, 2 * F:2 * F + 2], W1[:, 2 * F + 2:]
-    P = rnd(x[:, :F]) @ rnd(Wa).T + p["b1"] - (model_xy @ Wxy.T) / 100.0
+    Wa, Wb, Wxy, Wt = W1[:, :F], W1[:, F:2 * F], W1[:, 2 * F:2 * F + 2], W1[:, 2 * F + 2]
+    w = float(max(window, 1))
+    P = rnd(rnd(x[:, :F]) @ rnd(Wa).T + p["b1"] - (model_xy @ Wxy.T) / 100.0)
     Q = rnd(rnd(x[:, F:2 * F]) @ rnd(Wb).T + (scene_xy @ Wxy.T) / 100.0)
-    z1 = P + Q + x[:, 2 * F + 2:] @ Wt.T
-    z2 = rnd(np.maximum(z1, 0.0)) @ rnd(p["W2"]).T + p["b2"]
+    dt = rnd(np.rint(x[:, 2 * F + 2] * w))
+    h1 = np.maximum(rnd(dt[:, None] * rnd(Wt / w)[None, :] + rnd(P + Q)), 0.0)
+    z2 = h1 @ rnd(p["W2"]).T + p["b2"]
     return np.maximum(z2, 0.0) @ p["w3"] + p["b3"][0]
 
 

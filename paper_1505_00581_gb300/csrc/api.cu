@@ -149,7 +149,7 @@ struct Workspace {
     Buffer modelcat, U, cand_idx, cand_u, cand_cnt, beta, units, res, mrec, srec, counter, out_e, out_a, evaluated;
     Buffer mnorm, snorm, status;
     Buffer stage, perm_stage, flag;   // inputs of hgm_create_model / hgm_create_scene
-    Buffer P, Q, Qb, modelxy, cand2_idx, cand2_u, cand2_cnt, units2, beta2, fb_units, fb_count, beta_fb, scores;
+    Buffer P, Pb, Q, Qb, modelxy, cand2_idx, cand2_u, cand2_cnt, units2, beta2, fb_units, fb_count, beta_fb, scores;
     Buffer fb_total;   // fallback units since the last hgm_prune_counters reset (device counter)
     Buffer chain_e, chain_a, chain_tab, chain_oe, chain_oa;   // independent-chains variant
     Buffer rf_e, rf_a;        // refinement of the pruned form: device outputs when the caller's are on the host
@@ -685,10 +685,11 @@ hgm_status run_batch(Exec &ex, const hgm_model *const *models, int nm, const hgm
             CK(cudaMemcpyAsync(ws.modelxy.as<float>() + (size_t)urow[m] * 2, models[m]->d.xy,
                                (size_t)models[m]->d.M * 2 * sizeof(float), cudaMemcpyDeviceToDevice, st),
                "gather model positions");
+        CK(ws.Pb.ensure((size_t)R * kPropHidden * sizeof(__nv_bfloat16)), "workspace (projections)");
         CK(launch_prop_fold_xy(ws.P.as<float>(), R, ws.modelxy.as<float>(), th + prop->L.o_W1 + 2 * Fu,
-                               prop->L.dp, -1.0f, nullptr, st),
+                               prop->L.dp, -1.0f, ws.Pb.as<__nv_bfloat16>(), st),
            "projection kernel");
-        pi.P = ws.P.as<float>();
+        pi.Pb = ws.Pb.as<__nv_bfloat16>();
         pi.W2 = th + prop->L.o_W2;
         pi.b2 = th + prop->L.o_b2;
         pi.w3 = th + prop->L.o_w3;
@@ -2170,8 +2171,9 @@ hgm_status hgm_prop_scores(const hgm_prop *prop, const hgm_model *model, const h
     CK(launch_rowdot_plain(model->d.f, M, F, th + prop->L.o_W1, kPropHidden, prop->L.dp, Fu, th + prop->L.o_b1,
                            g_ws.P.as<float>(), kPropHidden, g_ws.status.as<int>(), st),
        "projection kernel");
+    CK(g_ws.Pb.ensure((size_t)M * kPropHidden * sizeof(__nv_bfloat16)), "workspace (projections)");
     CK(launch_prop_fold_xy(g_ws.P.as<float>(), M, reinterpret_cast<const float *>(model->d.xy),
-                           th + prop->L.o_W1 + 2 * Fu, prop->L.dp, -1.0f, nullptr, st),
+                           th + prop->L.o_W1 + 2 * Fu, prop->L.dp, -1.0f, g_ws.Pb.as<__nv_bfloat16>(), st),
        "projection kernel");
     CK(launch_rowdot_plain(scene->d.f, S, F, th + prop->L.o_W1 + Fu, kPropHidden, prop->L.dp, Fu, nullptr,
                            g_ws.Q.as<float>(), kPropHidden, g_ws.status.as<int>(), st),
@@ -2186,7 +2188,7 @@ hgm_status hgm_prop_scores(const hgm_prop *prop, const hgm_model *model, const h
     sr.pq = g_ws.Qb.as<__nv_bfloat16>();
     CK(cudaMemcpyAsync(g_ws.srec.p, &sr, sizeof sr, cudaMemcpyHostToDevice, st), "upload");
     PropInfer pi{};
-    pi.P = g_ws.P.as<float>();
+    pi.Pb = g_ws.Pb.as<__nv_bfloat16>();
     pi.W2 = th + prop->L.o_W2;
     pi.b2 = th + prop->L.o_b2;
     pi.w3 = th + prop->L.o_w3;

@@ -95,7 +95,7 @@ enum ProfKernel { kProfUnary = 0, kProfSelect = 1, kProfRecurse = 2, kProfBacktr
 
 // Proposal network operands for the pruning kernel (device pointers into the weights).
 struct PropInfer {
-    const float *P;      // [R x 128]: W1a f_i + b1 per model row of the batch
+    const __nv_bfloat16 *Pb;   // [R x 128]: W1a f_i + b1 - W1c (x_i, y_i) / 100 per model row, rounded to BF16
     const float *W2, *b2, *w3, *b3;
     const float *w1c;    // W1 columns 2F..2F+2 (row stride dp)
     int dp;

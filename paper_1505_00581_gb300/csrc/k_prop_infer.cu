@@ -11,6 +11,11 @@
 // tensor-core row-product kernel with the linear position terms folded in, so
 // a candidate's 128 hidden units cost one add and one fma each.
 //
+// P and Q are held as BF16 rows, so that a candidate's first layer is BF16x2
+// arithmetic: per pair of hidden units one add (P + Q, rounded to BF16) and
+// one fused multiply-add with ReLU (+ dt (W1c_t / w), rounded once), whose
+// result is the layer-2 operand as it stands.
+//
 // The scoring kernel stages 128 candidates per tile (128 / 2^ceil(log2 K)
 // lists) as BF16 and runs layer 2 (128 x 128) as tcgen05.mma with W2 resident
 // in shared memory. Tiles are double-buffered in shared memory and in tensor
@@ -86,9 +91,11 @@ __global__ void __launch_bounds__(256, 2) prop_score_kernel(const Unit *__restri
     // bank-conflict-free order of the A-tile stores)
     const int bh0 = 32 * (warp & 3) + 8 * (lane & 3);              // first of this lane's 8 hidden units
     const int brow0 = 64 * (warp >> 2) + (lane >> 2);                // its row in group 0 (+8 per group)
-    float w1t[8];                                                    // W1c_t / w for those units
+    __nv_bfloat162 w1t[4];                                           // W1c_t / w for those units, BF16 pairs
 #pragma unroll
-    for (int e = 0; e < 8; ++e) w1t[e] = pi.w1c[(int64_t)(bh0 + e) * pi.dp + 2] * pi.inv_window;
+    for (int e = 0; e < 4; ++e)
+        w1t[e] = __floats2bfloat162_rn(pi.w1c[(int64_t)(bh0 + 2 * e) * pi.dp + 2] * pi.inv_window,
+                                       pi.w1c[(int64_t)(bh0 + 2 * e + 1) * pi.dp + 2] * pi.inv_window);
 
     if (warp == 0) tc05::tmem_alloc<2 * H>(&sm.tslot);
     for (int e = tid; e < H * (H / 8); e += 256) {          // W2 -> BF16, canonical layout
@@ -197,30 +204,22 @@ __global__ void __launch_bounds__(256, 2) prop_score_kernel(const Unit *__restri
                 }
             }
             int plist = -1;
-            float pv[8];
+            uint4 pv = make_uint4(0, 0, 0, 0);
 #pragma unroll
             for (int g = 0; g < 8; ++g) {
                 const int r = brow0 + 8 * g, lst = i0 + (r >> kp_log2);
                 __align__(16) __nv_bfloat162 hh[4];
                 if (vg[g]) {
                     if (lst != plist) {   // the row's list: this lane's 8 units of P (rows of a group share it)
-                        const float4 *P4 = reinterpret_cast<const float4 *>(pi.P + (int64_t)(md.urow + lst) * H + bh0);
-                        const float4 pa = __ldg(P4), pb = __ldg(P4 + 1);
-                        pv[0] = pa.x; pv[1] = pa.y; pv[2] = pa.z; pv[3] = pa.w;
-                        pv[4] = pb.x; pv[5] = pb.y; pv[6] = pb.z; pv[7] = pb.w;
+                        pv = __ldg(reinterpret_cast<const uint4 *>(pi.Pb + (int64_t)(md.urow + lst) * H + bh0));
                         plist = lst;
                     }
-                    const float dt = (float)(tg[g] - md.t[lst] - un.offset);
+                    const __nv_bfloat162 dt = __float2bfloat162_rn((float)(tg[g] - md.t[lst] - un.offset));
+                    const __nv_bfloat162 *p2 = reinterpret_cast<const __nv_bfloat162 *>(&pv);
                     const __nv_bfloat162 *q2 = reinterpret_cast<const __nv_bfloat162 *>(&qg[g]);
 #pragma unroll
-                    for (int e = 0; e < 4; ++e) {   // two hidden units per packed FP32x2 add and FMA
-                        const float2 qf = __bfloat1622float2(q2[e]);
-                        float x0, x1;
-                        upk2(fma2(pk2(w1t[2 * e], w1t[2 * e + 1]), pk2(dt, dt),
-                                  add2(pk2(pv[2 * e], pv[2 * e + 1]), pk2(qf.x, qf.y))),
-                             x0, x1);
-                        hh[e] = __floats2bfloat162_rn(fmaxf(x0, 0.0f), fmaxf(x1, 0.0f));
-                    }
+                    for (int e = 0; e < 4; ++e)   // two hidden units per BF16x2 add and fused multiply-add-relu
+                        hh[e] = __hfma2_relu(dt, w1t[e], __hadd2(p2[e], q2[e]));
                 } else {
 #pragma unroll
                     for (int e = 0; e < 4; ++e) hh[e] = __floats2bfloat162_rn(0.0f, 0.0f);

@@ -212,7 +212,8 @@ def test_scoring_kernel_matches_fp64(env, K, window, precision):
     """The pruning pass's logits (first layer from the per-point projections with the position terms folded
     in, layer 2 on the tensor cores) against the FP64 network on the same candidates: to 2e-3 of the logit
     range against the emulation that rounds to BF16 what the kernels round (the descriptors and W1a/W1b in
-    the projections, the scene projection Q once it holds the position terms, h1 and W2 in layer 2); within
+    the projections, both projections once they hold the position terms, the first layer's BF16x2 add and
+    fused multiply-add, W2 in layer 2); within
     5% of the spread against plain FP64. Empty slots are
     -inf. K = 64 with w = 0: lists of about 30 candidates (many empty slots); K = 24 with w = 3: full lists,
     four lists of 32 rows (8 of them empty) in each 128-row tile."""
@@ -248,9 +249,9 @@ def test_scoring_kernel_matches_fp64(env, K, window, precision):
     g = got[valid]
     assert np.all(np.isfinite(g))
     z64 = mlp.forward(ref, X)["z3"]
-    # P per model point (FP32 in the kernel), Q per scene point rounded once to BF16, both with the position
-    # terms folded in; the time term per candidate (oracle/mlp.py: score_split_bf16)
-    z_emu = mlp.score_split_bf16(ref, X, mxy, sxy, F)
+    # P per model point and Q per scene point, each rounded once to BF16 with the position terms folded in;
+    # the first layer in BF16x2 arithmetic with the time term per candidate (oracle/mlp.py: score_split_bf16)
+    z_emu = mlp.score_split_bf16(ref, X, mxy, sxy, F, window=window)
     assert np.max(np.abs(g - z_emu)) <= 2e-3 * max(1.0, np.max(np.abs(z_emu))), np.max(np.abs(g - z_emu))
     assert np.max(np.abs(g - z64)) <= 0.05 * max(1.0, np.std(z64)), (np.max(np.abs(g - z64)), np.std(z64))
 

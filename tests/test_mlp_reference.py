@@ -150,8 +150,8 @@ def test_split_first_layer_without_rounding_is_forward():
     i, j, o = rng.integers(0, 5, n), rng.integers(0, 8, n), rng.integers(0, 20, n)
     x = mlp.features(mf, sf, mxy, sxy, mt, st, i, j, o, 3)
     ident = lambda v: np.asarray(v, dtype=np.float64)
-    z = mlp.score_split_bf16(p, x, mxy[i], sxy[j], F, rnd=ident)
+    z = mlp.score_split_bf16(p, x, mxy[i], sxy[j], F, rnd=ident, window=3)
     assert np.allclose(z, mlp.forward(p, x)["z3"], rtol=1e-12, atol=1e-12)
     # and with BF16 rounding it stays within BF16 relative error of the same logits
-    zb = mlp.score_split_bf16(p, x, mxy[i], sxy[j], F)
+    zb = mlp.score_split_bf16(p, x, mxy[i], sxy[j], F, window=3)
     assert np.max(np.abs(zb - z)) <= 0.05 * max(1.0, np.std(z))
