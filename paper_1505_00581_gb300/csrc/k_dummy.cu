@@ -9,7 +9,7 @@
 // One persistent CTA per unit, all tables in shared memory (L x L floats each): alpha_{i+1} and alpha_i
 // (ping-pong), base(b, a) = U(a) + lambda2 Delta(a, b) + alpha_{i+1}(a, b) (eps rules applied), and the
 // per-step directions P1(b, a) = A1 + theta(b->a), P2(b, a) = A2 + theta(a->b) (kept pairs only),
-// R(a, c) = theta(a->c).
+// R(a, c) = theta(a->c) (only for the a some row keeps, once the kept lists are built).
 // Every open cell (b, c) has a best of at most thr(b): base(b, eps), since the triple (eps, b, c) is
 // feasible and costs that alone, and base(b, a1) + max D^g when the row's smallest base a1 is feasible with
 // every open c. A warp per row keeps the a with base <= thr(b) that may follow b and ranks them by
@@ -39,6 +39,7 @@ struct DummySmem {
     float u[3][kL];
     uint8_t srt[kL][kMaxK];            // per row b: the kept real a by increasing base(b, a) (ties: lower slot)
     uint8_t kept[kL];                  // per row b: how many a srt[b] holds
+    unsigned akept[2];                 // real a kept by some real row b (bits of slots 0-31, 32-63)
     int cnt[3];
     float ang[2];                      // the step's model angles A1, A2 (one thread computes them)
 };
@@ -118,6 +119,8 @@ __global__ void __launch_bounds__(kDummyThreads, 2) dummy_recurse_kernel(
                 if (s == 0) sm.cnt[w] = n;
             }
             if (threadIdx.x == 0) {
+                sm.akept[0] = 0u;
+                sm.akept[1] = 0u;
                 const float2 mi = md.xy[i], mj = md.xy[i - 1], mk = md.xy[i - 2];
                 sm.ang[0] = signed_angle(mj, mi, mk);   // A1: at i-1, from ->i to ->i-2
                 sm.ang[1] = signed_angle(mi, mj, mk);   // A2: at i, from ->i-1 to ->i-2
@@ -128,7 +131,7 @@ __global__ void __launch_bounds__(kDummyThreads, 2) dummy_recurse_kernel(
             const int na = sm.cnt[sA], nb = sm.cnt[sB], nc = sm.cnt[sC];
             const float *an = sm.alpha[cur];
             const bool last = i == M - 1;
-            // base(b, a) and directions; rows/columns of empty slots are never read
+            // base(b, a); rows/columns of empty slots are never read
             for (int e = threadIdx.x; e < L * L; e += blockDim.x) {
                 const int b = (int)__umulhi((unsigned)e, divL), a = e - b * L;
                 const bool ra = a < na, rb = b < nb;
@@ -139,9 +142,6 @@ __global__ void __launch_bounds__(kDummyThreads, 2) dummy_recurse_kernel(
                     else bs = __fadd_rn(sm.u[sA][a], al);
                     sm.base[b * L + a] = bs;
                 }
-                const int a2 = b, c = a;   // R(a, c) over the same index space, where (a, c) can be feasible
-                if (a2 < na && c < nc && sm.t[sC][c] <= sm.t[sA][a2] && !(p.T > 0 && sm.t[sA][a2] - sm.t[sC][c] >= p.T))
-                    sm.r[a2 * kRL + c] = direction(sm.xy[sA][a2], sm.xy[sC][c]);
             }
             __syncthreads();
             // branch and bound (exact): v(a, b, c) >= base(b, a), and no open cell of row b has a best above
@@ -202,7 +202,13 @@ __global__ void __launch_bounds__(kDummyThreads, 2) dummy_recurse_kernel(
                     }
                     if (k0) sm.srt[b][r0] = (uint8_t)lane;
                     if (k1) sm.srt[b][r1] = (uint8_t)(lane + 32);
-                    if (lane == 0) sm.kept[b] = (uint8_t)(__popc(m0) + __popc(m1));
+                    if (lane == 0) {
+                        sm.kept[b] = (uint8_t)(__popc(m0) + __popc(m1));
+                        if (rb) {   // the cells of a real row read R(a, c) of its kept a
+                            if (m0) atomicOr(&sm.akept[0], m0);
+                            if (m1) atomicOr(&sm.akept[1], m1);
+                        }
+                    }
                     // directions of the kept pairs of a real b, the only ones the cells read: lane r takes the
                     // kept a of rank r
                     if (rb) {
@@ -214,6 +220,20 @@ __global__ void __launch_bounds__(kDummyThreads, 2) dummy_recurse_kernel(
                             sm.p1[b * L + a] = __fadd_rn(A1, direction(xb, sm.xy[sA][a]));
                             sm.p2[b * L + a] = __fadd_rn(A2, direction(sm.xy[sA][a], xb));
                         }
+                    }
+                }
+            }
+            __syncthreads();
+            // R(a, c) = theta(a->c) for the a some real row keeps, where (a, c) can be feasible (with W^d small
+            // most rows keep no a: their cells take eps without any direction)
+            {
+                const unsigned k0 = sm.akept[0], k1 = sm.akept[1];
+                if (k0 | k1) {
+                    for (int e = threadIdx.x; e < L * L; e += blockDim.x) {
+                        const int a2 = (int)__umulhi((unsigned)e, divL), c = e - a2 * L;
+                        if (a2 >= na || c >= nc || !(((a2 < 32 ? k0 : k1) >> (a2 & 31)) & 1u)) continue;
+                        if (sm.t[sC][c] <= sm.t[sA][a2] && !(p.T > 0 && sm.t[sA][a2] - sm.t[sC][c] >= p.T))
+                            sm.r[a2 * kRL + c] = direction(sm.xy[sA][a2], sm.xy[sC][c]);
                     }
                 }
             }
