@@ -138,7 +138,9 @@ def score_split_bf16(p, x, model_xy, scene_xy, F, rnd=bf16, window=3):
     (both products on BF16 operands, each part rounded once to BF16), and a time term: the hidden units are
     h1 = relu(rnd(dt * rnd(W1c_t / w) + rnd(P + Q))), dt = t'_j - t_i - o the integer frame difference and
     w = window (at least 1) -- one BF16 add and one fused BF16 multiply-add per unit, as BF16x2 arithmetic
-    does it. Layer 2 then runs on BF16 operands (h1 is one already) and the output layer is unrounded.
+    does it. Layer 2 then runs on BF16 operands (h1 is one already), its bias b2 rounded to BF16 as well (it
+    enters the tensor-core product as one more input against a constant 1), and the output layer is
+    unrounded.
     x holds the rows of features() built with the same window (the dx, dy columns are not used; the positions
     come in separately). With the identity as rnd it is forward()'s z3, the split being exact algebra."""
     W1 = p["W1"]
@@ -148,7 +150,7 @@ def score_split_bf16(p, x, model_xy, scene_xy, F, rnd=bf16, window=3):
     Q = rnd(rnd(x[:, F:2 * F]) @ rnd(Wb).T + (scene_xy @ Wxy.T) / 100.0)
     dt = rnd(np.rint(x[:, 2 * F + 2] * w))
     h1 = np.maximum(rnd(dt[:, None] * rnd(Wt / w)[None, :] + rnd(P + Q)), 0.0)
-    z2 = h1 @ rnd(p["W2"]).T + p["b2"]
+    z2 = h1 @ rnd(p["W2"]).T + rnd(p["b2"])
     return np.maximum(z2, 0.0) @ p["w3"] + p["b3"][0]
 
 

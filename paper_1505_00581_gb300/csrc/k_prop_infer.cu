@@ -18,9 +18,10 @@
 //
 // The scoring kernel stages 128 candidates per tile (128 / 2^ceil(log2 K)
 // lists) as BF16 and runs layer 2 (128 x 128) as tcgen05.mma with W2 resident
-// in shared memory. Tiles are double-buffered in shared memory and in tensor
-// memory: tile k is gathered while the MMA of tile k - 1 runs, its epilogue
-// (relu(+b2), dot with w3) follows the issue of tile k, and the two column
+// in shared memory, the bias b2 (BF16) entering as one more K step against a
+// constant column of ones. Tiles are double-buffered in shared memory and in
+// tensor memory: tile k is gathered while the MMA of tile k - 1 runs, its
+// epilogue (relu, dot with w3) follows the issue of tile k, and the two column
 // halves of a row are summed one tile later, so one barrier per tile suffices.
 #include "hgm_internal.cuh"
 #include "prop.cuh"
@@ -38,11 +39,17 @@ constexpr uint32_t kSBO = (H / 8) * 128;   // K = 128 components per row
 constexpr uint32_t kPolls = 1u << 26;
 constexpr float kNegInf = -__builtin_huge_valf();
 
+constexpr uint32_t kSBO16 = 2 * 128;       // K = 16 components per row (the bias block)
+
 struct Smem {
     unsigned char a[2][TM * H * 2];  // hidden layer 1 of two tiles, BF16, canonical K-major
     unsigned char w2[H * H * 2];     // W2 (rows = output units), BF16
+    // the layer-2 bias as a 17th K step of the MMA: A gets a constant block (component 0 = 1, the rest 0)
+    // shared by both tiles, W2 a block whose component 0 is b2 (BF16)
+    unsigned char a1[TM * 16 * 2];
+    unsigned char b2k[H * 16 * 2];
     float part[2][2][TM];            // [buffer][column half][row]: half-sums of the last layer
-    float b2[H], w3[H];              // layer-2 bias and output weights
+    float w3[H];                     // output weights
     float b3;
     uint64_t mbar[2];
     uint32_t tslot;
@@ -106,9 +113,17 @@ __global__ void __launch_bounds__(256, 2) prop_score_kernel(const Unit *__restri
             h[q] = __floats2bfloat162_rn(pi.W2[r * H + k + 2 * q], pi.W2[r * H + k + 2 * q + 1]);
         *reinterpret_cast<uint4 *>(sm.w2 + tc05::kmajor_offset(r, k, kLBO, kSBO)) = *reinterpret_cast<uint4 *>(h);
     }
-    for (int h = tid; h < H; h += 256) {
-        sm.b2[h] = pi.b2[h];
-        sm.w3[h] = pi.w3[h];
+    for (int h = tid; h < H; h += 256) sm.w3[h] = pi.w3[h];
+    for (int e = tid; e < TM * 2; e += 256) {          // the bias blocks: 16-byte chunks of 8 components
+        const int r = e >> 1, k = (e & 1) * 8;
+        __align__(16) __nv_bfloat16 ha[8], hb[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            ha[q] = __float2bfloat16_rn(k + q == 0 ? 1.0f : 0.0f);
+            hb[q] = __float2bfloat16_rn(k + q == 0 ? pi.b2[r] : 0.0f);
+        }
+        *reinterpret_cast<uint4 *>(sm.a1 + tc05::kmajor_offset(r, k, kLBO, kSBO16)) = *reinterpret_cast<uint4 *>(ha);
+        *reinterpret_cast<uint4 *>(sm.b2k + tc05::kmajor_offset(r, k, kLBO, kSBO16)) = *reinterpret_cast<uint4 *>(hb);
     }
     if (tid == 0) {
         sm.b3 = pi.b3[0];
@@ -130,7 +145,7 @@ __global__ void __launch_bounds__(256, 2) prop_score_kernel(const Unit *__restri
     bool bad = false, stop = false;
     int64_t k = 0;
 
-    // epilogue of the tile in accumulator b: relu(z + b2) . w3 over this thread's 64 columns
+    // epilogue of the tile in accumulator b: relu(z) . w3 over this thread's 64 columns (z holds b2)
     auto epilogue = [&](int b) {
         bool ok = tc05::mbar_wait(&sm.mbar[b], (parity >> b) & 1u, kPolls);
         ok = __all_sync(0xffffffffu, ok);
@@ -146,12 +161,10 @@ __global__ void __launch_bounds__(256, 2) prop_score_kernel(const Unit *__restri
                 float v[32];
                 tc05::tmem_ld32(tlane + (uint32_t)(H * b + c0), v);
 #pragma unroll
-                for (int q = 0; q < 32; q += 2) {
-                    const float2 b2 = *reinterpret_cast<const float2 *>(&sm.b2[h0 + c0 + q]);
-                    const float2 w3 = *reinterpret_cast<const float2 *>(&sm.w3[h0 + c0 + q]);
-                    float z0, z1;
-                    upk2(add2(pk2(v[q], v[q + 1]), pk2(b2.x, b2.y)), z0, z1);
-                    acc2 = fma2(pk2(fmaxf(z0, 0.0f), fmaxf(z1, 0.0f)), pk2(w3.x, w3.y), acc2);
+                for (int q = 0; q < 32; q += 4) {
+                    const float4 w3 = *reinterpret_cast<const float4 *>(&sm.w3[h0 + c0 + q]);
+                    acc2 = fma2(pk2(fmaxf(v[q], 0.0f), fmaxf(v[q + 1], 0.0f)), pk2(w3.x, w3.y), acc2);
+                    acc2 = fma2(pk2(fmaxf(v[q + 2], 0.0f), fmaxf(v[q + 3], 0.0f)), pk2(w3.z, w3.w), acc2);
                 }
             }
             float a0, a1;
@@ -242,6 +255,8 @@ __global__ void __launch_bounds__(256, 2) prop_score_kernel(const Unit *__restri
                 for (int ks = 0; ks < H / 16; ++ks)
                     tc05::mma_bf16(taddr + (uint32_t)(H * buf), tc05::smem_desc(a0 + ks * 2 * kLBO, kLBO, kSBO),
                                    tc05::smem_desc(b0 + ks * 2 * kLBO, kLBO, kSBO), idesc, ks > 0);
+                tc05::mma_bf16(taddr + (uint32_t)(H * buf), tc05::smem_desc(tc05::smem_u32(sm.a1), kLBO, kSBO16),
+                               tc05::smem_desc(tc05::smem_u32(sm.b2k), kLBO, kSBO16), idesc, true);
                 tc05::mma_commit(&sm.mbar[buf]);
             }
             pending |= 1u << buf;

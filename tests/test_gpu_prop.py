@@ -213,7 +213,7 @@ def test_scoring_kernel_matches_fp64(env, K, window, precision):
     in, layer 2 on the tensor cores) against the FP64 network on the same candidates: to 2e-3 of the logit
     range against the emulation that rounds to BF16 what the kernels round (the descriptors and W1a/W1b in
     the projections, both projections once they hold the position terms, the first layer's BF16x2 add and
-    fused multiply-add, W2 in layer 2); within
+    fused multiply-add, W2 and b2 in layer 2); within
     5% of the spread against plain FP64. Empty slots are
     -inf. K = 64 with w = 0: lists of about 30 candidates (many empty slots); K = 24 with w = 3: full lists,
     four lists of 32 rows (8 of them empty) in each 128-row tile."""
