@@ -30,7 +30,9 @@
 // a of smallest base, m(b,c) = base(w) wherever w is feasible with c; for the
 // cells where it is not, m(b,c) is at most the runner-up's base when the
 // runner-up is feasible with c; where neither the witness nor the runner-up is
-// feasible with some c, no threshold is taken and every a of b is kept. Only
+// feasible with some c, no threshold is taken and every a of b is kept. (Which
+// c rule them out is read off C by bisection: C is sorted by scene index, hence
+// by time, so "too far in time" is a prefix and "same point" a lookup.) Only
 // the kept a (about a third of the feasible ones on the batched workload) enter the
 // triple loop, in increasing slot order with a strict '<', so the lowest slot
 // still wins exact ties -- the result is bit-identical to the full minimisation.
@@ -283,21 +285,47 @@ recurse_kernel(const Unit *__restrict__ units, int64_t n_units, const ModelRec *
                 // (rare) every a is kept
                 bool anybad = false, loose = false;
                 if (live) {
+                    // C is in increasing scene index, hence in increasing time: the c with t'(c) <= x form a
+                    // prefix, and a point's slot in C is found by bisection. The cells of b's own point are
+                    // infeasible and never count; the witness and the runner-up are feasible with b, so their
+                    // points differ from b's.
                     const int tw = LA.t[s1], iw = LA.idx[s1];
-                    const int t2 = s2 < KM ? LA.t[s2] : 0, i2 = s2 < KM ? LA.idx[s2] : -2;
-#pragma unroll 4
-                    for (int k = 0; NP * k + h < ccount; ++k) {
-                        const int c = NP * k + h;
-                        const int tc = LC.t[c], ic = LC.idx[c];
-                        if (ic != ib && ((T > 0 && tw - tc >= T) || iw == ic)) {
-                            anybad = true;
-                            if (!(m2 < kInf) || (T > 0 && t2 - tc >= T) || i2 == ic) loose = true;
+                    const bool has2 = m2 < kInf;
+                    const int t2 = has2 ? LA.t[s2] : 0, i2 = has2 ? LA.idx[s2] : -2;
+                    auto count_le = [&](int x) {
+                        int lo = 0, hi = ccount;
+                        while (lo < hi) {
+                            const int mid = (lo + hi) >> 1;
+                            if (LC.t[mid] <= x) lo = mid + 1;
+                            else hi = mid;
+                        }
+                        return lo;
+                    };
+                    auto slot_of = [&](int j) {
+                        int lo = 0, hi = ccount;
+                        while (lo < hi) {
+                            const int mid = (lo + hi) >> 1;
+                            if (LC.idx[mid] < j) lo = mid + 1;
+                            else hi = mid;
+                        }
+                        return lo < ccount && LC.idx[lo] == j ? lo : -1;
+                    };
+                    const int pbs = slot_of(ib);
+                    const int nT = T > 0 ? count_le(tw - T) : 0;                  // c too far from the witness
+                    const int pw = slot_of(iw);                                   // c at the witness's point
+                    anybad = nT - (pbs >= 0 && pbs < nT ? 1 : 0) > 0 || pw >= 0;
+                    if (anybad) {
+                        if (!has2) {
+                            loose = true;
+                        } else {
+                            // a c that rules out both: too far from both, or at one's point and too far from
+                            // the other
+                            const int nT2 = T > 0 ? count_le(min(tw, t2) - T) : 0;
+                            const int p2 = slot_of(i2);
+                            loose = nT2 - (pbs >= 0 && pbs < nT2 ? 1 : 0) > 0 || (p2 >= 0 && p2 < nT) ||
+                                    (pw >= 0 && T > 0 && t2 - tw >= T);
                         }
                     }
-                }
-                if constexpr (NP == 2) {
-                    anybad |= __shfl_xor_sync(0xffffffffu, (int)anybad, 1) != 0;
-                    loose |= __shfl_xor_sync(0xffffffffu, (int)loose, 1) != 0;
                 }
                 float thr = bv + gmax + 1e-6f * bv;
                 if (anybad) thr = !loose && m2 < kInf ? fmaxf(thr, m2 + gmax + 1e-6f * m2) : kInf;
