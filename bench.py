@@ -42,8 +42,8 @@ L2_NOTE = "flushed (512 MiB write) before every step"
 # a small case, with the sources of the kernel it captured and the capture's argmin-table bytes
 # sum n_offsets (M - 2) K^2. Both the tables written and the lists read grow in proportion to that sum,
 # so a full launch's traffic is scaled by it; a changed kernel source voids the figure.
-RECURSE_NCU = {"sources_sha256": "79958b1f0a94cd03b633d216f8d6648011a21dd6f9f811969b90b30731098cbf",
-               "bytes": 846_869_248 + 1_285_779_456, "beta_bytes": 1_667_760_128, "case": "combined_small"}
+RECURSE_NCU = {"sources_sha256": "015ced47a289cc2cc1d45f3754dcef8c424ddc24374815637abff006ea0717e5",
+               "bytes": 847_114_240 + 1_286_494_000, "beta_bytes": 1_667_760_128, "case": "combined_small"}
 RECURSE_SOURCES = ("k_recurse.cu", "recurse_common.cuh", "f32x2.cuh")
 
 
@@ -288,7 +288,7 @@ def _time_plan(torch, hgm, models, scenes, p, energy, assign, steps, warmup, str
     return sum(a.elapsed_time(b) for a, b in zip(starts, ends)) / steps
 
 
-def _time_form(torch, hgm, models, scenes, p, energy, assign, steps, warmup, stream, flush):
+def _time_form(torch, hgm, models, scenes, p, energy, assign, steps, warmup, stream, flush, profile=False):
     for _ in range(warmup):
         hgm.match_batch(models, scenes, p, energy, assign)
     torch.cuda.synchronize()
@@ -296,12 +296,16 @@ def _time_form(torch, hgm, models, scenes, p, energy, assign, steps, warmup, str
     hgm.profile_enable(True)
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    if profile:
+        torch.cuda.profiler.start()
     for k in range(steps):
         flush.zero_()
         starts[k].record(stream)
         hgm.match_batch(models, scenes, p, energy, assign)
         ends[k].record(stream)
     torch.cuda.synchronize()
+    if profile:
+        torch.cuda.profiler.stop()
     hgm.profile_enable(False)
     return sum(a.elapsed_time(b) for a, b in zip(starts, ends)) / steps, hgm.profile_read()
 
@@ -529,10 +533,10 @@ def run_pruned(args, torch, hgm, wl, job_cs, models, scenes, energy, assign, fir
     a2 = torch.empty_like(assign)
     pk, pk_kind = peaks()
 
-    def form(p, label, with_graph=False):
+    def form(p, label, with_graph=False, profile=False):
         hgm.prune_counters(reset=True)
         hgm.refine_counter(reset=True)
-        ms, prof = _time_form(torch, hgm, models, scenes, p, e2, a2, steps, warm, stream, flush)
+        ms, prof = _time_form(torch, hgm, models, scenes, p, e2, a2, steps, warm, stream, flush, profile)
         ms = max_over_ranks(ms, dist, dev)
         n_pruned, n_fb = hgm.prune_counters(reset=True)
         n_ref = hgm.refine_counter(reset=True)
@@ -566,7 +570,8 @@ def run_pruned(args, torch, hgm, wl, job_cs, models, scenes, energy, assign, fir
     # exact solve, so its main form keeps 16
     keep = args.keep if args.keep is not None else (16 if job_cs is not None else 8)
     pruned, prof = form(params_of(hgm, wl, precision=1, prune=prop, keep=keep),
-                        f"BF16 unary + FP32 re-score of the kept candidates, network keeps {keep} of {wl.K}", True)
+                        f"BF16 unary + FP32 re-score of the kept candidates, network keeps {keep} of {wl.K}",
+                        args.profile_form != "pruned", args.profile_form == "pruned")
     cands = sum(wl.n_offsets(mi, si) * wl.models[mi].n * wl.K
                 for mi in range(len(wl.models)) for si in range(len(wl.scenes)))
     prune_ms = prof["prune"][0] / steps
@@ -577,6 +582,8 @@ def run_pruned(args, torch, hgm, wl, job_cs, models, scenes, energy, assign, fir
                                   "work": f"{cands} candidate slots x 2 x 128 x 128 (layer 2 on the tensor cores)",
                                   "peak_source": f"bf16_tflops of MEASURED_PEAKS.json ({pk_kind})"}
     pruned["keep"] = keep
+    if args.profile_form == "pruned":   # a profiling run: the main pruned form alone
+        return pruned
     if keep != 8:
         pruned["keep8"], _ = form(params_of(hgm, wl, precision=1, prune=prop, keep=8),
                                   f"network keeps 8 of {wl.K} (the learned stage as specified)")
@@ -632,6 +639,9 @@ def main():
     ap.add_argument("--fp64-dump", default=None,
                     help="write the exact and BF16 forms' energies at a seeded sample of units to this .npz")
     ap.add_argument("--fp64-sample-frac", type=float, default=0.01, help="fraction of units in --fp64-dump")
+    ap.add_argument("--profile-form", default="exact", choices=["exact", "pruned"],
+                    help="whose timed steps are bracketed by cudaProfilerStart/Stop (for ncu --profile-from-start "
+                         "off); pruned also skips the secondary pruned forms")
     ap.add_argument("--train-steps", type=int, default=2000)
     ap.add_argument("--checkpoint", default=None, help="load the proposal network from <path>.bin/.json")
     args = ap.parse_args()
@@ -704,7 +714,8 @@ def main():
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
-    torch.cuda.profiler.start()     # an ncu run with --profile-from-start off captures only the timed steps
+    if args.profile_form == "exact":
+        torch.cuda.profiler.start()     # an ncu run with --profile-from-start off captures only the timed steps
     with Clocks(local) as clk:
         for k in range(args.steps):
             flush.zero_()
@@ -712,7 +723,8 @@ def main():
             hgm.match_batch(models, scenes, p, energy, assign)
             ends[k].record(stream)
         torch.cuda.synchronize()
-    torch.cuda.profiler.stop()
+    if args.profile_form == "exact":
+        torch.cuda.profiler.stop()
     if dist:
         dist.barrier()
     hgm.profile_enable(False)
