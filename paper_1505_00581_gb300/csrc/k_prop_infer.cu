@@ -187,22 +187,31 @@ __global__ void __launch_bounds__(256, 2) prop_score_kernel(const Unit *__restri
         const SceneRec sc = scenes[un.scene];
         const int M = md.M;
         const int64_t lbase = un.cand / K;
+        // the 8 row groups' list counts and raw candidate indices of the tile at i0 (the slot clamped into the
+        // unit's lists, so the index load does not wait for the count); the next tile's are loaded right after
+        // this tile's build, so that they arrive while the barrier, the MMA issue and the epilogue run
+        int cn[8], jr[8];
+        auto load_idx = [&](int i0n) {
+#pragma unroll
+            for (int g = 0; g < 8; ++g) {
+                const int r = brow0 + 8 * g, lst = i0n + (r >> kp_log2), sl = r & ((1 << kp_log2) - 1);
+                const int lc = lst < M ? lst : M - 1, sc_ = sl < K ? sl : K - 1;
+                cn[g] = cand_cnt[lbase + lc];
+                jr[g] = cand_idx[un.cand + (int64_t)lc * K + sc_];
+            }
+        };
+        load_idx(0);
         for (int i0 = 0; i0 < M; i0 += lpt) {
             const int buf = (int)(k & 1);
             unsigned char *arow = sm.a[buf];
-            // gather: the 8 row groups' candidate indices first, then their frames and Q chunks
+            // gather: the candidate indices (loaded before), then their frames and Q chunks
             int jg[8];
             bool vg[8];
 #pragma unroll
             for (int g = 0; g < 8; ++g) {
                 const int r = brow0 + 8 * g, lst = i0 + (r >> kp_log2), sl = r & ((1 << kp_log2) - 1);
-                // count and index loaded together (the slot clamped into the unit's lists), so the index load
-                // does not wait for the count
-                const int lc = lst < M ? lst : M - 1, sc_ = sl < K ? sl : K - 1;
-                const int cnt = cand_cnt[lbase + lc];
-                const int jraw = cand_idx[un.cand + (int64_t)lc * K + sc_];
-                vg[g] = lst < M && sl < cnt;
-                jg[g] = vg[g] ? jraw : 0;
+                vg[g] = lst < M && sl < cn[g];
+                jg[g] = vg[g] ? jr[g] : 0;
             }
             int tg[8];
             uint4 qg[8];
@@ -240,6 +249,7 @@ __global__ void __launch_bounds__(256, 2) prop_score_kernel(const Unit *__restri
                 *reinterpret_cast<uint4 *>(arow + tc05::kmajor_offset(r, bh0, kLBO, kSBO)) =
                     *reinterpret_cast<uint4 *>(hh);
             }
+            if (i0 + lpt < M) load_idx(i0 + lpt);
             // this thread's epilogue row
             const int list = i0 + lsub;
             const bool valid = list < M && slot < cand_cnt[lbase + (list < M ? list : 0)];

@@ -201,7 +201,8 @@ __global__ void __launch_bounds__(128) unary_tma_kernel(const __grid_constant__ 
                                                         const __grid_constant__ CUtensorMap tmB, int64_t S, int R,
                                                         int Kp, const float *__restrict__ snorm,
                                                         const float *__restrict__ mnorm, float lambda1,
-                                                        float *__restrict__ U, int64_t ldu, int *__restrict__ status)
+                                                        float *__restrict__ U, int64_t ldu, int mrows_per_cta,
+                                                        int *__restrict__ status)
 {
     // the tiles start on a 1024-byte boundary of the shared window (TMA destinations want 128), whatever the
     // placement of the dynamic array after the static variables: the launch asks for 1024 bytes more
@@ -229,19 +230,21 @@ __global__ void __launch_bounds__(128) unary_tma_kernel(const __grid_constant__ 
     const uint32_t tile_bytes = (uint32_t)TM * Kp * 2;
     uint32_t tphase = 0, mphase = 0;
     const int64_t ntiles = (S + TM - 1) / TM;
+    // this CTA's model rows: [m_lo, m_hi) of the grid's y dimension
+    const int m_lo = (int)blockIdx.y * mrows_per_cta, m_hi = min(R, m_lo + mrows_per_cta);
     for (int64_t tile = blockIdx.x; tile < ntiles && !bad; tile += gridDim.x) {
         const int64_t r0 = tile * TM;
         const int64_t row = r0 + tid;
         const float xn = row < S ? snorm[row] : 0.0f;
-        for (int m0 = 0; m0 < R && !bad; m0 += TN) {
+        for (int m0 = m_lo; m0 < m_hi && !bad; m0 += TN) {
             if (tid == 0) {
                 // sA and sB are free: the previous tile's MMAs completed (mma_bar) before the last barrier
-                mbar_expect_tx(&tma_bar, m0 == 0 ? 2 * tile_bytes : tile_bytes);
-                if (m0 == 0)
+                mbar_expect_tx(&tma_bar, m0 == m_lo ? 2 * tile_bytes : tile_bytes);
+                if (m0 == m_lo)
                     for (int k8 = 0; k8 < nk8; ++k8) tma_load_2d(sA + (size_t)k8 * kTmaLBO, &tmA, 8 * k8, (int)r0, &tma_bar);
                 for (int k8 = 0; k8 < nk8; ++k8) tma_load_2d(sB + (size_t)k8 * kTmaLBO, &tmB, 8 * k8, m0, &tma_bar);
             }
-            wn[tid] = m0 + tid < R ? mnorm[m0 + tid] : 0.0f;
+            wn[tid] = m0 + tid < m_hi ? mnorm[m0 + tid] : 0.0f;
             if (tid == 0) {
                 if (tc05::mbar_wait(&tma_bar, tphase, kPolls)) {
                     tc05::fence_after_sync();
@@ -267,14 +270,14 @@ __global__ void __launch_bounds__(128) unary_tma_kernel(const __grid_constant__ 
             mphase ^= 1u;
             tc05::fence_after_sync();
             if (!bad) {
-                for (int cc = 0; cc < TN && m0 + cc < R; cc += 32) {
+                for (int cc = 0; cc < TN && m0 + cc < m_hi; cc += 32) {
                     float v[32];
                     tc05::tmem_ld32(tlane + (uint32_t)cc, v);
                     if (row < S) {
 #pragma unroll
                         for (int j = 0; j < 32; ++j) {
                             const int c = m0 + cc + j;
-                            if (c < R) {
+                            if (c < m_hi) {
                                 const float d2 = fmaxf(xn + wn[cc + j] - 2.0f * v[j], 0.0f);
                                 U[(int64_t)c * ldu + row] = lambda1 * sqrtf(d2);
                             }
@@ -394,9 +397,14 @@ cudaError_t launch_unary_bf16(const float *model, int R, const float *scene, int
         if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, unary_tma_kernel, 128, smem);
         if (e == cudaSuccess) {
             per_sm = per_sm < 1 ? 1 : (per_sm > 4 ? 4 : per_sm);   // 4 x 128 TMEM columns = the SM's 512
-            const int64_t grid = std::min<int64_t>(((int64_t)S + TM - 1) / TM, (int64_t)sms * per_sm);
-            unary_tma_kernel<<<(unsigned)grid, 128, smem, st>>>(tmA, tmB, S, R, Kp, snorm, mnorm, lambda1, U, ldu,
-                                                                status);
+            // scene tiles on x, chunks of kMTiles model tiles on y: enough CTAs that two per SM overlap one
+            // another's copies, products and epilogues even when the scene has few tiles
+            constexpr int kMTiles = 8;
+            const int64_t stiles = ((int64_t)S + TM - 1) / TM;
+            const int mchunks = (R + TN * kMTiles - 1) / (TN * kMTiles);
+            const int64_t gx = std::min<int64_t>(stiles, std::max<int64_t>(1, (int64_t)sms * per_sm * 8 / mchunks));
+            unary_tma_kernel<<<dim3((unsigned)gx, (unsigned)mchunks), 128, smem, st>>>(
+                tmA, tmB, S, R, Kp, snorm, mnorm, lambda1, U, ldu, TN * kMTiles, status);
             e = cudaGetLastError();
         }
     } else {
