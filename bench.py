@@ -431,12 +431,16 @@ def run_blocks(args, torch, hgm, dev, stream, flush):
     torch.cuda.synchronize()
     steps = max(1, min(args.steps, 10))
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    if args.profile_form == "whole_block":
+        torch.cuda.profiler.start()
     for x, y in evs:
         flush.zero_()
         x.record(stream)
         hgm.match_block(wm, wsc, p, ed, ad, stream=stream)
         y.record(stream)
     torch.cuda.synchronize()
+    if args.profile_form == "whole_block":
+        torch.cuda.profiler.stop()
     ms = sum(x.elapsed_time(y) for x, y in evs) / len(evs)
     whole = {"workload": ww.name, "scene_points": s0.n, "scene_frames": s0.n_frames, "models": len(wm),
              "ms": ms, "value": s0.n_frames / (ms / 1e3), "unit": "scene frames/s (all models, whole scene)",
@@ -453,7 +457,7 @@ def run_dummy(args, torch, hgm, wl, models, scenes, dev, stream, world, flush, d
     e = torch.empty(int(es[-1]), dtype=torch.float32, device=dev)
     a = torch.empty(int(as_[-1]), dtype=torch.int32, device=dev)
     steps = max(1, min(args.steps, 3))
-    ms, prof = _time_form(torch, hgm, models, scenes, p, e, a, steps, 1, stream, flush)
+    ms, prof = _time_form(torch, hgm, models, scenes, p, e, a, steps, 1, stream, flush, args.profile_form == "dummy")
     ms = max_over_ranks(ms, dist, dev)
     eps_fraction = float((a == -2).float().mean().item())
     finite = int(torch.isfinite(e).sum().item())
@@ -639,7 +643,7 @@ def main():
     ap.add_argument("--fp64-dump", default=None,
                     help="write the exact and BF16 forms' energies at a seeded sample of units to this .npz")
     ap.add_argument("--fp64-sample-frac", type=float, default=0.01, help="fraction of units in --fp64-dump")
-    ap.add_argument("--profile-form", default="exact", choices=["exact", "pruned"],
+    ap.add_argument("--profile-form", default="exact", choices=["exact", "pruned", "dummy", "whole_block"],
                     help="whose timed steps are bracketed by cudaProfilerStart/Stop (for ncu --profile-from-start "
                          "off); pruned also skips the secondary pruned forms")
     ap.add_argument("--train-steps", type=int, default=2000)
