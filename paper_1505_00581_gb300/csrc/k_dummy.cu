@@ -125,10 +125,11 @@ __global__ void __launch_bounds__(kDummyThreads, 2) dummy_recurse_kernel(
                 sm.ang[0] = signed_angle(mj, mi, mk);   // A1: at i-1, from ->i to ->i-2
                 sm.ang[1] = signed_angle(mi, mj, mk);   // A2: at i, from ->i-1 to ->i-2
             }
-            __syncthreads();
-            const float A1 = sm.ang[0], A2 = sm.ang[1];
+            // base reads lists i and i - 1 only: after the first step they are in place already, so the list
+            // being loaded (i - 2) and the base table share one barrier
+            if (i == M - 1) __syncthreads();
             const int dt1 = md.t[i] - md.t[i - 1], dt2 = md.t[i - 1] - md.t[i - 2];
-            const int na = sm.cnt[sA], nb = sm.cnt[sB], nc = sm.cnt[sC];
+            const int na = sm.cnt[sA], nb = sm.cnt[sB];
             const float *an = sm.alpha[cur];
             const bool last = i == M - 1;
             // base(b, a); rows/columns of empty slots are never read
@@ -144,6 +145,8 @@ __global__ void __launch_bounds__(kDummyThreads, 2) dummy_recurse_kernel(
                 }
             }
             __syncthreads();
+            const float A1 = sm.ang[0], A2 = sm.ang[1];
+            const int nc = sm.cnt[sC];
             // branch and bound (exact): v(a, b, c) >= base(b, a), and no open cell of row b has a best above
             // thr(b). A warp per row keeps the a with base <= thr(b) that may follow b (any real a after eps)
             // and ranks them by (base, slot) by counting.
