@@ -840,6 +840,11 @@ def main():
         pruned = run_pruned(args, torch, hgm, wl, job_cs, models, scenes, energy, assign, first, es, as_, dev,
                             stream, world, flush, sampled, dist)
         pruned["speedup_vs_exact"] = pruned["value"] / value
+        # the precision path's (BF16 distance + FP32 re-score, unpruned) error on the oracle's units, beside the
+        # exact path's
+        bf = pruned if args.no_network else pruned.get("bf16_unpruned")
+        if cpu is not None and bf and bf.get("fp64"):
+            cpu["fp64_check_bf16_rescore"] = bf["fp64"]
 
     if rank == 0:
         cfg = config_of(wl, job, args, world)
