@@ -320,21 +320,61 @@ __global__ void __launch_bounds__(256) prop_keep_kernel(const Unit *__restrict__
             const int nl = cand_cnt[lbase + li];
             const int kk = nl < keep ? nl : keep;
             const float *sl = scores + (lbase + li) * K;
-            float v0 = lane < nl ? sl[lane] : kNegInf;
-            float v1 = lane + 32 < nl ? sl[lane + 32] : kNegInf;
             bool c0 = false, c1 = false;
-            for (int q = 0; q < kk; ++q) {
-                float bv = v0 >= v1 ? v0 : v1;
-                int bs = v0 >= v1 ? lane : lane + 32;
-                if (lane >= nl) bs = 1 << 20;
+            if (kk <= 10) {
+                // a few rounds of a warp-wide argmax (ties: lower slot); longer keeps bisect for the threshold
+                float v0 = lane < nl ? sl[lane] : kNegInf;
+                float v1 = lane + 32 < nl ? sl[lane + 32] : kNegInf;
+                for (int q = 0; q < kk; ++q) {
+                    float bv = v0 >= v1 ? v0 : v1;
+                    int bs = v0 >= v1 ? lane : lane + 32;
+                    if (lane >= nl) bs = 1 << 20;
+#pragma unroll
+                    for (int off = 16; off > 0; off >>= 1) {
+                        const float ov = __shfl_xor_sync(0xffffffffu, bv, off);
+                        const int os = __shfl_xor_sync(0xffffffffu, bs, off);
+                        if (ov > bv || (ov == bv && os < bs)) { bv = ov; bs = os; }
+                    }
+                    if (bs == lane) { c0 = true; v0 = kNegInf; }
+                    if (bs == lane + 32) { c1 = true; v1 = kNegInf; }
+                }
+            } else {
+                // the kept set: the kk largest scores, ties to the lower slot (slots in [0, nl)). Scores become
+                // order-preserving keys (larger score, larger key); empty slots get key 0, below every score's key
+                // (a score is finite or -inf, whose key is 0x007fffff)
+                auto okey = [](float v) {
+                    const uint32_t b = __float_as_uint(v == 0.0f ? 0.0f : v);   // -0 ties with +0, as a float compare
+                    return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+                };
+                const uint32_t k0 = lane < nl ? okey(sl[lane]) : 0u;
+                const uint32_t k1 = lane + 32 < nl ? okey(sl[lane + 32]) : 0u;
+                // the kk-th largest key T, bit by bit from the top: the largest T with at least kk keys >= T.
+                // Bits on which every key of the list agrees are read off an AND and an OR of the keys.
+                uint32_t kand = k0 & k1, kor = k0 | k1;
 #pragma unroll
                 for (int off = 16; off > 0; off >>= 1) {
-                    const float ov = __shfl_xor_sync(0xffffffffu, bv, off);
-                    const int os = __shfl_xor_sync(0xffffffffu, bs, off);
-                    if (ov > bv || (ov == bv && os < bs)) { bv = ov; bs = os; }
+                    kand &= __shfl_xor_sync(0xffffffffu, kand, off);
+                    kor |= __shfl_xor_sync(0xffffffffu, kor, off);
                 }
-                if (bs == lane) { c0 = true; v0 = kNegInf; }
-                if (bs == lane + 32) { c1 = true; v1 = kNegInf; }
+                const uint32_t differ = kand ^ kor;
+                uint32_t T = kand & ~differ;   // the common bits
+                // only the differing bits need a test, from the highest down
+                for (int bit = differ ? 31 - __clz(differ) : -1; bit >= 0; --bit) {
+                    if (!((differ >> bit) & 1u)) continue;
+                    const uint32_t cand = T | (1u << bit);
+                    const int cnt = __popc(__ballot_sync(0xffffffffu, k0 >= cand)) +
+                                    __popc(__ballot_sync(0xffffffffu, k1 >= cand));
+                    if (cnt >= kk) T = cand;
+                }
+                // keep every key above T, then the keys equal to T in slot order up to kk
+                const int above =
+                    __popc(__ballot_sync(0xffffffffu, k0 > T)) + __popc(__ballot_sync(0xffffffffu, k1 > T));
+                const uint32_t e0 = __ballot_sync(0xffffffffu, k0 == T && lane < nl);
+                const uint32_t e1 = __ballot_sync(0xffffffffu, k1 == T && lane + 32 < nl);
+                const int need = kk - above;
+                const int r0 = __popc(e0 & lt), r1 = __popc(e0) + __popc(e1 & lt);
+                c0 = lane < nl && (k0 > T || (((e0 >> lane) & 1u) && r0 < need));
+                c1 = lane + 32 < nl && (k1 > T || (((e1 >> lane) & 1u) && r1 < need));
             }
             const uint32_t m0 = __ballot_sync(0xffffffffu, c0), m1 = __ballot_sync(0xffffffffu, c1);
             const int64_t obase = (lbase + li) * keep;
