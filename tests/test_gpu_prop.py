@@ -191,6 +191,57 @@ def test_pruning_is_a_restriction_with_fallback(env):
             assert abs(orc.energy(a1[k]) - e1[k]) <= 1e-5 * e1[k]
 
 
+@pytest.mark.parametrize("keep", [6, 12])
+def test_pruned_lists_are_the_top_scores(env, keep):
+    """The kept candidates of every list are its `keep` highest logits (ties: lower slot), in slot order:
+    on a 4-point model the pruned optimum of each offset equals the brute-force minimum of Eq. 9 over the
+    lists built that way in numpy from the scoring kernel's own logits (or, when those lists hold no
+    feasible chain, the exact optimum of the fallback). keep 6 takes the kernel's argmax rounds, keep 12
+    its threshold bisection."""
+    import itertools
+    torch, hgm, oracle = env
+    rng = np.random.default_rng(31)
+    mod = synth.make_model(rng, 4, t_span=8)
+    sc = synth.make_scene(rng, 40, (320.0, 240.0), ("poisson", 30.0), mod.centres, [mod], [(0, 10)])
+    wl = synth.Workload("tiny", [mod], [sc], K=64, window=3)
+    m, s = handles(hgm, mod, sc, torch)
+    prop = hgm.Proposal(162, seed=5)
+    base = hgm.default_params(K=64, window=3)
+    first, n = hgm.offsets(m, s, base)
+    idx = torch.empty((n, 4, 64), dtype=torch.int32, device="cuda")
+    cnt = torch.empty((n, 4), dtype=torch.int32, device="cuda")
+    hgm.candidates(m, s, base, first, n, idx, cnt)
+    sco = torch.full((n, 4, 64), 7.0, dtype=torch.float32, device="cuda")
+    hgm.prop_scores(prop, m, s, base, first, n, sco)
+    pr = hgm.default_params(K=64, window=3, prune=prop, keep=keep)
+    e1, _ = _run(torch, hgm, m, s, pr, n, 4)
+    idx, cnt, sco = idx.cpu().numpy(), cnt.cpu().numpy(), sco.cpu().numpy()
+    mperm, sperm = m.order(), s.order()
+    orc = oracle.Oracle.from_workload(wl)
+    assert orc.first_offset == first and orc.n_offsets == n
+    checked = 0
+    for k in range(0, n, 3):
+        lists = []
+        for i in range(4):
+            c = int(cnt[k, i])
+            top = sorted(range(c), key=lambda j: (-float(sco[k, i, j]), j))[:keep]
+            lists.append([int(sperm[idx[k, i, j]]) for j in sorted(top)])
+        best = np.inf
+        z = np.empty(4, np.int64)
+        for combo in itertools.product(*lists):
+            for i in range(4):
+                z[mperm[i]] = combo[i]
+            best = min(best, orc.energy(z))
+        if not np.isfinite(best):
+            best = orc.match(first + k)[0]   # no feasible chain through the kept candidates: the fallback
+        if np.isfinite(best):
+            assert abs(float(e1[k]) - best) <= 1e-5 * max(1.0, best), (k, e1[k], best)
+            checked += 1
+        else:
+            assert not np.isfinite(e1[k])
+    assert checked >= 5
+
+
 def _pair_features(mod, sc, m, s, first, idx, cnt, window):
     """FP64 network inputs of every candidate slot: [f_i, f'_j, dx/100, dy/100, dt/w] with i, j the caller
     indices behind the sorted indices of the candidate lists; mask of the filled slots."""
